@@ -1,0 +1,280 @@
+"""FP64 CPU oracle of the constrained-GR elliptic solve - TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library in
+``paper_1905_08890_gb300`` and its binding) never imports it and shares no
+code with it.
+
+The arithmetic lives in ``gr_oracle.c`` (plain C, FP64, one loop per
+formula).  This module compiles it with gcc and exposes numpy-level wrappers.
+Arrays are float64 [n][n][n] C-order, index (i*n + j)*n + k, i the x index,
+h = 1/n (box L = 1, G = c = 1).
+
+Equation kinds: POISSON (lap u = f), HELMHOLTZ (lap u - c0 u = f) and PSI
+(lap u + 2 pi c0/psi + c1/(8 psi^7) - 2 pi rho psi^5 = f with psi = 1 + u:
+the unknown of the psi kind is the deviation psi - 1).
+
+Field order used throughout: psi, alpha psi, V_x, V_y, V_z, U, B^x, B^y, B^z, b.
+Equation (solve) order: V_x, V_y, V_z, U, psi, alpha psi, B^x, B^y, B^z, b
+(Sec. 2.4 solution sequence; Sec. 4.3.1 equations MG-linear-1a ... 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gr_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_lib")
+_SO = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+POISSON, HELMHOLTZ, PSI = 0, 1, 2
+OK, ERR_ARG, ERR_NOMEM, ERR_NOCONV, ERR_NONFINITE = 0, 1, 3, 4, 5
+
+FIELDS = ("psi", "apsi", "Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b")
+EQUATIONS = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+SOURCES = ("s0", "sx", "sy", "sz", "sigma")
+
+
+def build(force: bool = False) -> str:
+    """Compile gr_oracle.c into oracle/_lib/liboracle.so (gcc, OpenMP, no
+    fast-math, no FMA contraction so x86 and Arm round alike)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            D, I, I64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            P = ctypes.c_void_p
+            L.orc_deposit.argtypes = [I, I64, P, P, D, P, P, P, P, P]
+            L.orc_mean.argtypes = [I, P]
+            L.orc_mean.restype = D
+            L.orc_rms.argtypes = [I, P]
+            L.orc_rms.restype = D
+            L.orc_laplacian.argtypes = [I, P, P]
+            L.orc_grad.argtypes = [I, I, P, P]
+            L.orc_div3.argtypes = [I, P, P, P, P]
+            L.orc_aij.argtypes = [I, P, P, P, P, P]
+            L.orc_aa.argtypes = [I, P, P]
+            L.orc_lapse_coef.argtypes = [I, P, P, P, P, D, D, P, P]
+            L.orc_shift_source.argtypes = [I, P, P, P, P]
+            L.orc_residual.argtypes = [I, I, P, P, P, P, D, P]
+            L.orc_residual.restype = D
+            L.orc_gs_colour.argtypes = [I, I, P, P, P, P, D, I]
+            L.orc_restrict.argtypes = [I, P, P]
+            L.orc_prolong_add.argtypes = [I, P, P]
+            L.orc_vcycle.argtypes = [I, I, P, P, P, P, D, I, I]
+            L.orc_vcycle.restype = I
+            L.orc_solve_eq.argtypes = [I, I, P, P, P, P, D, D, D, I, I, I, P, P, P]
+            L.orc_solve_eq.restype = I
+            L.orc_eq_setup.argtypes = [I, I, P, P, D, D, P, P, P, P]
+            L.orc_eq_setup.restype = I
+            L.orc_solve_constraints.argtypes = [I, P, P, D, D, D, I, I, I, P, P, P, P]
+            L.orc_solve_constraints.restype = I
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _grid(n):
+    return np.zeros((n, n, n), dtype=np.float64)
+
+
+# ---------------------------------------------------------------- deposit
+def deposit(n: int, x: np.ndarray, u: np.ndarray, mass: float) -> dict:
+    """CIC sources s0, s_x, s_y, s_z, sigma (Sec. 4.1.2); x, u are (3, np)."""
+    x = _f64(x)
+    u = _f64(u)
+    npart = x.shape[1] if x.ndim == 2 else 0
+    out = {k: _grid(n) for k in SOURCES}
+    lib().orc_deposit(n, npart, _p(x), _p(u), mass, *[_p(out[k]) for k in SOURCES])
+    return out
+
+
+# ---------------------------------------------------------------- operators
+def laplacian(f):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().orc_laplacian(f.shape[0], _p(f), _p(out))
+    return out
+
+
+def grad(f, axis: int):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().orc_grad(f.shape[0], axis, _p(f), _p(out))
+    return out
+
+
+def div3(Fx, Fy, Fz):
+    Fx, Fy, Fz = _f64(Fx), _f64(Fy), _f64(Fz)
+    out = np.empty_like(Fx)
+    lib().orc_div3(Fx.shape[0], _p(Fx), _p(Fy), _p(Fz), _p(out))
+    return out
+
+
+def aij(Vx, Vy, Vz, U):
+    """Six components xx, yy, zz, xy, xz, yz of A_ij (Eq. Aij-discrete-2)."""
+    Vx, Vy, Vz, U = map(_f64, (Vx, Vy, Vz, U))
+    n = U.shape[0]
+    A = np.empty((6, n, n, n))
+    lib().orc_aij(n, _p(Vx), _p(Vy), _p(Vz), _p(U), _p(A))
+    return A
+
+
+def aa(A):
+    A = _f64(A)
+    out = np.empty(A.shape[1:])
+    lib().orc_aa(A.shape[1], _p(A), _p(out))
+    return out
+
+
+def lapse_coef(psi, s0, sigma, AA, rho_hat, S_hat=0.0):
+    """m and f of  lap(alpha psi) - m alpha psi = f  (Eq. sol-scheme-CMC)."""
+    psi, s0, sigma, AA = map(_f64, (psi, s0, sigma, AA))
+    K2, Kdot = background(rho_hat, S_hat)
+    m = np.empty_like(psi)
+    f = np.empty_like(psi)
+    lib().orc_lapse_coef(psi.shape[0], _p(psi), _p(s0), _p(sigma), _p(AA), K2, Kdot, _p(m), _p(f))
+    return m, f
+
+
+def shift_source(A, psi, apsi):
+    A, psi, apsi = map(_f64, (A, psi, apsi))
+    n = psi.shape[0]
+    SB = np.empty((3, n, n, n))
+    lib().orc_shift_source(n, _p(A), _p(psi), _p(apsi), _p(SB))
+    return SB
+
+
+def background(rho_hat: float, S_hat: float = 0.0):
+    """K^2 = 24 pi rho_hat and Kdot = 12 pi rho_hat + 4 pi S_hat (Sec. 2.3)."""
+    return 24.0 * math.pi * rho_hat, 12.0 * math.pi * rho_hat + 4.0 * math.pi * S_hat
+
+
+# ---------------------------------------------------------------- multigrid
+def residual(kind, u, f, c0=None, c1=None, rho=0.0):
+    """(eps, RMS(eps)) with eps = L(u) - f."""
+    u, f = _f64(u), _f64(f)
+    c0 = None if c0 is None else _f64(c0)
+    c1 = None if c1 is None else _f64(c1)
+    eps = np.empty_like(u)
+    r = lib().orc_residual(kind, u.shape[0], _p(u), _p(f), _p(c0), _p(c1), rho, _p(eps))
+    return eps, r
+
+
+def gs_colour(kind, u, f, c0=None, c1=None, rho=0.0, color=0):
+    """One Gauss-Seidel (Newton for the psi kind) pass over the cells with
+    (i + j + k) % 2 == color, in place on u."""
+    f = _f64(f)
+    c0 = None if c0 is None else _f64(c0)
+    c1 = None if c1 is None else _f64(c1)
+    lib().orc_gs_colour(kind, u.shape[0], _p(u), _p(f), _p(c0), _p(c1), rho, color)
+
+
+def restrict(fine):
+    fine = _f64(fine)
+    n = fine.shape[0] // 2
+    out = np.empty((n, n, n))
+    lib().orc_restrict(fine.shape[0], _p(fine), _p(out))
+    return out
+
+
+def prolong_add(coarse, fine):
+    """fine += P(coarse), in place."""
+    coarse = _f64(coarse)
+    lib().orc_prolong_add(fine.shape[0], _p(coarse), _p(fine))
+
+
+def vcycle(kind, u, f, c0=None, c1=None, rho=0.0, nu1=2, nu2=2):
+    """One V(nu1, nu2) cycle, in place on u (float64 C-contiguous)."""
+    f = _f64(f)
+    c0 = None if c0 is None else _f64(c0)
+    c1 = None if c1 is None else _f64(c1)
+    st = lib().orc_vcycle(kind, u.shape[0], _p(u), _p(f), _p(c0), _p(c1), rho, nu1, nu2)
+    if st != OK:
+        raise RuntimeError(f"orc_vcycle status {st}")
+
+
+def solve_eq(kind, u, f, c0=None, c1=None, rho=0.0, ref=0.0, tol=1e-10, max_cycles=50, nu1=2, nu2=2):
+    """Solve one equation in place on u; returns (status, cycles, res0, res)."""
+    f = _f64(f)
+    c0 = None if c0 is None else _f64(c0)
+    c1 = None if c1 is None else _f64(c1)
+    cyc = ctypes.c_int(0)
+    r0 = ctypes.c_double(0)
+    r = ctypes.c_double(0)
+    st = lib().orc_solve_eq(kind, u.shape[0], _p(u), _p(f), _p(c0), _p(c1), rho, ref, tol, max_cycles, nu1, nu2,
+                            ctypes.byref(cyc), ctypes.byref(r0), ctypes.byref(r))
+    return st, cyc.value, r0.value, r.value
+
+
+def eq_setup(eq: int, src: dict, fld: dict, rho_hat: float, S_hat: float = 0.0):
+    """(kind, f, c0, c1, ref) of equation eq (solve order) from sources and fields."""
+    n = src["s0"].shape[0]
+    srcs = [_f64(src[k]) for k in SOURCES]
+    order = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+    flds = [_f64(fld[k]) for k in order]
+    sp = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in srcs])
+    fp = (ctypes.c_void_p * 10)(*[a.ctypes.data for a in flds])
+    f, c0, c1 = _grid(n), _grid(n), _grid(n)
+    ref = ctypes.c_double(0)
+    kind = lib().orc_eq_setup(eq, n, sp, fp, rho_hat, S_hat, _p(f), _p(c0), _p(c1), ctypes.byref(ref))
+    if kind < 0:
+        raise MemoryError("orc_eq_setup")
+    return kind, f, (c0 if kind != POISSON else None), (c1 if kind == PSI else None), ref.value
+
+
+def initial_fields(n: int) -> dict:
+    """The plain guess: psi = alpha psi = 1, vectors and scalars 0."""
+    fld = {k: _grid(n) for k in FIELDS}
+    fld["psi"][:] = 1.0
+    fld["apsi"][:] = 1.0
+    return fld
+
+
+def solve_constraints(src: dict, fld: dict, rho_hat: float, S_hat: float = 0.0, tol=1e-10, max_cycles=50, nu1=2,
+                      nu2=2):
+    """Ten-equation solve, in place on the float64 arrays of fld.  Returns
+    (status, report) with per-equation cycles, res0, res, status in solve order."""
+    n = src["s0"].shape[0]
+    srcs = [_f64(src[k]) for k in SOURCES]
+    for k in FIELDS:
+        a = fld[k]
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == (n, n, n)
+    sp = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in srcs])
+    fp = (ctypes.c_void_p * 10)(*[fld[k].ctypes.data for k in FIELDS])
+    cyc = (ctypes.c_int * 10)()
+    r0 = (ctypes.c_double * 10)()
+    r = (ctypes.c_double * 10)()
+    sts = (ctypes.c_int * 10)()
+    st = lib().orc_solve_constraints(n, sp, fp, rho_hat, S_hat, tol, max_cycles, nu1, nu2, cyc, r0, r, sts)
+    rep = {"cycles": list(cyc), "res0": list(r0), "res": list(r), "status": list(sts)}
+    return st, rep

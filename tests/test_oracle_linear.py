@@ -1,0 +1,156 @@
+"""Oracle pins: the linear (Poisson-like and Helmholtz) multigrid solves
+(Sec. 4.3.1, Eqs. GR-linear, GR-linear-coarse, epsilon-error-lin; Sec. 5.1.3)."""
+import math
+
+import numpy as np
+import pytest
+
+from trig import TrigSum
+
+
+def fft_solve(f, m=0.0):
+    """Exact solution of the periodic discrete system lap_h u - m u = f: the
+    FFT diagonalises the 7-point Laplacian with symbol -(4/h^2) sum sin^2(pi k/n).
+    For m = 0 the k = 0 mode (solution mean) is set to 0."""
+    n = f.shape[0]
+    s = 4.0 * n * n * np.sin(np.pi * np.arange(n) / n) ** 2
+    lam = -(s[:, None, None] + s[None, :, None] + s[None, None, :]) - m
+    F = np.fft.fftn(f)
+    if m == 0.0:
+        lam[0, 0, 0] = 1.0
+        F[0, 0, 0] = 0.0
+    return np.real(np.fft.ifftn(F / lam))
+
+
+def _rand_smooth(n, seed, amp=1.0):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((n, n, n))
+    return amp * f
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_poisson_matches_fft_exact_solution(orc, n):
+    f = _rand_smooth(n, 1)
+    u = np.zeros((n, n, n))
+    st, cyc, r0, r = orc.solve_eq(orc.POISSON, u, f, tol=1e-13, max_cycles=80)
+    assert st == 0 and r <= 1e-13
+    want = fft_solve(f - f.mean())
+    assert np.abs(u - want).max() <= 1e-11 * np.abs(want).max()
+    assert abs(u.mean()) < 1e-15 * np.abs(want).max()
+
+
+def test_poisson_source_mean_is_removed(orc):
+    """Sec. 4.3.1: the V_i source f is replaced by f - <f> so that both sides
+    sum to zero over the periodic grid."""
+    n = 16
+    f = _rand_smooth(n, 2) + 3.0
+    u = np.zeros((n, n, n))
+    st, *_ = orc.solve_eq(orc.POISSON, u, f, tol=1e-13, max_cycles=80)
+    assert st == 0
+    assert np.allclose(orc.laplacian(u), f - f.mean(), rtol=0, atol=1e-10 * np.abs(f).max())
+
+
+def test_helmholtz_constant_coefficient_matches_fft(orc):
+    n = 32
+    f = _rand_smooth(n, 3)
+    m = 1.7
+    u = np.ones((n, n, n))
+    st, cyc, r0, r = orc.solve_eq(orc.HELMHOLTZ, u, f, c0=np.full((n, n, n), m), tol=1e-13, max_cycles=80)
+    assert st == 0
+    want = fft_solve(f, m)
+    assert np.abs(u - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_helmholtz_variable_coefficient_matches_dense_solve(orc):
+    n = 8
+    rng = np.random.default_rng(4)
+    m = 0.2 + rng.random((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    N = n**3
+    L = _lap_matrix(n)
+    want = np.linalg.solve(L - np.diag(m.reshape(-1)), f.reshape(-1)).reshape(n, n, n)
+    u = np.zeros((n, n, n))
+    st, *_ = orc.solve_eq(orc.HELMHOLTZ, u, f, c0=m, tol=1e-14, max_cycles=80)
+    assert st == 0
+    assert np.abs(u - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def _lap_matrix(n):
+    """Dense 7-point periodic Laplacian built cell by cell (brute force)."""
+    N = n**3
+    L = np.zeros((N, N))
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                c = (i * n + j) * n + k
+                L[c, c] -= 6.0 * n * n
+                for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    nb = (((i + di) % n) * n + (j + dj) % n) * n + (k + dk) % n
+                    L[c, nb] += n * n
+    return L
+
+
+def test_point_source_green_function(orc):
+    """Sec. 5.1.3 point-like source: a single-cell source (mean removed).  The
+    solution equals the discrete periodic Green's function (FFT, exact), and
+    between the source cell and the box edge it follows the continuum
+    -1/(4 pi r) - r^2/6 + const (the r^2 term is the periodic image of the
+    removed mean) plus the simple-cubic Madelung constant 2.837297/(4 pi)."""
+    n = 64
+    f = np.zeros((n, n, n))
+    c = n // 2
+    f[c, c, c] = n**3  # unit charge
+    u = np.zeros((n, n, n))
+    st, cyc, r0, r = orc.solve_eq(orc.POISSON, u, f, tol=1e-12, max_cycles=80)
+    assert st == 0
+    want = fft_solve(f - f.mean())
+    assert np.abs(u - want).max() <= 1e-10 * np.abs(want).max()
+    x = (np.arange(n) - c) / n
+    R = np.sqrt(x[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2)
+    band = (R >= 8.0 / n) & (R <= 0.25)
+    resid = u[band] + 1.0 / (4 * np.pi * R[band]) + R[band] ** 2 / 6.0
+    spread = resid.max() - resid.min()
+    # the spread is small against the potential itself over the band
+    assert spread < 0.01 * (1.0 / (4 * np.pi * 8.0 / n))
+    # the constant is the Ewald/Madelung value of the zero-mean periodic
+    # Coulomb potential on the unit cubic lattice
+    assert abs(np.median(resid) - 2.837297 / (4 * np.pi)) < 2e-3 * 2.837297 / (4 * np.pi)
+    # and u rises monotonically away from the source along an axis
+    line = u[c, c, c:c + n // 4]
+    assert np.all(np.diff(line) > 0)
+
+
+def _ratios(orc, n, cycles=7):
+    f = _rand_smooth(n, 9)
+    f -= f.mean()
+    u = np.zeros((n, n, n))
+    res = []
+    for _ in range(cycles):
+        orc.vcycle(orc.POISSON, u, f, nu1=2, nu2=2)
+        res.append(orc.residual(orc.POISSON, u, f)[1])
+    res = np.array(res)
+    return res[2:] / res[1:-1]
+
+
+def test_vcycle_contraction_is_grid_independent(orc):
+    """Textbook multigrid property (not stated in the paper): the per-cycle
+    residual reduction of V(2,2) with red-black GS, 8-child restriction and
+    trilinear prolongation is bounded away from 1 independently of h."""
+    rates = {n: float(np.exp(np.mean(np.log(_ratios(orc, n))))) for n in (16, 32, 64)}
+    assert all(r < 0.25 for r in rates.values()), rates
+    assert max(rates.values()) / min(rates.values()) < 1.5, rates
+
+
+def test_zero_source_gives_zero_solution(orc):
+    n = 8
+    u = np.random.default_rng(0).standard_normal((n, n, n))
+    st, cyc, r0, r = orc.solve_eq(orc.POISSON, u, np.zeros((n, n, n)), tol=1e-12, max_cycles=50)
+    # reference 0 is replaced by 1 (absolute criterion)
+    assert st == 0 and np.abs(u).max() < 1e-12
+
+
+def test_bad_grid_sizes_are_rejected(orc):
+    for n in (2, 6, 12):
+        u = np.zeros((n, n, n))
+        st, *_ = orc.solve_eq(orc.POISSON, u, np.zeros((n, n, n)))
+        assert st == orc.ERR_ARG
