@@ -1,0 +1,180 @@
+/*
+ * gr.h - C ABI of the GB300 constrained-GR elliptic solver.
+ *
+ * The library solves, on a uniform periodic n^3 grid (box side L, cell size
+ * h = L/n, cell centres x_i = (i + 1/2) h, G = c = 1), the ten elliptic
+ * equations of the fully constrained ADM formulation with CMC slicing,
+ * minimal-distortion shift and conformal flatness (arXiv:1905.08890,
+ * Sec. 2.4 solution sequence, Sec. 4.3 multigrid):
+ *
+ *   V_i        lap V_i = 8 pi (s_i - <s_i>)             Eq. MG-linear-1a (geometric units)
+ *   U          lap U   = -1/4 div V                     Eq. MG-linear-1
+ *   psi        lap psi = -2 pi s0/psi - AA/(8 psi^7) + 2 pi rho_hat psi^5
+ *                                                        Eq. sol-scheme-H-constraint
+ *   alpha psi  lap(alpha psi) = m alpha psi - psi^5 Kdot Eq. sol-scheme-CMC
+ *              m = 2 pi psi^-2 (s0 + 2 psi^-4 sigma) + 7/8 psi^-8 AA + 5/12 psi^4 K^2
+ *   B^i        lap B^i = 2 d_j (alpha psi^-6 A^ij)      Eqs. MDC-CF, MG-linear-2a
+ *   b          lap b   = -1/4 div B                     Eq. MG-linear-2
+ *
+ * with A_ij = d_i V_j + d_j V_i - 1/2 delta_ij div V + 2 d_i d_j U
+ * (Eq. Aij-discrete-2), AA = A_ij A^ij, K^2 = 24 pi rho_hat and
+ * Kdot = 12 pi rho_hat + 4 pi S_hat (Eqs. 1-Friedmann, 2-Friedmann with
+ * rho_Lambda = 0).  Sources come from a cloud-in-cell deposit of particles
+ * (Sec. 4.1.2).  Discretisation: 7-point Laplacian, 3-point central
+ * differences, 4-cell cross derivative (Sec. 4.3.1).  Solver: red-black
+ * Gauss-Seidel V(nu1, nu2) cycles down to the 2^3 level.
+ *
+ * Conventions for every call:
+ *  - Arrays are double [n][n][n], C order, index (i*n + j)*n + k, i the x
+ *    index.  All array pointers are DEVICE pointers owned by the caller
+ *    (for example torch CUDA tensors), contiguous, 8-byte aligned, and must
+ *    not alias one another unless a call says so.  The context owns its own
+ *    multigrid scratch.
+ *  - All work is queued on the context's stream.  Calls that return host
+ *    scalars (norms, reports) synchronise that stream before returning.
+ *  - No call aborts or throws.  Errors are returned as gr_status; the
+ *    thread-local gr_last_error() describes the last one.  Arguments are
+ *    validated before any GPU work is queued.
+ *  - Not thread safe per context: one host thread drives a context at a time.
+ */
+#ifndef GR_H
+#define GR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GR_OK = 0,
+    GR_ERR_ARG = 1,       /* invalid argument (bad n, null pointer, bad option) */
+    GR_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    GR_ERR_NOMEM = 3,     /* device or host allocation failed */
+    GR_ERR_NOCONV = 4,    /* max_cycles reached above tol; fields hold the last iterate */
+    GR_ERR_NONFINITE = 5, /* a residual norm became NaN or Inf */
+    GR_ERR_STATE = 6      /* call not valid in the context's state */
+} gr_status;
+
+/* Equations in solve order (Sec. 2.4: momentum constraint, Hamiltonian
+   constraint, lapse, shift; Sec. 4.3.1 for the V/U and B/b split). */
+typedef enum {
+    GR_VX = 0, GR_VY, GR_VZ, GR_U, GR_PSI, GR_APSI, GR_BX, GR_BY, GR_BZ, GR_B_SCALAR,
+    GR_NEQ
+} gr_eq;
+
+typedef enum {
+    GR_PREC_FP64 = 0,  /* every sweep, transfer and residual in FP64 */
+    GR_PREC_MIXED = 1  /* FP64 fine residual and update; FP32 correction V-cycle
+                          (psi: on the Newton linearisation); FP64 2^3 level */
+} gr_prec;
+
+typedef struct gr_ctx gr_ctx; /* opaque */
+
+/* CIC sources, device arrays of n^3 doubles each:
+   s0 = sqrt(gamma) rho, s[l] = sqrt(gamma) S_l, sigma = sum_l s_ll (Sec. 3). */
+typedef struct {
+    double *s0;
+    double *s[3];
+    double *sigma;
+} gr_sources;
+
+/* The ten potentials, device arrays of n^3 doubles each.  psi is the
+   conformal factor, apsi = alpha psi; beta^i = B^i + d^i b and
+   W_i = V_i + d_i U (Sec. 4.3.1). */
+typedef struct {
+    double *psi;
+    double *apsi;
+    double *V[3];
+    double *U;
+    double *B[3];
+    double *b;
+} gr_fields;
+
+typedef struct {
+    double tol;       /* stop an equation when RMS(eps)/ref <= tol (see gr_solve_constraints) */
+    int max_cycles;   /* per equation; >= 0 */
+    int nu1, nu2;     /* pre- and post-smoothing red-black sweeps per level, 0..8 */
+    gr_prec prec;
+    double rho_hat;   /* fiducial density; <= 0 or NaN selects mass*np/L^3 of the last gr_deposit */
+    double S_hat;     /* fiducial trace of the stress (dust: 0); NaN selects 0 */
+    int verbose;      /* 0 silent; 1 one line per equation on stderr */
+} gr_opts;
+
+typedef struct {
+    int cycles[GR_NEQ];           /* V-cycles (mixed: outer iterations) per equation */
+    double res0[GR_NEQ];          /* relative residual of the initial guess */
+    double res[GR_NEQ];           /* relative residual at exit */
+    gr_status eq_status[GR_NEQ];
+    double seconds;               /* wall time of the whole call (host clock around the stream) */
+    double eq_seconds[GR_NEQ];    /* per equation, CUDA events */
+    long long cell_updates;       /* cells relaxed: every sweep on every level, all equations */
+} gr_report;
+
+/* Fill *o with the defaults: tol 1e-10, max_cycles 50, V(2,2), FP64,
+   rho_hat and S_hat from the deposit / dust, verbose 0. */
+void gr_default_opts(gr_opts *o);
+
+/* Create a context for an n^3 grid of box side L.  n must be a power of two,
+   4 <= n <= 1024; L > 0.  cuda_stream is a cudaStream_t (NULL = the legacy
+   default stream); the device is the current device of the calling thread.
+   Allocates the multigrid scratch (about 12 n^3 doubles).  On success *out
+   owns it; release with gr_destroy. */
+gr_status gr_create(int n, double L, void *cuda_stream, gr_ctx **out);
+
+/* Release a context and its device memory (synchronises its stream).  NULL is ignored. */
+void gr_destroy(gr_ctx *ctx);
+
+/* Cloud-in-cell deposit (Sec. 4.1.2, Eqs. s0/si/sij-code-unit-cic) of np
+   identical particles of rest mass `mass`.  x and u are device arrays in
+   structure-of-arrays layout [3][np]: positions (wrapped periodically into
+   [0, L)) and lower-index 4-velocities u_l.  Each particle adds, with CIC
+   weight w over the 8 surrounding cell centres, m W w/h^3 to s0,
+   m u_l w/h^3 to s_l and m |u|^2/W w/h^3 to sigma, W = sqrt(1 + |u|^2)
+   (the conformal factor is taken as 1 in the Lorentz factor).  The five
+   output arrays are overwritten.  np = 0 gives zero sources.  Also records
+   mass*np/L^3 as the default rho_hat of the context. */
+gr_status gr_deposit(gr_ctx *ctx, int64_t np, const double *x, const double *u, double mass, gr_sources *out);
+
+/* Solve the ten equations in solve order (gr_eq), each until its relative
+   residual RMS(eps)/ref <= opts->tol, eps = L(u) - f (Eqs. epsilon-error-lin,
+   epsilon-error-nonlin-1), with ref: V_i RMS(8 pi (s_i - <s_i>)); U
+   RMS(1/4 div V); psi RMS(2 pi s0); alpha psi RMS(psi^5 Kdot); B^i RMS of
+   its source; b RMS(1/4 div B); a ref below 1e-300 is replaced by 1.
+   Poisson-type sources have their mean removed and their solutions are
+   returned with zero mean (periodic zero mode).  inout holds the initial
+   guesses on entry (for example the previous solution, or psi = apsi = 1
+   and zero vectors) and the solutions on return; the sources are not
+   modified.  Each equation uses the fields solved before it.  Returns GR_OK,
+   or the first failing equation's status (NOCONV: fields keep the last
+   iterate and the remaining equations are still solved; NONFINITE: stops).
+   rep (host, may be NULL) receives per-equation cycles and residuals. */
+gr_status gr_solve_constraints(gr_ctx *ctx, const gr_sources *src, gr_fields *inout, const gr_opts *opts,
+                               gr_report *rep);
+
+/* One V(nu1, nu2) cycle (mixed precision: one defect-correction iteration)
+   of equation eq, with its right-hand side and coefficients derived from the
+   sources and the current fields exactly as in gr_solve_constraints.  For
+   Poisson-type equations the solution mean is set to zero afterwards.
+   *res_after (host, may be NULL) receives the relative residual after the
+   cycle. */
+gr_status gr_vcycle(gr_ctx *ctx, gr_eq eq, const gr_sources *src, gr_fields *inout, const gr_opts *opts,
+                    double *res_after);
+
+/* Residual eps = L(u) - f of equation eq at the current fields (right-hand
+   side and coefficients derived as in gr_solve_constraints; for Poisson-type
+   equations the source mean is removed first).  res_field (device, n^3
+   doubles, may be NULL) receives eps; *rel_norm (host, may be NULL)
+   receives RMS(eps)/ref.  Always evaluated in FP64. */
+gr_status gr_residual(gr_ctx *ctx, gr_eq eq, const gr_sources *src, const gr_fields *fields, const gr_opts *opts,
+                      double *res_field, double *rel_norm);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *gr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GR_H */

@@ -1,0 +1,565 @@
+// gr_capi.cu - host orchestration and the C ABI declared in include/gr.h.
+//
+// Each equation is solved on a hierarchy of levels n, n/2, ..., 2 (Sec. 4.3.1,
+// last paragraph) held in red-black split layout.  FP64 path: V(nu1, nu2)
+// cycles, correction form for the linear equations (Eq. GR-linear-coarse),
+// full approximation scheme for psi (Sec. 4.3.2.1).  Mixed path: an FP64
+// defect-correction loop whose correction equation lap e - m e = -eps is
+// relaxed by one FP32 V-cycle per iteration (for psi, m is the Newton
+// linearisation of the Hamiltonian-constraint operator); the 2^3 level and
+// all reductions stay FP64.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gr.h"
+#include "gr_internal.cuh"
+
+using namespace gr;
+
+namespace {
+
+thread_local std::string g_err;
+
+gr_status fail(gr_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+struct Level {
+    int n = 0;
+    double h = 0, h2 = 0, ih2 = 0;
+    double *u = nullptr, *f = nullptr, *c0 = nullptr, *c1 = nullptr, *ur = nullptr;  // FP64
+    float *e = nullptr, *r = nullptr, *m = nullptr, *inv = nullptr;                 // FP32
+};
+
+struct EqInfo {
+    int kind;      // operator on the FP64 fine level
+    int kind32;    // operator of the FP32 correction equation
+    int dev;       // unknown is field - 1
+    int poisson;   // zero-mean solution
+    double ref;    // reference norm of the relative residual
+};
+
+}  // namespace
+
+struct gr_ctx {
+    int n = 0, nlev = 0;
+    double L = 1, h = 1;
+    cudaStream_t st = nullptr;
+    std::vector<Level> lev;  // lev[0] is 2^3, lev[nlev-1] the finest
+    double *A6 = nullptr, *AA = nullptr, *tmp = nullptr;
+    double *partials = nullptr, *dscal = nullptr, *hscal = nullptr;
+    double rho_dep = NAN;
+    bool a_valid = false;  // A6/AA current for the V, U in the fields
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+gr_status cuda_check(const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(GR_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    return GR_OK;
+}
+
+template <typename T>
+gr_status dalloc(gr_ctx *c, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) < 256 ? 256 : count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GR_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = (T *)q;
+    return GR_OK;
+}
+
+int log2i(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+bool valid_opts(const gr_opts *o)
+{
+    return o && !(o->tol < 0) && o->max_cycles >= 0 && o->nu1 >= 0 && o->nu1 <= 8 && o->nu2 >= 0 && o->nu2 <= 8 &&
+           (o->prec == GR_PREC_FP64 || o->prec == GR_PREC_MIXED);
+}
+
+bool src_ok(const gr_sources *s)
+{
+    return s && s->s0 && s->s[0] && s->s[1] && s->s[2] && s->sigma;
+}
+
+bool fld_ok(const gr_fields *f)
+{
+    return f && f->psi && f->apsi && f->V[0] && f->V[1] && f->V[2] && f->U && f->B[0] && f->B[1] && f->B[2] && f->b;
+}
+
+double *field_ptr(const gr_fields *f, int eq)
+{
+    switch (eq) {
+    case GR_VX: return f->V[0];
+    case GR_VY: return f->V[1];
+    case GR_VZ: return f->V[2];
+    case GR_U: return f->U;
+    case GR_PSI: return f->psi;
+    case GR_APSI: return f->apsi;
+    case GR_BX: return f->B[0];
+    case GR_BY: return f->B[1];
+    case GR_BZ: return f->B[2];
+    default: return f->b;
+    }
+}
+
+// device sums (sum, sum of squares) of cnt doubles into c->dscal[0..1]
+void dsum(gr_ctx *c, int64_t cnt, const double *a)
+{
+    int g = gr::sum_sq(cnt, a, c->partials, c->st);
+    gr::finalize(c->partials, g, c->dscal, c->st);
+}
+
+gr_status read_scalars(gr_ctx *c, double *a, double *b)
+{
+    cudaMemcpyAsync(c->hscal, c->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(GR_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    gr_status s = cuda_check("kernel");
+    if (s != GR_OK) return s;
+    *a = c->hscal[0];
+    if (b) *b = c->hscal[1];
+    return GR_OK;
+}
+
+// mean-free Poisson right-hand side on the fine level (split layout);
+// ref = RMS after the first mean removal, then the mean is removed again
+gr_status poisson_rhs_finish(gr_ctx *c, Level &F, double *ref)
+{
+    const int64_t N = (int64_t)c->n * c->n * c->n;
+    dsum(c, N, F.f);
+    gr::scale_sub_mean(N, F.f, c->dscal, 1.0 / N, 1.0, c->st);
+    dsum(c, N, F.f);
+    double s, q;
+    gr_status st = read_scalars(c, &s, &q);
+    if (st != GR_OK) return st;
+    *ref = std::sqrt(q / N);
+    gr::scale_sub_mean(N, F.f, c->dscal, 1.0 / N, 1.0, c->st);
+    return GR_OK;
+}
+
+void ensure_aij(gr_ctx *c, const gr_fields *fl)
+{
+    if (c->a_valid) return;
+    gr::aij_aa(c->n, 0.5 / c->h, 1.0 / (c->h * c->h), fl->V[0], fl->V[1], fl->V[2], fl->U, c->A6, c->AA, c->st);
+    c->a_valid = true;
+}
+
+// Build the fine-level unknown, right-hand side and coefficients of equation eq
+// (split layout) from the sources and current fields; fills info.
+gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, double rho, double S_hat, EqInfo *info)
+{
+    const int n = c->n;
+    const int64_t N = (int64_t)n * n * n;
+    Level &F = c->lev[c->nlev - 1];
+    const double K2 = 24.0 * kPi * rho, Kdot = 12.0 * kPi * rho + 4.0 * kPi * S_hat;
+    info->dev = (eq == GR_PSI || eq == GR_APSI);
+    info->poisson = !info->dev;
+    info->kind = eq == GR_PSI ? KPSI : (eq == GR_APSI ? KHELM : KPOISSON);
+    info->kind32 = info->kind == KPOISSON ? KPOISSON : KHELM;
+    gr_status st = GR_OK;
+    if (eq <= GR_VZ) {
+        // lap V_i = 8 pi (s_i - <s_i>)  (Eq. MG-linear-1a; mean removal of Sec. 4.3.1)
+        gr::to_split(n, s->s[eq], F.f, 0.0, c->st);
+        dsum(c, N, F.f);
+        gr::scale_sub_mean(N, F.f, c->dscal, 1.0 / N, 8.0 * kPi, c->st);
+        st = poisson_rhs_finish(c, F, &info->ref);
+    } else if (eq == GR_U || eq == GR_B_SCALAR) {
+        // lap U = -1/4 div V ; lap b = -1/4 div B  (Eqs. MG-linear-1, MG-linear-2)
+        double *const *Fv = eq == GR_U ? fl->V : fl->B;
+        gr::div_to_split(n, 0.5 / c->h, Fv[0], Fv[1], Fv[2], -0.25, F.f, c->st);
+        st = poisson_rhs_finish(c, F, &info->ref);
+    } else if (eq == GR_PSI) {
+        ensure_aij(c, fl);
+        gr::psi_setup(n, fl->psi, s->s0, c->AA, F.u, F.c0, F.c1, F.f, c->st);
+        dsum(c, N, s->s0);
+        double a, q;
+        st = read_scalars(c, &a, &q);
+        info->ref = 2.0 * kPi * std::sqrt(q / N);
+    } else if (eq == GR_APSI) {
+        ensure_aij(c, fl);
+        gr::apsi_setup(n, c->h * c->h, fl->psi, fl->apsi, s->s0, s->sigma, c->AA, K2, Kdot, F.u, F.c0, F.c1, F.f,
+                       c->tmp, c->st);
+        dsum(c, N, c->tmp);
+        double a, q;
+        st = read_scalars(c, &a, &q);
+        info->ref = std::sqrt(q / N);
+    } else {
+        // lap B^i = 2 d_j (alpha psi^-6 A^ij)  (Eqs. MDC-CF, MG-linear-2a)
+        ensure_aij(c, fl);
+        gr::shift_weight(n, fl->psi, fl->apsi, c->tmp, c->st);
+        gr::shift_source(n, 0.5 / c->h, c->A6, c->tmp, eq - GR_BX, F.f, c->st);
+        st = poisson_rhs_finish(c, F, &info->ref);
+    }
+    if (st != GR_OK) return st;
+    if (!info->dev) gr::to_split(n, field_ptr(fl, eq), F.u, 0.0, c->st);
+    if (!(info->ref >= 1e-300)) info->ref = 1.0;
+    return cuda_check("setup");
+}
+
+void restrict_coefs64(gr_ctx *c, int kind)
+{
+    if (kind == KPOISSON) return;
+    for (int l = c->nlev - 1; l >= 1; l--) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        gr::restrict_coef<double>(kind, A.n, A.c0, A.c1, C.c0, C.c1, C.h2, c->st);
+    }
+}
+
+void restrict_coefs32(gr_ctx *c)
+{
+    for (int l = c->nlev - 1; l >= 1; l--) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        gr::restrict_coef<float>(KHELM, A.n, A.m, A.inv, C.m, C.inv, C.h2, c->st);
+    }
+}
+
+long long vcycle_cells(const gr_ctx *c, int nu1, int nu2)
+{
+    long long s = 0;
+    for (int l = 1; l < c->nlev; l++) s += (long long)(nu1 + nu2) * c->lev[l].n * c->lev[l].n * c->lev[l].n;
+    return s + (long long)kCoarsestSweeps * 8;
+}
+
+void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
+{
+    const int fas = kind == KPSI;
+    for (int l = c->nlev - 1; l >= 1; l--) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        for (int s = 0; s < nu1; s++)
+            for (int col = 0; col < 2; col++)
+                gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+        gr::resid_restrict<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.ih2, rho, C.u, C.f, C.ur, fas, c->st);
+        if (fas) gr::fas_rhs(C.n, C.u, C.f, C.c0, C.c1, C.ih2, rho, c->st);
+    }
+    Level &Z = c->lev[0];
+    gr::coarsest<double>(kind, Z.u, Z.f, Z.c0, Z.c1, Z.h2, Z.ih2, rho, c->st);
+    for (int l = 1; l < c->nlev; l++) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        if (fas) gr::fas_diff(C.n, C.u, C.ur, c->st);
+        gr::prolong_add<double>(A.n, A.u, C.u, c->st);
+        for (int s = 0; s < nu2; s++)
+            for (int col = 0; col < 2; col++)
+                gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+    }
+}
+
+// one FP32 correction V-cycle on lev[*].e with fine right-hand side lev[fine].r
+void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
+{
+    Level &F = c->lev[c->nlev - 1];
+    cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
+    for (int l = c->nlev - 1; l >= 1; l--) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        for (int s = 0; s < nu1; s++)
+            for (int col = 0; col < 2; col++)
+                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+        gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+    }
+    Level &Z = c->lev[0];
+    gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
+    for (int l = 1; l < c->nlev; l++) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        gr::prolong_add<float>(A.n, A.e, C.e, c->st);
+        for (int s = 0; s < nu2; s++)
+            for (int col = 0; col < 2; col++)
+                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+    }
+}
+
+gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, double *r)
+{
+    Level &F = c->lev[c->nlev - 1];
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    int g = gr::resid_norm<double>(kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, rho, c->partials, eps_nat, c->st);
+    gr::finalize(c->partials, g, c->dscal, c->st);
+    double q;
+    gr_status st = read_scalars(c, &q, nullptr);
+    *r = std::sqrt(q / N) / ref;
+    return st;
+}
+
+gr_status mixed_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
+{
+    Level &F = c->lev[c->nlev - 1];
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    int g = gr::mixed_resid(in.kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, F.h2, rho, F.r, F.m, F.inv, c->partials,
+                            c->st);
+    gr::finalize(c->partials, g, c->dscal, c->st);
+    double q;
+    gr_status st = read_scalars(c, &q, nullptr);
+    *r = std::sqrt(q / N) / in.ref;
+    return st;
+}
+
+// Solve (or cycle) one equation; writes the field back.  tol < 0 with
+// max_cycles = 1 performs exactly one cycle and reports OK.
+gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const gr_opts *o, double rho,
+                   double S_hat, double tol, int max_cycles, int *cycles, double *res0, double *res,
+                   long long *cells)
+{
+    EqInfo in;
+    gr_status st = setup_eq(c, eq, s, fl, rho, S_hat, &in);
+    if (st != GR_OK) return st;
+    Level &F = c->lev[c->nlev - 1];
+    const bool mixed = o->prec == GR_PREC_MIXED;
+    const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
+    if (mixed) {
+        if (in.kind == KHELM) {
+            gr::to_float((int64_t)F.n * F.n * F.n, F.c0, F.m, c->st);
+            gr::helm_invdiag<float>(F.n, F.m, F.inv, F.h2, c->st);
+            restrict_coefs32(c);
+        }
+    } else {
+        restrict_coefs64(c, in.kind);
+    }
+    double r = 0;
+    st = mixed ? mixed_norm(c, in, rho, &r) : norm64(c, in.kind, rho, in.ref, nullptr, &r);
+    if (st != GR_OK) return st;
+    if (res0) *res0 = r;
+    int cyc = 0;
+    if (!std::isfinite(r)) st = fail(GR_ERR_NONFINITE, "equation %d: initial residual is not finite", eq);
+    while (st == GR_OK && r > tol && cyc < max_cycles) {
+        if (mixed) {
+            if (in.kind == KPSI) restrict_coefs32(c);
+            vcycle32(c, in.kind32, o->nu1, o->nu2);
+            gr::mixed_update(F.n, F.u, F.e, c->st);
+            st = mixed_norm(c, in, rho, &r);
+        } else {
+            vcycle64(c, in.kind, rho, o->nu1, o->nu2);
+            st = norm64(c, in.kind, rho, in.ref, nullptr, &r);
+        }
+        cyc++;
+        if (cells) *cells += per_cycle;
+        if (st == GR_OK && !std::isfinite(r)) st = fail(GR_ERR_NONFINITE, "equation %d: residual not finite", eq);
+    }
+    if (cycles) *cycles = cyc;
+    if (res) *res = r;
+    // write back: +1 for the deviation unknowns, zero mean for Poisson-type
+    // (the last norm kernel left the sum of u in dscal[1])
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, in.poisson ? c->dscal + 1 : nullptr, 1.0 / N,
+                   c->st);
+    gr_status cs = cuda_check("write back");
+    if (cs != GR_OK) return cs;
+    if (st == GR_OK && tol >= 0 && r > tol)
+        st = fail(GR_ERR_NOCONV, "equation %d: %d cycles, relative residual %.3e > tol %.3e", eq, cyc, r, tol);
+    return st;
+}
+
+gr_status resolve_bg(gr_ctx *c, const gr_opts *o, double *rho, double *S_hat)
+{
+    *rho = (o->rho_hat > 0) ? o->rho_hat : c->rho_dep;
+    *S_hat = std::isnan(o->S_hat) ? 0.0 : o->S_hat;
+    if (!(*rho > 0)) return fail(GR_ERR_ARG, "rho_hat not given and no gr_deposit on this context");
+    return GR_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void gr_default_opts(gr_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_cycles = 50;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->prec = GR_PREC_FP64;
+    o->rho_hat = 0.0;
+    o->S_hat = 0.0;
+    o->verbose = 0;
+}
+
+const char *gr_last_error(void) { return g_err.c_str(); }
+
+void gr_destroy(gr_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
+{
+    g_err.clear();
+    if (!out) return fail(GR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 4 || n > 1024 || (n & (n - 1))) return fail(GR_ERR_ARG, "n = %d: must be a power of two in [4, 1024]", n);
+    if (!(L > 0) || !std::isfinite(L)) return fail(GR_ERR_ARG, "L must be finite and > 0");
+    gr_ctx *c = new (std::nothrow) gr_ctx();
+    if (!c) return fail(GR_ERR_NOMEM, "host allocation");
+    c->n = n;
+    c->L = L;
+    c->h = L / n;
+    c->st = (cudaStream_t)stream;
+    c->nlev = log2i(n);
+    c->lev.resize(c->nlev);
+    gr_status st = GR_OK;
+    for (int l = 0; l < c->nlev && st == GR_OK; l++) {
+        Level &A = c->lev[l];
+        A.n = 2 << l;
+        A.h = L / A.n;
+        A.h2 = A.h * A.h;
+        A.ih2 = 1.0 / A.h2;
+        const size_t N = (size_t)A.n * A.n * A.n;
+        if (st == GR_OK) st = dalloc(c, &A.u, N);
+        if (st == GR_OK) st = dalloc(c, &A.f, N);
+        if (st == GR_OK) st = dalloc(c, &A.c0, N);
+        if (st == GR_OK) st = dalloc(c, &A.c1, N);
+        if (st == GR_OK) st = dalloc(c, &A.ur, N);
+        if (st == GR_OK) st = dalloc(c, &A.e, N);
+        if (st == GR_OK) st = dalloc(c, &A.r, N);
+        if (st == GR_OK) st = dalloc(c, &A.m, N);
+        if (st == GR_OK) st = dalloc(c, &A.inv, N);
+    }
+    const size_t N = (size_t)n * n * n;
+    if (st == GR_OK) st = dalloc(c, &c->A6, 6 * N);
+    if (st == GR_OK) st = dalloc(c, &c->AA, N);
+    if (st == GR_OK) st = dalloc(c, &c->tmp, N);
+    if (st == GR_OK) st = dalloc(c, &c->partials, 2 * kMaxRedBlocks);
+    if (st == GR_OK) st = dalloc(c, &c->dscal, 16);
+    if (st == GR_OK && cudaMallocHost((void **)&c->hscal, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(GR_ERR_NOMEM, "cudaMallocHost");
+    }
+    if (st == GR_OK && (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(GR_ERR_CUDA, "cudaEventCreate");
+    }
+    if (st != GR_OK) {
+        gr_destroy(c);
+        return st;
+    }
+    *out = c;
+    return GR_OK;
+}
+
+gr_status gr_deposit(gr_ctx *c, int64_t np, const double *x, const double *u, double mass, gr_sources *out)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if (np < 0) return fail(GR_ERR_ARG, "np < 0");
+    if (np > 0 && (!x || !u)) return fail(GR_ERR_ARG, "x or u is NULL");
+    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL");
+    if (!(mass >= 0) || !std::isfinite(mass)) return fail(GR_ERR_ARG, "mass must be finite and >= 0");
+    gr::deposit(c->n, c->L, np, x, u, mass, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
+    c->rho_dep = mass * (double)np / (c->L * c->L * c->L);
+    return cuda_check("gr_deposit");
+}
+
+gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, const gr_opts *o, gr_report *rep)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
+    double rho, S_hat;
+    gr_status st = resolve_bg(c, o, &rho, &S_hat);
+    if (st != GR_OK) return st;
+    gr_report R;
+    memset(&R, 0, sizeof(R));
+    auto t0 = std::chrono::steady_clock::now();
+    c->a_valid = false;
+    gr_status worst = GR_OK;
+    std::string first_err;
+    for (int eq = 0; eq < GR_NEQ; eq++) {
+        if (eq == GR_PSI) c->a_valid = false;  // V and U are final now
+        cudaEventRecord(c->ev0, c->st);
+        st = solve_eq(c, eq, s, fl, o, rho, S_hat, o->tol, o->max_cycles, &R.cycles[eq], &R.res0[eq], &R.res[eq],
+                      &R.cell_updates);
+        cudaEventRecord(c->ev1, c->st);
+        cudaEventSynchronize(c->ev1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        R.eq_seconds[eq] = ms * 1e-3;
+        R.eq_status[eq] = st;
+        if (o->verbose)
+            fprintf(stderr, "[gr] eq %d: %d cycles, res %.3e -> %.3e, %.3f ms, status %d\n", eq, R.cycles[eq],
+                    R.res0[eq], R.res[eq], ms, (int)st);
+        if (st != GR_OK && worst == GR_OK) {
+            worst = st;
+            first_err = g_err;
+        }
+        if (st != GR_OK && st != GR_ERR_NOCONV) break;
+    }
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    if (worst != GR_OK) g_err = first_err;
+    return worst;
+}
+
+gr_status gr_vcycle(gr_ctx *c, gr_eq eq, const gr_sources *s, gr_fields *fl, const gr_opts *o, double *res_after)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if ((int)eq < 0 || (int)eq >= GR_NEQ) return fail(GR_ERR_ARG, "bad equation %d", (int)eq);
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
+    double rho, S_hat;
+    gr_status st = resolve_bg(c, o, &rho, &S_hat);
+    if (st != GR_OK) return st;
+    c->a_valid = false;
+    double r = NAN;
+    st = solve_eq(c, eq, s, fl, o, rho, S_hat, -1.0, 1, nullptr, nullptr, &r, nullptr);
+    if (res_after) *res_after = r;
+    return st;
+}
+
+gr_status gr_residual(gr_ctx *c, gr_eq eq, const gr_sources *s, const gr_fields *fl, const gr_opts *o,
+                      double *res_field, double *rel_norm)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if ((int)eq < 0 || (int)eq >= GR_NEQ) return fail(GR_ERR_ARG, "bad equation %d", (int)eq);
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
+    double rho, S_hat;
+    gr_status st = resolve_bg(c, o, &rho, &S_hat);
+    if (st != GR_OK) return st;
+    c->a_valid = false;
+    EqInfo in;
+    st = setup_eq(c, eq, s, fl, rho, S_hat, &in);
+    if (st != GR_OK) return st;
+    double r;
+    st = norm64(c, in.kind, rho, in.ref, res_field, &r);
+    if (rel_norm) *rel_norm = r;
+    return st;
+}
+
+}  // extern "C"

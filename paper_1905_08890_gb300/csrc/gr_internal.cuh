@@ -1,0 +1,117 @@
+// gr_internal.cuh - shared definitions of the CUDA library (not part of the C ABI).
+//
+// Multigrid level arrays use a red-black split layout: on a level of extent
+// n (a power of two, n >= 2) the cell (i, j, k) of colour c = (i + j + k) & 1
+// lives at
+//     c * n^3/2 + (i * n + j) * (n/2) + (k >> 1).
+// A red cell's six neighbours are black cells at the same half-index q = k>>1
+// in rows (i +- 1, j) and (i, j +- 1), and at q and q + (p ? 1 : -1) in its own
+// row, p = (i + j + c) & 1 the parity of k.  A colour pass therefore reads one
+// contiguous half-array and writes the other, with no idle threads, and the
+// 8 children of a coarse cell (I, J, K) all sit at q = K in rows (2I + a, 2J + b).
+// Caller-facing fields and sources use the natural [n][n][n] layout.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gr {
+
+constexpr double kPi = 3.14159265358979323846;
+
+enum Kind : int { KPOISSON = 0, KHELM = 1, KPSI = 2 };
+
+constexpr int kBlock = 256;
+constexpr int kMaxRedBlocks = 1024;  // blocks of the norm/mean reductions
+constexpr int kCoarsestSweeps = 32;  // red-black sweeps on the 2^3 level
+
+// ---- multigrid kernels (templated on the working precision T) ---------------
+// One Gauss-Seidel pass over colour `color` of a level.  KPOISSON: f;
+// KHELM: f and c1 = 1/(6 + h^2 m); KPSI (double only): f, c0 = s0, c1 = AA,
+// unknown u = psi - 1, one Newton step per cell.
+template <typename T>
+void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, double h2, double ih2, double rho,
+                  int color, cudaStream_t st);
+
+// Residual eps = L(u) - f of the fine level restricted to the coarse level.
+// Correction form (fas = 0): fc = -R eps, uc = 0.  FAS (fas = 1, KPSI):
+// fc = R eps, uc = urc = R u.  c0 is m for KHELM (the operator), s0 for KPSI.
+template <typename T>
+void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const T *c1, double ih2, double rho, T *uc,
+                    T *fc, T *urc, int fas, cudaStream_t st);
+
+// FAS coarse right-hand side: fc = N(uc) - fc (KPSI, double).
+void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
+             cudaStream_t st);
+// uc -= urc (the FAS coarse correction).
+void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st);
+
+// Fine u += P(uc), cell-centred trilinear.
+template <typename T>
+void prolong_add(int nf, T *u, const T *uc, cudaStream_t st);
+
+// The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage);
+// Poisson: source mean removed before and solution mean after.  KHELM reads
+// c0 = m (the inverse diagonal is formed in FP64).
+template <typename T>
+void coarsest(int kind, T *u, T *f, const T *c0, const T *c1, double h2, double ih2, double rho, cudaStream_t st);
+
+// Coarse coefficients.  KPSI: c0c = R c0f, c1c = R c1f.  KHELM: c0c = R c0f
+// (m) and c1c = 1/(6 + h2c c0c).
+template <typename T>
+void restrict_coef(int kind, int nf, const T *c0f, const T *c1f, T *c0c, T *c1c, double h2c, cudaStream_t st);
+// KHELM inverse diagonal on one level: c1 = 1/(6 + h2 c0).
+template <typename T>
+void helm_invdiag(int n, const T *c0, T *c1, double h2, cudaStream_t st);
+
+// Block partial sums of eps^2 and of u over a level (split layout);
+// eps_nat (may be null) receives eps in natural layout (double).
+// Partials: 2 doubles per block; returns the number of blocks.
+template <typename T>
+int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1, double ih2, double rho,
+               double *partials, double *eps_nat, cudaStream_t st);
+// out[0] = sum of partials[2b], out[1] = sum of partials[2b + 1].
+void finalize(const double *partials, int nblk, double *out, cudaStream_t st);
+
+// ---- mixed precision -------------------------------------------------------
+// FP64 residual on the fine level; writes r32 = -eps (split), and for KPSI
+// the Jacobian coefficient m32 = -dN/du > 0 and its inverse diagonal inv32.
+int mixed_resid(int kind, int n, const double *u, const double *f, const double *c0, const double *c1, double ih2,
+                double h2, double rho, float *r32, float *m32, float *inv32, double *partials, cudaStream_t st);
+// u64 += e32 (split layout).
+void mixed_update(int n, double *u, const float *e, cudaStream_t st);
+// c32 = (float) c64.
+void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
+
+// ---- sources, coefficients, layouts (field_kernels.cu) ---------------------
+void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
+             double *sy, double *sz, double *sig, cudaStream_t st);
+// Partial sums of a and a^2 over cnt doubles; returns the block count.
+int sum_sq(int64_t cnt, const double *a, double *partials, cudaStream_t st);
+// a[i] = scale * (a[i] - s[0] / cnt_total), s a device scalar (a sum).
+void scale_sub_mean(int64_t cnt, double *a, const double *sum, double inv_cnt, double scale, cudaStream_t st);
+// natural -> split with a shift: split = nat + shift; split -> natural:
+// nat = split + shift - sum[0] * inv_cnt (sum may be null).
+void to_split(int n, const double *nat, double *split, double shift, cudaStream_t st);
+void from_split(int n, const double *split, double *nat, double shift, const double *sum, double inv_cnt,
+                cudaStream_t st);
+// f (split) = scale * div3(F) from natural F (3-point central differences).
+void div_to_split(int n, double inv2h, const double *Fx, const double *Fy, const double *Fz, double scale, double *f,
+                  cudaStream_t st);
+// A_ij (6 natural arrays: xx yy zz xy xz yz) and AA (natural) from V, U.
+void aij_aa(int n, double inv2h, double ih2, const double *Vx, const double *Vy, const double *Vz, const double *U,
+            double *A, double *AA, cudaStream_t st);
+// psi equation: u = psi - 1, c0 = s0, c1 = AA, f = 0 (split).
+void psi_setup(int n, const double *psi, const double *s0, const double *AA, double *u, double *c0, double *c1,
+               double *f, cudaStream_t st);
+// alpha psi equation: u = apsi - 1, c0 = m, c1 = 1/(6 + h^2 m), f = m - psi^5 Kdot (split);
+// g = psi^5 Kdot (natural scratch) for the reference norm.
+void apsi_setup(int n, double h2, const double *psi, const double *apsi, const double *s0, const double *sig,
+                const double *AA, double K2, double Kdot, double *u, double *c0, double *c1, double *f, double *g,
+                cudaStream_t st);
+// B^i source: f (split) = 2 sum_j D_j (w A^ij), w = apsi psi^-7 (natural scratch).
+void shift_weight(int n, const double *psi, const double *apsi, double *w, cudaStream_t st);
+void shift_source(int n, double inv2h, const double *A, const double *w, int comp, double *f, cudaStream_t st);
+
+}  // namespace gr

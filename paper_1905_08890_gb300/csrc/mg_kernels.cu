@@ -1,0 +1,550 @@
+// mg_kernels.cu - multigrid kernels on red-black split level arrays.
+//
+// Operators (Sec. 4.3): 7-point Laplacian (nb - 6u)/h^2 and
+//   KPOISSON  L(u) = lap u
+//   KHELM     L(u) = lap u - m u                          (alpha psi, Eq. sol-scheme-CMC)
+//   KPSI      L(u) = lap u + 2 pi s0/psi + AA/(8 psi^7) - 2 pi rho psi^5,  psi = 1 + u
+//                                                         (Eq. sol-scheme-H-constraint)
+// Relaxation: red-black Gauss-Seidel, one Newton step per cell for KPSI (Sec. 4.3.2).
+// Transfers: R = average of the 8 children, P = cell-centred trilinear (3/4, 1/4).
+#include "gr_internal.cuh"
+
+namespace gr {
+namespace {
+
+inline int grid_for(int64_t work)
+{
+    int64_t b = (work + kBlock - 1) / kBlock;
+    const int64_t cap = 152 * 16;  // grid-stride beyond 16 resident blocks per SM
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+inline int log2i(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// split-layout index of natural coordinates on a level of extent 2^lgn
+__device__ __forceinline__ int64_t sidx(int lgn, int i, int j, int k)
+{
+    const int64_t half = (int64_t)1 << (3 * lgn - 1);
+    return (int64_t)((i + j + k) & 1) * half + ((((int64_t)i << lgn) + j) << (lgn - 1)) + (k >> 1);
+}
+
+// natural coordinates of split index t
+__device__ __forceinline__ void scoord(int lgn, int64_t t, int &i, int &j, int &k)
+{
+    const int n1 = (1 << lgn) - 1, h1 = (1 << (lgn - 1)) - 1;
+    const int c = (int)(t >> (3 * lgn - 1));
+    const int q = (int)(t & h1);
+    j = (int)((t >> (lgn - 1)) & n1);
+    i = (int)((t >> (2 * lgn - 1)) & n1);
+    k = 2 * q + ((i + j + c) & 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T nbsum(const T *__restrict__ u, int lgn, int i, int j, int k)
+{
+    const int m = (1 << lgn) - 1;
+    return u[sidx(lgn, (i + 1) & m, j, k)] + u[sidx(lgn, (i - 1) & m, j, k)] + u[sidx(lgn, i, (j + 1) & m, k)] +
+           u[sidx(lgn, i, (j - 1) & m, k)] + u[sidx(lgn, i, j, (k + 1) & m)] + u[sidx(lgn, i, j, (k - 1) & m)];
+}
+
+// L(u) at one cell: u value uc, neighbour sum nb, coefficients at the cell
+template <typename T, int KIND>
+__device__ __forceinline__ T op_cell(T uc, T nb, T ih2, T c0, T c1, T rho)
+{
+    T lap = (nb - T(6) * uc) * ih2;
+    if (KIND == KPOISSON) return lap;
+    if (KIND == KHELM) return lap - c0 * uc;
+    const double v = 1.0 + (double)uc, iv = 1.0 / v, iv2 = iv * iv, iv4 = iv2 * iv2;
+    const double v2 = v * v, v4 = v2 * v2;
+    return (T)((double)lap + 2.0 * kPi * (double)c0 * iv + 0.125 * (double)c1 * (iv4 * iv2 * iv) -
+               2.0 * kPi * (double)rho * (v4 * v));
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ T resid_cell(const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
+                                        const T *__restrict__ c1, int lgn, int i, int j, int k, T ih2, T rho)
+{
+    const int64_t id = sidx(lgn, i, j, k);
+    const T a0 = (KIND == KPOISSON) ? T(0) : c0[id];
+    const T a1 = (KIND == KPSI) ? c1[id] : T(0);
+    return op_cell<T, KIND>(u[id], nbsum(u, lgn, i, j, k), ih2, a0, a1, rho) - f[id];
+}
+
+// ---------------------------------------------------------------- sweep
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock)
+    k_sweep(int lgn, T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
+            T h2, T ih2, T rho, int color)
+{
+    const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
+    const int64_t half = (int64_t)1 << (3 * lgn - 1);
+    const int64_t off = color ? half : 0;
+    T *__restrict__ own = u + off;
+    const T *__restrict__ oth = u + (half - off);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < half; t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t & mh);
+        const int j = (int)((t >> lgh) & mn);
+        const int i = (int)(t >> (lgh + lgn));
+        const int p = (i + j + color) & 1;
+        const int64_t r0 = t - q;
+        const int64_t ri = (int64_t)j << lgh;
+        const int64_t rip = ((int64_t)((i + 1) & mn) << (lgn + lgh)) + ri;
+        const int64_t rim = ((int64_t)((i - 1) & mn) << (lgn + lgh)) + ri;
+        const int64_t rj = (int64_t)i << (lgn + lgh);
+        const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh);
+        const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh);
+        const int qs = (q + (p ? 1 : -1)) & mh;
+        const T nb = oth[rip + q] + oth[rim + q] + oth[rjp + q] + oth[rjm + q] + oth[r0 + q] + oth[r0 + qs];
+        const int64_t c = off + t;
+        if (KIND == KPOISSON) {
+            own[t] = (nb - h2 * f[c]) * T(1.0 / 6.0);
+        } else if (KIND == KHELM) {
+            own[t] = (nb - h2 * f[c]) * c1[c];  // c1 = 1/(6 + h^2 m)
+        } else {
+            const double uc = (double)own[t];
+            const double v = 1.0 + uc, iv = 1.0 / v, iv2 = iv * iv, iv4 = iv2 * iv2, iv8 = iv4 * iv4;
+            const double v2 = v * v, v4 = v2 * v2;
+            const double s0 = (double)c0[c], aa = (double)c1[c], ihd = (double)ih2, rh = (double)rho;
+            const double g = ((double)nb - 6.0 * uc) * ihd + 2.0 * kPi * s0 * iv + 0.125 * aa * (iv4 * iv2 * iv) -
+                             2.0 * kPi * rh * (v4 * v) - (double)f[c];
+            const double dg = -6.0 * ihd - 2.0 * kPi * s0 * iv2 - 0.875 * aa * iv8 - 10.0 * kPi * rh * v4;
+            own[t] = (T)(uc - g / dg);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- residual + restriction
+template <typename T, int KIND, int FAS>
+__global__ void __launch_bounds__(kBlock)
+    k_resid_restrict(int lgf, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
+                     const T *__restrict__ c1, T ih2, T rho, T *__restrict__ uc, T *__restrict__ fc,
+                     T *__restrict__ urc)
+{
+    const int lgc = lgf - 1;
+    const int mc = (1 << lgc) - 1;
+    const int64_t ncells = (int64_t)1 << (3 * lgc);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+        T s = T(0), su = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+                    s += resid_cell<T, KIND>(u, f, c0, c1, lgf, i, j, k, ih2, rho);
+                    if (FAS) su += u[sidx(lgf, i, j, k)];
+                }
+        const int64_t cid = lgc > 0 ? sidx(lgc, I, J, K) : 0;
+        if (FAS) {
+            fc[cid] = T(0.125) * s;
+            uc[cid] = T(0.125) * su;
+            urc[cid] = T(0.125) * su;
+        } else {
+            fc[cid] = -(T(0.125) * s);
+            uc[cid] = T(0);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_fas_rhs(int lgc, const double *__restrict__ uc, double *__restrict__ fc, const double *__restrict__ c0,
+              const double *__restrict__ c1, double ih2, double rho)
+{
+    const int64_t ncells = (int64_t)1 << (3 * lgc);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        scoord(lgc, t, i, j, k);
+        fc[t] = op_cell<double, KPSI>(uc[t], nbsum(uc, lgc, i, j, k), ih2, c0[t], c1[t], rho) - fc[t];
+    }
+}
+
+__global__ void k_fas_diff(int64_t cnt, double *__restrict__ uc, const double *__restrict__ urc)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        uc[t] -= urc[t];
+}
+
+// ---------------------------------------------------------------- prolongation
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
+{
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1;
+    const int64_t ncells = (int64_t)1 << (3 * lgf);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        scoord(lgf, t, i, j, k);
+        int Ia[2], Jb[2], Kc[2];
+        Ia[0] = i >> 1;
+        Ia[1] = (i & 1) ? ((Ia[0] + 1) & mc) : ((Ia[0] - 1) & mc);
+        Jb[0] = j >> 1;
+        Jb[1] = (j & 1) ? ((Jb[0] + 1) & mc) : ((Jb[0] - 1) & mc);
+        Kc[0] = k >> 1;
+        Kc[1] = (k & 1) ? ((Kc[0] + 1) & mc) : ((Kc[0] - 1) & mc);
+        const T w[2] = {T(0.75), T(0.25)};
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int64_t cid = lgc > 0 ? sidx(lgc, Ia[a], Jb[b], Kc[c]) : 0;
+                    s += w[a] * w[b] * w[c] * uc[cid];
+                }
+        u[t] += s;
+    }
+}
+
+// ---------------------------------------------------------------- 2^3 level
+template <typename T, int KIND>
+__global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
+                           double h2, double ih2, double rho)
+{
+    __shared__ double su[8], sf[8], s0[8], s1[8];
+    const int t = threadIdx.x;
+    if (t < 8) {
+        su[t] = (double)u[t];
+        sf[t] = (double)f[t];
+        s0[t] = (KIND == KPOISSON) ? 0.0 : (double)c0[t];
+        s1[t] = (KIND == KPSI) ? (double)c1[t] : 0.0;
+    }
+    __syncthreads();
+    if (KIND == KPOISSON && t == 0) {
+        double m = 0.0;
+        for (int q = 0; q < 8; q++) m += sf[q];
+        m *= 0.125;
+        for (int q = 0; q < 8; q++) sf[q] -= m;
+    }
+    __syncthreads();
+    // on 2^3 the split index of (i, j, k) is 4 c + 2 i + j; every neighbour
+    // along an axis is the same cell, counted twice
+    for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
+        for (int color = 0; color < 2; color++) {
+            if (t < 4) {
+                const int i = t >> 1, j = t & 1;
+                const int id = 4 * color + t;
+                const int o = 4 * (color ^ 1);
+                const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
+                if (KIND == KPOISSON) {
+                    su[id] = (nb - h2 * sf[id]) / 6.0;
+                } else if (KIND == KHELM) {
+                    su[id] = (nb - h2 * sf[id]) / (6.0 + h2 * s0[id]);
+                } else {
+                    const double uc = su[id], v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
+                    const double g = (nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[id] / v + s1[id] / (8.0 * v4 * v2 * v) -
+                                     2.0 * kPi * rho * v4 * v - sf[id];
+                    const double dg =
+                        -6.0 * ih2 - 2.0 * kPi * s0[id] / v2 - 7.0 * s1[id] / (8.0 * v4 * v4) - 10.0 * kPi * rho * v4;
+                    su[id] = uc - g / dg;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (KIND == KPOISSON && t == 0) {
+        double m = 0.0;
+        for (int q = 0; q < 8; q++) m += su[q];
+        m *= 0.125;
+        for (int q = 0; q < 8; q++) su[q] -= m;
+    }
+    __syncthreads();
+    if (t < 8) {
+        u[t] = (T)su[t];
+        f[t] = (T)sf[t];
+    }
+}
+
+// ---------------------------------------------------------------- coefficients
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock) k_restrict_coef(int lgf, const T *__restrict__ c0f, const T *__restrict__ c1f,
+                                                          T *__restrict__ c0c, T *__restrict__ c1c, T h2c)
+{
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1;
+    const int64_t ncells = (int64_t)1 << (3 * lgc);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+        T s0 = T(0), s1 = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int64_t id = sidx(lgf, 2 * I + a, 2 * J + b, 2 * K + c);
+                    s0 += c0f[id];
+                    if (KIND == KPSI) s1 += c1f[id];
+                }
+        const int64_t cid = lgc > 0 ? sidx(lgc, I, J, K) : 0;
+        c0c[cid] = T(0.125) * s0;
+        if (KIND == KPSI)
+            c1c[cid] = T(0.125) * s1;
+        else
+            c1c[cid] = T(1) / (T(6) + h2c * (T(0.125) * s0));
+    }
+}
+
+template <typename T>
+__global__ void k_helm_invdiag(int64_t cnt, const T *__restrict__ c0, T *__restrict__ c1, T h2)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        c1[t] = T(1) / (T(6) + h2 * c0[t]);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ void block_sum2(double a, double b, double *out)
+{
+    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int q = 0; q < kBlock / 32; q++) {
+            ta += sa[q];
+            tb += sb[q];
+        }
+        out[2 * blockIdx.x] = ta;
+        out[2 * blockIdx.x + 1] = tb;
+    }
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock)
+    k_resid_norm(int lgn, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
+                 const T *__restrict__ c1, T ih2, T rho, double *__restrict__ partials, double *__restrict__ eps_nat)
+{
+    const int64_t ncells = (int64_t)1 << (3 * lgn);
+    double s2 = 0.0, su = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        scoord(lgn, t, i, j, k);
+        const double e = (double)resid_cell<T, KIND>(u, f, c0, c1, lgn, i, j, k, ih2, rho);
+        s2 += e * e;
+        su += (double)u[t];
+        if (eps_nat) eps_nat[((((int64_t)i << lgn) + j) << lgn) + k] = e;
+    }
+    block_sum2(s2, su, partials);
+}
+
+__global__ void k_finalize(const double *__restrict__ partials, int nblk, double *__restrict__ out)
+{
+    // one warp, fixed summation order
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += 32) {
+        a += partials[2 * q];
+        b += partials[2 * q + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// ---------------------------------------------------------------- mixed precision
+template <int KIND>
+__global__ void __launch_bounds__(kBlock)
+    k_mixed_resid(int lgn, const double *__restrict__ u, const double *__restrict__ f, const double *__restrict__ c0,
+                  const double *__restrict__ c1, double ih2, double h2, double rho, float *__restrict__ r32,
+                  float *__restrict__ m32, float *__restrict__ inv32, double *__restrict__ partials)
+{
+    const int64_t ncells = (int64_t)1 << (3 * lgn);
+    double s2 = 0.0, su = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        scoord(lgn, t, i, j, k);
+        const double e = resid_cell<double, KIND>(u, f, c0, c1, lgn, i, j, k, ih2, rho);
+        s2 += e * e;
+        su += u[t];
+        r32[t] = (float)(-e);
+        if (KIND == KPSI) {
+            const double v = 1.0 + u[t], iv = 1.0 / v, iv2 = iv * iv, iv4 = iv2 * iv2, v2 = v * v;
+            const double mj = 2.0 * kPi * c0[t] * iv2 + 0.875 * c1[t] * (iv4 * iv4) + 10.0 * kPi * rho * (v2 * v2);
+            const float mf = (float)mj;
+            m32[t] = mf;
+            inv32[t] = 1.0f / (6.0f + (float)h2 * mf);
+        }
+    }
+    block_sum2(s2, su, partials);
+}
+
+__global__ void k_mixed_update(int64_t cnt, double *__restrict__ u, const float *__restrict__ e)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        u[t] += (double)e[t];
+}
+
+__global__ void k_to_float(int64_t cnt, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+
+}  // namespace
+
+// ================================================================ launchers
+template <typename T>
+void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, double h2, double ih2, double rho,
+                  int color, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = grid_for((int64_t)n * n * n / 2);
+    if (kind == KPOISSON)
+        k_sweep<T, KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+    else if (kind == KHELM)
+        k_sweep<T, KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+    else
+        k_sweep<T, KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+}
+
+template <typename T>
+void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const T *c1, double ih2, double rho, T *uc,
+                    T *fc, T *urc, int fas, cudaStream_t st)
+{
+    const int lgf = log2i(nf);
+    const int g = grid_for((int64_t)nf * nf * nf / 8);
+    if (kind == KPOISSON)
+        k_resid_restrict<T, KPOISSON, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+    else if (kind == KHELM)
+        k_resid_restrict<T, KHELM, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+    else if (fas)
+        k_resid_restrict<T, KPSI, 1><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+    else
+        k_resid_restrict<T, KPSI, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+}
+
+void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
+             cudaStream_t st)
+{
+    k_fas_rhs<<<grid_for((int64_t)nc * nc * nc), kBlock, 0, st>>>(log2i(nc), uc, fc, c0, c1, ih2, rho);
+}
+
+void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
+{
+    const int64_t cnt = (int64_t)nc * nc * nc;
+    k_fas_diff<<<grid_for(cnt), kBlock, 0, st>>>(cnt, uc, urc);
+}
+
+template <typename T>
+void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
+{
+    k_prolong_add<T><<<grid_for((int64_t)nf * nf * nf), kBlock, 0, st>>>(log2i(nf), u, uc);
+}
+
+template <typename T>
+void coarsest(int kind, T *u, T *f, const T *c0, const T *c1, double h2, double ih2, double rho, cudaStream_t st)
+{
+    if (kind == KPOISSON)
+        k_coarsest<T, KPOISSON><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+    else if (kind == KHELM)
+        k_coarsest<T, KHELM><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+    else
+        k_coarsest<T, KPSI><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+}
+
+template <typename T>
+void restrict_coef(int kind, int nf, const T *c0f, const T *c1f, T *c0c, T *c1c, double h2c, cudaStream_t st)
+{
+    const int g = grid_for((int64_t)nf * nf * nf / 8);
+    if (kind == KPSI)
+        k_restrict_coef<T, KPSI><<<g, kBlock, 0, st>>>(log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
+    else
+        k_restrict_coef<T, KHELM><<<g, kBlock, 0, st>>>(log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
+}
+
+template <typename T>
+void helm_invdiag(int n, const T *c0, T *c1, double h2, cudaStream_t st)
+{
+    const int64_t cnt = (int64_t)n * n * n;
+    k_helm_invdiag<T><<<grid_for(cnt), kBlock, 0, st>>>(cnt, c0, c1, (T)h2);
+}
+
+static int red_grid(int64_t cnt)
+{
+    int g = grid_for(cnt);
+    return g > kMaxRedBlocks ? kMaxRedBlocks : g;
+}
+
+template <typename T>
+int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1, double ih2, double rho,
+               double *partials, double *eps_nat, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = red_grid((int64_t)n * n * n);
+    if (kind == KPOISSON)
+        k_resid_norm<T, KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+    else if (kind == KHELM)
+        k_resid_norm<T, KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+    else
+        k_resid_norm<T, KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+    return g;
+}
+
+void finalize(const double *partials, int nblk, double *out, cudaStream_t st)
+{
+    k_finalize<<<1, 32, 0, st>>>(partials, nblk, out);
+}
+
+int mixed_resid(int kind, int n, const double *u, const double *f, const double *c0, const double *c1, double ih2,
+                double h2, double rho, float *r32, float *m32, float *inv32, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = red_grid((int64_t)n * n * n);
+    if (kind == KPOISSON)
+        k_mixed_resid<KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+    else if (kind == KHELM)
+        k_mixed_resid<KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+    else
+        k_mixed_resid<KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+    return g;
+}
+
+void mixed_update(int n, double *u, const float *e, cudaStream_t st)
+{
+    const int64_t cnt = (int64_t)n * n * n;
+    k_mixed_update<<<grid_for(cnt), kBlock, 0, st>>>(cnt, u, e);
+}
+
+void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st)
+{
+    k_to_float<<<grid_for(cnt), kBlock, 0, st>>>(cnt, a, b);
+}
+
+#define GR_INST(T)                                                                                                  \
+    template void sweep_colour<T>(int, int, T *, const T *, const T *, const T *, double, double, double, int,     \
+                                  cudaStream_t);                                                                   \
+    template void resid_restrict<T>(int, int, const T *, const T *, const T *, const T *, double, double, T *, T *, \
+                                    T *, int, cudaStream_t);                                                       \
+    template void prolong_add<T>(int, T *, const T *, cudaStream_t);                                               \
+    template void coarsest<T>(int, T *, T *, const T *, const T *, double, double, double, cudaStream_t);           \
+    template void restrict_coef<T>(int, int, const T *, const T *, T *, T *, double, cudaStream_t);                \
+    template void helm_invdiag<T>(int, const T *, T *, double, cudaStream_t);                                      \
+    template int resid_norm<T>(int, int, const T *, const T *, const T *, const T *, double, double, double *,     \
+                               double *, cudaStream_t);
+GR_INST(double)
+GR_INST(float)
+
+}  // namespace gr

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of the C ABI in include/gr.h.
+
+Argument marshalling only: every step of the deposit and the solve runs in
+the CUDA kernels of libgr.so.  Arrays are torch CUDA tensors (float64,
+contiguous); torch provides device memory and streams.  There is no CPU
+fallback: if libgr.so cannot be built or loaded, every call raises.
+
+The functions keep the C names (gr_create, gr_deposit, gr_solve_constraints,
+gr_vcycle, gr_residual, ...).  ``Context`` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+GR_OK, GR_ERR_ARG, GR_ERR_CUDA, GR_ERR_NOMEM, GR_ERR_NOCONV, GR_ERR_NONFINITE, GR_ERR_STATE = range(7)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOMEM", "ERR_NOCONV", "ERR_NONFINITE", "ERR_STATE"]
+EQUATIONS = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+GR_VX, GR_VY, GR_VZ, GR_U, GR_PSI, GR_APSI, GR_BX, GR_BY, GR_BZ, GR_B_SCALAR = range(10)
+GR_NEQ = 10
+GR_PREC_FP64, GR_PREC_MIXED = 0, 1
+FIELDS = ("psi", "apsi", "Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b")
+SOURCES = ("s0", "sx", "sy", "sz", "sigma")
+
+_P = ctypes.c_void_p
+
+
+class gr_sources(ctypes.Structure):
+    _fields_ = [("s0", _P), ("s", _P * 3), ("sigma", _P)]
+
+
+class gr_fields(ctypes.Structure):
+    _fields_ = [("psi", _P), ("apsi", _P), ("V", _P * 3), ("U", _P), ("B", _P * 3), ("b", _P)]
+
+
+class gr_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
+                ("verbose", ctypes.c_int)]
+
+
+class gr_report(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int * 10), ("res0", ctypes.c_double * 10), ("res", ctypes.c_double * 10),
+                ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
+                ("cell_updates", ctypes.c_longlong)]
+
+
+_lib = None
+_lock = threading.Lock()
+EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_solve_constraints", "gr_vcycle",
+            "gr_residual", "gr_last_error")
+
+
+def lib():
+    """Build (if stale) and load libgr.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = os.environ.get("GR_LIBRARY") or _build.build()
+            L = ctypes.CDLL(path)
+            L.gr_default_opts.argtypes = [ctypes.POINTER(gr_opts)]
+            L.gr_default_opts.restype = None
+            L.gr_create.argtypes = [ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(_P)]
+            L.gr_create.restype = ctypes.c_int
+            L.gr_destroy.argtypes = [_P]
+            L.gr_destroy.restype = None
+            L.gr_deposit.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.c_double, ctypes.POINTER(gr_sources)]
+            L.gr_deposit.restype = ctypes.c_int
+            L.gr_solve_constraints.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
+                                               ctypes.POINTER(gr_opts), ctypes.POINTER(gr_report)]
+            L.gr_solve_constraints.restype = ctypes.c_int
+            L.gr_vcycle.argtypes = [_P, ctypes.c_int, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
+                                    ctypes.POINTER(gr_opts), ctypes.POINTER(ctypes.c_double)]
+            L.gr_vcycle.restype = ctypes.c_int
+            L.gr_residual.argtypes = [_P, ctypes.c_int, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
+                                      ctypes.POINTER(gr_opts), _P, ctypes.POINTER(ctypes.c_double)]
+            L.gr_residual.restype = ctypes.c_int
+            L.gr_last_error.argtypes = []
+            L.gr_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+class GRError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str, allow=()):
+    if st != GR_OK and st not in allow:
+        raise GRError(st, where, lib().gr_last_error().decode())
+    return st
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def make_sources(src: dict) -> gr_sources:
+    s = gr_sources()
+    s.s0 = _ptr(src["s0"])
+    for d, k in enumerate(("sx", "sy", "sz")):
+        s.s[d] = _ptr(src[k])
+    s.sigma = _ptr(src["sigma"])
+    return s
+
+
+def make_fields(fld: dict) -> gr_fields:
+    f = gr_fields()
+    f.psi = _ptr(fld["psi"])
+    f.apsi = _ptr(fld["apsi"])
+    for d, k in enumerate(("Vx", "Vy", "Vz")):
+        f.V[d] = _ptr(fld[k])
+    f.U = _ptr(fld["U"])
+    for d, k in enumerate(("Bx", "By", "Bz")):
+        f.B[d] = _ptr(fld[k])
+    f.b = _ptr(fld["b"])
+    return f
+
+
+def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0) -> gr_opts:
+    o = gr_opts()
+    lib().gr_default_opts(ctypes.byref(o))
+    o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
+    o.prec = {"fp64": GR_PREC_FP64, "mixed": GR_PREC_MIXED}[prec] if isinstance(prec, str) else int(prec)
+    o.rho_hat, o.S_hat, o.verbose = rho_hat, S_hat, verbose
+    return o
+
+
+def report_dict(r: gr_report) -> dict:
+    return {"cycles": list(r.cycles), "res0": list(r.res0), "res": list(r.res), "status": list(r.eq_status),
+            "seconds": r.seconds, "eq_seconds": list(r.eq_seconds), "cell_updates": int(r.cell_updates)}
+
+
+# ------------------------------------------------------------------ C names
+def gr_create(n: int, L: float = 1.0, stream=None):
+    h = _P()
+    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    _check(lib().gr_create(n, L, st, ctypes.byref(h)), "gr_create")
+    return h
+
+
+def gr_destroy(ctx):
+    lib().gr_destroy(ctx)
+
+
+def gr_deposit(ctx, x, u, mass: float, src: dict):
+    npart = x.shape[1] if x.numel() else 0
+    s = make_sources(src)
+    _check(lib().gr_deposit(ctx, npart, _ptr(x) if npart else None, _ptr(u) if npart else None, mass,
+                            ctypes.byref(s)), "gr_deposit")
+
+
+def gr_solve_constraints(ctx, src: dict, fld: dict, opts: gr_opts, allow_noconv=False) -> dict:
+    s, f, r = make_sources(src), make_fields(fld), gr_report()
+    st = lib().gr_solve_constraints(ctx, ctypes.byref(s), ctypes.byref(f), ctypes.byref(opts), ctypes.byref(r))
+    _check(st, "gr_solve_constraints", allow=(GR_ERR_NOCONV,) if allow_noconv else ())
+    d = report_dict(r)
+    d["status_code"] = st
+    return d
+
+
+def gr_vcycle(ctx, eq: int, src: dict, fld: dict, opts: gr_opts) -> float:
+    s, f, r = make_sources(src), make_fields(fld), ctypes.c_double(0)
+    _check(lib().gr_vcycle(ctx, eq, ctypes.byref(s), ctypes.byref(f), ctypes.byref(opts), ctypes.byref(r)),
+           "gr_vcycle")
+    return r.value
+
+
+def gr_residual(ctx, eq: int, src: dict, fld: dict, opts: gr_opts, res_field=None) -> float:
+    s, f, r = make_sources(src), make_fields(fld), ctypes.c_double(0)
+    _check(lib().gr_residual(ctx, eq, ctypes.byref(s), ctypes.byref(f), ctypes.byref(opts), _ptr(res_field),
+                             ctypes.byref(r)), "gr_residual")
+    return r.value
+
+
+def gr_last_error() -> str:
+    return lib().gr_last_error().decode()
+
+
+# ------------------------------------------------------------------ convenience
+class Context:
+    """One n^3 periodic grid of side L on the current CUDA device."""
+
+    def __init__(self, n: int, L: float = 1.0, stream=None):
+        import torch
+
+        self.n, self.L = n, L
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = gr_create(n, L, self.stream)
+
+    def close(self):
+        if self.h:
+            gr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _grid(self):
+        import torch
+
+        return torch.empty((self.n,) * 3, dtype=torch.float64, device=self.device)
+
+    def new_sources(self) -> dict:
+        return {k: self._grid() for k in SOURCES}
+
+    def initial_fields(self) -> dict:
+        """The plain guess psi = alpha psi = 1, vectors and scalars 0."""
+        fld = {k: self._grid().zero_() for k in FIELDS}
+        fld["psi"].fill_(1.0)
+        fld["apsi"].fill_(1.0)
+        return fld
+
+    def deposit(self, x, u, mass: float, src: dict | None = None) -> dict:
+        src = src if src is not None else self.new_sources()
+        gr_deposit(self.h, x, u, mass, src)
+        return src
+
+    def solve(self, src, fld, **kw) -> dict:
+        allow = kw.pop("allow_noconv", False)
+        return gr_solve_constraints(self.h, src, fld, make_opts(**kw), allow_noconv=allow)
+
+    def vcycle(self, eq: int, src, fld, **kw) -> float:
+        return gr_vcycle(self.h, eq, src, fld, make_opts(**kw))
+
+    def residual(self, eq: int, src, fld, res_field=None, **kw) -> float:
+        return gr_residual(self.h, eq, src, fld, make_opts(**kw), res_field)

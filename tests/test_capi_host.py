@@ -1,0 +1,50 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every function include/gr.h declares, and arguments are
+validated before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1905_08890_gb300 import gr
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gr.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gr_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_function():
+    L = gr.lib()
+    names = _declared()
+    assert "gr_solve_constraints" in names and "gr_deposit" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_default_opts():
+    o = gr.make_opts()
+    assert o.tol == 1e-10 and o.max_cycles == 50 and o.nu1 == 2 and o.nu2 == 2 and o.prec == 0
+
+
+@pytest.mark.parametrize("n", [0, 2, 6, 12, 2048])
+def test_bad_grid_size_rejected_without_gpu(n):
+    h = ctypes.c_void_p()
+    st = gr.lib().gr_create(n, 1.0, None, ctypes.byref(h))
+    assert st == gr.GR_ERR_ARG and not h.value
+    assert "power of two" in gr.gr_last_error()
+
+
+def test_bad_box_and_null_arguments_rejected():
+    h = ctypes.c_void_p()
+    assert gr.lib().gr_create(8, -1.0, None, ctypes.byref(h)) == gr.GR_ERR_ARG
+    assert gr.lib().gr_create(8, 1.0, None, None) == gr.GR_ERR_ARG
+    o = gr.make_opts()
+    assert gr.lib().gr_solve_constraints(None, None, None, ctypes.byref(o), None) == gr.GR_ERR_ARG
+    assert gr.lib().gr_vcycle(None, 0, None, None, ctypes.byref(o), None) == gr.GR_ERR_ARG
+    assert gr.lib().gr_residual(None, 0, None, None, ctypes.byref(o), None, None) == gr.GR_ERR_ARG
+    assert gr.lib().gr_deposit(None, 0, None, None, 1.0, None) == gr.GR_ERR_ARG

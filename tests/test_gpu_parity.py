@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (deposit, each equation's V-cycle and residual, the full
+ten-equation solve, mixed precision, error handling)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_08890_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker deselects these on CPU
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1905_08890_gb300 import gr  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+RHO = synth.RHO_BAR
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _fields_to_gpu(fld):
+    return {k: _t(v) for k, v in fld.items()}
+
+
+def _dev(k, a):
+    return a - 1.0 if k in ("psi", "apsi") else a
+
+
+# ------------------------------------------------------------------ deposit
+@pytest.mark.parametrize("npart", [0, 1, 1000, 12345])
+def test_deposit_matches_oracle_random(npart):
+    n = 16
+    rng = np.random.default_rng(npart)
+    x = rng.random((3, npart)) * 2.0 - 0.5  # some outside the box: wrapped
+    u = 0.1 * rng.standard_normal((3, npart))
+    m = 0.7
+    ctx = gr.Context(n)
+    src = ctx.deposit(_t(x), _t(u), m)
+    want = oracle.deposit(n, x, u, m)
+    for k in oracle.SOURCES:
+        got = _np(src[k])
+        scale = max(np.abs(want[k]).max(), 1e-300)
+        assert np.abs(got - want[k]).max() <= 1e-13 * scale, k
+        if npart == 0:
+            assert not got.any()
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_deposit_matches_oracle_zeldovich(n):
+    p = synth.zeldovich(n, 3, 1.0, 0.003, True)
+    ctx = gr.Context(n)
+    src = ctx.deposit(_t(p.x), _t(p.u), p.mass)
+    want = oracle.deposit(n, p.x, p.u, p.mass)
+    for k in oracle.SOURCES:
+        assert rel_linf(_np(src[k]), want[k]) <= 1e-13, k
+    ctx.close()
+
+
+# ------------------------------------------------------------------ helpers
+def _problem(n, seed=1, sigma=0.3, v_rms=0.01, lognormal=False):
+    p = synth.zeldovich(n, seed, sigma, v_rms, lognormal)
+    p.u[0] += 0.2 * v_rms  # a bulk flow so the momentum sources have a mean
+    src = oracle.deposit(n, p.x, p.u, p.mass)
+    return p, src
+
+
+def _partial_fields(src, rho, cycles=2):
+    """Fields after a few oracle cycles per equation: not converged, so that
+    one more V-cycle changes every field."""
+    n = src["s0"].shape[0]
+    fld = oracle.initial_fields(n)
+    oracle.solve_constraints(src, fld, rho, tol=0.0, max_cycles=cycles)
+    return fld
+
+
+# ------------------------------------------------------------------ single equations
+@pytest.mark.parametrize("eq", list(range(10)))
+def test_vcycle_each_equation_matches_oracle(eq):
+    n = 32
+    p, src = _problem(n)
+    fld = _partial_fields(src, p.rho_hat)
+    name = gr.EQUATIONS[eq]
+    # oracle: one cycle of this equation from the same state
+    kind, f, c0, c1, ref = oracle.eq_setup(eq, src, fld, p.rho_hat)
+    u = _dev(name, fld[name]).copy()
+    oracle.solve_eq(kind, u, f, c0, c1, p.rho_hat, ref, tol=0.0, max_cycles=1)
+    if kind == oracle.POISSON:
+        u -= u.mean()
+    # GPU
+    ctx = gr.Context(n)
+    gs, gf = _fields_to_gpu(src), _fields_to_gpu(fld)
+    r_after = ctx.vcycle(eq, gs, gf, rho_hat=p.rho_hat)
+    got = _dev(name, _np(gf[name]))
+    assert rel_linf(got, u) <= 1e-12, (name, rel_linf(got, u))
+    # the other fields are untouched
+    for k in oracle.FIELDS:
+        if k != name:
+            assert np.array_equal(_np(gf[k]), fld[k]), k
+    _, r_or = oracle.residual(kind, u, f - (f.mean() if kind == oracle.POISSON else 0.0), c0, c1, p.rho_hat)
+    assert math.isclose(r_after, r_or / ref, rel_tol=1e-6, abs_tol=1e-14)
+    ctx.close()
+
+
+@pytest.mark.parametrize("eq", list(range(10)))
+def test_residual_each_equation_matches_oracle(eq):
+    n = 16
+    p, src = _problem(n, seed=4)
+    fld = _partial_fields(src, p.rho_hat, cycles=1)
+    name = gr.EQUATIONS[eq]
+    kind, f, c0, c1, ref = oracle.eq_setup(eq, src, fld, p.rho_hat)
+    if kind == oracle.POISSON:
+        f = f - f.mean()
+    eps, r = oracle.residual(kind, _dev(name, fld[name]), f, c0, c1, p.rho_hat)
+    ctx = gr.Context(n)
+    out = torch.empty((n, n, n), dtype=torch.float64, device=DEV)
+    rel = ctx.residual(eq, _fields_to_gpu(src), _fields_to_gpu(fld), res_field=out, rho_hat=p.rho_hat)
+    got = _np(out)
+    assert np.abs(got - eps).max() <= 1e-12 * np.abs(eps).max() + 1e-13 * ref, name
+    assert math.isclose(rel, r / ref, rel_tol=1e-10), name
+    ctx.close()
+
+
+# ------------------------------------------------------------------ full solve
+def _solve_both(n, tol, max_cycles, prec="fp64", **gen):
+    p, src = _problem(n, **gen)
+    ofld = oracle.initial_fields(n)
+    ost, orep = oracle.solve_constraints(src, ofld, p.rho_hat, tol=tol, max_cycles=max_cycles)
+    ctx = gr.Context(n)
+    gs = _fields_to_gpu(src)
+    gf = _fields_to_gpu(oracle.initial_fields(n))
+    rep = ctx.solve(gs, gf, tol=tol, max_cycles=max_cycles, prec=prec, allow_noconv=True)
+    out = {k: _np(v) for k, v in gf.items()}
+    ctx.close()
+    return p, ofld, orep, out, rep
+
+
+def test_full_solve_equal_cycle_counts_config1():
+    """32^3 Gaussian Zel'dovich input; three V-cycles per equation on both
+    sides: same algorithm, so fields agree to rounding."""
+    p, ofld, orep, gfld, rep = _solve_both(32, 0.0, 3)
+    assert rep["cycles"] == orep["cycles"] == [3] * 10
+    for k in oracle.FIELDS:
+        assert rel_linf(_dev(k, gfld[k]), _dev(k, ofld[k])) <= 1e-11, (k, rel_linf(_dev(k, gfld[k]), _dev(k, ofld[k])))
+
+
+def test_full_solve_converged_config1():
+    """32^3, both solved to relative residual 1e-12: every field within 1e-11
+    relative L-infinity of the oracle (psi and alpha psi also as deviations)."""
+    p, ofld, orep, gfld, rep = _solve_both(32, 1e-12, 60)
+    assert rep["status_code"] == gr.GR_OK, rep
+    assert all(abs(a - b) <= 1 for a, b in zip(rep["cycles"], orep["cycles"])), (rep["cycles"], orep["cycles"])
+    for k in oracle.FIELDS:
+        assert rel_linf(gfld[k], ofld[k]) <= 1e-11, k
+        assert rel_linf(_dev(k, gfld[k]), _dev(k, ofld[k])) <= 1e-9, k
+    assert rep["cell_updates"] > 0
+
+
+def test_full_solve_converged_config2_size():
+    """128^3 lognormal (rms delta 1, rms |u| 0.003), residual 1e-12 on both
+    sides: fields within 1e-11 relative L-infinity."""
+    p, ofld, orep, gfld, rep = _solve_both(128, 1e-12, 60, seed=2, sigma=1.0, v_rms=0.003, lognormal=True)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for k in oracle.FIELDS:
+        assert rel_linf(gfld[k], ofld[k]) <= 1e-11, (k, rel_linf(gfld[k], ofld[k]))
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_mixed_precision_within_1e8_of_oracle(n):
+    """FP32 correction cycles inside the FP64 defect-correction loop, residual
+    1e-9: every field within 1e-8 relative of the converged FP64 oracle."""
+    p, src = _problem(n, seed=3, sigma=1.0, v_rms=0.003, lognormal=True)
+    ofld = oracle.initial_fields(n)
+    ost, _ = oracle.solve_constraints(src, ofld, p.rho_hat, tol=1e-12, max_cycles=60)
+    assert ost == 0
+    ctx = gr.Context(n)
+    gf = _fields_to_gpu(oracle.initial_fields(n))
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec="mixed")
+    assert rep["status_code"] == gr.GR_OK
+    assert all(r <= 1e-9 for r in rep["res"])
+    for k in oracle.FIELDS:
+        assert rel_linf(_np(gf[k]), ofld[k]) <= 1e-8, (k, rel_linf(_np(gf[k]), ofld[k]))
+    ctx.close()
+
+
+def test_homogeneous_background_from_random_guesses():
+    """Sec. 5.1.2 on the GPU: s0 = rho_hat, no momentum, random guesses:
+    psi = alpha = 1 and every vector potential 0."""
+    n = 16
+    src = {k: np.zeros((n, n, n)) for k in oracle.SOURCES}
+    src["s0"][:] = RHO
+    rng = np.random.default_rng(0)
+    fld = oracle.initial_fields(n)
+    fld["psi"][:] = 1 + 0.2 * rng.random((n, n, n))
+    fld["apsi"][:] = 1 + 0.2 * rng.random((n, n, n))
+    for prec in ("fp64", "mixed"):
+        ctx = gr.Context(n)
+        gf = _fields_to_gpu(fld)
+        rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-12, max_cycles=60, rho_hat=RHO, prec=prec)
+        assert rep["status_code"] == gr.GR_OK
+        assert np.abs(_np(gf["psi"]) - 1).max() < 1e-12
+        assert np.abs(_np(gf["apsi"]) - 1).max() < 1e-12
+        for k in ("Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b"):
+            assert np.abs(_np(gf[k])).max() < 1e-14
+        ctx.close()
+
+
+# ------------------------------------------------------------------ errors
+def test_nonfinite_source_is_reported():
+    n = 8
+    p, src = _problem(n)
+    src["s0"][1, 2, 3] = np.nan
+    ctx = gr.Context(n)
+    with pytest.raises(gr.GRError) as ei:
+        ctx.solve(_fields_to_gpu(src), _fields_to_gpu(oracle.initial_fields(n)), rho_hat=p.rho_hat)
+    assert ei.value.status == gr.GR_ERR_NONFINITE
+    ctx.close()
+
+
+def test_max_cycles_reports_noconv_with_report():
+    n = 16
+    p, src = _problem(n)
+    ctx = gr.Context(n)
+    rep = ctx.solve(_fields_to_gpu(src), _fields_to_gpu(oracle.initial_fields(n)), tol=1e-14, max_cycles=1,
+                    rho_hat=p.rho_hat, allow_noconv=True)
+    assert rep["status_code"] == gr.GR_ERR_NOCONV
+    assert rep["cycles"] == [1] * 10
+    assert all(s == gr.GR_ERR_NOCONV for s in rep["status"])
+    assert all(r1 < r0 for r0, r1 in zip(rep["res0"], rep["res"]) if r0 > 0)
+    ctx.close()
+
+
+def test_missing_background_density_is_an_argument_error():
+    n = 8
+    ctx = gr.Context(n)
+    src = {k: torch.zeros((n, n, n), dtype=torch.float64, device=DEV) for k in gr.SOURCES}
+    with pytest.raises(gr.GRError) as ei:
+        ctx.solve(src, ctx.initial_fields())
+    assert ei.value.status == gr.GR_ERR_ARG
+    ctx.close()
