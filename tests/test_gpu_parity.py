@@ -144,7 +144,7 @@ def _solve_both(n, tol, max_cycles, prec="fp64", **gen):
     ctx = gr.Context(n)
     gs = _fields_to_gpu(src)
     gf = _fields_to_gpu(oracle.initial_fields(n))
-    rep = ctx.solve(gs, gf, tol=tol, max_cycles=max_cycles, prec=prec, allow_noconv=True)
+    rep = ctx.solve(gs, gf, tol=tol, max_cycles=max_cycles, prec=prec, rho_hat=p.rho_hat, allow_noconv=True)
     out = {k: _np(v) for k, v in gf.items()}
     ctx.close()
     return p, ofld, orep, out, rep
@@ -190,7 +190,7 @@ def test_mixed_precision_within_1e8_of_oracle(n):
     assert ost == 0
     ctx = gr.Context(n)
     gf = _fields_to_gpu(oracle.initial_fields(n))
-    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec="mixed")
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec="mixed", rho_hat=p.rho_hat)
     assert rep["status_code"] == gr.GR_OK
     assert all(r <= 1e-9 for r in rep["res"])
     for k in oracle.FIELDS:
