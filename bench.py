@@ -1,0 +1,383 @@
+"""Benchmark: CIC deposit + ten-equation constraint solve to relative residual 1e-8.
+
+One step = deposit of the resident particles, reset of the ten fields to the
+plain guess (psi = alpha psi = 1, vectors 0) and the full solve.  The
+headline path is the mixed-precision solve (FP64 defect correction, FP32
+correction V-cycles); the plain FP64 GPU solve of the same step is timed
+next to it.  Multi-GPU runs are independent replicas (one problem per rank,
+different seeds: weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec mixed|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-residual-1e-8 per 10-eq solve & Gcell-updates/s: learned+FP32 vs plain FP64"
+UNIT = "Gcell-updates/s"
+DEFAULT_WORKLOAD = "zeldovich512_lognormal5"
+
+# algorithmic bytes per finest-level cell and launch, per profiled kernel
+# class and equation kind (split layout: a colour pass touches half the cells)
+BYTES = {
+    # class: {kind: bytes per cell}
+    "sweep32": {"poisson": 6.0, "helm": 8.0},
+    "sweep64": {"poisson": 12.0, "helm": 16.0, "psi": 24.0},
+    "resid_restrict32": {"poisson": 9.0, "helm": 13.0},
+    "resid_restrict64": {"poisson": 18.0, "helm": 26.0, "psi": 35.0},
+    "prolong32": {"any": 8.5},
+    "prolong64": {"any": 17.0},
+    "mixed_resid": {"poisson": 20.0, "helm": 28.0, "psi": 44.0},
+    "mixed_update": {"any": 20.0},
+    "norm64": {"poisson": 16.0, "helm": 24.0, "psi": 32.0},
+}
+EQ_KIND = ["poisson"] * 4 + ["psi", "helm"] + ["poisson"] * 4
+EQ_KIND32 = ["poisson"] * 4 + ["helm", "helm"] + ["poisson"] * 4
+
+
+def class_bytes(cls, cycles, n, nu1, nu2, mixed):
+    """Algorithmic bytes of every finest-level launch of one profiled class
+    over a solve with the given per-equation cycle counts."""
+    cells = float(n) ** 3
+    total = 0.0
+    for eq, cyc in enumerate(cycles):
+        k64, k32 = EQ_KIND[eq], EQ_KIND32[eq]
+        if cls == "sweep32" and mixed:
+            total += cyc * 2 * (nu1 + nu2) * BYTES["sweep32"][k32] * cells
+        elif cls == "sweep64" and not mixed:
+            total += cyc * 2 * (nu1 + nu2) * BYTES["sweep64"][k64] * cells
+        elif cls == "resid_restrict":
+            key = "resid_restrict32" if mixed else "resid_restrict64"
+            total += cyc * BYTES[key][k32 if mixed else k64] * cells
+        elif cls == "prolong":
+            total += cyc * BYTES["prolong32" if mixed else "prolong64"]["any"] * cells
+        elif cls == "mixed_resid" and mixed:
+            total += (cyc + 1) * BYTES["mixed_resid"][k64] * cells
+        elif cls == "mixed_update" and mixed:
+            total += cyc * BYTES["mixed_update"]["any"] * cells
+        elif cls == "norm64" and not mixed:
+            total += (cyc + 1) * BYTES["norm64"][k64] * cells
+    return total
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 7:
+                continue
+            try:
+                sm.append(float(row[0]))
+                smax = float(row[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(n, src_np, rho_hat, cycles=1):
+    """Time the FP64 CPU oracle (as it stands) on a bounded sample of the
+    workload: `cycles` V(2,2) cycles of the V_x and psi equations at the full
+    grid, from the plain guess.  Returns (Gcell-updates/s, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+
+    cells_per_cycle = sum(4 * (n >> l) ** 3 for l in range(0, int(math.log2(n)) - 1)) + 32 * 8
+    fld = oracle.initial_fields(n)
+    t_total, updates = 0.0, 0
+    for eq in (0, 4):
+        kind, f, c0, c1, ref = oracle.eq_setup(eq, src_np, fld, rho_hat)
+        u = np.zeros((n, n, n))
+        t0 = time.perf_counter()
+        for _ in range(cycles):
+            oracle.vcycle(kind, u, f, c0, c1, rho_hat)
+        t_total += time.perf_counter() - t0
+        updates += cycles * cells_per_cycle
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return updates / t_total / 1e9, t_total, threads
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+    from paper_1905_08890_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    n, tol = w["n"], w["tol"]
+    config = {"workload": args.workload, "n": n, "particles": n ** 3, "delta": ("lognormal" if w["lognormal"] else
+              "gaussian") + f" rms {w['sigma']}", "v_rms": w["v_rms"], "tol": tol, "cycle": "V(2,2) red-black GS",
+              "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world, n, w, config)
+
+    import torch
+
+    from paper_1905_08890_gb300 import gr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    p = synth.zeldovich(n, w["seed"] + 1000 * rank, w["sigma"], w["v_rms"], w["lognormal"])
+    ctx = gr.Context(n)
+    x = torch.from_numpy(p.x).cuda()
+    u = torch.from_numpy(p.u).cuda()
+    src = ctx.new_sources()
+    fld = ctx.initial_fields()
+    opts = dict(tol=tol, max_cycles=60, prec=args.prec, rho_hat=p.rho_hat)
+
+    def step(profile=0):
+        ctx.deposit(x, u, p.mass, src)
+        fld["psi"].fill_(1.0)
+        fld["apsi"].fill_(1.0)
+        for k in ("Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b"):
+            fld[k].zero_()
+        return ctx.solve(src, fld, profile=profile, **opts)
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    reps = [step(profile=1) for _ in range(args.steps)]
+    ev1.record()
+    barrier()
+    clk = clocks.stop()
+    launches = gr.gr_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cell_updates = sum(r["cell_updates"] for r in reps)
+    value = cell_updates * world / (ms * 1e-3) / 1e9
+    solve_ms = 1e3 * sum(sum(r["eq_seconds"]) for r in reps) / len(reps)
+
+    # per-class roofline over the timed region
+    mixed = args.prec == "mixed"
+    hbm, peak_kind = peaks()
+    kernels = {}
+    for cls, d in reps[0]["prof"].items():
+        tot_ms = sum(r["prof"][cls]["ms"] for r in reps)
+        launches_c = sum(r["prof"][cls]["launches"] for r in reps)
+        if launches_c == 0 or cls == "setup":
+            continue
+        byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, mixed) for r in reps)
+        gbs = byt / (tot_ms * 1e-3) / 1e9
+        kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "avg_us": round(1e3 * tot_ms / launches_c, 2),
+                        "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3),
+                        "share_of_step": round(tot_ms / ms, 3)}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if dom and os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        ent = tj.get(dom)
+        if ent and ent.get("n") == n and ent.get("source_hash") == _source_hash():
+            traffic = ent["bytes_per_launch"]
+    roofline = None
+    if dom:
+        avg_bytes = class_bytes(dom, reps[0]["cycles"], n, 2, 2, mixed) / reps[0]["prof"][dom]["launches"]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["algorithmic_GBps"], "peak": hbm,
+                    "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
+                    "algorithmic_bytes_per_launch": round(avg_bytes), "peak_source": f"{peak_kind} hbm_gbs"}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64",
+           "data": "synthetic (seeded Zel'dovich particles)", "config": config,
+           "time_to_residual_ms": round(solve_ms, 3), "path": "mixed" if mixed else "fp64", "learned": None,
+           "cycles": reps[-1]["cycles"], "res": [float(f"{r:.3e}") for r in reps[-1]["res"]],
+           "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels, "clocks": clk}
+
+    if rank == 0 and not args.no_fp64 and mixed:
+        mixed_fields = {k: v.clone() for k, v in fld.items()}
+        o64 = dict(opts, prec="fp64")
+        ctx.deposit(x, u, p.mass, src)
+        fld64 = ctx.initial_fields()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        r64 = ctx.solve(src, fld64, **o64)
+        t1.record()
+        torch.cuda.synchronize()
+        ms64 = t0.elapsed_time(t1)
+        diff = {k: float((mixed_fields[k] - fld64[k]).abs().max() / fld64[k].abs().max().clamp_min(1e-300))
+                for k in fld64}
+        out["fp64"] = {"time_to_residual_ms": round(ms64, 3),
+                       "gcell_updates_per_s": round(r64["cell_updates"] / (ms64 * 1e-3) / 1e9, 3),
+                       "cycles": r64["cycles"], "speedup_mixed_vs_fp64": round(ms64 / solve_ms, 3),
+                       "max_rel_linf_mixed_vs_fp64": max(diff.values())}
+        del fld64, mixed_fields
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 2))
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import numpy as np
+
+        src_np = {k: v.cpu().numpy() for k, v in src.items()}
+        del src, fld
+        val, secs, thr = oracle_sample(n, src_np, p.rho_hat)
+        out["cpu_baseline"] = {"value": round(val, 5), "unit": UNIT, "cores": thr, "kind": "oracle",
+                               "sample": f"one V(2,2) cycle each of the V_x and psi equations at {n}^3 from the "
+                                         f"plain guess ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def e2e_measure(ctx, p, n, opts, world, steps):
+    """The same metric through the public API with host buffers: each step
+    copies the particles from pinned host memory, deposits, solves and reads
+    the ten fields back into pinned host memory."""
+    import torch
+
+    xh = torch.from_numpy(p.x).pin_memory()
+    uh = torch.from_numpy(p.u).pin_memory()
+    host_out = {k: torch.empty((n, n, n), dtype=torch.float64).pin_memory() for k in
+                ("psi", "apsi", "Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b")}
+    xd = torch.empty_like(xh, device="cuda")
+    ud = torch.empty_like(uh, device="cuda")
+    src = ctx.new_sources()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(steps):
+        xd.copy_(xh, non_blocking=True)
+        ud.copy_(uh, non_blocking=True)
+        ctx.deposit(xd, ud, p.mass, src)
+        fld = ctx.initial_fields()
+        r = ctx.solve(src, fld, **opts)
+        updates += r["cell_updates"]
+        for k, v in fld.items():
+            host_out[k].copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
+            "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3)}
+
+
+def _source_hash():
+    import hashlib
+
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1905_08890_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def run_reference(args, rank, world, n, w, config):
+    """The FP64 CPU oracle as it stands, on the host cores: each step is the
+    bounded sample of oracle_sample (one V(2,2) cycle of V_x and psi)."""
+    if rank != 0:
+        return
+    from paper_1905_08890_gb300 import synth
+
+    import oracle
+
+    p = synth.zeldovich(n, w["seed"], w["sigma"], w["v_rms"], w["lognormal"])
+    src_np = oracle.deposit(n, p.x, p.u, p.mass)
+    for _ in range(args.warmup):
+        oracle_sample(n, src_np, p.rho_hat)
+    t_sum, v_sum = 0.0, []
+    for _ in range(args.steps):
+        v, secs, thr = oracle_sample(n, src_np, p.rho_hat)
+        t_sum += secs
+        v_sum.append(v)
+    value = sum(v_sum) / len(v_sum)
+    sample = f"one V(2,2) cycle each of the V_x and psi equations at {n}^3 from the plain guess"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_sum / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Zel'dovich particles)", "config": config,
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": thr, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -100,7 +100,21 @@ typedef struct {
     double rho_hat;   /* fiducial density; <= 0 or NaN selects mass*np/L^3 of the last gr_deposit */
     double S_hat;     /* fiducial trace of the stress (dust: 0); NaN selects 0 */
     int verbose;      /* 0 silent; 1 one line per equation on stderr */
+    int profile;      /* nonzero: time the finest-level kernels with CUDA events (gr_report.prof_*) */
 } gr_opts;
+
+/* Finest-level kernel classes timed when gr_opts.profile is set. */
+typedef enum {
+    GR_PROF_SWEEP64 = 0,   /* FP64 red-black colour pass */
+    GR_PROF_SWEEP32,       /* FP32 red-black colour pass (mixed) */
+    GR_PROF_RESTRICT,      /* residual fused with restriction (FP64 or FP32) */
+    GR_PROF_PROLONG,       /* trilinear prolongation + correction (FP64 or FP32) */
+    GR_PROF_MIXED_RESID,   /* FP64 residual feeding the FP32 correction (mixed) */
+    GR_PROF_MIXED_UPDATE,  /* FP64 += FP32 correction (mixed) */
+    GR_PROF_NORM64,        /* FP64 residual norm (FP64 path) */
+    GR_PROF_SETUP,         /* sources, coefficients and layout changes of the finest level */
+    GR_NPROF
+} gr_prof_class;
 
 typedef struct {
     int cycles[GR_NEQ];           /* V-cycles (mixed: outer iterations) per equation */
@@ -110,10 +124,13 @@ typedef struct {
     double seconds;               /* wall time of the whole call (host clock around the stream) */
     double eq_seconds[GR_NEQ];    /* per equation, CUDA events */
     long long cell_updates;       /* cells relaxed: every sweep on every level, all equations */
+    long long kernel_launches;    /* kernels this call launched */
+    int prof_launches[GR_NPROF];  /* with gr_opts.profile: launches per gr_prof_class */
+    double prof_ms[GR_NPROF];     /* with gr_opts.profile: summed CUDA-event time per class */
 } gr_report;
 
 /* Fill *o with the defaults: tol 1e-10, max_cycles 50, V(2,2), FP64,
-   rho_hat and S_hat from the deposit / dust, verbose 0. */
+   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0. */
 void gr_default_opts(gr_opts *o);
 
 /* Create a context for an n^3 grid of box side L.  n must be a power of two,
@@ -172,6 +189,9 @@ gr_status gr_residual(gr_ctx *ctx, gr_eq eq, const gr_sources *src, const gr_fie
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *gr_last_error(void);
+
+/* Kernels launched by this library in this process so far (all contexts). */
+long long gr_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -310,68 +310,68 @@ void deposit(int n, double L, int64_t np, const double *x, const double *u, doub
     if (np <= 0) return;
     const double h = L / n;
     const double q = mass / (h * h * h);
-    k_deposit<<<grid_for(np), kBlock, 0, st>>>(log2i(n), L, 1.0 / h, np, x, u, q, s0, sx, sy, sz, sig);
+    GR_LAUNCH(k_deposit, grid_for(np), kBlock, st, log2i(n), L, 1.0 / h, np, x, u, q, s0, sx, sy, sz, sig);
 }
 
 int sum_sq(int64_t cnt, const double *a, double *partials, cudaStream_t st)
 {
     int g = grid_for(cnt);
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
-    k_sum_sq<<<g, kBlock, 0, st>>>(cnt, a, partials);
+    GR_LAUNCH(k_sum_sq, g, kBlock, st, cnt, a, partials);
     return g;
 }
 
 void scale_sub_mean(int64_t cnt, double *a, const double *sum, double inv_cnt, double scale, cudaStream_t st)
 {
-    k_scale_sub_mean<<<grid_for(cnt), kBlock, 0, st>>>(cnt, a, sum, inv_cnt, scale);
+    GR_LAUNCH(k_scale_sub_mean, grid_for(cnt), kBlock, st, cnt, a, sum, inv_cnt, scale);
 }
 
 void to_split(int n, const double *nat, double *split, double shift, cudaStream_t st)
 {
-    k_to_split<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), nat, split, shift);
+    GR_LAUNCH(k_to_split, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), nat, split, shift);
 }
 
 void from_split(int n, const double *split, double *nat, double shift, const double *sum, double inv_cnt,
                 cudaStream_t st)
 {
-    k_from_split<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), split, nat, shift, sum, inv_cnt);
+    GR_LAUNCH(k_from_split, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), split, nat, shift, sum, inv_cnt);
 }
 
 void div_to_split(int n, double inv2h, const double *Fx, const double *Fy, const double *Fz, double scale, double *f,
                   cudaStream_t st)
 {
-    k_div_to_split<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), inv2h, Fx, Fy, Fz, scale, f);
+    GR_LAUNCH(k_div_to_split, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), inv2h, Fx, Fy, Fz, scale, f);
 }
 
 void aij_aa(int n, double inv2h, double ih2, const double *Vx, const double *Vy, const double *Vz, const double *U,
             double *A, double *AA, cudaStream_t st)
 {
-    k_aij_aa<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), inv2h, ih2, Vx, Vy, Vz, U, A, AA);
+    GR_LAUNCH(k_aij_aa, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), inv2h, ih2, Vx, Vy, Vz, U, A, AA);
 }
 
 void psi_setup(int n, const double *psi, const double *s0, const double *AA, double *u, double *c0, double *c1,
                double *f, cudaStream_t st)
 {
-    k_psi_setup<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), psi, s0, AA, u, c0, c1, f);
+    GR_LAUNCH(k_psi_setup, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), psi, s0, AA, u, c0, c1, f);
 }
 
 void apsi_setup(int n, double h2, const double *psi, const double *apsi, const double *s0, const double *sig,
                 const double *AA, double K2, double Kdot, double *u, double *c0, double *c1, double *f, double *g,
                 cudaStream_t st)
 {
-    k_apsi_setup<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), h2, psi, apsi, s0, sig, AA, K2, Kdot, u,
+    GR_LAUNCH(k_apsi_setup, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), h2, psi, apsi, s0, sig, AA, K2, Kdot, u,
                                                                    c0, c1, f, g);
 }
 
 void shift_weight(int n, const double *psi, const double *apsi, double *w, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)n * n * n;
-    k_shift_weight<<<grid_for(cnt), kBlock, 0, st>>>(cnt, psi, apsi, w);
+    GR_LAUNCH(k_shift_weight, grid_for(cnt), kBlock, st, cnt, psi, apsi, w);
 }
 
 void shift_source(int n, double inv2h, const double *A, const double *w, int comp, double *f, cudaStream_t st)
 {
-    k_shift_source<<<grid_for((int64_t)n * n * n), kBlock, 0, st>>>(log2i(n), inv2h, A, w, comp, f);
+    GR_LAUNCH(k_shift_source, grid_for((int64_t)n * n * n), kBlock, st, log2i(n), inv2h, A, w, comp, f);
 }
 
 }  // namespace gr

@@ -10,6 +10,7 @@
 // all reductions stay FP64.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -23,6 +24,8 @@
 #include "gr_internal.cuh"
 
 using namespace gr;
+
+std::atomic<long long> gr::g_launches{0};
 
 namespace {
 
@@ -67,6 +70,16 @@ struct gr_ctx {
     bool a_valid = false;  // A6/AA current for the V, U in the fields
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void *> allocs;
+    // finest-level kernel timing (gr_opts.profile)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    int prof_launches[GR_NPROF] = {};
+    double prof_ms[GR_NPROF] = {};
 };
 
 namespace {
@@ -138,6 +151,49 @@ void dsum(gr_ctx *c, int64_t cnt, const double *a)
     gr::finalize(c->partials, g, c->dscal, c->st);
 }
 
+cudaEvent_t pool_event(gr_ctx *c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run f (which queues finest-level kernels) and, when profiling, bracket it
+// with a pair of events attributed to class cls.
+template <class F>
+void timed(gr_ctx *c, int cls, F &&f)
+{
+    if (!c->prof_on) {
+        f();
+        return;
+    }
+    const long long before = gr::g_launches.load(std::memory_order_relaxed);
+    cudaEvent_t a = pool_event(c), b = pool_event(c);
+    cudaEventRecord(a, c->st);
+    f();
+    cudaEventRecord(b, c->st);
+    c->pending.push_back({cls, a, b});
+    c->prof_launches[cls] += (int)(gr::g_launches.load(std::memory_order_relaxed) - before);
+}
+
+// after a stream synchronisation: accumulate the finished event pairs
+void prof_collect(gr_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof_ms[p.cls] += ms;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    cudaGetLastError();
+}
+
 gr_status read_scalars(gr_ctx *c, double *a, double *b)
 {
     cudaMemcpyAsync(c->hscal, c->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st);
@@ -145,6 +201,7 @@ gr_status read_scalars(gr_ctx *c, double *a, double *b)
     if (e != cudaSuccess) return fail(GR_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     gr_status s = cuda_check("kernel");
     if (s != GR_OK) return s;
+    if (c->prof_on) prof_collect(c);
     *a = c->hscal[0];
     if (b) *b = c->hscal[1];
     return GR_OK;
@@ -249,6 +306,16 @@ long long vcycle_cells(const gr_ctx *c, int nu1, int nu2)
     return s + (long long)kCoarsestSweeps * 8;
 }
 
+// classes are attributed on the finest level only (the coarse levels are untimed)
+int fine_cls(const gr_ctx *c, int l, int cls) { return l == c->nlev - 1 ? cls : -1; }
+
+template <class F>
+void timed_at(gr_ctx *c, int cls, F &&f)
+{
+    if (cls < 0) f();
+    else timed(c, cls, f);
+}
+
 void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
 {
     const int fas = kind == KPSI;
@@ -256,8 +323,12 @@ void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
         Level &A = c->lev[l], &C = c->lev[l - 1];
         for (int s = 0; s < nu1; s++)
             for (int col = 0; col < 2; col++)
-                gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
-        gr::resid_restrict<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.ih2, rho, C.u, C.f, C.ur, fas, c->st);
+                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP64), [&] {
+                    gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+                });
+        timed_at(c, fine_cls(c, l, GR_PROF_RESTRICT), [&] {
+            gr::resid_restrict<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.ih2, rho, C.u, C.f, C.ur, fas, c->st);
+        });
         if (fas) gr::fas_rhs(C.n, C.u, C.f, C.c0, C.c1, C.ih2, rho, c->st);
     }
     Level &Z = c->lev[0];
@@ -265,10 +336,12 @@ void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
     for (int l = 1; l < c->nlev; l++) {
         Level &A = c->lev[l], &C = c->lev[l - 1];
         if (fas) gr::fas_diff(C.n, C.u, C.ur, c->st);
-        gr::prolong_add<double>(A.n, A.u, C.u, c->st);
+        timed_at(c, fine_cls(c, l, GR_PROF_PROLONG), [&] { gr::prolong_add<double>(A.n, A.u, C.u, c->st); });
         for (int s = 0; s < nu2; s++)
             for (int col = 0; col < 2; col++)
-                gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP64), [&] {
+                    gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+                });
     }
 }
 
@@ -281,17 +354,23 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
         Level &A = c->lev[l], &C = c->lev[l - 1];
         for (int s = 0; s < nu1; s++)
             for (int col = 0; col < 2; col++)
-                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
-        gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP32), [&] {
+                    gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+                });
+        timed_at(c, fine_cls(c, l, GR_PROF_RESTRICT), [&] {
+            gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+        });
     }
     Level &Z = c->lev[0];
     gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
     for (int l = 1; l < c->nlev; l++) {
         Level &A = c->lev[l], &C = c->lev[l - 1];
-        gr::prolong_add<float>(A.n, A.e, C.e, c->st);
+        timed_at(c, fine_cls(c, l, GR_PROF_PROLONG), [&] { gr::prolong_add<float>(A.n, A.e, C.e, c->st); });
         for (int s = 0; s < nu2; s++)
             for (int col = 0; col < 2; col++)
-                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP32), [&] {
+                    gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+                });
     }
 }
 
@@ -299,7 +378,10 @@ gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, d
 {
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
-    int g = gr::resid_norm<double>(kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, rho, c->partials, eps_nat, c->st);
+    int g = 0;
+    timed(c, GR_PROF_NORM64, [&] {
+        g = gr::resid_norm<double>(kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, rho, c->partials, eps_nat, c->st);
+    });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;
     gr_status st = read_scalars(c, &q, nullptr);
@@ -311,8 +393,11 @@ gr_status mixed_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
 {
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
-    int g = gr::mixed_resid(in.kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, F.h2, rho, F.r, F.m, F.inv, c->partials,
+    int g = 0;
+    timed(c, GR_PROF_MIXED_RESID, [&] {
+        g = gr::mixed_resid(in.kind, F.n, F.u, F.f, F.c0, F.c1, F.ih2, F.h2, rho, F.r, F.m, F.inv, c->partials,
                             c->st);
+    });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;
     gr_status st = read_scalars(c, &q, nullptr);
@@ -327,7 +412,8 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
                    long long *cells)
 {
     EqInfo in;
-    gr_status st = setup_eq(c, eq, s, fl, rho, S_hat, &in);
+    gr_status st = GR_OK;
+    timed(c, GR_PROF_SETUP, [&] { st = setup_eq(c, eq, s, fl, rho, S_hat, &in); });
     if (st != GR_OK) return st;
     Level &F = c->lev[c->nlev - 1];
     const bool mixed = o->prec == GR_PREC_MIXED;
@@ -351,7 +437,7 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         if (mixed) {
             if (in.kind == KPSI) restrict_coefs32(c);
             vcycle32(c, in.kind32, o->nu1, o->nu2);
-            gr::mixed_update(F.n, F.u, F.e, c->st);
+            timed(c, GR_PROF_MIXED_UPDATE, [&] { gr::mixed_update(F.n, F.u, F.e, c->st); });
             st = mixed_norm(c, in, rho, &r);
         } else {
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
@@ -399,9 +485,12 @@ void gr_default_opts(gr_opts *o)
     o->rho_hat = 0.0;
     o->S_hat = 0.0;
     o->verbose = 0;
+    o->profile = 0;
 }
 
 const char *gr_last_error(void) { return g_err.c_str(); }
+
+long long gr_kernel_launches(void) { return gr::g_launches.load(); }
 
 void gr_destroy(gr_ctx *c)
 {
@@ -412,6 +501,11 @@ void gr_destroy(gr_ctx *c)
     if (c->hscal) cudaFreeHost(c->hscal);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (auto &p : c->pending) {
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -495,7 +589,11 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     gr_report R;
     memset(&R, 0, sizeof(R));
     auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = gr::g_launches.load();
     c->a_valid = false;
+    c->prof_on = o->profile != 0;
+    memset(c->prof_launches, 0, sizeof(c->prof_launches));
+    memset(c->prof_ms, 0, sizeof(c->prof_ms));
     gr_status worst = GR_OK;
     std::string first_err;
     for (int eq = 0; eq < GR_NEQ; eq++) {
@@ -519,6 +617,16 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
         if (st != GR_OK && st != GR_ERR_NOCONV) break;
     }
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (c->prof_on) {
+        cudaStreamSynchronize(c->st);
+        prof_collect(c);
+        for (int k = 0; k < GR_NPROF; k++) {
+            R.prof_launches[k] = c->prof_launches[k];
+            R.prof_ms[k] = c->prof_ms[k];
+        }
+        c->prof_on = false;
+    }
+    R.kernel_launches = gr::g_launches.load() - launches0;
     if (rep) *rep = R;
     if (worst != GR_OK) g_err = first_err;
     return worst;

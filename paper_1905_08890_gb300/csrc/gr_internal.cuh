@@ -16,7 +16,17 @@
 
 #include <cstdint>
 
+#include <atomic>
+
 namespace gr {
+
+// kernels launched by this library since load; every launch goes through GR_LAUNCH
+extern std::atomic<long long> g_launches;
+#define GR_LAUNCH(kernel, grid, block, stream, ...)                         \
+    do {                                                                    \
+        kernel<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__);              \
+        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
+    } while (0)
 
 constexpr double kPi = 3.14159265358979323846;
 

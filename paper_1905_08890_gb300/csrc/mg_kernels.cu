@@ -413,11 +413,11 @@ void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, d
     const int lgn = log2i(n);
     const int g = grid_for((int64_t)n * n * n / 2);
     if (kind == KPOISSON)
-        k_sweep<T, KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+        GR_LAUNCH((k_sweep<T, KPOISSON>), g, kBlock, st, lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
     else if (kind == KHELM)
-        k_sweep<T, KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+        GR_LAUNCH((k_sweep<T, KHELM>), g, kBlock, st, lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
     else
-        k_sweep<T, KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
+        GR_LAUNCH((k_sweep<T, KPSI>), g, kBlock, st, lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
 }
 
 template <typename T>
@@ -427,42 +427,42 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
     const int lgf = log2i(nf);
     const int g = grid_for((int64_t)nf * nf * nf / 8);
     if (kind == KPOISSON)
-        k_resid_restrict<T, KPOISSON, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPOISSON, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
     else if (kind == KHELM)
-        k_resid_restrict<T, KHELM, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KHELM, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
     else if (fas)
-        k_resid_restrict<T, KPSI, 1><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPSI, 1>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
     else
-        k_resid_restrict<T, KPSI, 0><<<g, kBlock, 0, st>>>(lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPSI, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
 }
 
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
              cudaStream_t st)
 {
-    k_fas_rhs<<<grid_for((int64_t)nc * nc * nc), kBlock, 0, st>>>(log2i(nc), uc, fc, c0, c1, ih2, rho);
+    GR_LAUNCH(k_fas_rhs, grid_for((int64_t)nc * nc * nc), kBlock, st, log2i(nc), uc, fc, c0, c1, ih2, rho);
 }
 
 void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)nc * nc * nc;
-    k_fas_diff<<<grid_for(cnt), kBlock, 0, st>>>(cnt, uc, urc);
+    GR_LAUNCH(k_fas_diff, grid_for(cnt), kBlock, st, cnt, uc, urc);
 }
 
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
 {
-    k_prolong_add<T><<<grid_for((int64_t)nf * nf * nf), kBlock, 0, st>>>(log2i(nf), u, uc);
+    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf), kBlock, st, log2i(nf), u, uc);
 }
 
 template <typename T>
 void coarsest(int kind, T *u, T *f, const T *c0, const T *c1, double h2, double ih2, double rho, cudaStream_t st)
 {
     if (kind == KPOISSON)
-        k_coarsest<T, KPOISSON><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+        GR_LAUNCH((k_coarsest<T, KPOISSON>), 1, 32, st, u, f, c0, c1, h2, ih2, rho);
     else if (kind == KHELM)
-        k_coarsest<T, KHELM><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+        GR_LAUNCH((k_coarsest<T, KHELM>), 1, 32, st, u, f, c0, c1, h2, ih2, rho);
     else
-        k_coarsest<T, KPSI><<<1, 32, 0, st>>>(u, f, c0, c1, h2, ih2, rho);
+        GR_LAUNCH((k_coarsest<T, KPSI>), 1, 32, st, u, f, c0, c1, h2, ih2, rho);
 }
 
 template <typename T>
@@ -470,16 +470,16 @@ void restrict_coef(int kind, int nf, const T *c0f, const T *c1f, T *c0c, T *c1c,
 {
     const int g = grid_for((int64_t)nf * nf * nf / 8);
     if (kind == KPSI)
-        k_restrict_coef<T, KPSI><<<g, kBlock, 0, st>>>(log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
+        GR_LAUNCH((k_restrict_coef<T, KPSI>), g, kBlock, st, log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
     else
-        k_restrict_coef<T, KHELM><<<g, kBlock, 0, st>>>(log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
+        GR_LAUNCH((k_restrict_coef<T, KHELM>), g, kBlock, st, log2i(nf), c0f, c1f, c0c, c1c, (T)h2c);
 }
 
 template <typename T>
 void helm_invdiag(int n, const T *c0, T *c1, double h2, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)n * n * n;
-    k_helm_invdiag<T><<<grid_for(cnt), kBlock, 0, st>>>(cnt, c0, c1, (T)h2);
+    GR_LAUNCH((k_helm_invdiag<T>), grid_for(cnt), kBlock, st, cnt, c0, c1, (T)h2);
 }
 
 static int red_grid(int64_t cnt)
@@ -495,17 +495,17 @@ int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1
     const int lgn = log2i(n);
     const int g = red_grid((int64_t)n * n * n);
     if (kind == KPOISSON)
-        k_resid_norm<T, KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+        GR_LAUNCH((k_resid_norm<T, KPOISSON>), g, kBlock, st, lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
     else if (kind == KHELM)
-        k_resid_norm<T, KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+        GR_LAUNCH((k_resid_norm<T, KHELM>), g, kBlock, st, lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
     else
-        k_resid_norm<T, KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
+        GR_LAUNCH((k_resid_norm<T, KPSI>), g, kBlock, st, lgn, u, f, c0, c1, (T)ih2, (T)rho, partials, eps_nat);
     return g;
 }
 
 void finalize(const double *partials, int nblk, double *out, cudaStream_t st)
 {
-    k_finalize<<<1, 32, 0, st>>>(partials, nblk, out);
+    GR_LAUNCH(k_finalize, 1, 32, st, partials, nblk, out);
 }
 
 int mixed_resid(int kind, int n, const double *u, const double *f, const double *c0, const double *c1, double ih2,
@@ -514,23 +514,23 @@ int mixed_resid(int kind, int n, const double *u, const double *f, const double 
     const int lgn = log2i(n);
     const int g = red_grid((int64_t)n * n * n);
     if (kind == KPOISSON)
-        k_mixed_resid<KPOISSON><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+        GR_LAUNCH((k_mixed_resid<KPOISSON>), g, kBlock, st, lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
     else if (kind == KHELM)
-        k_mixed_resid<KHELM><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+        GR_LAUNCH((k_mixed_resid<KHELM>), g, kBlock, st, lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
     else
-        k_mixed_resid<KPSI><<<g, kBlock, 0, st>>>(lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
+        GR_LAUNCH((k_mixed_resid<KPSI>), g, kBlock, st, lgn, u, f, c0, c1, ih2, h2, rho, r32, m32, inv32, partials);
     return g;
 }
 
 void mixed_update(int n, double *u, const float *e, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)n * n * n;
-    k_mixed_update<<<grid_for(cnt), kBlock, 0, st>>>(cnt, u, e);
+    GR_LAUNCH(k_mixed_update, grid_for(cnt), kBlock, st, cnt, u, e);
 }
 
 void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st)
 {
-    k_to_float<<<grid_for(cnt), kBlock, 0, st>>>(cnt, a, b);
+    GR_LAUNCH(k_to_float, grid_for(cnt), kBlock, st, cnt, a, b);
 }
 
 #define GR_INST(T)                                                                                                  \

@@ -39,19 +39,23 @@ class gr_fields(ctypes.Structure):
 class gr_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class gr_report(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int * 10), ("res0", ctypes.c_double * 10), ("res", ctypes.c_double * 10),
                 ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
-                ("cell_updates", ctypes.c_longlong)]
+                ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("prof_launches", ctypes.c_int * 8), ("prof_ms", ctypes.c_double * 8)]
+
+
+PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid", "mixed_update", "norm64", "setup")
 
 
 _lib = None
 _lock = threading.Lock()
 EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_solve_constraints", "gr_vcycle",
-            "gr_residual", "gr_last_error")
+            "gr_residual", "gr_last_error", "gr_kernel_launches")
 
 
 def lib():
@@ -80,6 +84,8 @@ def lib():
             L.gr_residual.restype = ctypes.c_int
             L.gr_last_error.argtypes = []
             L.gr_last_error.restype = ctypes.c_char_p
+            L.gr_kernel_launches.argtypes = []
+            L.gr_kernel_launches.restype = ctypes.c_longlong
             _lib = L
     return _lib
 
@@ -128,18 +134,22 @@ def make_fields(fld: dict) -> gr_fields:
     return f
 
 
-def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0) -> gr_opts:
+def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
+              profile=0) -> gr_opts:
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
     o.prec = {"fp64": GR_PREC_FP64, "mixed": GR_PREC_MIXED}[prec] if isinstance(prec, str) else int(prec)
-    o.rho_hat, o.S_hat, o.verbose = rho_hat, S_hat, verbose
+    o.rho_hat, o.S_hat, o.verbose, o.profile = rho_hat, S_hat, verbose, int(profile)
     return o
 
 
 def report_dict(r: gr_report) -> dict:
     return {"cycles": list(r.cycles), "res0": list(r.res0), "res": list(r.res), "status": list(r.eq_status),
-            "seconds": r.seconds, "eq_seconds": list(r.eq_seconds), "cell_updates": int(r.cell_updates)}
+            "seconds": r.seconds, "eq_seconds": list(r.eq_seconds), "cell_updates": int(r.cell_updates),
+            "kernel_launches": int(r.kernel_launches),
+            "prof": {k: {"launches": int(r.prof_launches[i]), "ms": float(r.prof_ms[i])}
+                     for i, k in enumerate(PROF_CLASSES)}}
 
 
 # ------------------------------------------------------------------ C names
@@ -186,6 +196,10 @@ def gr_residual(ctx, eq: int, src: dict, fld: dict, opts: gr_opts, res_field=Non
 
 def gr_last_error() -> str:
     return lib().gr_last_error().decode()
+
+
+def gr_kernel_launches() -> int:
+    return int(lib().gr_kernel_launches())
 
 
 # ------------------------------------------------------------------ convenience
