@@ -193,6 +193,32 @@ const char *gr_last_error(void);
 /* Kernels launched by this library in this process so far (all contexts). */
 long long gr_kernel_launches(void);
 
+/* Allocation-free residual of one momentum-constraint equation,
+   lap V_i = 8 pi (s_i - <s_i>): the same residual and relative norm as
+   gr_residual for GR_VX..GR_VZ, for callers that cannot allocate device
+   memory.  The paper has no counterpart; this entry point exists for
+   callers whose device memory is owned entirely by another allocator (a
+   framework's caching pool or a fixed pre-reserved arena) and for loops that
+   must not pay the device-wide synchronisation of cudaMalloc/cudaFree, so
+   they cannot create a gr_ctx.
+   n: power of two, 4 <= n <= 256 (larger n returns GR_ERR_ARG: the fixed
+   scratch covers at most 256^3 cells).  L > 0: box side.  V, s: device
+   arrays of n^3 doubles, natural layout (V_i and s_i).  res_field (device,
+   n^3 doubles, may be NULL) receives eps = lap_h V - 8 pi (s - <s>);
+   *rel_norm (host, may be NULL) receives RMS(eps) / RMS(8 pi (s - <s>))
+   (reference 1 below 1e-300).  cuda_stream: cudaStream_t (NULL = legacy
+   default stream); the call synchronises it.
+   No device memory is allocated or freed: the scratch is a 256 KB array
+   compiled into the library, present on every device that loads it until
+   the process exits.  The first call on a device looks up that array's
+   device address (cudaGetSymbolAddress), so make a first call on each device
+   before capturing any stream.  All calls share the array: every slot a
+   call reads is written earlier in the same call, so stale contents are
+   harmless, but calls that overlap on the GPU (different streams or host
+   threads at the same time) race on it and must be serialised by the caller. */
+gr_status gr_momentum_residual_noalloc(int n, double L, const double *V, const double *s, double *res_field,
+                                       double *rel_norm, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,12 @@ struct gr_ctx {
 
 namespace {
 
+}  // namespace
+
+void gr::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
+
 gr_status cuda_check(const char *where)
 {
     cudaError_t e = cudaGetLastError();

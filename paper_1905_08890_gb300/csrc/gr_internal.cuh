@@ -28,6 +28,9 @@ extern std::atomic<long long> g_launches;
         ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
     } while (0)
 
+// sets the thread's message returned by gr_last_error()
+void set_last_error(const char *msg);
+
 constexpr double kPi = 3.14159265358979323846;
 
 enum Kind : int { KPOISSON = 0, KHELM = 1, KPSI = 2 };

@@ -55,7 +55,7 @@ PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid"
 _lib = None
 _lock = threading.Lock()
 EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_solve_constraints", "gr_vcycle",
-            "gr_residual", "gr_last_error", "gr_kernel_launches")
+            "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc")
 
 
 def lib():
@@ -86,6 +86,9 @@ def lib():
             L.gr_last_error.restype = ctypes.c_char_p
             L.gr_kernel_launches.argtypes = []
             L.gr_kernel_launches.restype = ctypes.c_longlong
+            L.gr_momentum_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                                                       ctypes.POINTER(ctypes.c_double), _P]
+            L.gr_momentum_residual_noalloc.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -200,6 +203,16 @@ def gr_last_error() -> str:
 
 def gr_kernel_launches() -> int:
     return int(lib().gr_kernel_launches())
+
+
+def gr_momentum_residual_noalloc(n: int, L: float, V, s, res_field=None, stream=None) -> float:
+    """Allocation-free residual of lap V_i = 8 pi (s_i - <s_i>); returns the
+    relative norm (see include/gr.h).  V, s, res_field: float64 CUDA tensors."""
+    r = ctypes.c_double(0)
+    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    _check(lib().gr_momentum_residual_noalloc(n, L, _ptr(V), _ptr(s), _ptr(res_field), ctypes.byref(r), st),
+           "gr_momentum_residual_noalloc")
+    return r.value
 
 
 # ------------------------------------------------------------------ convenience
