@@ -65,6 +65,7 @@ struct gr_ctx {
     cudaStream_t st = nullptr;
     std::vector<Level> lev;  // lev[0] is 2^3, lev[nlev-1] the finest
     double *A6 = nullptr, *AA = nullptr, *tmp = nullptr;
+    float *dfu = nullptr, *dff = nullptr, *dfa = nullptr, *dfb = nullptr;  // finest level hi|lo pairs
     double *partials = nullptr, *dscal = nullptr, *hscal = nullptr;
     double rho_dep = NAN;
     bool a_valid = false;  // A6/AA current for the V, U in the fields
@@ -121,7 +122,7 @@ int log2i(int n)
 bool valid_opts(const gr_opts *o)
 {
     return o && !(o->tol < 0) && o->max_cycles >= 0 && o->nu1 >= 0 && o->nu1 <= 8 && o->nu2 >= 0 && o->nu2 <= 8 &&
-           (o->prec == GR_PREC_FP64 || o->prec == GR_PREC_MIXED);
+           (o->prec == GR_PREC_FP64 || o->prec == GR_PREC_MIXED || o->prec == GR_PREC_MIXED_DF);
 }
 
 bool src_ok(const gr_sources *s)
@@ -395,6 +396,22 @@ gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, d
     return st;
 }
 
+gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
+{
+    Level &F = c->lev[c->nlev - 1];
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    int g = 0;
+    timed(c, GR_PROF_MIXED_RESID, [&] {
+        g = gr::df_resid(in.kind, F.n, c->dfu, c->dfu + N, c->dff, c->dff + N, c->dfa, c->dfa + N, c->dfb,
+                         c->dfb + N, F.ih2, rho, F.h2, in.ref, F.r, F.m, F.inv, c->partials, c->st);
+    });
+    gr::finalize(c->partials, g, c->dscal, c->st);
+    double q;
+    gr_status st = read_scalars(c, &q, nullptr);
+    *r = std::sqrt(q / N);
+    return st;
+}
+
 gr_status mixed_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
 {
     Level &F = c->lev[c->nlev - 1];
@@ -422,19 +439,33 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     timed(c, GR_PROF_SETUP, [&] { st = setup_eq(c, eq, s, fl, rho, S_hat, &in); });
     if (st != GR_OK) return st;
     Level &F = c->lev[c->nlev - 1];
-    const bool mixed = o->prec == GR_PREC_MIXED;
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    const bool dfm = o->prec == GR_PREC_MIXED_DF;
+    const bool mixed = o->prec == GR_PREC_MIXED || dfm;
     const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
     if (mixed) {
         if (in.kind == KHELM) {
-            gr::to_float((int64_t)F.n * F.n * F.n, F.c0, F.m, c->st);
+            gr::to_float(N, F.c0, F.m, c->st);
             gr::helm_invdiag<float>(F.n, F.m, F.inv, F.h2, c->st);
             restrict_coefs32(c);
         }
+        if (dfm)
+            timed(c, GR_PROF_SETUP, [&] {
+                gr::df_split(N, F.u, c->dfu, c->dfu + N, c->st);
+                gr::df_split(N, F.f, c->dff, c->dff + N, c->st);
+                if (in.kind != KPOISSON) gr::df_split(N, F.c0, c->dfa, c->dfa + N, c->st);
+                if (in.kind == KPSI) gr::df_split(N, F.c1, c->dfb, c->dfb + N, c->st);
+            });
     } else {
         restrict_coefs64(c, in.kind);
     }
+    auto fine_norm = [&](double *r) {
+        if (dfm) return df_norm(c, in, rho, r);
+        if (mixed) return mixed_norm(c, in, rho, r);
+        return norm64(c, in.kind, rho, in.ref, nullptr, r);
+    };
     double r = 0;
-    st = mixed ? mixed_norm(c, in, rho, &r) : norm64(c, in.kind, rho, in.ref, nullptr, &r);
+    st = fine_norm(&r);
     if (st != GR_OK) return st;
     if (res0) *res0 = r;
     int cyc = 0;
@@ -443,12 +474,14 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         if (mixed) {
             if (in.kind == KPSI) restrict_coefs32(c);
             vcycle32(c, in.kind32, o->nu1, o->nu2);
-            timed(c, GR_PROF_MIXED_UPDATE, [&] { gr::mixed_update(F.n, F.u, F.e, c->st); });
-            st = mixed_norm(c, in, rho, &r);
+            timed(c, GR_PROF_MIXED_UPDATE, [&] {
+                if (dfm) gr::df_update(F.n, c->dfu, c->dfu + N, F.e, c->st);
+                else gr::mixed_update(F.n, F.u, F.e, c->st);
+            });
         } else {
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
-            st = norm64(c, in.kind, rho, in.ref, nullptr, &r);
         }
+        st = fine_norm(&r);
         cyc++;
         if (cells) *cells += per_cycle;
         if (st == GR_OK && !std::isfinite(r)) st = fail(GR_ERR_NONFINITE, "equation %d: residual not finite", eq);
@@ -456,10 +489,16 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     if (cycles) *cycles = cyc;
     if (res) *res = r;
     // write back: +1 for the deviation unknowns, zero mean for Poisson-type
-    // (the last norm kernel left the sum of u in dscal[1])
-    const int64_t N = (int64_t)F.n * F.n * F.n;
-    gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, in.poisson ? c->dscal + 1 : nullptr, 1.0 / N,
-                   c->st);
+    // (the FP64 norm kernels leave the sum of u in dscal[1])
+    const double *usum = in.poisson ? c->dscal + 1 : nullptr;
+    if (dfm) {
+        gr::df_join(N, c->dfu, c->dfu + N, F.u, c->st);
+        if (in.poisson) {
+            dsum(c, N, F.u);
+            usum = c->dscal;
+        }
+    }
+    gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
     gr_status cs = cuda_check("write back");
     if (cs != GR_OK) return cs;
     if (st == GR_OK && tol >= 0 && r > tol)
@@ -550,6 +589,10 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     }
     const size_t N = (size_t)n * n * n;
     if (st == GR_OK) st = dalloc(c, &c->A6, 6 * N);
+    if (st == GR_OK) st = dalloc(c, &c->dfu, 2 * N);
+    if (st == GR_OK) st = dalloc(c, &c->dff, 2 * N);
+    if (st == GR_OK) st = dalloc(c, &c->dfa, 2 * N);
+    if (st == GR_OK) st = dalloc(c, &c->dfb, 2 * N);
     if (st == GR_OK) st = dalloc(c, &c->AA, N);
     if (st == GR_OK) st = dalloc(c, &c->tmp, N);
     if (st == GR_OK) st = dalloc(c, &c->partials, 2 * kMaxRedBlocks);

@@ -97,6 +97,18 @@ void mixed_update(int n, double *u, const float *e, cudaStream_t st);
 // c32 = (float) c64.
 void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
 
+// ---- double-float fine level (df_kernels.cu) -------------------------------
+// hi/lo = a split into FP32 pairs; a = hi + lo.
+void df_split(int64_t cnt, const double *a, float *hi, float *lo, cudaStream_t st);
+void df_join(int64_t cnt, const float *hi, const float *lo, double *a, cudaStream_t st);
+// Fine residual in double-float: r32 = -eps, KPSI also m32/inv32 (Newton
+// coefficient and FP32 inverse diagonal); a = c0, b = c1 pairs; partials:
+// block sums of (eps/ref)^2.  Returns the block count.
+int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
+             const float *al, const float *bh, const float *bl, double ih2, double rho, double h2, double ref,
+             float *r32, float *m32, float *inv32, double *partials, cudaStream_t st);
+void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st);
+
 // ---- sources, coefficients, layouts (field_kernels.cu) ---------------------
 void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
              double *sy, double *sz, double *sig, cudaStream_t st);

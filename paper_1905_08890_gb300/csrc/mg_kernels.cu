@@ -118,7 +118,67 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
+// FP32 colour pass, four consecutive half-indices per thread (float4): the
+// rows (i +- 1, j), (i, j +- 1) and the own row of the other colour are read
+// as float4; the shifted own-row neighbour q + (p ? 1 : -1) takes one extra
+// scalar load.  Needs n >= 8 (rows of at least four half-indices).
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ u, const float *__restrict__ f,
+                                                   const float *__restrict__ c1, float h2, int color)
+{
+    const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
+    const int64_t half = (int64_t)1 << (3 * lgn - 1);
+    const int64_t off = color ? half : 0;
+    float *__restrict__ own = u + off;
+    const float *__restrict__ oth = u + (half - off);
+    const int64_t nvec = half >> 2;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvec; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = v << 2;
+        const int q = (int)(t & mh);
+        const int j = (int)((t >> lgh) & mn);
+        const int i = (int)(t >> (lgh + lgn));
+        const int p = (i + j + color) & 1;
+        const int64_t r0 = t - q;
+        const int64_t ri = (int64_t)j << lgh;
+        const int64_t rip = ((int64_t)((i + 1) & mn) << (lgn + lgh)) + ri;
+        const int64_t rim = ((int64_t)((i - 1) & mn) << (lgn + lgh)) + ri;
+        const int64_t rj = (int64_t)i << (lgn + lgh);
+        const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh);
+        const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh);
+        const float4 A = *reinterpret_cast<const float4 *>(oth + rip + q);
+        const float4 B = *reinterpret_cast<const float4 *>(oth + rim + q);
+        const float4 C = *reinterpret_cast<const float4 *>(oth + rjp + q);
+        const float4 D = *reinterpret_cast<const float4 *>(oth + rjm + q);
+        const float4 E = *reinterpret_cast<const float4 *>(oth + r0 + q);
+        const float4 F = *reinterpret_cast<const float4 *>(f + off + t);
+        const float x = oth[r0 + ((q + (p ? 4 : -1)) & mh)];
+        const float4 Sh = p ? make_float4(E.y, E.z, E.w, x) : make_float4(x, E.x, E.y, E.z);
+        float4 nb;
+        nb.x = A.x + B.x + C.x + D.x + E.x + Sh.x;
+        nb.y = A.y + B.y + C.y + D.y + E.y + Sh.y;
+        nb.z = A.z + B.z + C.z + D.z + E.z + Sh.z;
+        nb.w = A.w + B.w + C.w + D.w + E.w + Sh.w;
+        float4 out;
+        if (KIND == KPOISSON) {
+            const float s6 = 1.0f / 6.0f;
+            out = make_float4((nb.x - h2 * F.x) * s6, (nb.y - h2 * F.y) * s6, (nb.z - h2 * F.z) * s6,
+                              (nb.w - h2 * F.w) * s6);
+        } else {
+            const float4 G = *reinterpret_cast<const float4 *>(c1 + off + t);
+            out = make_float4((nb.x - h2 * F.x) * G.x, (nb.y - h2 * F.y) * G.y, (nb.z - h2 * F.z) * G.z,
+                              (nb.w - h2 * F.w) * G.w);
+        }
+        *reinterpret_cast<float4 *>(own + t) = out;
+    }
+}
+
 // ---------------------------------------------------------------- residual + restriction
+// One thread per coarse cell (I, J, K).  Its 8 children sit at half-index K
+// of the fine rows (2I + a, 2J + b), a, b in {0, 1}; their residuals need the
+// 32 values of those rows at k = 2K - 1 .. 2K + 2 and of the 8 side rows at
+// k = 2K, 2K + 1, which are loaded once into registers.  In a fine row (i, j)
+// the value at k = 2K + c has colour (i + j + c) & 1 and half-index K - 1,
+// K, K or K + 1 for c = -1, 0, 1, 2.
 template <typename T, int KIND, int FAS>
 __global__ void __launch_bounds__(kBlock)
     k_resid_restrict(int lgf, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
@@ -126,23 +186,47 @@ __global__ void __launch_bounds__(kBlock)
                      T *__restrict__ urc)
 {
     const int lgc = lgf - 1;
-    const int mc = (1 << lgc) - 1;
+    const int mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
+    const int64_t half = (int64_t)1 << (3 * lgf - 1);
     const int64_t ncells = (int64_t)1 << (3 * lgc);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+        T v[4][4][4];  // v[a + 1][b + 1][c + 1]
+#pragma unroll
+        for (int a = -1; a <= 2; a++)
+#pragma unroll
+            for (int b = -1; b <= 2; b++) {
+                if ((a == -1 || a == 2) && (b == -1 || b == 2)) continue;
+                const int i = (2 * I + a) & mf, j = (2 * J + b) & mf;
+                const int64_t row = (((int64_t)i << lgf) + j) << lgc;
+                const bool central = a >= 0 && a <= 1 && b >= 0 && b <= 1;
+#pragma unroll
+                for (int c = -1; c <= 2; c++) {
+                    if (!central && (c == -1 || c == 2)) continue;
+                    const int q = (K + (c < 0 ? -1 : (c > 1 ? 1 : 0))) & mc;
+                    v[a + 1][b + 1][c + 1] = u[(int64_t)((i + j + c) & 1) * half + row + q];
+                }
+            }
         T s = T(0), su = T(0);
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < 2; b++) {
+                const int64_t row = (((int64_t)(2 * I + a) << lgf) + 2 * J + b) << lgc;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
-                    s += resid_cell<T, KIND>(u, f, c0, c1, lgf, i, j, k, ih2, rho);
-                    if (FAS) su += u[sidx(lgf, i, j, k)];
+                    const int64_t id = (int64_t)((a + b + c) & 1) * half + row + K;
+                    const T uc0 = v[a + 1][b + 1][c + 1];
+                    const T nb = v[a + 2][b + 1][c + 1] + v[a][b + 1][c + 1] + v[a + 1][b + 2][c + 1] +
+                                 v[a + 1][b][c + 1] + v[a + 1][b + 1][c + 2] + v[a + 1][b + 1][c];
+                    const T a0 = (KIND == KPOISSON) ? T(0) : c0[id];
+                    const T a1 = (KIND == KPSI) ? c1[id] : T(0);
+                    s += op_cell<T, KIND>(uc0, nb, ih2, a0, a1, rho) - f[id];
+                    if (FAS) su += uc0;
                 }
-        const int64_t cid = lgc > 0 ? sidx(lgc, I, J, K) : 0;
+            }
+        const int64_t cid = sidx(lgc, I, J, K);
         if (FAS) {
             fc[cid] = T(0.125) * s;
             uc[cid] = T(0.125) * su;
@@ -174,34 +258,49 @@ __global__ void k_fas_diff(int64_t cnt, double *__restrict__ uc, const double *_
 }
 
 // ---------------------------------------------------------------- prolongation
+// One thread per coarse cell: the 27 coarse values around (I, J, K) give its
+// 8 children by separable trilinear interpolation (3/4 from the parent, 1/4
+// from the neighbour on the child's side, per axis).  The children of
+// (I, J, K) are at half-index K of the fine rows (2I + a, 2J + b), colour
+// (a + b + c) & 1, so consecutive threads write consecutive addresses.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
 {
     const int lgc = lgf - 1, mc = (1 << lgc) - 1;
-    const int64_t ncells = (int64_t)1 << (3 * lgf);
+    const int64_t half = (int64_t)1 << (3 * lgf - 1);
+    const int64_t ncells = (int64_t)1 << (3 * lgc);
+    const T w0 = T(0.25), w1 = T(0.75);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int i, j, k;
-        scoord(lgf, t, i, j, k);
-        int Ia[2], Jb[2], Kc[2];
-        Ia[0] = i >> 1;
-        Ia[1] = (i & 1) ? ((Ia[0] + 1) & mc) : ((Ia[0] - 1) & mc);
-        Jb[0] = j >> 1;
-        Jb[1] = (j & 1) ? ((Jb[0] + 1) & mc) : ((Jb[0] - 1) & mc);
-        Kc[0] = k >> 1;
-        Kc[1] = (k & 1) ? ((Kc[0] + 1) & mc) : ((Kc[0] - 1) & mc);
-        const T w[2] = {T(0.75), T(0.25)};
-        T s = T(0);
+        const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+        T z[3][3][2];  // interpolated along k: children c = 0, 1
+#pragma unroll
+        for (int x = 0; x < 3; x++)
+#pragma unroll
+            for (int y = 0; y < 3; y++) {
+                const int Ii = (I + x - 1) & mc, Jj = (J + y - 1) & mc;
+                const T cm = uc[sidx(lgc, Ii, Jj, (K - 1) & mc)];
+                const T c0 = uc[sidx(lgc, Ii, Jj, K)];
+                const T cp = uc[sidx(lgc, Ii, Jj, (K + 1) & mc)];
+                z[x][y][0] = w0 * cm + w1 * c0;
+                z[x][y][1] = w1 * c0 + w0 * cp;
+            }
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < 2; b++) {
+                const int64_t row = (((int64_t)(2 * I + a) << lgf) + 2 * J + b) << lgc;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const int64_t cid = lgc > 0 ? sidx(lgc, Ia[a], Jb[b], Kc[c]) : 0;
-                    s += w[a] * w[b] * w[c] * uc[cid];
+                    // along j, then along i
+                    T yv[3];
+#pragma unroll
+                    for (int x = 0; x < 3; x++)
+                        yv[x] = b ? (w1 * z[x][1][c] + w0 * z[x][2][c]) : (w0 * z[x][0][c] + w1 * z[x][1][c]);
+                    const T val = a ? (w1 * yv[1] + w0 * yv[2]) : (w0 * yv[0] + w1 * yv[1]);
+                    u[(int64_t)((a + b + c) & 1) * half + row + K] += val;
                 }
-        u[t] += s;
+            }
     }
 }
 
@@ -411,6 +510,16 @@ void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, d
                   int color, cudaStream_t st)
 {
     const int lgn = log2i(n);
+    if (sizeof(T) == 4 && n >= 8 && kind != KPSI) {
+        float *uf = (float *)u;
+        const float *ff = (const float *)f, *cf = (const float *)c1;
+        const int gv = grid_for((int64_t)n * n * n / 8);
+        if (kind == KPOISSON)
+            GR_LAUNCH(k_sweep4<KPOISSON>, gv, kBlock, st, lgn, uf, ff, cf, (float)h2, color);
+        else
+            GR_LAUNCH(k_sweep4<KHELM>, gv, kBlock, st, lgn, uf, ff, cf, (float)h2, color);
+        return;
+    }
     const int g = grid_for((int64_t)n * n * n / 2);
     if (kind == KPOISSON)
         GR_LAUNCH((k_sweep<T, KPOISSON>), g, kBlock, st, lgn, u, f, c0, c1, (T)h2, (T)ih2, (T)rho, color);
@@ -451,7 +560,7 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
 {
-    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf), kBlock, st, log2i(nf), u, uc);
+    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf / 8), kBlock, st, log2i(nf), u, uc);
 }
 
 template <typename T>

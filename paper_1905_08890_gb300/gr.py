@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOMEM", "ERR_NOCONV", "ERR_NON
 EQUATIONS = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
 GR_VX, GR_VY, GR_VZ, GR_U, GR_PSI, GR_APSI, GR_BX, GR_BY, GR_BZ, GR_B_SCALAR = range(10)
 GR_NEQ = 10
-GR_PREC_FP64, GR_PREC_MIXED = 0, 1
+GR_PREC_FP64, GR_PREC_MIXED, GR_PREC_MIXED_DF = 0, 1, 2
 FIELDS = ("psi", "apsi", "Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b")
 SOURCES = ("s0", "sx", "sy", "sz", "sigma")
 
@@ -142,7 +142,8 @@ def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, 
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
-    o.prec = {"fp64": GR_PREC_FP64, "mixed": GR_PREC_MIXED}[prec] if isinstance(prec, str) else int(prec)
+    o.prec = ({"fp64": GR_PREC_FP64, "mixed": GR_PREC_MIXED, "mixed_df": GR_PREC_MIXED_DF}[prec]
+              if isinstance(prec, str) else int(prec))
     o.rho_hat, o.S_hat, o.verbose, o.profile = rho_hat, S_hat, verbose, int(profile)
     return o
 

@@ -180,17 +180,19 @@ def test_full_solve_converged_config2_size():
         assert rel_linf(gfld[k], ofld[k]) <= 1e-11, (k, rel_linf(gfld[k], ofld[k]))
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
 @pytest.mark.parametrize("n", [32, 64])
-def test_mixed_precision_within_1e8_of_oracle(n):
-    """FP32 correction cycles inside the FP64 defect-correction loop, residual
-    1e-9: every field within 1e-8 relative of the converged FP64 oracle."""
+def test_mixed_precision_within_1e8_of_oracle(n, prec):
+    """FP32 correction cycles inside the defect-correction loop (fine residual
+    in FP64, or in double-float), residual 1e-9: every field within 1e-8
+    relative of the converged FP64 oracle."""
     p, src = _problem(n, seed=3, sigma=1.0, v_rms=0.003, lognormal=True)
     ofld = oracle.initial_fields(n)
     ost, _ = oracle.solve_constraints(src, ofld, p.rho_hat, tol=1e-12, max_cycles=60)
     assert ost == 0
     ctx = gr.Context(n)
     gf = _fields_to_gpu(oracle.initial_fields(n))
-    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec="mixed", rho_hat=p.rho_hat)
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec=prec, rho_hat=p.rho_hat)
     assert rep["status_code"] == gr.GR_OK
     assert all(r <= 1e-9 for r in rep["res"])
     for k in oracle.FIELDS:
@@ -208,7 +210,7 @@ def test_homogeneous_background_from_random_guesses():
     fld = oracle.initial_fields(n)
     fld["psi"][:] = 1 + 0.2 * rng.random((n, n, n))
     fld["apsi"][:] = 1 + 0.2 * rng.random((n, n, n))
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_df"):
         ctx = gr.Context(n)
         gf = _fields_to_gpu(fld)
         rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-12, max_cycles=60, rho_hat=RHO, prec=prec)
@@ -252,4 +254,33 @@ def test_missing_background_density_is_an_argument_error():
     with pytest.raises(gr.GRError) as ei:
         ctx.solve(src, ctx.initial_fields())
     assert ei.value.status == gr.GR_ERR_ARG
+    ctx.close()
+
+
+def test_mixed_df_config3_style_within_1e8():
+    """128^3 lognormal rms 3 (the strongly clustered mixed-precision case at a
+    size the oracle solves quickly): the double-float mixed solve to 1e-8
+    against the FP64 oracle at 1e-12, per field."""
+    p, src = _problem(128, seed=3, sigma=3.0, v_rms=0.003, lognormal=True)
+    ofld = oracle.initial_fields(128)
+    ost, _ = oracle.solve_constraints(src, ofld, p.rho_hat, tol=1e-12, max_cycles=60)
+    assert ost == 0
+    ctx = gr.Context(128)
+    gf = _fields_to_gpu(oracle.initial_fields(128))
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-8, max_cycles=60, prec="mixed_df", rho_hat=p.rho_hat)
+    assert rep["status_code"] == gr.GR_OK
+    for k in oracle.FIELDS:
+        assert rel_linf(_np(gf[k]), ofld[k]) <= 1e-8, (k, rel_linf(_np(gf[k]), ofld[k]))
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
+def test_mixed_tight_tolerance_reaches_1e11(prec):
+    """The defect correction keeps converging below FP32 precision: residual
+    1e-11 at 64^3 in both mixed modes."""
+    p, src = _problem(64, seed=5, sigma=1.0, v_rms=0.003, lognormal=True)
+    ctx = gr.Context(64)
+    gf = _fields_to_gpu(oracle.initial_fields(64))
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-11, max_cycles=60, prec=prec, rho_hat=p.rho_hat)
+    assert rep["status_code"] == gr.GR_OK and max(rep["res"]) <= 1e-11
     ctx.close()
