@@ -194,8 +194,17 @@ def main():
     fld = ctx.initial_fields()
     opts = dict(tol=tol, max_cycles=60, prec=args.prec, rho_hat=p.rho_hat)
 
+    dep_ev = []
+
     def step(profile=0):
-        ctx.deposit(x, u, p.mass, src)
+        if profile:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.deposit(x, u, p.mass, src)
+            e1.record()
+            dep_ev.append((e0, e1))
+        else:
+            ctx.deposit(x, u, p.mass, src)
         fld["psi"].fill_(1.0)
         fld["apsi"].fill_(1.0)
         for k in ("Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b"):
@@ -239,14 +248,23 @@ def main():
     for cls, d in reps[0]["prof"].items():
         tot_ms = sum(r["prof"][cls]["ms"] for r in reps)
         launches_c = sum(r["prof"][cls]["launches"] for r in reps)
-        if launches_c == 0 or cls == "setup":
+        if launches_c == 0:
+            continue
+        if cls in ("setup", "coarse"):
+            kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "share_of_step": round(tot_ms / ms, 3)}
             continue
         byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, mixed) for r in reps)
         gbs = byt / (tot_ms * 1e-3) / 1e9
         kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "avg_us": round(1e3 * tot_ms / launches_c, 2),
                         "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3),
                         "share_of_step": round(tot_ms / ms, 3)}
-    dom = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
+    dep_ms = sum(a.elapsed_time(b) for a, b in dep_ev)
+    kernels["deposit"] = {"launches": len(dep_ev), "ms": round(dep_ms, 3),
+                          "avg_us": round(1e3 * dep_ms / max(len(dep_ev), 1), 2),
+                          "algorithmic_GBps": round((48 + 40) * n ** 3 * len(dep_ev) / (dep_ms * 1e-3) / 1e9, 1),
+                          "frac_hbm": round((48 + 40) * n ** 3 * len(dep_ev) / (dep_ms * 1e-3) / 1e9 / hbm, 3),
+                          "share_of_step": round(dep_ms / ms, 3)}
+    dom = max((k for k in kernels if k not in ("coarse", "deposit")), key=lambda k: kernels[k]["ms"]) if kernels else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if dom and os.path.exists(tpath):

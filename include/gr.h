@@ -115,6 +115,7 @@ typedef enum {
     GR_PROF_MIXED_UPDATE,  /* FP64 += FP32 correction (mixed) */
     GR_PROF_NORM64,        /* FP64 residual norm (FP64 path) */
     GR_PROF_SETUP,         /* sources, coefficients and layout changes of the finest level */
+    GR_PROF_COARSE,        /* every multigrid kernel below the finest level */
     GR_NPROF
 } gr_prof_class;
 

@@ -90,12 +90,21 @@ __global__ void __launch_bounds__(kBlock)
         const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh);
         const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh);
         const int qs = (q + (p ? 1 : -1)) & mh;
-        auto ld = [&](int64_t k) { return df{uh[k], ul[k]}; };
-        df nb = df_add_acc(ld(rip + q), ld(rim + q));
-        nb = df_add_acc(nb, df_add_acc(ld(rjp + q), ld(rjm + q)));
-        nb = df_add_acc(nb, df_add_acc(ld(r0 + q), ld(r0 + qs)));
-        const df u = ld(t);
-        df e = df_mul(df_add_acc(nb, df_mulf(u, -6.0f)), ih2);
+        // sum of the six neighbours minus 6 u by compensated summation
+        // (Ogita, Rump and Oishi 2005, Sum2): the high parts go through a
+        // two-sum chain, the chain's errors and all low parts are added in
+        // FP32, which is exact enough since they are 2^-24 smaller
+        const int64_t nbi[6] = {rip + q, rim + q, rjp + q, rjm + q, r0 + q, r0 + qs};
+        const df u = {uh[t], ul[t]};
+        const df p6 = two_prod(u.hi, -6.0f);
+        float s = p6.hi, sig = __fmaf_rn(u.lo, -6.0f, p6.lo);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const df a = two_sum(s, uh[nbi[k]]);
+            s = a.hi;
+            sig = __fadd_rn(sig, __fadd_rn(a.lo, ul[nbi[k]]));
+        }
+        df e = df_mul(fast_two_sum(s, sig), ih2);
         if (KIND == KHELM) {
             e = df_sub(e, df_mul(df{ah[t], al[t]}, u));
         } else if (KIND == KPSI) {

@@ -313,72 +313,80 @@ long long vcycle_cells(const gr_ctx *c, int nu1, int nu2)
     return s + (long long)kCoarsestSweeps * 8;
 }
 
-// classes are attributed on the finest level only (the coarse levels are untimed)
-int fine_cls(const gr_ctx *c, int l, int cls) { return l == c->nlev - 1 ? cls : -1; }
-
-template <class F>
-void timed_at(gr_ctx *c, int cls, F &&f)
-{
-    if (cls < 0) f();
-    else timed(c, cls, f);
-}
-
+// Relaxation and transfers of one V-cycle.  With profiling, the finest
+// level's launches are timed per class and everything below it (which runs
+// as one contiguous stretch between the finest restriction and
+// prolongation) as GR_PROF_COARSE.
 void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
 {
     const int fas = kind == KPSI;
-    for (int l = c->nlev - 1; l >= 1; l--) {
-        Level &A = c->lev[l], &C = c->lev[l - 1];
-        for (int s = 0; s < nu1; s++)
+    const int top = c->nlev - 1;
+    auto smooth = [&](Level &A, int nu) {
+        for (int s = 0; s < nu; s++)
             for (int col = 0; col < 2; col++)
-                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP64), [&] {
-                    gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
-                });
-        timed_at(c, fine_cls(c, l, GR_PROF_RESTRICT), [&] {
-            gr::resid_restrict<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.ih2, rho, C.u, C.f, C.ur, fas, c->st);
-        });
+                gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
+    };
+    auto down = [&](int l) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        gr::resid_restrict<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.ih2, rho, C.u, C.f, C.ur, fas, c->st);
         if (fas) gr::fas_rhs(C.n, C.u, C.f, C.c0, C.c1, C.ih2, rho, c->st);
-    }
-    Level &Z = c->lev[0];
-    gr::coarsest<double>(kind, Z.u, Z.f, Z.c0, Z.c1, Z.h2, Z.ih2, rho, c->st);
-    for (int l = 1; l < c->nlev; l++) {
+    };
+    auto up = [&](int l) {
         Level &A = c->lev[l], &C = c->lev[l - 1];
         if (fas) gr::fas_diff(C.n, C.u, C.ur, c->st);
-        timed_at(c, fine_cls(c, l, GR_PROF_PROLONG), [&] { gr::prolong_add<double>(A.n, A.u, C.u, c->st); });
-        for (int s = 0; s < nu2; s++)
-            for (int col = 0; col < 2; col++)
-                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP64), [&] {
-                    gr::sweep_colour<double>(kind, A.n, A.u, A.f, A.c0, A.c1, A.h2, A.ih2, rho, col, c->st);
-                });
-    }
+        gr::prolong_add<double>(A.n, A.u, C.u, c->st);
+    };
+    Level &F = c->lev[top];
+    timed(c, GR_PROF_SWEEP64, [&] { smooth(F, nu1); });
+    timed(c, GR_PROF_RESTRICT, [&] { down(top); });
+    timed(c, GR_PROF_COARSE, [&] {
+        for (int l = top - 1; l >= 1; l--) {
+            smooth(c->lev[l], nu1);
+            down(l);
+        }
+        Level &Z = c->lev[0];
+        gr::coarsest<double>(kind, Z.u, Z.f, Z.c0, Z.c1, Z.h2, Z.ih2, rho, c->st);
+        for (int l = 1; l < top; l++) {
+            up(l);
+            smooth(c->lev[l], nu2);
+        }
+    });
+    timed(c, GR_PROF_PROLONG, [&] { up(top); });
+    timed(c, GR_PROF_SWEEP64, [&] { smooth(F, nu2); });
 }
 
 // one FP32 correction V-cycle on lev[*].e with fine right-hand side lev[fine].r
 void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
 {
-    Level &F = c->lev[c->nlev - 1];
+    const int top = c->nlev - 1;
+    Level &F = c->lev[top];
+    auto smooth = [&](Level &A, int nu) {
+        for (int s = 0; s < nu; s++)
+            for (int col = 0; col < 2; col++)
+                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+    };
+    auto down = [&](int l) {
+        Level &A = c->lev[l], &C = c->lev[l - 1];
+        gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+    };
+    auto up = [&](int l) { gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st); };
     cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
-    for (int l = c->nlev - 1; l >= 1; l--) {
-        Level &A = c->lev[l], &C = c->lev[l - 1];
-        for (int s = 0; s < nu1; s++)
-            for (int col = 0; col < 2; col++)
-                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP32), [&] {
-                    gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
-                });
-        timed_at(c, fine_cls(c, l, GR_PROF_RESTRICT), [&] {
-            gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
-        });
-    }
-    Level &Z = c->lev[0];
-    gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
-    for (int l = 1; l < c->nlev; l++) {
-        Level &A = c->lev[l], &C = c->lev[l - 1];
-        timed_at(c, fine_cls(c, l, GR_PROF_PROLONG), [&] { gr::prolong_add<float>(A.n, A.e, C.e, c->st); });
-        for (int s = 0; s < nu2; s++)
-            for (int col = 0; col < 2; col++)
-                timed_at(c, fine_cls(c, l, GR_PROF_SWEEP32), [&] {
-                    gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
-                });
-    }
+    timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu1); });
+    timed(c, GR_PROF_RESTRICT, [&] { down(top); });
+    timed(c, GR_PROF_COARSE, [&] {
+        for (int l = top - 1; l >= 1; l--) {
+            smooth(c->lev[l], nu1);
+            down(l);
+        }
+        Level &Z = c->lev[0];
+        gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
+        for (int l = 1; l < top; l++) {
+            up(l);
+            smooth(c->lev[l], nu2);
+        }
+    });
+    timed(c, GR_PROF_PROLONG, [&] { up(top); });
+    timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu2); });
 }
 
 gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, double *r)
