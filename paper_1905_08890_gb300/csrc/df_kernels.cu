@@ -28,13 +28,37 @@ inline int log2i(int n)
     return l;
 }
 
+// Split a double into hi + lo FP32 with integer operations only (GB300's
+// FP64 and conversion pipes are slow): hi keeps the sign, the exponent and the
+// top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32
+// (rounded to 24 bits, so hi + lo carries at least 48 significant bits) and
+// scaled by 2^(e - 52).  The pair is renormalised by fast-two-sum.  Values
+// whose exponent leaves FP32's normal range for lo (|x| < 2^-74) or hi
+// (|x| >= 2^128) take the FP64 conversion instead.
+__device__ __forceinline__ df split_double(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+    if (ex < -74 || ex > 127) {
+        const float h = (float)x;
+        return {h, (float)(x - (double)h)};
+    }
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned hib = sign | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+    const unsigned rem = (unsigned)(b & 0x1fffffffu);
+    const float scale = __int_as_float((ex - 52 + 127) << 23);  // 2^(ex - 52), normal since ex >= -74
+    const float mag = (float)rem * scale;
+    const float lo = sign ? -mag : mag;
+    return fast_two_sum(__uint_as_float(hib), lo);
+}
+
 __global__ void k_df_split(int64_t cnt, const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const double x = a[t];
-        const float h = (float)x;
-        hi[t] = h;
-        lo[t] = (float)(x - (double)h);
+        const df d = x == 0.0 ? df{0.0f, 0.0f} : split_double(x);
+        hi[t] = d.hi;
+        lo[t] = d.lo;
     }
 }
 
@@ -59,8 +83,46 @@ __device__ __forceinline__ void block_sum1(double a, double *out)
     }
 }
 
-// eps = L(u) - f on every cell of the finest level; writes r32 = -eps and,
-// for the psi kind, the Newton coefficient m32 = -dN/du and 1/(6 + h^2 m32).
+// L(u) - f at one cell from the compensated neighbour sum (Sum2 of Ogita,
+// Rump and Oishi 2005: the high parts through a two-sum chain, the chain's
+// errors and all low parts added in FP32, which suffices since they are
+// 2^-24 smaller).  nh/nl: the six neighbours' high and low parts.
+template <int KIND>
+__device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df f, df a, df b, df ih2, df two_pi,
+                                      df two_pi_rho, float rho10pi, float h2, float *mj_out, float *inv_out)
+{
+    const df p6 = two_prod(u.hi, -6.0f);
+    float s = p6.hi, sig = __fmaf_rn(u.lo, -6.0f, p6.lo);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const df q = two_sum(s, nh[k]);
+        s = q.hi;
+        sig = __fadd_rn(sig, __fadd_rn(q.lo, nl[k]));
+    }
+    df e = df_mul(fast_two_sum(s, sig), ih2);
+    if (KIND == KHELM) {
+        e = df_sub(e, df_mul(a, u));
+    } else if (KIND == KPSI) {
+        const df v = df_add({1.0f, 0.0f}, u);
+        const df iv = df_recip(v);
+        const df iv2 = df_mul(iv, iv), iv4 = df_mul(iv2, iv2);
+        const df v2 = df_mul(v, v), v4 = df_mul(v2, v2);
+        e = df_add(e, df_mul(df_mul(a, iv), two_pi));
+        e = df_add(e, df_mulf(df_mul(b, df_mul(df_mul(iv4, iv2), iv)), 0.125f));
+        e = df_sub(e, df_mul(df_mul(v4, v), two_pi_rho));
+        const float mj = two_pi.hi * a.hi * iv2.hi + 0.875f * b.hi * (iv4.hi * iv4.hi) + rho10pi * v4.hi;
+        *mj_out = mj;
+        *inv_out = 1.0f / (6.0f + h2 * mj);
+    }
+    return df_sub(e, f);
+}
+
+// eps = L(u) - f on the finest level; writes r32 = -eps and, for the psi
+// kind, the Newton coefficient m32 = -dN/du with its FP32 inverse diagonal.
+// One thread per row position (i, j, q) handles the red and the black cell
+// there: each needs the other colour at the same q in rows (i +- 1, j),
+// (i, j +- 1) and at q, q +- 1 in its own row, so every array element is
+// read once as a cell and, close in time, as its neighbours' neighbour.
 // Block partials: sum of (eps / ref)^2.
 template <int KIND>
 __global__ void __launch_bounds__(kBlock)
@@ -72,58 +134,48 @@ __global__ void __launch_bounds__(kBlock)
 {
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int64_t half = (int64_t)1 << (3 * lgn - 1);
-    const int64_t cnt = 2 * half;
     float acc = 0.0f;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
-        const int color = (int)(t >> (3 * lgn - 1));
-        const int64_t tt = t - (color ? half : 0);
-        const int64_t o = color ? 0 : half;  // start of the other colour
-        const int q = (int)(tt & mh);
-        const int j = (int)((tt >> lgh) & mn);
-        const int i = (int)(tt >> (lgh + lgn));
-        const int p = (i + j + color) & 1;
-        const int64_t r0 = o + tt - q;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < half; t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t & mh);
+        const int j = (int)((t >> lgh) & mn);
+        const int i = (int)(t >> (lgh + lgn));
+        const int64_t r0 = t - q;
         const int64_t ri = (int64_t)j << lgh;
-        const int64_t rip = o + ((int64_t)((i + 1) & mn) << (lgn + lgh)) + ri;
-        const int64_t rim = o + ((int64_t)((i - 1) & mn) << (lgn + lgh)) + ri;
-        const int64_t rj = o + ((int64_t)i << (lgn + lgh));
-        const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh);
-        const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh);
-        const int qs = (q + (p ? 1 : -1)) & mh;
-        // sum of the six neighbours minus 6 u by compensated summation
-        // (Ogita, Rump and Oishi 2005, Sum2): the high parts go through a
-        // two-sum chain, the chain's errors and all low parts are added in
-        // FP32, which is exact enough since they are 2^-24 smaller
-        const int64_t nbi[6] = {rip + q, rim + q, rjp + q, rjm + q, r0 + q, r0 + qs};
-        const df u = {uh[t], ul[t]};
-        const df p6 = two_prod(u.hi, -6.0f);
-        float s = p6.hi, sig = __fmaf_rn(u.lo, -6.0f, p6.lo);
+        const int64_t rip = ((int64_t)((i + 1) & mn) << (lgn + lgh)) + ri + q;
+        const int64_t rim = ((int64_t)((i - 1) & mn) << (lgn + lgh)) + ri + q;
+        const int64_t rj = (int64_t)i << (lgn + lgh);
+        const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh) + q;
+        const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh) + q;
+        const int pr = (i + j) & 1;                           // k parity of the red cell in this row
+        const int64_t sr = r0 + ((q + (pr ? 1 : -1)) & mh);   // red cell's shifted neighbour (black array)
+        const int64_t sb = r0 + ((q + (pr ? -1 : 1)) & mh);   // black cell's shifted neighbour (red array)
+        const int64_t idx[5] = {rip, rim, rjp, rjm, t};
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const df a = two_sum(s, uh[nbi[k]]);
-            s = a.hi;
-            sig = __fadd_rn(sig, __fadd_rn(a.lo, ul[nbi[k]]));
+        for (int c = 0; c < 2; c++) {
+            const int64_t own = (c ? half : 0) + t;
+            const int64_t oth = c ? 0 : half;
+            float nh[6], nl[6];
+#pragma unroll
+            for (int k = 0; k < 5; k++) {
+                nh[k] = uh[oth + idx[k]];
+                nl[k] = ul[oth + idx[k]];
+            }
+            const int64_t sh = oth + (c ? sb : sr);
+            nh[5] = uh[sh];
+            nl[5] = ul[sh];
+            const df u = {uh[own], ul[own]}, f = {fh[own], fl[own]};
+            const df a = (KIND == KPOISSON) ? df{0.0f, 0.0f} : df{ah[own], al[own]};
+            const df b = (KIND == KPSI) ? df{bh[own], bl[own]} : df{0.0f, 0.0f};
+            float mj = 0.0f, iv = 0.0f;
+            const df e = df_cell<KIND>(nh, nl, u, f, a, b, ih2, two_pi, two_pi_rho, rho10pi, h2, &mj, &iv);
+            r32[own] = -(e.hi + e.lo);
+            if (KIND == KPSI) {
+                m32[own] = mj;
+                inv32[own] = iv;
+            }
+            const float z = e.hi * inv_ref;
+            acc = __fmaf_rn(z, z, acc);
         }
-        df e = df_mul(fast_two_sum(s, sig), ih2);
-        if (KIND == KHELM) {
-            e = df_sub(e, df_mul(df{ah[t], al[t]}, u));
-        } else if (KIND == KPSI) {
-            const df s0 = {ah[t], al[t]}, aa = {bh[t], bl[t]};
-            const df v = df_add({1.0f, 0.0f}, u);
-            const df iv = df_recip(v);
-            const df iv2 = df_mul(iv, iv), iv4 = df_mul(iv2, iv2);
-            const df v2 = df_mul(v, v), v4 = df_mul(v2, v2);
-            e = df_add(e, df_mul(df_mul(s0, iv), two_pi));
-            e = df_add(e, df_mulf(df_mul(aa, df_mul(df_mul(iv4, iv2), iv)), 0.125f));
-            e = df_sub(e, df_mul(df_mul(v4, v), two_pi_rho));
-            const float mj = two_pi.hi * s0.hi * iv2.hi + 0.875f * aa.hi * (iv4.hi * iv4.hi) + rho10pi * v4.hi;
-            m32[t] = mj;
-            inv32[t] = 1.0f / (6.0f + h2 * mj);
-        }
-        e = df_sub(e, df{fh[t], fl[t]});
-        r32[t] = -(e.hi + e.lo);
-        const float z = e.hi * inv_ref;
-        acc = __fmaf_rn(z, z, acc);
     }
     block_sum1((double)acc, partials);
 }
@@ -157,7 +209,7 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
              float *r32, float *m32, float *inv32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    int g = grid_for((int64_t)n * n * n);
+    int g = grid_for((int64_t)n * n * n / 2);
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
     const df dih2 = df_from_double_host(ih2), d2pi = df_from_double_host(2.0 * kPi),
              d2pr = df_from_double_host(2.0 * kPi * rho);

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -69,6 +70,8 @@ struct gr_ctx {
     double *partials = nullptr, *dscal = nullptr, *hscal = nullptr;
     double rho_dep = NAN;
     bool a_valid = false;  // A6/AA current for the V, U in the fields
+    bool w_valid = false;  // tmp holds alpha psi psi^-7 for the psi, alpha psi in the fields
+    bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void *> allocs;
     // finest-level kernel timing (gr_opts.profile)
@@ -272,6 +275,7 @@ gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, 
         ensure_aij(c, fl);
         gr::apsi_setup(n, c->h * c->h, fl->psi, fl->apsi, s->s0, s->sigma, c->AA, K2, Kdot, F.u, F.c0, F.c1, F.f,
                        c->tmp, c->st);
+        c->w_valid = false;  // tmp now holds psi^5 Kdot
         dsum(c, N, c->tmp);
         double a, q;
         st = read_scalars(c, &a, &q);
@@ -279,7 +283,8 @@ gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, 
     } else {
         // lap B^i = 2 d_j (alpha psi^-6 A^ij)  (Eqs. MDC-CF, MG-linear-2a)
         ensure_aij(c, fl);
-        gr::shift_weight(n, fl->psi, fl->apsi, c->tmp, c->st);
+        if (!c->w_valid) gr::shift_weight(n, fl->psi, fl->apsi, c->tmp, c->st);
+        c->w_valid = true;
         gr::shift_source(n, 0.5 / c->h, c->A6, c->tmp, eq - GR_BX, F.f, c->st);
         st = poisson_rhs_finish(c, F, &info->ref);
     }
@@ -373,14 +378,30 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
     cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
     timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu1); });
     timed(c, GR_PROF_RESTRICT, [&] { down(top); });
+    // levels up to 16^3 run in one block (coarse_tail) when the grid is finer than that
+    const int tail = (top > 3 && c->tail_on) ? 3 : 0;
     timed(c, GR_PROF_COARSE, [&] {
-        for (int l = top - 1; l >= 1; l--) {
+        for (int l = top - 1; l >= (tail ? tail + 1 : 1); l--) {
             smooth(c->lev[l], nu1);
             down(l);
         }
-        Level &Z = c->lev[0];
-        gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
-        for (int l = 1; l < top; l++) {
+        if (tail) {
+            float *e[4], *r[4];
+            const float *m[4], *iv[4];
+            double h2[4];
+            for (int l = 0; l < 4; l++) {
+                e[l] = c->lev[l].e;
+                r[l] = c->lev[l].r;
+                m[l] = c->lev[l].m;
+                iv[l] = c->lev[l].inv;
+                h2[l] = c->lev[l].h2;
+            }
+            gr::coarse_tail(kind32, e, r, m, iv, h2, nu1, nu2, c->st);
+        } else {
+            Level &Z = c->lev[0];
+            gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
+        }
+        for (int l = tail ? tail + 1 : 1; l < top; l++) {
             up(l);
             smooth(c->lev[l], nu2);
         }
@@ -573,6 +594,7 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     if (!c) return fail(GR_ERR_NOMEM, "host allocation");
     c->n = n;
     c->L = L;
+    if (const char *env = getenv("GR_COARSE_TAIL")) c->tail_on = env[0] != '0';
     c->h = L / n;
     c->st = (cudaStream_t)stream;
     c->nlev = log2i(n);
@@ -648,6 +670,7 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = gr::g_launches.load();
     c->a_valid = false;
+    c->w_valid = false;
     c->prof_on = o->profile != 0;
     memset(c->prof_launches, 0, sizeof(c->prof_launches));
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
@@ -700,6 +723,7 @@ gr_status gr_vcycle(gr_ctx *c, gr_eq eq, const gr_sources *s, gr_fields *fl, con
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
     if (st != GR_OK) return st;
     c->a_valid = false;
+    c->w_valid = false;
     double r = NAN;
     st = solve_eq(c, eq, s, fl, o, rho, S_hat, -1.0, 1, nullptr, nullptr, &r, nullptr);
     if (res_after) *res_after = r;
@@ -718,6 +742,7 @@ gr_status gr_residual(gr_ctx *c, gr_eq eq, const gr_sources *s, const gr_fields 
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
     if (st != GR_OK) return st;
     c->a_valid = false;
+    c->w_valid = false;
     EqInfo in;
     st = setup_eq(c, eq, s, fl, rho, S_hat, &in);
     if (st != GR_OK) return st;

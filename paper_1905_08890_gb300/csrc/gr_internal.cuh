@@ -27,6 +27,11 @@ extern std::atomic<long long> g_launches;
         kernel<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__);              \
         ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
     } while (0)
+#define GR_LAUNCH_SMEM(kernel, grid, block, smem, stream, ...)              \
+    do {                                                                    \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);         \
+        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
+    } while (0)
 
 // sets the thread's message returned by gr_last_error()
 void set_last_error(const char *msg);
@@ -36,7 +41,7 @@ constexpr double kPi = 3.14159265358979323846;
 enum Kind : int { KPOISSON = 0, KHELM = 1, KPSI = 2 };
 
 constexpr int kBlock = 256;
-constexpr int kMaxRedBlocks = 1024;  // blocks of the norm/mean reductions
+constexpr int kMaxRedBlocks = 152 * 16;  // blocks of the norm/mean reductions (16 per SM)
 constexpr int kCoarsestSweeps = 32;  // red-black sweeps on the 2^3 level
 
 // ---- multigrid kernels (templated on the working precision T) ---------------
@@ -86,6 +91,13 @@ int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1
                double *partials, double *eps_nat, cudaStream_t st);
 // out[0] = sum of partials[2b], out[1] = sum of partials[2b + 1].
 void finalize(const double *partials, int nblk, double *out, cudaStream_t st);
+
+// The FP32 correction cycle's levels coarse_tail_n()^3 .. 2^3 in one thread
+// block (shared memory): e/r/m/inv of levels 2^3, 4^3, 8^3, 16^3 (index 0 =
+// 2^3); e and r of the top tail level in and e out; h2 per level.
+int coarse_tail_n();
+void coarse_tail(int kind, float *const *e, float *const *r, const float *const *m, const float *const *inv,
+                 const double *h2, int nu1, int nu2, cudaStream_t st);
 
 // ---- mixed precision -------------------------------------------------------
 // FP64 residual on the fine level; writes r32 = -eps (split), and for KPSI

@@ -656,4 +656,224 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st)
 GR_INST(double)
 GR_INST(float)
 
+// ================================================================ coarse tail
+// Levels 16^3 down to 2^3 and back up of one FP32 correction V-cycle
+// (correction form, KPOISSON or KHELM) inside one thread block, with every
+// level's e, r, m and 1/(6 + h^2 m) in shared memory.  The block runs the
+// same operations in the same order as the per-level kernels (red then black
+// sweeps, residual-restriction, FP64 2^3 solve, trilinear prolongation), so
+// the coarse levels cost one launch per cycle instead of about thirty.
+namespace {
+
+constexpr int kTailN = 16;
+constexpr int kTailThreads = 1024;
+
+struct TailLevel {
+    float *e, *r, *m, *inv;
+    int lg;
+    float h2, ih2;
+};
+
+__device__ __forceinline__ int tail_sidx(int lg, int i, int j, int k)
+{
+    return ((i + j + k) & 1) * (1 << (3 * lg - 1)) + ((((i << lg) + j) << (lg - 1)) + (k >> 1));
+}
+
+template <int KIND>
+__device__ void tail_sweep(const TailLevel &L, int color)
+{
+    const int lg = L.lg, n1 = (1 << lg) - 1, half = 1 << (3 * lg - 1);
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int q = t & ((1 << (lg - 1)) - 1);
+        const int j = (t >> (lg - 1)) & n1, i = t >> (2 * lg - 1);
+        const int k = 2 * q + ((i + j + color) & 1);
+        const float nb = L.e[tail_sidx(lg, (i + 1) & n1, j, k)] + L.e[tail_sidx(lg, (i - 1) & n1, j, k)] +
+                         L.e[tail_sidx(lg, i, (j + 1) & n1, k)] + L.e[tail_sidx(lg, i, (j - 1) & n1, k)] +
+                         L.e[tail_sidx(lg, i, j, (k + 1) & n1)] + L.e[tail_sidx(lg, i, j, (k - 1) & n1)];
+        const int id = color * half + t;
+        L.e[id] = KIND == KPOISSON ? (nb - L.h2 * L.r[id]) * (1.0f / 6.0f) : (nb - L.h2 * L.r[id]) * L.inv[id];
+    }
+    __syncthreads();
+}
+
+template <int KIND>
+__device__ void tail_down(const TailLevel &A, const TailLevel &C)
+{
+    const int lc = C.lg, mc = (1 << lc) - 1, nf1 = (1 << A.lg) - 1;
+    for (int t = threadIdx.x; t < (1 << (3 * lc)); t += blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
+        float s = 0.0f;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                for (int c = 0; c < 2; c++) {
+                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+                    const int id = tail_sidx(A.lg, i, j, k);
+                    const float u = A.e[id];
+                    const float nb = A.e[tail_sidx(A.lg, (i + 1) & nf1, j, k)] +
+                                     A.e[tail_sidx(A.lg, (i - 1) & nf1, j, k)] +
+                                     A.e[tail_sidx(A.lg, i, (j + 1) & nf1, k)] +
+                                     A.e[tail_sidx(A.lg, i, (j - 1) & nf1, k)] +
+                                     A.e[tail_sidx(A.lg, i, j, (k + 1) & nf1)] +
+                                     A.e[tail_sidx(A.lg, i, j, (k - 1) & nf1)];
+                    float lap = (nb - 6.0f * u) * A.ih2;
+                    if (KIND == KHELM) lap -= A.m[id] * u;
+                    s += lap - A.r[id];
+                }
+        const int cid = tail_sidx(lc, I, J, K);
+        C.r[cid] = -(0.125f * s);
+        C.e[cid] = 0.0f;
+    }
+    __syncthreads();
+}
+
+__device__ void tail_up(const TailLevel &A, const TailLevel &C)
+{
+    const int lc = C.lg, mc = (1 << lc) - 1, lf = A.lg, nf1 = (1 << lf) - 1;
+    for (int t = threadIdx.x; t < (1 << (3 * lf)); t += blockDim.x) {
+        const int k = t & nf1, j = (t >> lf) & nf1, i = t >> (2 * lf);
+        int Ia[2], Jb[2], Kc[2];
+        Ia[0] = i >> 1;
+        Ia[1] = (i & 1) ? ((Ia[0] + 1) & mc) : ((Ia[0] - 1) & mc);
+        Jb[0] = j >> 1;
+        Jb[1] = (j & 1) ? ((Jb[0] + 1) & mc) : ((Jb[0] - 1) & mc);
+        Kc[0] = k >> 1;
+        Kc[1] = (k & 1) ? ((Kc[0] + 1) & mc) : ((Kc[0] - 1) & mc);
+        const float w[2] = {0.75f, 0.25f};
+        float z[2][2];
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                z[a][b] = w[0] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[0])] + w[1] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[1])];
+        const float y0 = w[0] * z[0][0] + w[1] * z[0][1], y1 = w[0] * z[1][0] + w[1] * z[1][1];
+        A.e[tail_sidx(lf, i, j, k)] += w[0] * y0 + w[1] * y1;
+    }
+    __syncthreads();
+}
+
+// FP64 solve of the 2^3 level (same steps as k_coarsest)
+template <int KIND>
+__device__ void tail_coarsest(const TailLevel &Z)
+{
+    __shared__ double su[8], sf[8], sm[8];
+    const int t = threadIdx.x;
+    if (t < 8) {
+        su[t] = Z.e[t];
+        sf[t] = Z.r[t];
+        sm[t] = KIND == KPOISSON ? 0.0 : (double)Z.m[t];
+    }
+    __syncthreads();
+    if (KIND == KPOISSON && t == 0) {
+        double m = 0.0;
+        for (int q = 0; q < 8; q++) m += sf[q];
+        m *= 0.125;
+        for (int q = 0; q < 8; q++) sf[q] -= m;
+    }
+    __syncthreads();
+    const double h2 = (double)Z.h2;
+    for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
+        for (int color = 0; color < 2; color++) {
+            if (t < 4) {
+                const int i = t >> 1, j = t & 1, id = 4 * color + t, o = 4 * (color ^ 1);
+                const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
+                su[id] = KIND == KPOISSON ? (nb - h2 * sf[id]) / 6.0 : (nb - h2 * sf[id]) / (6.0 + h2 * sm[id]);
+            }
+            __syncthreads();
+        }
+    }
+    if (KIND == KPOISSON && t == 0) {
+        double m = 0.0;
+        for (int q = 0; q < 8; q++) m += su[q];
+        m *= 0.125;
+        for (int q = 0; q < 8; q++) su[q] -= m;
+    }
+    __syncthreads();
+    if (t < 8) Z.e[t] = (float)su[t];
+    __syncthreads();
+}
+
+// gl: the global arrays of levels 2^3 .. 16^3 (index 0 = 2^3); e/r of 16^3
+// in and out, m/inv read for KHELM.
+struct TailArgs {
+    float *e[4], *r[4];
+    const float *m[4], *inv[4];
+    float h2[4];
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs g, int nu1, int nu2)
+{
+    extern __shared__ float sh[];
+    TailLevel L[4];
+    float *p = sh;
+    for (int l = 0; l < 4; l++) {
+        const int cells = 1 << (3 * (l + 1));
+        L[l].lg = l + 1;
+        L[l].h2 = g.h2[l];
+        L[l].ih2 = 1.0f / g.h2[l];
+        L[l].e = p;
+        L[l].r = p + cells;
+        L[l].m = p + 2 * cells;
+        L[l].inv = p + 3 * cells;
+        p += 4 * cells;
+        for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+            if (l == 3) {
+                L[l].e[t] = g.e[3][t];
+                L[l].r[t] = g.r[3][t];
+            }
+            if (KIND == KHELM) {
+                L[l].m[t] = g.m[l][t];
+                L[l].inv[t] = g.inv[l][t];
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = 3; l >= 1; l--) {
+        for (int s = 0; s < nu1; s++) {
+            tail_sweep<KIND>(L[l], 0);
+            tail_sweep<KIND>(L[l], 1);
+        }
+        tail_down<KIND>(L[l], L[l - 1]);
+    }
+    tail_coarsest<KIND>(L[0]);
+    for (int l = 1; l <= 3; l++) {
+        tail_up(L[l], L[l - 1]);
+        for (int s = 0; s < nu2; s++) {
+            tail_sweep<KIND>(L[l], 0);
+            tail_sweep<KIND>(L[l], 1);
+        }
+    }
+    for (int t = threadIdx.x; t < (1 << 12); t += blockDim.x) g.e[3][t] = L[3].e[t];
+}
+
+}  // namespace
+
+int coarse_tail_n() { return kTailN; }
+
+void coarse_tail(int kind, float *const *e, float *const *r, const float *const *m, const float *const *inv,
+                 const double *h2, int nu1, int nu2, cudaStream_t st)
+{
+    TailArgs a;
+    for (int l = 0; l < 4; l++) {
+        a.e[l] = e[l];
+        a.r[l] = r[l];
+        a.m[l] = m[l];
+        a.inv[l] = inv[l];
+        a.h2[l] = (float)h2[l];
+    }
+    const size_t smem = 4 * sizeof(float) * (8 + 64 + 512 + 4096);
+    static bool attr_set[2] = {false, false};
+    if (kind == KPOISSON) {
+        if (!attr_set[0]) {
+            cudaFuncSetAttribute(k_coarse_tail<KPOISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set[0] = true;
+        }
+        GR_LAUNCH_SMEM(k_coarse_tail<KPOISSON>, 1, kTailThreads, smem, st, a, nu1, nu2);
+    } else {
+        if (!attr_set[1]) {
+            cudaFuncSetAttribute(k_coarse_tail<KHELM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set[1] = true;
+        }
+        GR_LAUNCH_SMEM(k_coarse_tail<KHELM>, 1, kTailThreads, smem, st, a, nu1, nu2);
+    }
+}
+
 }  // namespace gr

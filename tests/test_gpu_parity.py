@@ -284,3 +284,23 @@ def test_mixed_tight_tolerance_reaches_1e11(prec):
     rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-11, max_cycles=60, prec=prec, rho_hat=p.rho_hat)
     assert rep["status_code"] == gr.GR_OK and max(rep["res"]) <= 1e-11
     ctx.close()
+
+
+def test_coarse_tail_block_matches_per_level_kernels(monkeypatch):
+    """The single-block coarse tail (levels <= 16^3 of the FP32 cycle) runs the
+    same operations as the per-level kernels: same cycle counts, fields equal
+    to FP32 rounding of the corrections."""
+    p, src = _problem(64, seed=6, sigma=1.0, v_rms=0.003, lognormal=True)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GR_COARSE_TAIL", flag)
+        ctx = gr.Context(64)
+        gf = _fields_to_gpu(oracle.initial_fields(64))
+        rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-9, max_cycles=60, prec="mixed_df", rho_hat=p.rho_hat)
+        out.append((rep, {k: _np(v) for k, v in gf.items()}))
+        ctx.close()
+    (ra, fa), (rb, fb) = out
+    assert ra["cycles"] == rb["cycles"]
+    assert ra["kernel_launches"] < rb["kernel_launches"]
+    for k in oracle.FIELDS:
+        assert rel_linf(fa[k], fb[k]) <= 1e-9, k
