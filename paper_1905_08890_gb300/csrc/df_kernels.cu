@@ -132,37 +132,32 @@ __global__ void __launch_bounds__(kBlock)
                float rho10pi, float h2, float inv_ref, float *__restrict__ r32, float *__restrict__ m32,
                float *__restrict__ inv32, double *__restrict__ partials)
 {
+    // 32-bit offsets: grids up to 1024^3 have fewer than 2^31 cells
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
-    const int64_t half = (int64_t)1 << (3 * lgn - 1);
+    const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < half; t += (int64_t)gridDim.x * blockDim.x) {
-        const int q = (int)(t & mh);
-        const int j = (int)((t >> lgh) & mn);
-        const int i = (int)(t >> (lgh + lgn));
-        const int64_t r0 = t - q;
-        const int64_t ri = (int64_t)j << lgh;
-        const int64_t rip = ((int64_t)((i + 1) & mn) << (lgn + lgh)) + ri + q;
-        const int64_t rim = ((int64_t)((i - 1) & mn) << (lgn + lgh)) + ri + q;
-        const int64_t rj = (int64_t)i << (lgn + lgh);
-        const int64_t rjp = rj + ((int64_t)((j + 1) & mn) << lgh) + q;
-        const int64_t rjm = rj + ((int64_t)((j - 1) & mn) << lgh) + q;
-        const int pr = (i + j) & 1;                           // k parity of the red cell in this row
-        const int64_t sr = r0 + ((q + (pr ? 1 : -1)) & mh);   // red cell's shifted neighbour (black array)
-        const int64_t sb = r0 + ((q + (pr ? -1 : 1)) & mh);   // black cell's shifted neighbour (red array)
-        const int64_t idx[5] = {rip, rim, rjp, rjm, t};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < half; t += gridDim.x * blockDim.x) {
+        const int q = t & mh;
+        const int j = (t >> lgh) & mn;
+        const int i = t >> (lgh + lgn);
+        const int r0 = t - q;
+        const int ri = j << lgh;
+        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri + q;
+        const int rim = (((i - 1) & mn) << (lgn + lgh)) + ri + q;
+        const int rj = i << (lgn + lgh);
+        const int rjp = rj + (((j + 1) & mn) << lgh) + q;
+        const int rjm = rj + (((j - 1) & mn) << lgh) + q;
+        const int pr = (i + j) & 1;                      // k parity of the red cell in this row
+        const int sr = r0 + ((q + (pr ? 1 : -1)) & mh);  // red cell's shifted neighbour (black array)
+        const int sb = r0 + ((q + (pr ? -1 : 1)) & mh);  // black cell's shifted neighbour (red array)
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            const int64_t own = (c ? half : 0) + t;
-            const int64_t oth = c ? 0 : half;
-            float nh[6], nl[6];
-#pragma unroll
-            for (int k = 0; k < 5; k++) {
-                nh[k] = uh[oth + idx[k]];
-                nl[k] = ul[oth + idx[k]];
-            }
-            const int64_t sh = oth + (c ? sb : sr);
-            nh[5] = uh[sh];
-            nl[5] = ul[sh];
+            const int own = (c ? half : 0) + t;
+            const float *__restrict__ oh = uh + (c ? 0 : half);
+            const float *__restrict__ ol = ul + (c ? 0 : half);
+            const int sh = c ? sb : sr;
+            const float nh[6] = {oh[rip], oh[rim], oh[rjp], oh[rjm], oh[t], oh[sh]};
+            const float nl[6] = {ol[rip], ol[rim], ol[rjp], ol[rjm], ol[t], ol[sh]};
             const df u = {uh[own], ul[own]}, f = {fh[own], fl[own]};
             const df a = (KIND == KPOISSON) ? df{0.0f, 0.0f} : df{ah[own], al[own]};
             const df b = (KIND == KPSI) ? df{bh[own], bl[own]} : df{0.0f, 0.0f};
