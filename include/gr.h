@@ -103,6 +103,9 @@ typedef struct {
     double S_hat;     /* fiducial trace of the stress (dust: 0); NaN selects 0 */
     int verbose;      /* 0 silent; 1 one line per equation on stderr */
     int profile;      /* nonzero: time the finest-level kernels with CUDA events (gr_report.prof_*) */
+    int check_guess;  /* nonzero: per equation, drop the given guess for the plain one (psi = alpha psi = 1,
+                         vectors 0) when its residual is not finite or, after the first cycle, still above
+                         the plain guess's initial residual (gr_report.guess_rejected) */
 } gr_opts;
 
 /* Finest-level kernel classes timed when gr_opts.profile is set. */
@@ -130,10 +133,11 @@ typedef struct {
     long long kernel_launches;    /* kernels this call launched */
     int prof_launches[GR_NPROF];  /* with gr_opts.profile: launches per gr_prof_class */
     double prof_ms[GR_NPROF];     /* with gr_opts.profile: summed CUDA-event time per class */
+    int guess_rejected[GR_NEQ];   /* with gr_opts.check_guess: 1 where the plain guess replaced the given one */
 } gr_report;
 
 /* Fill *o with the defaults: tol 1e-10, max_cycles 50, V(2,2), FP64,
-   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0. */
+   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0, check_guess 0. */
 void gr_default_opts(gr_opts *o);
 
 /* Create a context for an n^3 grid of box side L.  n must be a power of two,
@@ -195,6 +199,51 @@ const char *gr_last_error(void);
 
 /* Kernels launched by this library in this process so far (all contexts). */
 long long gr_kernel_launches(void);
+
+/* ------------------------------------------------------------------------
+   Learned initial guess.  The paper has no counterpart: this is a small 3D
+   U-Net that maps the sources to an initial guess of the ten fields, to
+   shorten the V-cycle iterations of gr_solve_constraints.  Architecture:
+   four levels of 16, 32, 64, 128 channels, two circular 3^3 convolutions with
+   ReLU per level and side, 2^3 average pooling, cell-centred trilinear x2
+   upsampling, concatenated skips, 1x1 head to 10 channels (psi - 1,
+   alpha psi - 1, V_x, V_y, V_z, U, B^x, B^y, B^z, b), standardised per
+   channel.  Inputs: log(0.01 + s0/rho_hat) and s_i/(rho_hat v_rms),
+   standardised.  BF16 activations and weights, FP32 accumulation on the
+   tensor cores, FP32 master weights and Adam.  The network owns its device
+   memory (about 1.4 GB at 128^3); calls queue on its stream and synchronise it
+   where they return host values.
+   ------------------------------------------------------------------------ */
+typedef struct gr_net gr_net;
+
+/* Create a network for n^3 grids (power of two, 32 <= n <= 512) with
+   He-normal weights drawn from seed and identity normalisation. */
+gr_status gr_net_create(int n, void *cuda_stream, uint64_t seed, gr_net **out);
+void gr_net_destroy(gr_net *net);
+/* Number of FP32 parameters (conv weights [27][cout][cin] and biases per
+   layer in order, then the head [10][16] and its bias). */
+size_t gr_net_num_params(const gr_net *net);
+/* Copy the FP32 parameters to / from host memory (set also resets Adam). */
+gr_status gr_net_get_params(gr_net *net, float *host);
+gr_status gr_net_set_params(gr_net *net, const float *host);
+/* Input (4 channels) and output (10 channels) standardisation: value =
+   (x - mean) / std going in, std * y + mean coming out. */
+gr_status gr_net_set_norm(gr_net *net, const float *in_mean, const float *in_std, const float *out_mean,
+                          const float *out_std);
+/* Write the network's guess of all ten fields into guess (device arrays). */
+gr_status gr_net_infer(gr_net *net, const gr_sources *src, double rho_hat, double v_rms, gr_fields *guess);
+/* Mean squared error of the standardised output against target (device
+   fields, e.g. a converged solve) and its gradient; host_grads (may be NULL)
+   receives gr_net_num_params floats.  Parameters are not changed. */
+gr_status gr_net_loss_grad(gr_net *net, const gr_sources *src, const gr_fields *target, double rho_hat,
+                           double v_rms, float *loss_out, float *host_grads);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on that loss with learning rate lr. */
+gr_status gr_net_train_step(gr_net *net, const gr_sources *src, const gr_fields *target, double rho_hat,
+                            double v_rms, float lr, float *loss_out);
+/* Copy activation tensor `tensor` (forward order: 0 input, 1..20 the layer
+   outputs, pools and concatenations) of the last forward pass to host FP32;
+   count must equal its size. */
+gr_status gr_net_activation(gr_net *net, int tensor, float *host, size_t count);
 
 /* Allocation-free residual of one momentum-constraint equation,
    lap V_i = 8 pi (s_i - <s_i>): the same residual and relative norm as

@@ -461,7 +461,7 @@ gr_status mixed_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
 // max_cycles = 1 performs exactly one cycle and reports OK.
 gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const gr_opts *o, double rho,
                    double S_hat, double tol, int max_cycles, int *cycles, double *res0, double *res,
-                   long long *cells)
+                   long long *cells, int *rejected = nullptr)
 {
     EqInfo in;
     gr_status st = GR_OK;
@@ -470,6 +470,18 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
     const bool dfm = o->prec == GR_PREC_MIXED_DF;
+    // residual of the plain guess (unknown 0: psi = alpha psi = 1, vectors 0),
+    // the bar a given guess must beat after its first cycle
+    double r_plain = NAN;
+    const bool check = o->check_guess != 0 && rejected != nullptr;
+    if (check) {
+        *rejected = 0;
+        cudaMemcpyAsync(F.ur, F.u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+        cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
+        st = norm64(c, in.kind, rho, in.ref, nullptr, &r_plain);
+        if (st != GR_OK) return st;
+        cudaMemcpyAsync(F.u, F.ur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    }
     const bool mixed = o->prec == GR_PREC_MIXED || dfm;
     const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
     if (mixed) {
@@ -493,9 +505,19 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         if (mixed) return mixed_norm(c, in, rho, r);
         return norm64(c, in.kind, rho, in.ref, nullptr, r);
     };
+    auto use_plain_guess = [&]() {
+        cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
+        if (dfm) cudaMemsetAsync(c->dfu, 0, 2 * N * sizeof(float), c->st);
+        *rejected = 1;
+    };
     double r = 0;
     st = fine_norm(&r);
     if (st != GR_OK) return st;
+    if (check && !std::isfinite(r)) {
+        use_plain_guess();
+        st = fine_norm(&r);
+        if (st != GR_OK) return st;
+    }
     if (res0) *res0 = r;
     int cyc = 0;
     if (!std::isfinite(r)) st = fail(GR_ERR_NONFINITE, "equation %d: initial residual is not finite", eq);
@@ -513,6 +535,10 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         st = fine_norm(&r);
         cyc++;
         if (cells) *cells += per_cycle;
+        if (st == GR_OK && check && cyc == 1 && !*rejected && !(r <= r_plain)) {
+            use_plain_guess();
+            st = fine_norm(&r);
+        }
         if (st == GR_OK && !std::isfinite(r)) st = fail(GR_ERR_NONFINITE, "equation %d: residual not finite", eq);
     }
     if (cycles) *cycles = cyc;
@@ -560,6 +586,7 @@ void gr_default_opts(gr_opts *o)
     o->S_hat = 0.0;
     o->verbose = 0;
     o->profile = 0;
+    o->check_guess = 0;
 }
 
 const char *gr_last_error(void) { return g_err.c_str(); }
@@ -680,7 +707,7 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
         if (eq == GR_PSI) c->a_valid = false;  // V and U are final now
         cudaEventRecord(c->ev0, c->st);
         st = solve_eq(c, eq, s, fl, o, rho, S_hat, o->tol, o->max_cycles, &R.cycles[eq], &R.res0[eq], &R.res[eq],
-                      &R.cell_updates);
+                      &R.cell_updates, &R.guess_rejected[eq]);
         cudaEventRecord(c->ev1, c->st);
         cudaEventSynchronize(c->ev1);
         float ms = 0;

@@ -39,14 +39,15 @@ class gr_fields(ctypes.Structure):
 class gr_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
-                ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("profile", ctypes.c_int), ("check_guess", ctypes.c_int)]
 
 
 class gr_report(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int * 10), ("res0", ctypes.c_double * 10), ("res", ctypes.c_double * 10),
                 ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
                 ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
-                ("prof_launches", ctypes.c_int * 9), ("prof_ms", ctypes.c_double * 9)]
+                ("prof_launches", ctypes.c_int * 9), ("prof_ms", ctypes.c_double * 9),
+                ("guess_rejected", ctypes.c_int * 10)]
 
 
 PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid", "mixed_update", "norm64", "setup",
@@ -90,6 +91,30 @@ def lib():
             L.gr_momentum_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                        ctypes.POINTER(ctypes.c_double), _P]
             L.gr_momentum_residual_noalloc.restype = ctypes.c_int
+            FP = ctypes.POINTER(ctypes.c_float)
+            L.gr_net_create.argtypes = [ctypes.c_int, _P, ctypes.c_uint64, ctypes.POINTER(_P)]
+            L.gr_net_create.restype = ctypes.c_int
+            L.gr_net_destroy.argtypes = [_P]
+            L.gr_net_destroy.restype = None
+            L.gr_net_num_params.argtypes = [_P]
+            L.gr_net_num_params.restype = ctypes.c_size_t
+            L.gr_net_get_params.argtypes = [_P, _P]
+            L.gr_net_get_params.restype = ctypes.c_int
+            L.gr_net_set_params.argtypes = [_P, _P]
+            L.gr_net_set_params.restype = ctypes.c_int
+            L.gr_net_set_norm.argtypes = [_P, _P, _P, _P, _P]
+            L.gr_net_set_norm.restype = ctypes.c_int
+            L.gr_net_infer.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(gr_fields)]
+            L.gr_net_infer.restype = ctypes.c_int
+            L.gr_net_loss_grad.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields), ctypes.c_double,
+                                           ctypes.c_double, FP, _P]
+            L.gr_net_loss_grad.restype = ctypes.c_int
+            L.gr_net_train_step.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_float, FP]
+            L.gr_net_train_step.restype = ctypes.c_int
+            L.gr_net_activation.argtypes = [_P, ctypes.c_int, _P, ctypes.c_size_t]
+            L.gr_net_activation.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -139,20 +164,21 @@ def make_fields(fld: dict) -> gr_fields:
 
 
 def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
-              profile=0) -> gr_opts:
+              profile=0, check_guess=0) -> gr_opts:
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
     o.prec = ({"fp64": GR_PREC_FP64, "mixed": GR_PREC_MIXED, "mixed_df": GR_PREC_MIXED_DF}[prec]
               if isinstance(prec, str) else int(prec))
     o.rho_hat, o.S_hat, o.verbose, o.profile = rho_hat, S_hat, verbose, int(profile)
+    o.check_guess = int(check_guess)
     return o
 
 
 def report_dict(r: gr_report) -> dict:
     return {"cycles": list(r.cycles), "res0": list(r.res0), "res": list(r.res), "status": list(r.eq_status),
             "seconds": r.seconds, "eq_seconds": list(r.eq_seconds), "cell_updates": int(r.cell_updates),
-            "kernel_launches": int(r.kernel_launches),
+            "kernel_launches": int(r.kernel_launches), "guess_rejected": list(r.guess_rejected),
             "prof": {k: {"launches": int(r.prof_launches[i]), "ms": float(r.prof_ms[i])}
                      for i, k in enumerate(PROF_CLASSES)}}
 
@@ -269,3 +295,92 @@ class Context:
 
     def residual(self, eq: int, src, fld, res_field=None, **kw) -> float:
         return gr_residual(self.h, eq, src, fld, make_opts(**kw), res_field)
+
+
+# ------------------------------------------------------------------ learned initial guess
+NET_TENSORS = ("x0", "e0a", "e0b", "p1", "e1a", "e1b", "p2", "e2a", "e2b", "p3", "e3a", "e3b", "cat2", "d2a", "d2b",
+               "cat1", "d1a", "d1b", "cat0", "d0a", "d0b")
+NET_TENSOR_SHAPE = {"x0": (0, 16), "e0a": (0, 16), "e0b": (0, 16), "p1": (1, 16), "e1a": (1, 32), "e1b": (1, 32),
+                    "p2": (2, 32), "e2a": (2, 64), "e2b": (2, 64), "p3": (3, 64), "e3a": (3, 128), "e3b": (3, 128),
+                    "cat2": (2, 192), "d2a": (2, 64), "d2b": (2, 64), "cat1": (1, 96), "d1a": (1, 32),
+                    "d1b": (1, 32), "cat0": (0, 48), "d0a": (0, 16), "d0b": (0, 16)}
+
+
+class Net:
+    """The U-Net initial-guess network of include/gr.h (gr_net_*)."""
+
+    def __init__(self, n: int, seed: int = 0, stream=None):
+        import torch
+
+        self.n = n
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _P()
+        _check(lib().gr_net_create(n, self.stream.cuda_stream, seed, ctypes.byref(h)), "gr_net_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().gr_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().gr_net_num_params(self.h))
+
+    def get_params(self):
+        import numpy as np
+
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().gr_net_get_params(self.h, out.ctypes.data), "gr_net_get_params")
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(lib().gr_net_set_params(self.h, p.ctypes.data), "gr_net_set_params")
+
+    def set_norm(self, in_mean, in_std, out_mean, out_std):
+        import numpy as np
+
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mean, in_std, out_mean, out_std)]
+        _check(lib().gr_net_set_norm(self.h, *[a.ctypes.data for a in arrs]), "gr_net_set_norm")
+        self.norm = arrs
+
+    def infer(self, src: dict, fld: dict, rho_hat: float, v_rms: float):
+        s, f = make_sources(src), make_fields(fld)
+        _check(lib().gr_net_infer(self.h, ctypes.byref(s), rho_hat, v_rms, ctypes.byref(f)), "gr_net_infer")
+
+    def loss_grad(self, src: dict, target: dict, rho_hat: float, v_rms: float, want_grads=True):
+        import numpy as np
+
+        s, f = make_sources(src), make_fields(target)
+        loss = ctypes.c_float(0)
+        g = np.empty(self.num_params, dtype=np.float32) if want_grads else None
+        _check(lib().gr_net_loss_grad(self.h, ctypes.byref(s), ctypes.byref(f), rho_hat, v_rms, ctypes.byref(loss),
+                                      g.ctypes.data if g is not None else None), "gr_net_loss_grad")
+        return loss.value, g
+
+    def train_step(self, src: dict, target: dict, rho_hat: float, v_rms: float, lr: float) -> float:
+        s, f = make_sources(src), make_fields(target)
+        loss = ctypes.c_float(0)
+        _check(lib().gr_net_train_step(self.h, ctypes.byref(s), ctypes.byref(f), rho_hat, v_rms, lr,
+                                       ctypes.byref(loss)), "gr_net_train_step")
+        return loss.value
+
+    def activation(self, name: str):
+        import numpy as np
+
+        lev, c = NET_TENSOR_SHAPE[name]
+        m = self.n >> lev
+        out = np.empty((m, m, m, c), dtype=np.float32)
+        _check(lib().gr_net_activation(self.h, NET_TENSORS.index(name), out.ctypes.data, out.size),
+               "gr_net_activation")
+        return out

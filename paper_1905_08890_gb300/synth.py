@@ -130,3 +130,46 @@ def lattice(n: int, per_dim: int = 1, offset: float = 0.5, velocity=None) -> Par
     x = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)])
     u = np.zeros_like(x) if velocity is None else np.ascontiguousarray(velocity(x), dtype=np.float64)
     return Particles(n=n, x=x, u=u, mass=RHO_BAR / float(m) ** 3, delta_rms=0.0, seed=-1)
+
+
+def zeldovich_torch(n: int, seed: int, sigma: float, v_rms: float, lognormal: bool, device="cuda"):
+    """The same recipe as zeldovich() drawn with torch on `device` (a torch
+    Generator seeded with `seed`, so the noise stream differs from numpy's):
+    for building training sets quickly.  Returns (x, u, mass) as float64
+    tensors (3, n^3) and the particle mass."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    w = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float64)
+    f = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float64) * 2.0 * math.pi
+    fr = torch.fft.rfftfreq(n, d=1.0 / n, device=device, dtype=torch.float64) * 2.0 * math.pi
+    kx, ky, kz = f[:, None, None], f[None, :, None], fr[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    wk = torch.fft.rfftn(w) / torch.sqrt(k2)
+    wk[0, 0, 0] = 0.0
+    gf = torch.fft.irfftn(wk, s=(n, n, n))
+    gf /= gf.std()
+    if lognormal:
+        lam = math.sqrt(math.log1p(sigma * sigma))
+        delta = torch.clamp(torch.exp(lam * gf - 0.5 * lam * lam) - 1.0, min=-0.95)
+    else:
+        delta = sigma * gf
+    dk = torch.fft.rfftn(delta)
+    dk[0, 0, 0] = 0.0
+    q = (torch.arange(n, device=device, dtype=torch.float64) + 0.5) / n
+    x = torch.empty((3, n * n * n), device=device, dtype=torch.float64)
+    u = torch.empty_like(x)
+    for d, kd in enumerate((kx, ky, kz)):
+        disp = torch.fft.irfftn(1j * kd * dk / k2, s=(n, n, n))
+        u[d] = disp.reshape(-1)
+        shape = [1, 1, 1]
+        shape[d] = n
+        x[d] = (disp + q.reshape(shape)).reshape(-1)
+    x = torch.remainder(x, 1.0)
+    x[x >= 1.0] = 0.0
+    norm = torch.sqrt(torch.mean(torch.sum(u * u, dim=0)))
+    if norm > 0:
+        u *= v_rms / norm
+    return x, u, RHO_BAR / float(n) ** 3
