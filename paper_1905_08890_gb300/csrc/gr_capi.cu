@@ -476,11 +476,16 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     const bool check = o->check_guess != 0 && rejected != nullptr;
     if (check) {
         *rejected = 0;
-        cudaMemcpyAsync(F.ur, F.u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-        cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
-        st = norm64(c, in.kind, rho, in.ref, nullptr, &r_plain);
-        if (st != GR_OK) return st;
-        cudaMemcpyAsync(F.u, F.ur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+        if (in.kind == KPOISSON) {
+            // u = 0 leaves eps = -f, and ref is RMS(f): the plain guess's relative residual is 1
+            r_plain = 1.0;
+        } else {
+            cudaMemcpyAsync(F.ur, F.u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+            cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
+            st = norm64(c, in.kind, rho, in.ref, nullptr, &r_plain);
+            if (st != GR_OK) return st;
+            cudaMemcpyAsync(F.u, F.ur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+        }
     }
     const bool mixed = o->prec == GR_PREC_MIXED || dfm;
     const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
