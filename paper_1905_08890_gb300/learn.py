@@ -8,7 +8,7 @@ and test seeds are disjoint (1000-2799, 2800-2999, 5000-5099).  Sources are
 regenerated from their seeds at every use (particle drawing and deposit take
 milliseconds on the GPU); targets are kept on the GPU in BF16.
 
-    python -m paper_1905_08890_gb300.learn --train 1800 --epochs 3 --out weights.npz
+    python -m paper_1905_08890_gb300.learn --train 1800 --epochs 12 --out weights.npz
 """
 from __future__ import annotations
 
@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--train", type=int, default=len(TRAIN_SEEDS))
     ap.add_argument("--val", type=int, default=40)
     ap.add_argument("--test", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--max-minutes", type=float, default=None)
     ap.add_argument("--out", default=WEIGHTS)
