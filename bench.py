@@ -157,6 +157,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison at 128^3")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -312,6 +313,9 @@ def main():
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 2))
 
+    if rank == 0 and not args.no_learned:
+        out["learned"] = learned_measure(args.prec)
+
     if rank == 0 and world == 1 and not args.no_cpu:
         import numpy as np
 
@@ -357,6 +361,56 @@ def e2e_measure(ctx, p, n, opts, world, steps):
     dt = time.perf_counter() - t0
     return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
             "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3)}
+
+
+def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
+    """The learned initial guess on its own workload (128^3, lognormal rms
+    delta U[0.3, 3], held-out seeds): time to residual 1e-8 and V-cycles from
+    the plain guess and from the network's guess (inference included, guess
+    check on), CUDA events."""
+    import torch
+
+    from paper_1905_08890_gb300 import gr, learn
+
+    if not os.path.exists(learn.WEIGHTS):
+        return {"unavailable": "no trained weights"}
+    ctx = gr.Context(learn.N)
+    net = learn.load(learn.WEIGHTS)
+    src = ctx.new_sources()
+    kw = dict(prec=prec)
+    res = {"plain_ms": 0.0, "learned_ms": 0.0, "inference_ms": 0.0, "cycles_plain": 0, "cycles_learned": 0,
+           "rejected": 0}
+    for rep_i in range(2):  # first pass warms up
+        for k in res:
+            res[k] = 0
+        for seed in seeds:
+            src, rho = learn.sources(ctx, seed, src)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record()
+            _, rp = learn.solve(ctx, src, rho, **kw)
+            e[1].record()
+            guess = ctx.initial_fields()
+            e[2].record()
+            _, rw, t_inf = learn.warm_solve(ctx, net, src, rho, **kw)
+            e[3].record()
+            torch.cuda.synchronize()
+            res["plain_ms"] += e[0].elapsed_time(e[1])
+            res["learned_ms"] += e[2].elapsed_time(e[3])
+            res["inference_ms"] += 1e3 * t_inf
+            res["cycles_plain"] += sum(rp["cycles"])
+            res["cycles_learned"] += sum(rw["cycles"])
+            res["rejected"] += sum(rw["guess_rejected"])
+            del guess
+    k = len(seeds)
+    out = {"workload": "zeldovich128, lognormal rms delta U[0.3,3], rms|u| 0.003, tol 1e-8, held-out seeds 5000-5003",
+           "time_to_residual_ms_plain": round(res["plain_ms"] / k, 3),
+           "time_to_residual_ms_learned": round(res["learned_ms"] / k, 3),
+           "inference_ms": round(res["inference_ms"] / k, 3),
+           "vcycles_plain": res["cycles_plain"] / k, "vcycles_learned": res["cycles_learned"] / k,
+           "guesses_rejected": res["rejected"], "path": prec}
+    net.close()
+    ctx.close()
+    return out
 
 
 def _source_hash():

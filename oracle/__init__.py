@@ -88,6 +88,8 @@ def lib():
             L.orc_eq_setup.restype = I
             L.orc_solve_constraints.argtypes = [I, P, P, D, D, D, I, I, I, P, P, P, P]
             L.orc_solve_constraints.restype = I
+            L.orc_residual_at.argtypes = [I, I, P, P, D, D, I64, P, P, P]
+            L.orc_residual_at.restype = None
             _lib = L
     return _lib
 
@@ -278,3 +280,22 @@ def solve_constraints(src: dict, fld: dict, rho_hat: float, S_hat: float = 0.0, 
     st = lib().orc_solve_constraints(n, sp, fp, rho_hat, S_hat, tol, max_cycles, nu1, nu2, cyc, r0, r, sts)
     rep = {"cycles": list(cyc), "res0": list(r0), "res": list(r), "status": list(sts)}
     return st, rep
+
+
+def residual_at(eq: int, src: dict, fld: dict, rho_hat: float, cells, S_hat: float = 0.0):
+    """(eps, f) of equation eq at the natural indices `cells`, from the given
+    sources and fields (for sampled checks of grids too large to solve here);
+    f is the local value of the quantity whose RMS is the equation's reference.
+    Poisson-type right-hand sides here carry only the source mean of V_i (the
+    divergence sources are mean-free up to rounding)."""
+    order = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+    srcs = [_f64(src[k]) for k in SOURCES]
+    flds = [_f64(fld[k]) for k in order]
+    n = srcs[0].shape[0]
+    sp = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in srcs])
+    fp = (ctypes.c_void_p * 10)(*[a.ctypes.data for a in flds])
+    idx = np.ascontiguousarray(cells, dtype=np.int64)
+    eps = np.empty(idx.size)
+    f = np.empty(idx.size)
+    lib().orc_residual_at(eq, n, sp, fp, rho_hat, S_hat, idx.size, idx.ctypes.data, eps.ctypes.data, f.ctypes.data)
+    return eps, f

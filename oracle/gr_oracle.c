@@ -736,3 +736,125 @@ int orc_solve_constraints(int n, const double *const *src, double *const *fld, d
     free(c1);
     return worst;
 }
+
+
+/* ------------------------------------------------------------------ */
+/* Residuals at sampled cells, for grids too large for a full oracle   */
+/* solve: each equation's right-hand side and coefficients evaluated   */
+/* locally from the sources and fields (same formulas as orc_eq_setup) */
+/* ------------------------------------------------------------------ */
+
+/* A_ij (xx yy zz xy xz yz) at one cell from the V and U stencils */
+static void aij_at(int n, const double *const *V, const double *U, int i, int j, int k, double A[6])
+{
+    const double i2h = 0.5 * n, ih2 = (double)n * n;
+    double D[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int l = 0; l < 3; l++) D[a][l] = (at(V[l], n, i, j, k, a, 1) - at(V[l], n, i, j, k, a, -1)) * i2h;
+    const double divV = D[0][0] + D[1][1] + D[2][2];
+    const double u0 = U[ix(n, i, j, k)];
+    for (int a = 0; a < 3; a++) {
+        const double Uaa = (at(U, n, i, j, k, a, 1) - 2.0 * u0 + at(U, n, i, j, k, a, -1)) * ih2;
+        A[a] = 2.0 * D[a][a] - 0.5 * divV + 2.0 * Uaa;
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int p = 0; p < 3; p++) {
+        const int a = pa[p], b = pb[p];
+        double s = 0.0;
+        for (int sa = -1; sa <= 1; sa += 2)
+            for (int sb = -1; sb <= 1; sb += 2) {
+                int c[3] = {i, j, k};
+                c[a] = (c[a] + sa + n) % n;
+                c[b] = (c[b] + sb + n) % n;
+                s += (double)(sa * sb) * U[ix(n, c[0], c[1], c[2])];
+            }
+        A[3 + p] = D[a][b] + D[b][a] + 2.0 * s * 0.25 * ih2;
+    }
+}
+
+static double aa_of(const double A[6])
+{
+    return A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + 2.0 * (A[3] * A[3] + A[4] * A[4] + A[5] * A[5]);
+}
+
+static double div_at(int n, const double *const *F, int i, int j, int k)
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; a++) s += at(F[a], n, i, j, k, a, 1) - at(F[a], n, i, j, k, a, -1);
+    return s * 0.5 * n;
+}
+
+/* S_B^comp at one cell: 2 sum_l D_l (phi psi^-7 A^{comp l}) */
+static double shift_source_at(int n, const double *const *V, const double *U, const double *psi, const double *apsi,
+                              int comp, int i, int j, int k)
+{
+    const int tab[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+    double s = 0.0;
+    for (int l = 0; l < 3; l++)
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {i, j, k};
+            c[l] = (c[l] + sg + n) % n;
+            double A[6];
+            aij_at(n, V, U, c[0], c[1], c[2], A);
+            const int64_t id = ix(n, c[0], c[1], c[2]);
+            const double p = psi[id], p2 = p * p, p4 = p2 * p2;
+            s += (double)sg * apsi[id] / (p4 * p2 * p) * A[tab[comp][l]];
+        }
+    return 2.0 * s * 0.5 * n;
+}
+
+/* eps = L(u) - f of equation eq (solve order) at the ncell cells idx[] of the
+   natural layout, with the fields and sources given (fld in solve order:
+   V_x V_y V_z U psi apsi B^x B^y B^z b).  The global source means of the
+   Poisson-type equations are computed with one pass each.  eps[c] and the
+   local right-hand side scale f[c] (the quantity whose RMS is the equation's
+   reference: the Poisson source, 2 pi s0, psi^5 Kdot) are written out. */
+void orc_residual_at(int eq, int n, const double *const *src, const double *const *fld, double rho_hat,
+                     double S_hat, int64_t ncell, const int64_t *idx, double *eps, double *fscale)
+{
+    const double ih2 = (double)n * n;
+    const double K2 = 24.0 * PI * rho_hat, Kdot = 12.0 * PI * rho_hat + 4.0 * PI * S_hat;
+    const double *const *V = fld;     /* V_x V_y V_z */
+    const double *U = fld[3];
+    const double *B[3] = {fld[6], fld[7], fld[8]};
+    double mean = 0.0;
+    if (eq <= 2) mean = orc_mean(n, src[1 + eq]);
+    for (int64_t c = 0; c < ncell; c++) {
+        const int64_t id = idx[c];
+        const int k = (int)(id % n), j = (int)((id / n) % n), i = (int)(id / ((int64_t)n * n));
+        const double *u = fld[eq];
+        const double sh = (eq == 4 || eq == 5) ? 1.0 : 0.0; /* Laplacian of the deviation from 1 */
+        const double nb = (at(u, n, i, j, k, 0, 1) - sh) + (at(u, n, i, j, k, 0, -1) - sh) +
+                          (at(u, n, i, j, k, 1, 1) - sh) + (at(u, n, i, j, k, 1, -1) - sh) +
+                          (at(u, n, i, j, k, 2, 1) - sh) + (at(u, n, i, j, k, 2, -1) - sh);
+        const double lap = (nb - 6.0 * (u[id] - sh)) * ih2;
+        double e, f;
+        if (eq <= 2) {
+            f = 8.0 * PI * (src[1 + eq][id] - mean);
+            e = lap - f;
+        } else if (eq == 3 || eq == 9) {
+            const double *F[3] = {eq == 3 ? V[0] : B[0], eq == 3 ? V[1] : B[1], eq == 3 ? V[2] : B[2]};
+            f = -0.25 * div_at(n, F, i, j, k);
+            e = lap - f;
+        } else if (eq == 4) {
+            double A[6];
+            aij_at(n, V, U, i, j, k, A);
+            const double p = u[id], p2 = p * p, p4 = p2 * p2;
+            f = 2.0 * PI * src[0][id];
+            e = lap + 2.0 * PI * src[0][id] / p + aa_of(A) / (8.0 * p4 * p2 * p) - 2.0 * PI * rho_hat * p4 * p;
+        } else if (eq == 5) {
+            double A[6];
+            aij_at(n, V, U, i, j, k, A);
+            const double p = fld[4][id], p2 = p * p, p4 = p2 * p2, p8 = p4 * p4;
+            const double m = 2.0 * PI / p2 * (src[0][id] + 2.0 * src[4][id] / p4) + 0.875 * aa_of(A) / p8 +
+                             (5.0 / 12.0) * p4 * K2;
+            f = p4 * p * Kdot;
+            e = lap - m * u[id] + f;
+        } else {
+            f = shift_source_at(n, V, U, fld[4], fld[5], eq - 6, i, j, k);
+            e = lap - f;
+        }
+        eps[c] = e;
+        fscale[c] = f;
+    }
+}

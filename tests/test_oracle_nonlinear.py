@@ -192,3 +192,22 @@ def test_axis_permutation_permutes_fields(orc):
         want = np.transpose(a[swap.get(k, k)], (1, 0, 2))
         scale = max(np.abs(want - want.mean()).max(), 1e-300)
         assert np.abs(b[k] - want).max() <= 1e-9 * scale, k
+
+
+def test_sampled_residuals_equal_full_residuals(orc):
+    """orc_residual_at (the pointwise check used at grid sizes too large for
+    a full oracle solve) reproduces the full-grid residual of every equation."""
+    p = synth.zeldovich(16, 13, 0.5, 0.01, True)
+    src = orc.deposit(16, p.x, p.u, p.mass)
+    fld = orc.initial_fields(16)
+    orc.solve_constraints(src, fld, p.rho_hat, tol=0.0, max_cycles=2)
+    cells = np.random.default_rng(0).choice(16 ** 3, 300, replace=False)
+    for e, name in enumerate(orc.EQUATIONS):
+        kind, f, c0, c1, ref = orc.eq_setup(e, src, fld, p.rho_hat)
+        u = fld[name] - 1 if name in ("psi", "apsi") else fld[name]
+        eps, _ = orc.residual(kind, u, f, c0, c1, p.rho_hat)
+        got, fs = orc.residual_at(e, src, fld, p.rho_hat, cells)
+        want = eps.reshape(-1)[cells]
+        assert np.allclose(got, want, rtol=1e-9, atol=1e-11 * max(np.abs(want).max(), ref)), name
+        if kind == orc.POISSON:
+            assert np.allclose(fs, f.reshape(-1)[cells], rtol=1e-9, atol=1e-12 * ref)
