@@ -132,11 +132,13 @@ __global__ void __launch_bounds__(kBlock)
                float rho10pi, float h2, float inv_ref, float *__restrict__ r32, float *__restrict__ m32,
                float *__restrict__ inv32, double *__restrict__ partials)
 {
-    // 32-bit offsets: grids up to 1024^3 have fewer than 2^31 cells
+    // Two neighbouring half-indices q0, q0 + 1 of one row per thread (float2
+    // loads), both colours: four cells.  32-bit offsets: grids up to 1024^3.
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < half; t += gridDim.x * blockDim.x) {
+    for (int tp = blockIdx.x * blockDim.x + threadIdx.x; tp < (half >> 1); tp += gridDim.x * blockDim.x) {
+        const int t = tp << 1;  // even: q0 = t & mh
         const int q = t & mh;
         const int j = (t >> lgh) & mn;
         const int i = t >> (lgh + lgn);
@@ -147,29 +149,68 @@ __global__ void __launch_bounds__(kBlock)
         const int rj = i << (lgn + lgh);
         const int rjp = rj + (((j + 1) & mn) << lgh) + q;
         const int rjm = rj + (((j - 1) & mn) << lgh) + q;
-        const int pr = (i + j) & 1;                      // k parity of the red cell in this row
-        const int sr = r0 + ((q + (pr ? 1 : -1)) & mh);  // red cell's shifted neighbour (black array)
-        const int sb = r0 + ((q + (pr ? -1 : 1)) & mh);  // black cell's shifted neighbour (red array)
+        const int pr = (i + j) & 1;  // k parity of the red cells in this row
+        // the own-row neighbour outside the pair: q0 + 2 (shift +1) or q0 - 1 (shift -1)
+        const int xp = r0 + ((q + 2) & mh), xm = r0 + ((q - 1) & mh);
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const int own = (c ? half : 0) + t;
-            const float *__restrict__ oh = uh + (c ? 0 : half);
-            const float *__restrict__ ol = ul + (c ? 0 : half);
-            const int sh = c ? sb : sr;
-            const float nh[6] = {oh[rip], oh[rim], oh[rjp], oh[rjm], oh[t], oh[sh]};
-            const float nl[6] = {ol[rip], ol[rim], ol[rjp], ol[rjm], ol[t], ol[sh]};
-            const df u = {uh[own], ul[own]}, f = {fh[own], fl[own]};
-            const df a = (KIND == KPOISSON) ? df{0.0f, 0.0f} : df{ah[own], al[own]};
-            const df b = (KIND == KPSI) ? df{bh[own], bl[own]} : df{0.0f, 0.0f};
-            float mj = 0.0f, iv = 0.0f;
-            const df e = df_cell<KIND>(nh, nl, u, f, a, b, ih2, two_pi, two_pi_rho, rho10pi, h2, &mj, &iv);
-            r32[own] = -(e.hi + e.lo);
-            if (KIND == KPSI) {
-                m32[own] = mj;
-                inv32[own] = iv;
+            const int oth = c ? 0 : half;
+            const int up = c ? !pr : pr;  // this colour's shift is +1 when its k parity is 1
+            float2 nh[5], nl[5];
+            const int rows[5] = {rip, rim, rjp, rjm, t};
+#pragma unroll
+            for (int k = 0; k < 5; k++) {
+                nh[k] = *reinterpret_cast<const float2 *>(uh + oth + rows[k]);
+                nl[k] = *reinterpret_cast<const float2 *>(ul + oth + rows[k]);
             }
-            const float z = e.hi * inv_ref;
-            acc = __fmaf_rn(z, z, acc);
+            const int xi = oth + (up ? xp : xm);
+            const float xh = uh[xi], xl = ul[xi];
+            const float2 u2h = *reinterpret_cast<const float2 *>(uh + own);
+            const float2 u2l = *reinterpret_cast<const float2 *>(ul + own);
+            const float2 f2h = *reinterpret_cast<const float2 *>(fh + own);
+            const float2 f2l = *reinterpret_cast<const float2 *>(fl + own);
+            float2 a2h = {0.0f, 0.0f}, a2l = {0.0f, 0.0f}, b2h = {0.0f, 0.0f}, b2l = {0.0f, 0.0f};
+            if (KIND != KPOISSON) {
+                a2h = *reinterpret_cast<const float2 *>(ah + own);
+                a2l = *reinterpret_cast<const float2 *>(al + own);
+            }
+            if (KIND == KPSI) {
+                b2h = *reinterpret_cast<const float2 *>(bh + own);
+                b2l = *reinterpret_cast<const float2 *>(bl + own);
+            }
+            float mj[2] = {0.0f, 0.0f}, iv[2] = {0.0f, 0.0f};
+            float rr[2];
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                float h6[6], l6[6];
+#pragma unroll
+                for (int k = 0; k < 5; k++) {
+                    h6[k] = e ? nh[k].y : nh[k].x;
+                    l6[k] = e ? nl[k].y : nl[k].x;
+                }
+                // shifted neighbour of cell q0 + e in the other colour's own row
+                if (up) {
+                    h6[5] = e ? xh : nh[4].y;
+                    l6[5] = e ? xl : nl[4].y;
+                } else {
+                    h6[5] = e ? nh[4].x : xh;
+                    l6[5] = e ? nl[4].x : xl;
+                }
+                const df u = {e ? u2h.y : u2h.x, e ? u2l.y : u2l.x};
+                const df f = {e ? f2h.y : f2h.x, e ? f2l.y : f2l.x};
+                const df a = {e ? a2h.y : a2h.x, e ? a2l.y : a2l.x};
+                const df b = {e ? b2h.y : b2h.x, e ? b2l.y : b2l.x};
+                const df r = df_cell<KIND>(h6, l6, u, f, a, b, ih2, two_pi, two_pi_rho, rho10pi, h2, &mj[e], &iv[e]);
+                rr[e] = -(r.hi + r.lo);
+                const float z = r.hi * inv_ref;
+                acc = __fmaf_rn(z, z, acc);
+            }
+            *reinterpret_cast<float2 *>(r32 + own) = make_float2(rr[0], rr[1]);
+            if (KIND == KPSI) {
+                *reinterpret_cast<float2 *>(m32 + own) = make_float2(mj[0], mj[1]);
+                *reinterpret_cast<float2 *>(inv32 + own) = make_float2(iv[0], iv[1]);
+            }
         }
     }
     block_sum1((double)acc, partials);
@@ -204,7 +245,7 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
              float *r32, float *m32, float *inv32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    int g = grid_for((int64_t)n * n * n / 2);
+    int g = grid_for((int64_t)n * n * n / 4);
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
     const df dih2 = df_from_double_host(ih2), d2pi = df_from_double_host(2.0 * kPi),
              d2pr = df_from_double_host(2.0 * kPi * rho);

@@ -33,6 +33,12 @@ __device__ __forceinline__ int64_t sidx(int lgn, int i, int j, int k)
     return (int64_t)((i + j + k) & 1) * half + ((((int64_t)i << lgn) + j) << (lgn - 1)) + (k >> 1);
 }
 
+// 32-bit variant (grids up to 1024^3 have fewer than 2^31 cells)
+__device__ __forceinline__ int sidx32(int lgn, int i, int j, int k)
+{
+    return (((i + j + k) & 1) << (3 * lgn - 1)) + ((((i << lgn) + j) << (lgn - 1)) + (k >> 1));
+}
+
 // natural coordinates of split index t
 __device__ __forceinline__ void scoord(int lgn, int64_t t, int &i, int &j, int &k)
 {
@@ -187,11 +193,11 @@ __global__ void __launch_bounds__(kBlock)
 {
     const int lgc = lgf - 1;
     const int mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
-    const int64_t half = (int64_t)1 << (3 * lgf - 1);
-    const int64_t ncells = (int64_t)1 << (3 * lgc);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+    const int half = 1 << (3 * lgf - 1);
+    const int ncells = 1 << (3 * lgc);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lgc) & mc, I = t >> (2 * lgc);
+        const int qm = (K - 1) & mc, qp = (K + 1) & mc;
         T v[4][4][4];  // v[a + 1][b + 1][c + 1]
 #pragma unroll
         for (int a = -1; a <= 2; a++)
@@ -199,13 +205,14 @@ __global__ void __launch_bounds__(kBlock)
             for (int b = -1; b <= 2; b++) {
                 if ((a == -1 || a == 2) && (b == -1 || b == 2)) continue;
                 const int i = (2 * I + a) & mf, j = (2 * J + b) & mf;
-                const int64_t row = (((int64_t)i << lgf) + j) << lgc;
+                const int row = ((i << lgf) + j) << lgc;
+                const int c0h = ((i + j) & 1) ? half : 0, c1h = half - c0h;  // colour of k even / odd
                 const bool central = a >= 0 && a <= 1 && b >= 0 && b <= 1;
-#pragma unroll
-                for (int c = -1; c <= 2; c++) {
-                    if (!central && (c == -1 || c == 2)) continue;
-                    const int q = (K + (c < 0 ? -1 : (c > 1 ? 1 : 0))) & mc;
-                    v[a + 1][b + 1][c + 1] = u[(int64_t)((i + j + c) & 1) * half + row + q];
+                v[a + 1][b + 1][1] = u[c0h + row + K];
+                v[a + 1][b + 1][2] = u[c1h + row + K];
+                if (central) {
+                    v[a + 1][b + 1][0] = u[c1h + row + qm];  // k = 2K - 1 (odd)
+                    v[a + 1][b + 1][3] = u[c0h + row + qp];  // k = 2K + 2 (even)
                 }
             }
         T s = T(0), su = T(0);
@@ -213,10 +220,10 @@ __global__ void __launch_bounds__(kBlock)
         for (int a = 0; a < 2; a++)
 #pragma unroll
             for (int b = 0; b < 2; b++) {
-                const int64_t row = (((int64_t)(2 * I + a) << lgf) + 2 * J + b) << lgc;
+                const int row = (((2 * I + a) << lgf) + 2 * J + b) << lgc;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const int64_t id = (int64_t)((a + b + c) & 1) * half + row + K;
+                    const int id = (((a + b + c) & 1) ? half : 0) + row + K;
                     const T uc0 = v[a + 1][b + 1][c + 1];
                     const T nb = v[a + 2][b + 1][c + 1] + v[a][b + 1][c + 1] + v[a + 1][b + 2][c + 1] +
                                  v[a + 1][b][c + 1] + v[a + 1][b + 1][c + 2] + v[a + 1][b + 1][c];
@@ -226,7 +233,7 @@ __global__ void __launch_bounds__(kBlock)
                     if (FAS) su += uc0;
                 }
             }
-        const int64_t cid = sidx(lgc, I, J, K);
+        const int cid = sidx32(lgc, I, J, K);
         if (FAS) {
             fc[cid] = T(0.125) * s;
             uc[cid] = T(0.125) * su;
@@ -267,21 +274,21 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
 {
     const int lgc = lgf - 1, mc = (1 << lgc) - 1;
-    const int64_t half = (int64_t)1 << (3 * lgf - 1);
-    const int64_t ncells = (int64_t)1 << (3 * lgc);
+    const int half = 1 << (3 * lgf - 1);
+    const int ncells = 1 << (3 * lgc);
     const T w0 = T(0.25), w1 = T(0.75);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lgc) & mc, I = t >> (2 * lgc);
+        const int Km = (K - 1) & mc, Kp = (K + 1) & mc;
         T z[3][3][2];  // interpolated along k: children c = 0, 1
 #pragma unroll
         for (int x = 0; x < 3; x++)
 #pragma unroll
             for (int y = 0; y < 3; y++) {
                 const int Ii = (I + x - 1) & mc, Jj = (J + y - 1) & mc;
-                const T cm = uc[sidx(lgc, Ii, Jj, (K - 1) & mc)];
-                const T c0 = uc[sidx(lgc, Ii, Jj, K)];
-                const T cp = uc[sidx(lgc, Ii, Jj, (K + 1) & mc)];
+                const T cm = uc[sidx32(lgc, Ii, Jj, Km)];
+                const T c0 = uc[sidx32(lgc, Ii, Jj, K)];
+                const T cp = uc[sidx32(lgc, Ii, Jj, Kp)];
                 z[x][y][0] = w0 * cm + w1 * c0;
                 z[x][y][1] = w1 * c0 + w0 * cp;
             }
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__
         for (int a = 0; a < 2; a++)
 #pragma unroll
             for (int b = 0; b < 2; b++) {
-                const int64_t row = (((int64_t)(2 * I + a) << lgf) + 2 * J + b) << lgc;
+                const int row = (((2 * I + a) << lgf) + 2 * J + b) << lgc;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     // along j, then along i
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__
                     for (int x = 0; x < 3; x++)
                         yv[x] = b ? (w1 * z[x][1][c] + w0 * z[x][2][c]) : (w0 * z[x][0][c] + w1 * z[x][1][c]);
                     const T val = a ? (w1 * yv[1] + w0 * yv[2]) : (w0 * yv[0] + w1 * yv[1]);
-                    u[(int64_t)((a + b + c) & 1) * half + row + K] += val;
+                    u[(((a + b + c) & 1) ? half : 0) + row + K] += val;
                 }
             }
     }
