@@ -187,7 +187,7 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    p = synth.zeldovich(n, w["seed"] + 1000 * rank, w["sigma"], w["v_rms"], w["lognormal"])
+    p = synth.zeldovich(n, replica_seed(w["seed"], rank), w["sigma"], w["v_rms"], w["lognormal"])
     ctx = gr.Context(n)
     x = torch.from_numpy(p.x).cuda()
     u = torch.from_numpy(p.u).cuda()
@@ -233,13 +233,7 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = gr.gr_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    cell_updates = sum(r["cell_updates"] for r in reps)
-    value = cell_updates * world / (ms * 1e-3) / 1e9
+    value, ms = job_throughput(sum(r["cell_updates"] for r in reps), ev0.elapsed_time(ev1), dist, "cuda")
     solve_ms = 1e3 * sum(sum(r["eq_seconds"]) for r in reps) / len(reps)
 
     # per-class roofline over the timed region
@@ -330,6 +324,25 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank solves its own problem (weak scaling): rank r draws seed base + 1000 r."""
+    return base_seed + 1000 * rank
+
+
+def job_throughput(cell_updates: int, ms: float, dist=None, device="cpu"):
+    """Whole-job Gcell-updates/s: cell updates summed over the ranks divided by
+    the slowest rank's time (max over ranks).  Returns (value, max ms)."""
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(cell_updates)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, cell_updates = float(t.item()), float(u.item())
+    return cell_updates / (ms * 1e-3) / 1e9, ms
 
 
 def e2e_measure(ctx, p, n, opts, world, steps):
