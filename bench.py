@@ -32,41 +32,47 @@ DEFAULT_WORKLOAD = "zeldovich512_lognormal5"
 # algorithmic bytes per finest-level cell and launch, per profiled kernel
 # class and equation kind (split layout: a colour pass touches half the cells)
 BYTES = {
-    # class: {kind: bytes per cell}
-    "sweep32": {"poisson": 6.0, "helm": 8.0},
+    # class: {kind: bytes per finest-level cell}
+    "sweep32": {"poisson": 6.0, "helm": 8.0},  # one colour pass
     "sweep64": {"poisson": 12.0, "helm": 16.0, "psi": 24.0},
     "resid_restrict32": {"poisson": 9.0, "helm": 13.0},
+    "resid_restrict32_red": {"poisson": 7.0, "helm": 9.0},  # red children only, after a black pass
     "resid_restrict64": {"poisson": 18.0, "helm": 26.0, "psi": 35.0},
     "prolong32": {"any": 8.5},
     "prolong64": {"any": 17.0},
     "mixed_resid": {"poisson": 20.0, "helm": 28.0, "psi": 44.0},
+    "df_resid": {"poisson": 22.0, "helm": 32.0, "psi": 46.0},  # + the first red pass of the next cycle
     "mixed_update": {"any": 20.0},
+    "df_black_update": {"poisson": 20.0, "helm": 22.0},  # last black pass + update of both colours
     "norm64": {"poisson": 16.0, "helm": 24.0, "psi": 32.0},
 }
 EQ_KIND = ["poisson"] * 4 + ["psi", "helm"] + ["poisson"] * 4
 EQ_KIND32 = ["poisson"] * 4 + ["helm", "helm"] + ["poisson"] * 4
 
 
-def class_bytes(cls, cycles, n, nu1, nu2, mixed):
+def class_bytes(cls, cycles, n, nu1, nu2, prec):
     """Algorithmic bytes of every finest-level launch of one profiled class
-    over a solve with the given per-equation cycle counts."""
+    over a solve with the given per-equation cycle counts (n >= 8, nu1, nu2 >= 1).
+    In the double-float mode the residual kernel also makes the first red
+    pass of each cycle and the last black pass is fused with the update."""
+    mixed, dfm = prec != "fp64", prec == "mixed_df"
     cells = float(n) ** 3
     total = 0.0
     for eq, cyc in enumerate(cycles):
         k64, k32 = EQ_KIND[eq], EQ_KIND32[eq]
         if cls == "sweep32" and mixed:
-            total += cyc * 2 * (nu1 + nu2) * BYTES["sweep32"][k32] * cells
+            total += cyc * (2 * (nu1 + nu2) - (2 if dfm else 0)) * BYTES["sweep32"][k32] * cells
         elif cls == "sweep64" and not mixed:
             total += cyc * 2 * (nu1 + nu2) * BYTES["sweep64"][k64] * cells
         elif cls == "resid_restrict":
-            key = "resid_restrict32" if mixed else "resid_restrict64"
+            key = "resid_restrict32_red" if mixed else "resid_restrict64"
             total += cyc * BYTES[key][k32 if mixed else k64] * cells
         elif cls == "prolong":
             total += cyc * BYTES["prolong32" if mixed else "prolong64"]["any"] * cells
         elif cls == "mixed_resid" and mixed:
-            total += (cyc + 1) * BYTES["mixed_resid"][k64] * cells
+            total += (cyc + 1) * BYTES["df_resid" if dfm else "mixed_resid"][k64] * cells
         elif cls == "mixed_update" and mixed:
-            total += cyc * BYTES["mixed_update"]["any"] * cells
+            total += cyc * (BYTES["df_black_update"][k32] if dfm else BYTES["mixed_update"]["any"]) * cells
         elif cls == "norm64" and not mixed:
             total += (cyc + 1) * BYTES["norm64"][k64] * cells
     return total
@@ -248,7 +254,7 @@ def main():
         if cls in ("setup", "coarse"):
             kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "share_of_step": round(tot_ms / ms, 3)}
             continue
-        byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, mixed) for r in reps)
+        byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, args.prec) for r in reps)
         gbs = byt / (tot_ms * 1e-3) / 1e9
         kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "avg_us": round(1e3 * tot_ms / launches_c, 2),
                         "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3),
@@ -269,7 +275,7 @@ def main():
             traffic = ent["bytes_per_launch"]
     roofline = None
     if dom:
-        avg_bytes = class_bytes(dom, reps[0]["cycles"], n, 2, 2, mixed) / reps[0]["prof"][dom]["launches"]
+        avg_bytes = class_bytes(dom, reps[0]["cycles"], n, 2, 2, args.prec) / reps[0]["prof"][dom]["launches"]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["algorithmic_GBps"], "peak": hbm,
                     "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
                     "algorithmic_bytes_per_launch": round(avg_bytes), "peak_source": f"{peak_kind} hbm_gbs"}

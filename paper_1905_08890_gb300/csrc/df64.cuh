@@ -39,7 +39,7 @@ __device__ __forceinline__ df two_prod(float a, float b)
 }
 
 // a + b with both low parts folded in after the exact high-part sum
-// (absolute error about 2^-44 (|a| + |b|)): for terms of unequal size
+// (absolute error about 2^-47 (|a| + |b|), not relative to a + b)
 __device__ __forceinline__ df df_add(df a, df b)
 {
     df s = two_sum(a.hi, b.hi);
@@ -88,6 +88,65 @@ __device__ __forceinline__ df df_recip(df a)
 }
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// Split a double into hi + lo FP32 with integer operations only (GB300's
+// FP64 and conversion pipes are slow): hi keeps the sign, the exponent and the
+// top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32
+// (rounded to 24 bits, so hi + lo carries at least 48 significant bits) and
+// scaled by 2^(e - 52).  The pair is renormalised by fast-two-sum.  Values
+// whose exponent leaves FP32's normal range for lo (|x| < 2^-74) or hi
+// (|x| >= 2^128) take the FP64 conversion instead; zeros keep their sign.
+__device__ __forceinline__ df split_double(double x)
+{
+    // on the two 32-bit halves of x: hi32 = sign | exponent (11) | mantissa bits 51..32
+    const unsigned hi32 = (unsigned)__double2hiint(x), lo32 = (unsigned)__double2loint(x);
+    if (((hi32 << 1) | lo32) == 0u) return {__uint_as_float(hi32), 0.0f};  // +-0
+    const int ex = (int)((hi32 >> 20) & 0x7ffu) - 1023;
+    if ((unsigned)(ex + 74) > 201u) {  // ex < -74 or ex > 127
+        const float h = (float)x;
+        return {h, (float)(x - (double)h)};
+    }
+    const unsigned sign = hi32 & 0x80000000u;
+    // top 23 stored mantissa bits: 20 from hi32, 3 from lo32
+    const unsigned hib = sign | ((unsigned)(ex + 127) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+    const unsigned rem = lo32 & 0x1fffffffu;
+    const float scale = __int_as_float((ex - 52 + 127) << 23);  // 2^(ex - 52), normal since ex >= -74
+    const float lo = __uint_as_float(__float_as_uint((float)rem * scale) | sign);
+    return fast_two_sum(__uint_as_float(hib), lo);
+}
+
+// hi + lo rounded to the nearest double, with integer operations only: both
+// significands are placed in one 64-bit integer in units of 2^-38 ulp(hi),
+// added or subtracted, and the sum is rounded to 53 bits (ties to even).  Bits
+// of lo below 2^-38 ulp(hi) are dropped first, so in rare near-tie cases the
+// result can differ from the correctly rounded one by one unit in the last
+// place.  Needs a renormalised pair (|lo| <= ulp(hi)/2, as fast_two_sum
+// leaves it) and a normal, finite hi; anything else takes the FP64 sum.
+__device__ __forceinline__ double join_double(df v)
+{
+    const unsigned bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
+    const int e1 = (int)((bh >> 23) & 0xffu), e2 = (int)((bl >> 23) & 0xffu);
+    const int d = e1 - (e2 ? e2 : 1);  // lo is below 2^(24 - d) ulp(hi)
+    if (e1 == 0 || e1 == 255 || e2 == 255 || d < 24) return (double)v.hi + (double)v.lo;
+    const unsigned long long m1 = (unsigned long long)((bh & 0x7fffffu) | 0x800000u);
+    const unsigned long long m2 = (unsigned long long)((bl & 0x7fffffu) | (e2 ? 0x800000u : 0u));
+    const int sh = 38 - d;  // <= 14
+    const unsigned long long x2 = sh >= 0 ? (m2 << sh) : (-sh < 64 ? (m2 >> -sh) : 0ull);
+    const unsigned long long x1 = m1 << 38;  // in [2^61, 2^62)
+    const unsigned long long x = ((bh ^ bl) >> 31) ? x1 - x2 : x1 + x2;  // value = x 2^(e1 - 188)
+    const int s = 63 - __clzll((long long)x) - 52;  // 8, 9 or 10
+    unsigned long long m = x >> s;
+    const unsigned long long rem = x & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    int k = e1 - 188 + s;  // value = m 2^k
+    if (m >> 53) {
+        m >>= 1;
+        ++k;
+    }
+    const unsigned long long bits = ((unsigned long long)(bh >> 31) << 63) |
+                                    ((unsigned long long)(k + 52 + 1023) << 52) | (m & ((1ull << 52) - 1ull));
+    return __longlong_as_double((long long)bits);
+}
 
 // host-side split of a double constant into a double-float
 inline df df_from_double_host(double x)

@@ -28,61 +28,6 @@ inline int log2i(int n)
     return l;
 }
 
-// Split a double into hi + lo FP32 with integer operations only (GB300's
-// FP64 and conversion pipes are slow): hi keeps the sign, the exponent and the
-// top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32
-// (rounded to 24 bits, so hi + lo carries at least 48 significant bits) and
-// scaled by 2^(e - 52).  The pair is renormalised by fast-two-sum.  Values
-// whose exponent leaves FP32's normal range for lo (|x| < 2^-74) or hi
-// (|x| >= 2^128) take the FP64 conversion instead.
-__device__ __forceinline__ df split_double(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
-    if (ex < -74 || ex > 127) {
-        const float h = (float)x;
-        return {h, (float)(x - (double)h)};
-    }
-    const unsigned sign = (unsigned)(b >> 63) << 31;
-    const unsigned hib = sign | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
-    const unsigned rem = (unsigned)(b & 0x1fffffffu);
-    const float scale = __int_as_float((ex - 52 + 127) << 23);  // 2^(ex - 52), normal since ex >= -74
-    const float mag = (float)rem * scale;
-    const float lo = sign ? -mag : mag;
-    return fast_two_sum(__uint_as_float(hib), lo);
-}
-
-__global__ void k_df_split(int64_t cnt, const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
-        const double x = a[t];
-        const df d = x == 0.0 ? df{0.0f, 0.0f} : split_double(x);
-        hi[t] = d.hi;
-        lo[t] = d.lo;
-    }
-}
-
-__global__ void k_df_join(int64_t cnt, const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ a)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
-        a[t] = (double)hi[t] + (double)lo[t];
-}
-
-__device__ __forceinline__ void block_sum1(double a, double *out)
-{
-    __shared__ double sa[kBlock / 32];
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sa[w] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kBlock / 32; q++) t += sa[q];
-        out[2 * blockIdx.x] = t;
-        out[2 * blockIdx.x + 1] = 0.0;
-    }
-}
-
 // L(u) - f at one cell from the compensated neighbour sum (Sum2 of Ogita,
 // Rump and Oishi 2005: the high parts through a two-sum chain, the chain's
 // errors and all low parts added in FP32, which suffices since they are
@@ -130,10 +75,13 @@ __global__ void __launch_bounds__(kBlock)
                const float *__restrict__ fl, const float *__restrict__ ah, const float *__restrict__ al,
                const float *__restrict__ bh, const float *__restrict__ bl, df ih2, df two_pi, df two_pi_rho,
                float rho10pi, float h2, float inv_ref, float *__restrict__ r32, float *__restrict__ m32,
-               float *__restrict__ inv32, double *__restrict__ partials)
+               float *__restrict__ inv32, const float *__restrict__ inv_in, float *__restrict__ e32,
+               double *__restrict__ partials)
 {
     // Two neighbouring half-indices q0, q0 + 1 of one row per thread (float2
     // loads), both colours: four cells.  32-bit offsets: grids up to 1024^3.
+    // Also the first red relaxation of the FP32 correction cycle, which starts
+    // from e = 0: e_red = -h^2 r / 6 (Poisson) or -h^2 r / (6 + h^2 m).
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
@@ -211,38 +159,103 @@ __global__ void __launch_bounds__(kBlock)
                 *reinterpret_cast<float2 *>(m32 + own) = make_float2(mj[0], mj[1]);
                 *reinterpret_cast<float2 *>(inv32 + own) = make_float2(iv[0], iv[1]);
             }
+            if (c == 0 && e32) {
+                float2 d;
+                if (KIND == KPOISSON) {
+                    d = make_float2(-h2 * rr[0] * (1.0f / 6.0f), -h2 * rr[1] * (1.0f / 6.0f));
+                } else if (KIND == KHELM) {
+                    const float2 g = *reinterpret_cast<const float2 *>(inv_in + own);
+                    d = make_float2(-h2 * rr[0] * g.x, -h2 * rr[1] * g.y);
+                } else {
+                    d = make_float2(-h2 * rr[0] * iv[0], -h2 * rr[1] * iv[1]);
+                }
+                *reinterpret_cast<float2 *>(e32 + own) = d;
+            }
         }
     }
-    block_sum1((double)acc, partials);
+    block_sum2((double)acc, 0.0, partials);
+}
+
+// (hi, lo) + e, renormalised
+__device__ __forceinline__ df df_plus_f(float hi, float lo, float e)
+{
+    df s = two_sum(hi, e);
+    s.lo = __fadd_rn(s.lo, lo);
+    return fast_two_sum(s.hi, s.lo);
 }
 
 // u (double-float) += e
 __global__ void k_df_update(int64_t cnt, float *__restrict__ uh, float *__restrict__ ul, const float *__restrict__ e)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
-        df s = two_sum(uh[t], e[t]);
-        s.lo = __fadd_rn(s.lo, ul[t]);
-        s = fast_two_sum(s.hi, s.lo);
+        const df s = df_plus_f(uh[t], ul[t], e[t]);
         uh[t] = s.hi;
         ul[t] = s.lo;
     }
 }
 
+// The last (black) relaxation pass of the FP32 correction cycle fused with the
+// update u += e of both colours: the black corrections are formed as in a
+// colour pass and added to u straight away, the red ones (this pass's
+// neighbours, read anyway) likewise, so e's black half is never written.
+// Four consecutive half-indices per thread (float4), n >= 8; inv: KHELM's
+// 1/(6 + h^2 m).
+template <int KIND>
+__global__ void __launch_bounds__(kBlock)
+    k_df_black_update(int lgn, const float *__restrict__ e, const float *__restrict__ r, const float *__restrict__ inv,
+                      float h2, float *__restrict__ uh, float *__restrict__ ul)
+{
+    const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
+    const int half = 1 << (3 * lgn - 1);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (half >> 2); v += gridDim.x * blockDim.x) {
+        const int t = v << 2;
+        const int q = t & mh;
+        const int j = (t >> lgh) & mn;
+        const int i = t >> (lgh + lgn);
+        const int p = (i + j + 1) & 1;  // black cells' k parity offset in this row
+        const int r0 = t - q;
+        const int ri = j << lgh;
+        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri;
+        const int rim = (((i - 1) & mn) << (lgn + lgh)) + ri;
+        const int rj = i << (lgn + lgh);
+        const int rjp = rj + (((j + 1) & mn) << lgh);
+        const int rjm = rj + (((j - 1) & mn) << lgh);
+        const float4 A = *reinterpret_cast<const float4 *>(e + rip + q);
+        const float4 B = *reinterpret_cast<const float4 *>(e + rim + q);
+        const float4 C = *reinterpret_cast<const float4 *>(e + rjp + q);
+        const float4 D = *reinterpret_cast<const float4 *>(e + rjm + q);
+        const float4 E = *reinterpret_cast<const float4 *>(e + r0 + q);
+        const float4 F = *reinterpret_cast<const float4 *>(r + half + t);
+        const float x = e[r0 + ((q + (p ? 4 : -1)) & mh)];
+        const float4 Sh = p ? make_float4(E.y, E.z, E.w, x) : make_float4(x, E.x, E.y, E.z);
+        float4 G = make_float4(1.0f / 6.0f, 1.0f / 6.0f, 1.0f / 6.0f, 1.0f / 6.0f);
+        if (KIND == KHELM) G = *reinterpret_cast<const float4 *>(inv + half + t);
+        float blk[4];
+        blk[0] = (A.x + B.x + C.x + D.x + E.x + Sh.x - h2 * F.x) * G.x;
+        blk[1] = (A.y + B.y + C.y + D.y + E.y + Sh.y - h2 * F.y) * G.y;
+        blk[2] = (A.z + B.z + C.z + D.z + E.z + Sh.z - h2 * F.z) * G.z;
+        blk[3] = (A.w + B.w + C.w + D.w + E.w + Sh.w - h2 * F.w) * G.w;
+        const float red[4] = {E.x, E.y, E.z, E.w};
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            float4 *H = reinterpret_cast<float4 *>(uh + (c ? half : 0) + t);
+            float4 *L = reinterpret_cast<float4 *>(ul + (c ? half : 0) + t);
+            const float4 h4 = *H, l4 = *L;
+            const float *d = c ? blk : red;
+            const df s0 = df_plus_f(h4.x, l4.x, d[0]), s1 = df_plus_f(h4.y, l4.y, d[1]),
+                     s2 = df_plus_f(h4.z, l4.z, d[2]), s3 = df_plus_f(h4.w, l4.w, d[3]);
+            *H = make_float4(s0.hi, s1.hi, s2.hi, s3.hi);
+            *L = make_float4(s0.lo, s1.lo, s2.lo, s3.lo);
+        }
+    }
+}
+
 }  // namespace
-
-void df_split(int64_t cnt, const double *a, float *hi, float *lo, cudaStream_t st)
-{
-    GR_LAUNCH(k_df_split, grid_for(cnt), kBlock, st, cnt, a, hi, lo);
-}
-
-void df_join(int64_t cnt, const float *hi, const float *lo, double *a, cudaStream_t st)
-{
-    GR_LAUNCH(k_df_join, grid_for(cnt), kBlock, st, cnt, hi, lo, a);
-}
 
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double ih2, double rho, double h2, double ref,
-             float *r32, float *m32, float *inv32, double *partials, cudaStream_t st)
+             float *r32, float *m32, float *inv32, const float *inv_in, float *e32, double *partials,
+             cudaStream_t st)
 {
     const int lgn = log2i(n);
     int g = grid_for((int64_t)n * n * n / 4);
@@ -252,14 +265,25 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
     const float r10 = (float)(10.0 * kPi * rho), fh2 = (float)h2, iref = (float)(1.0 / ref);
     if (kind == KPOISSON)
         GR_LAUNCH(k_df_resid<KPOISSON>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10,
-                  fh2, iref, r32, m32, inv32, partials);
+                  fh2, iref, r32, m32, inv32, inv_in, e32, partials);
     else if (kind == KHELM)
         GR_LAUNCH(k_df_resid<KHELM>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10, fh2,
-                  iref, r32, m32, inv32, partials);
+                  iref, r32, m32, inv32, inv_in, e32, partials);
     else
         GR_LAUNCH(k_df_resid<KPSI>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10, fh2,
-                  iref, r32, m32, inv32, partials);
+                  iref, r32, m32, inv32, inv_in, e32, partials);
     return g;
+}
+
+void df_black_update(int kind, int n, const float *e, const float *r, const float *inv, double h2, float *uh,
+                     float *ul, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = grid_for((int64_t)n * n * n / 8);
+    if (kind == KPOISSON)
+        GR_LAUNCH(k_df_black_update<KPOISSON>, g, kBlock, st, lgn, e, r, inv, (float)h2, uh, ul);
+    else
+        GR_LAUNCH(k_df_black_update<KHELM>, g, kBlock, st, lgn, e, r, inv, (float)h2, uh, ul);
 }
 
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st)

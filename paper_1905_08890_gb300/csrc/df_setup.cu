@@ -1,0 +1,486 @@
+// df_setup.cu - set-up and write-back of the double-float mixed solve.
+//
+// In the double-float mode the finest level is never held in FP64.  These
+// kernels read the natural [n][n][n] FP64 sources and fields and write the
+// unknown, the right-hand side and the coefficients of one equation as hi/lo
+// FP32 pairs in the red-black split layout; the arithmetic of the sources
+// (mean removal, the central differences of Sec. 4.3.1, the powers of psi) is
+// double-float, fed by the integer split of df64.cuh.  FP64 appears once per
+// thread (the block sums), never per cell: GB300 issues FP64 at 1/58 of its
+// FP32 rate, and per-cell FP64 arithmetic would make these memory-sized
+// passes compute bound.  The write-back joins each pair into a double with
+// integer operations (join_double).
+//
+// Threads of the split-layout kernels own a pair of cells k0 = 2q, k0 + 1 of
+// row (i, j): one is red, one black, so both colours' arrays are written
+// coalesced at the same split offset t, and the natural arrays are read in
+// whole rows.
+#include "df64.cuh"
+#include "gr_internal.cuh"
+
+namespace gr {
+namespace {
+
+inline int grid_for(int64_t work)
+{
+    int64_t b = (work + kBlock - 1) / kBlock;
+    const int64_t cap = kMaxRedBlocks;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+inline int log2i(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+__device__ __forceinline__ int64_t nat(int lgn, int i, int j, int k)
+{
+    return ((((int64_t)i << lgn) + j) << lgn) + k;
+}
+
+__device__ __forceinline__ df ld(const double *__restrict__ a, int64_t id) { return split_double(a[id]); }
+
+__device__ __forceinline__ df ldp(const float *__restrict__ h, const float *__restrict__ l, int64_t id)
+{
+    return {h[id], l[id]};
+}
+
+__device__ __forceinline__ void stp(float *__restrict__ h, float *__restrict__ l, int64_t id, df v)
+{
+    h[id] = v.hi;
+    l[id] = v.lo;
+}
+
+// cell pair of split offset t: row (i, j), columns k0 = 2q and k0 + 1; the
+// cell k0 + e has colour c0 ^ e and split index (c0 ^ e) * n^3/2 + t
+struct PairPos {
+    int i, j, k0, c0;
+    int64_t t, half;
+    __device__ __forceinline__ int64_t split(int e) const { return ((c0 ^ e) ? half : 0) + t; }
+};
+
+__device__ __forceinline__ PairPos pair_pos(int lgn, int64_t t)
+{
+    const int lgh = lgn - 1, mn = (1 << lgn) - 1;
+    PairPos p;
+    p.t = t;
+    p.half = (int64_t)1 << (3 * lgn - 1);
+    p.k0 = 2 * (int)(t & ((1 << lgh) - 1));
+    p.j = (int)((t >> lgh) & mn);
+    p.i = (int)(t >> (lgh + lgn));
+    p.c0 = (p.i + p.j) & 1;
+    return p;
+}
+
+// running sum of df values (high parts through two-sum, errors and low parts
+// in FP32) and sum of squares of the high parts
+struct Acc {
+    df s = {0.0f, 0.0f};
+    float q = 0.0f;
+    __device__ __forceinline__ void add(df x)
+    {
+        const df t = two_sum(s.hi, x.hi);
+        s.hi = t.hi;
+        s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, x.lo));
+        q = __fmaf_rn(x.hi, x.hi, q);
+    }
+    __device__ __forceinline__ void flush(double *partials) const
+    {
+        block_sum2((double)s.hi + (double)s.lo, (double)q, partials);
+    }
+};
+
+__device__ __forceinline__ df df_scale2(df a, float p2) { return {a.hi * p2, a.lo * p2}; }  // exact for p2 = 2^k
+
+// ---------------------------------------------------------------- sums
+__global__ void __launch_bounds__(kBlock) k_dfs_sum(int64_t cnt, const double *__restrict__ a, double *partials)
+{
+    Acc acc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        acc.add(ld(a, t));
+    acc.flush(partials);
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_pair_sum(int64_t cnt, const float *__restrict__ h, const float *__restrict__ l, double *partials)
+{
+    Acc acc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        acc.add(ldp(h, l, t));
+    acc.flush(partials);
+}
+
+// ---------------------------------------------------------------- Poisson right-hand sides
+// SRC_MEAN: f = scale (s - <s>), <s> = sum[0] inv_cnt           (V_i, Eq. MG-linear-1a)
+// SRC_DIV:  f = scale sum_l (F_l(+l) - F_l(-l)), scale = -1/(8h) (U and b, Eqs. MG-linear-1, -2)
+// SRC_SHIFT: f = scale sum_l (A^{cl} w)(+l) - (A^{cl} w)(-l), scale = 1/h  (B^c, Eq. MG-linear-2a)
+// Each also loads the unknown from the field and accumulates sum f, sum f^2.
+// Differences of neighbouring values use the plain double-float sum: its
+// absolute error, about 2^-47 of the operands, is near 2^-37 of a central
+// difference at 512^3.
+enum Src : int { SRC_MEAN = 0, SRC_DIV = 1, SRC_SHIFT = 2 };
+
+struct PoissonArgs {
+    const double *s[3];  // SRC_MEAN: s[0]; SRC_DIV: F_x, F_y, F_z
+    const double *sum;   // SRC_MEAN: device sum of s[0]
+    double inv_cnt;
+    const float *A;      // SRC_SHIFT: A^{ij} pairs, natural, component c at A + 2 c N (hi), A + (2c+1) N (lo)
+    const float *wh, *wl;  // SRC_SHIFT: weight pairs, natural
+    int comp;            // SRC_SHIFT: the component c of B^c
+    df scale;
+    const double *fld;  // the unknown (natural)
+    float *uh, *ul, *fh, *fl;
+};
+
+template <int SRC>
+__global__ void __launch_bounds__(kBlock) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
+{
+    const int mn = (1 << lgn) - 1;
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    df mu = {0.0f, 0.0f};
+    if (SRC == SRC_MEAN) mu = split_double(a.sum[0] * a.inv_cnt);
+    const df nmu = df_neg(mu);
+    int tab[3] = {0, 0, 0};
+    if (SRC == SRC_SHIFT) {
+        // A^{c l} for l = x, y, z in the xx yy zz xy xz yz order
+        const int rows[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+        for (int l = 0; l < 3; l++) tab[l] = rows[a.comp][l];
+    }
+    Acc acc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, t);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int i = p.i, j = p.j, k = p.k0 + e;
+            const int64_t id = nat(lgn, i, j, k);
+            const int64_t nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
+                                      {nat(lgn, i, (j + 1) & mn, k), nat(lgn, i, (j - 1) & mn, k)},
+                                      {nat(lgn, i, j, (k + 1) & mn), nat(lgn, i, j, (k - 1) & mn)}};
+            df f;
+            if (SRC == SRC_MEAN) {
+                f = df_mul(df_add_acc(ld(a.s[0], id), nmu), a.scale);
+            } else if (SRC == SRC_DIV) {
+                df d = df_add(ld(a.s[0], nb[0][0]), df_neg(ld(a.s[0], nb[0][1])));
+#pragma unroll
+                for (int l = 1; l < 3; l++) d = df_add(d, df_add(ld(a.s[l], nb[l][0]), df_neg(ld(a.s[l], nb[l][1]))));
+                f = df_mul(d, a.scale);
+            } else {
+                df d = {0.0f, 0.0f};
+#pragma unroll
+                for (int l = 0; l < 3; l++) {
+                    const float *Ah = a.A + 2 * tab[l] * N, *Al = Ah + N;
+                    const df fp = df_mul(ldp(Ah, Al, nb[l][0]), ldp(a.wh, a.wl, nb[l][0]));
+                    const df fm = df_mul(ldp(Ah, Al, nb[l][1]), ldp(a.wh, a.wl, nb[l][1]));
+                    d = df_add(d, df_add(fp, df_neg(fm)));
+                }
+                f = df_mul(d, a.scale);
+            }
+            const int64_t sid = p.split(e);
+            stp(a.fh, a.fl, sid, f);
+            stp(a.uh, a.ul, sid, ld(a.fld, id));
+            acc.add(f);
+        }
+    }
+    acc.flush(partials);
+}
+
+// ---------------------------------------------------------------- A_ij
+// Natural-layout pairs of four fields (V_x, V_y, V_z, U): split once, since
+// the A_ij stencil reads each value up to 19 times.
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_split4(int64_t cnt, const double *__restrict__ a0, const double *__restrict__ a1,
+                 const double *__restrict__ a2, const double *__restrict__ a3, float *__restrict__ p0,
+                 float *__restrict__ p1, float *__restrict__ p2, float *__restrict__ p3)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+        stp(p0, p0 + cnt, t, ld(a0, t));
+        stp(p1, p1 + cnt, t, ld(a1, t));
+        stp(p2, p2 + cnt, t, ld(a2, t));
+        stp(p3, p3 + cnt, t, ld(a3, t));
+    }
+}
+
+// A_ij of Eq. Aij-discrete-2 (xx yy zz xy xz yz) and AA = A_ij A^ij as
+// natural-layout pairs, from the pairs of V_x, V_y, V_z, U (hi at P[f],
+// lo at P[f] + n^3); D_a V_l central, U's second derivatives by the
+// three-point and four-corner stencils (Eq. U-cross-deriv), differences by
+// the plain double-float sum as in the Poisson right-hand sides.
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_aij(int lgn, df inv2h, df ih2, const float *__restrict__ Pvx, const float *__restrict__ Pvy,
+              const float *__restrict__ Pvz, const float *__restrict__ Pu, float *__restrict__ A,
+              float *__restrict__ AAh, float *__restrict__ AAl)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const int m = (1 << lgn) - 1;
+    const float *V[3] = {Pvx, Pvy, Pvz};
+    const df qih2 = df_scale2(ih2, 0.25f);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t & m), j = (int)((t >> lgn) & m), i = (int)(t >> (2 * lgn));
+        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m, kp = (k + 1) & m,
+                  km = (k - 1) & m;
+        const int64_t plus[3] = {nat(lgn, ip, j, k), nat(lgn, i, jp, k), nat(lgn, i, j, kp)};
+        const int64_t minus[3] = {nat(lgn, im, j, k), nat(lgn, i, jm, k), nat(lgn, i, j, km)};
+        auto P = [&](const float *f, int64_t id) { return ldp(f, f + N, id); };
+        auto diff = [&](df a, df b) { return df_add(a, df_neg(b)); };
+        df D[3][3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++)
+#pragma unroll
+            for (int l = 0; l < 3; l++) D[ax][l] = df_mul(diff(P(V[l], plus[ax]), P(V[l], minus[ax])), inv2h);
+        const df divV = df_add(df_add(D[0][0], D[1][1]), D[2][2]);
+        const df u0m2 = df_scale2(P(Pu, t), -2.0f);
+        df Ad[3], Ao[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const df Uaa = df_mul(df_add(df_add(P(Pu, plus[ax]), P(Pu, minus[ax])), u0m2), ih2);
+            Ad[ax] = df_add(df_add(df_scale2(D[ax][ax], 2.0f), df_scale2(divV, -0.5f)), df_scale2(Uaa, 2.0f));
+        }
+        const df Uxy = df_mul(diff(df_add(P(Pu, nat(lgn, ip, jp, k)), P(Pu, nat(lgn, im, jm, k))),
+                                   df_add(P(Pu, nat(lgn, im, jp, k)), P(Pu, nat(lgn, ip, jm, k)))),
+                              qih2);
+        const df Uxz = df_mul(diff(df_add(P(Pu, nat(lgn, ip, j, kp)), P(Pu, nat(lgn, im, j, km))),
+                                   df_add(P(Pu, nat(lgn, im, j, kp)), P(Pu, nat(lgn, ip, j, km)))),
+                              qih2);
+        const df Uyz = df_mul(diff(df_add(P(Pu, nat(lgn, i, jp, kp)), P(Pu, nat(lgn, i, jm, km))),
+                                   df_add(P(Pu, nat(lgn, i, jm, kp)), P(Pu, nat(lgn, i, jp, km)))),
+                              qih2);
+        Ao[0] = df_add(df_add(D[0][1], D[1][0]), df_scale2(Uxy, 2.0f));
+        Ao[1] = df_add(df_add(D[0][2], D[2][0]), df_scale2(Uxz, 2.0f));
+        Ao[2] = df_add(df_add(D[1][2], D[2][1]), df_scale2(Uyz, 2.0f));
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            stp(A + 2 * c * N, A + (2 * c + 1) * N, t, Ad[c]);
+            stp(A + 2 * (3 + c) * N, A + (2 * (3 + c) + 1) * N, t, Ao[c]);
+        }
+        const df dd = df_add(df_add(df_mul(Ad[0], Ad[0]), df_mul(Ad[1], Ad[1])), df_mul(Ad[2], Ad[2]));
+        const df oo = df_add(df_add(df_mul(Ao[0], Ao[0]), df_mul(Ao[1], Ao[1])), df_mul(Ao[2], Ao[2]));
+        stp(AAh, AAl, t, df_add(dd, df_scale2(oo, 2.0f)));
+    }
+}
+
+// ---------------------------------------------------------------- psi, alpha psi
+// psi (Eq. MG-nonlinear): unknown psi - 1, c0 = s0, c1 = AA, f = 0; sums of s0^2
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_psi(int lgn, const double *__restrict__ psi, const double *__restrict__ s0, const float *__restrict__ AAh,
+              const float *__restrict__ AAl, float *__restrict__ uh, float *__restrict__ ul, float *__restrict__ ah,
+              float *__restrict__ al, float *__restrict__ bh, float *__restrict__ bl, float *__restrict__ fh,
+              float *__restrict__ fl, double *partials)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const df m1 = {-1.0f, 0.0f};
+    Acc acc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, t);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int64_t id = nat(lgn, p.i, p.j, p.k0 + e), sid = p.split(e);
+            const df s = ld(s0, id);
+            stp(uh, ul, sid, df_add_acc(ld(psi, id), m1));
+            stp(ah, al, sid, s);
+            stp(bh, bl, sid, ldp(AAh, AAl, id));
+            stp(fh, fl, sid, df{0.0f, 0.0f});
+            acc.add(s);
+        }
+    }
+    acc.flush(partials);
+}
+
+// lapse equation for phi = alpha psi (Eq. sol-scheme-CMC with s = psi^-4 sigma),
+// unknown phi - 1:  lap(phi - 1) - m (phi - 1) = m - psi^5 Kdot, with
+// m = 2 pi psi^-2 (s0 + 2 sigma psi^-4) + 7/8 AA psi^-8 + 5/12 K^2 psi^4.
+// Writes u, c0 = m and f as pairs, m and 1/(6 + h^2 m) in FP32; sums of
+// (psi^5 Kdot)^2.  k2c = 5/12 K^2.
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_apsi(int lgn, float h2, const double *__restrict__ psi, const double *__restrict__ apsi,
+               const double *__restrict__ s0, const double *__restrict__ sig, const float *__restrict__ AAh,
+               const float *__restrict__ AAl, df two_pi, df k2c, df kdot, float *__restrict__ uh,
+               float *__restrict__ ul, float *__restrict__ ah, float *__restrict__ al, float *__restrict__ fh,
+               float *__restrict__ fl, float *__restrict__ m32, float *__restrict__ inv32, double *partials)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const df m1 = {-1.0f, 0.0f};
+    Acc acc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, t);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int64_t id = nat(lgn, p.i, p.j, p.k0 + e), sid = p.split(e);
+            const df ps = ld(psi, id);
+            const df ip = df_recip(ps);
+            const df ip2 = df_mul(ip, ip), ip4 = df_mul(ip2, ip2), ip8 = df_mul(ip4, ip4);
+            const df p2 = df_mul(ps, ps), p4 = df_mul(p2, p2), p5 = df_mul(p4, ps);
+            const df inner = df_add(ld(s0, id), df_mul(df_scale2(ld(sig, id), 2.0f), ip4));
+            const df mm = df_add(df_add(df_mul(df_mul(two_pi, ip2), inner), df_mulf(df_mul(ldp(AAh, AAl, id), ip8), 0.875f)),
+                                 df_mul(p4, k2c));
+            const df src = df_mul(p5, kdot);
+            stp(uh, ul, sid, df_add_acc(ld(apsi, id), m1));
+            stp(ah, al, sid, mm);
+            stp(fh, fl, sid, df_add(mm, df_neg(src)));
+            m32[sid] = mm.hi;
+            inv32[sid] = 1.0f / (6.0f + h2 * mm.hi);
+            acc.add(src);
+        }
+    }
+    acc.flush(partials);
+}
+
+// shift weight alpha psi^-6 = (alpha psi) psi^-7, natural pairs
+__global__ void __launch_bounds__(kBlock) k_dfs_weight(int64_t cnt, const double *__restrict__ psi,
+                                                       const double *__restrict__ apsi, float *__restrict__ wh,
+                                                       float *__restrict__ wl)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+        const df ip = df_recip(ld(psi, t));
+        const df ip2 = df_mul(ip, ip), ip4 = df_mul(ip2, ip2);
+        stp(wh, wl, t, df_mul(ld(apsi, t), df_mul(df_mul(ip4, ip2), ip)));
+    }
+}
+
+// ---------------------------------------------------------------- write-back
+// nat = join(u - <u>) (+ 1 for the deviation unknowns), <u> = sum[0] inv_cnt
+__global__ void __launch_bounds__(kBlock)
+    k_dfs_store(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const double *__restrict__ sum,
+                double inv_cnt, int dev, double *__restrict__ out)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const df nmu = sum ? df_neg(split_double(sum[0] * inv_cnt)) : df{0.0f, 0.0f};
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, t);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            df v = ldp(uh, ul, p.split(e));
+            if (sum) v = df_add_acc(v, nmu);
+            double d = join_double(v);
+            if (dev) d += 1.0;
+            out[nat(lgn, p.i, p.j, p.k0 + e)] = d;
+        }
+    }
+}
+
+}  // namespace
+
+// ================================================================ launchers
+int dfs_sum(int64_t cnt, const double *a, double *partials, cudaStream_t st)
+{
+    const int g = grid_for(cnt);
+    GR_LAUNCH(k_dfs_sum, g, kBlock, st, cnt, a, partials);
+    return g;
+}
+
+int dfs_pair_sum(int64_t cnt, const float *h, const float *l, double *partials, cudaStream_t st)
+{
+    const int g = grid_for(cnt);
+    GR_LAUNCH(k_dfs_pair_sum, g, kBlock, st, cnt, h, l, partials);
+    return g;
+}
+
+int dfs_mean_rhs(int n, const double *s, const double *sum, double scale, const double *fld, float *uh, float *ul,
+                 float *fh, float *fl, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    PoissonArgs a = {};
+    a.s[0] = s;
+    a.sum = sum;
+    a.inv_cnt = 1.0 / ((double)n * n * n);
+    a.scale = df_from_double_host(scale);
+    a.fld = fld;
+    a.uh = uh;
+    a.ul = ul;
+    a.fh = fh;
+    a.fl = fl;
+    const int g = grid_for((int64_t)n * n * n / 2);
+    GR_LAUNCH(k_dfs_poisson<SRC_MEAN>, g, kBlock, st, lgn, a, partials);
+    return g;
+}
+
+int dfs_div_rhs(int n, double scale, const double *Fx, const double *Fy, const double *Fz, const double *fld,
+                float *uh, float *ul, float *fh, float *fl, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    PoissonArgs a = {};
+    a.s[0] = Fx;
+    a.s[1] = Fy;
+    a.s[2] = Fz;
+    a.scale = df_from_double_host(scale);
+    a.fld = fld;
+    a.uh = uh;
+    a.ul = ul;
+    a.fh = fh;
+    a.fl = fl;
+    const int g = grid_for((int64_t)n * n * n / 2);
+    GR_LAUNCH(k_dfs_poisson<SRC_DIV>, g, kBlock, st, lgn, a, partials);
+    return g;
+}
+
+int dfs_shift_rhs(int n, double scale, const float *A, const float *wh, const float *wl, int comp, const double *fld,
+                  float *uh, float *ul, float *fh, float *fl, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    PoissonArgs a = {};
+    a.A = A;
+    a.wh = wh;
+    a.wl = wl;
+    a.comp = comp;
+    a.scale = df_from_double_host(scale);
+    a.fld = fld;
+    a.uh = uh;
+    a.ul = ul;
+    a.fh = fh;
+    a.fl = fl;
+    const int g = grid_for((int64_t)n * n * n / 2);
+    GR_LAUNCH(k_dfs_poisson<SRC_SHIFT>, g, kBlock, st, lgn, a, partials);
+    return g;
+}
+
+void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy, const double *Vz, const double *U,
+             float *const scratch[4], float *A, float *AAh, float *AAl, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int64_t N = (int64_t)n * n * n;
+    GR_LAUNCH(k_dfs_split4, grid_for(N), kBlock, st, N, Vx, Vy, Vz, U, scratch[0], scratch[1], scratch[2],
+              scratch[3]);
+    GR_LAUNCH(k_dfs_aij, grid_for(N), kBlock, st, lgn, df_from_double_host(inv2h), df_from_double_host(ih2),
+              scratch[0], scratch[1], scratch[2], scratch[3], A, AAh, AAl);
+}
+
+int dfs_psi(int n, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh, float *ul,
+            float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = grid_for((int64_t)n * n * n / 2);
+    GR_LAUNCH(k_dfs_psi, g, kBlock, st, lgn, psi, s0, AAh, AAl, uh, ul, ah, al, bh, bl, fh, fl, partials);
+    return g;
+}
+
+int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const double *s0, const double *sig,
+             const float *AAh, const float *AAl, double K2, double Kdot, float *uh, float *ul, float *ah, float *al,
+             float *fh, float *fl, float *m32, float *inv32, double *partials, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int g = grid_for((int64_t)n * n * n / 2);
+    GR_LAUNCH(k_dfs_apsi, g, kBlock, st, lgn, (float)h2, psi, apsi, s0, sig, AAh, AAl,
+              df_from_double_host(2.0 * kPi), df_from_double_host(5.0 / 12.0 * K2), df_from_double_host(Kdot), uh,
+              ul, ah, al, fh, fl, m32, inv32, partials);
+    return g;
+}
+
+void dfs_weight(int n, const double *psi, const double *apsi, float *wh, float *wl, cudaStream_t st)
+{
+    const int64_t cnt = (int64_t)n * n * n;
+    GR_LAUNCH(k_dfs_weight, grid_for(cnt), kBlock, st, cnt, psi, apsi, wh, wl);
+}
+
+void dfs_store(int n, const float *uh, const float *ul, const double *sum, int dev, double *out, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int64_t N = (int64_t)n * n * n;
+    GR_LAUNCH(k_dfs_store, grid_for(N / 2), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, dev, out);
+}
+
+}  // namespace gr

@@ -96,30 +96,6 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // ---------------------------------------------------------------- reductions
-__device__ __forceinline__ void block_sum2(double a, double b, double *out)
-{
-    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sa[w] = a;
-        sb[w] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tb = 0.0;
-        for (int q = 0; q < kBlock / 32; q++) {
-            ta += sa[q];
-            tb += sb[q];
-        }
-        out[2 * blockIdx.x] = ta;
-        out[2 * blockIdx.x + 1] = tb;
-    }
-}
-
 __global__ void __launch_bounds__(kBlock) k_sum_sq(int64_t cnt, const double *__restrict__ a, double *__restrict__ part)
 {
     double s = 0.0, s2 = 0.0;

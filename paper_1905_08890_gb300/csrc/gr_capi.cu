@@ -69,8 +69,10 @@ struct gr_ctx {
     float *dfu = nullptr, *dff = nullptr, *dfa = nullptr, *dfb = nullptr;  // finest level hi|lo pairs
     double *partials = nullptr, *dscal = nullptr, *hscal = nullptr;
     double rho_dep = NAN;
-    bool a_valid = false;  // A6/AA current for the V, U in the fields
-    bool w_valid = false;  // tmp holds alpha psi psi^-7 for the psi, alpha psi in the fields
+    // what A6/AA hold for the V, U in the fields, and tmp (alpha psi psi^-7) for
+    // the psi, alpha psi in the fields: 0 nothing current, 1 FP64, 2 double-float pairs
+    int a_fmt = 0;
+    int w_fmt = 0;
     bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void *> allocs;
@@ -235,9 +237,9 @@ gr_status poisson_rhs_finish(gr_ctx *c, Level &F, double *ref)
 
 void ensure_aij(gr_ctx *c, const gr_fields *fl)
 {
-    if (c->a_valid) return;
+    if (c->a_fmt == 1) return;
     gr::aij_aa(c->n, 0.5 / c->h, 1.0 / (c->h * c->h), fl->V[0], fl->V[1], fl->V[2], fl->U, c->A6, c->AA, c->st);
-    c->a_valid = true;
+    c->a_fmt = 1;
 }
 
 // Build the fine-level unknown, right-hand side and coefficients of equation eq
@@ -275,7 +277,7 @@ gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, 
         ensure_aij(c, fl);
         gr::apsi_setup(n, c->h * c->h, fl->psi, fl->apsi, s->s0, s->sigma, c->AA, K2, Kdot, F.u, F.c0, F.c1, F.f,
                        c->tmp, c->st);
-        c->w_valid = false;  // tmp now holds psi^5 Kdot
+        c->w_fmt = 0;  // tmp now holds psi^5 Kdot
         dsum(c, N, c->tmp);
         double a, q;
         st = read_scalars(c, &a, &q);
@@ -283,13 +285,82 @@ gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, 
     } else {
         // lap B^i = 2 d_j (alpha psi^-6 A^ij)  (Eqs. MDC-CF, MG-linear-2a)
         ensure_aij(c, fl);
-        if (!c->w_valid) gr::shift_weight(n, fl->psi, fl->apsi, c->tmp, c->st);
-        c->w_valid = true;
+        if (c->w_fmt != 1) gr::shift_weight(n, fl->psi, fl->apsi, c->tmp, c->st);
+        c->w_fmt = 1;
         gr::shift_source(n, 0.5 / c->h, c->A6, c->tmp, eq - GR_BX, F.f, c->st);
         st = poisson_rhs_finish(c, F, &info->ref);
     }
     if (st != GR_OK) return st;
     if (!info->dev) gr::to_split(n, field_ptr(fl, eq), F.u, 0.0, c->st);
+    if (!(info->ref >= 1e-300)) info->ref = 1.0;
+    return cuda_check("setup");
+}
+
+// Double-float set-up of equation eq: unknown, right-hand side and
+// coefficients as split-layout pairs in dfu, dff, dfa, dfb (and, for alpha psi,
+// lev[fine].m and .inv), from the natural FP64 sources and fields.  The same
+// equations as setup_eq; the Poisson right-hand sides lose their mean once in
+// double-float, which leaves it at the double-float rounding level.
+gr_status setup_eq_df(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, double rho, double S_hat,
+                      EqInfo *info)
+{
+    const int n = c->n;
+    const int64_t N = (int64_t)n * n * n;
+    Level &F = c->lev[c->nlev - 1];
+    const double K2 = 24.0 * kPi * rho, Kdot = 12.0 * kPi * rho + 4.0 * kPi * S_hat;
+    info->dev = (eq == GR_PSI || eq == GR_APSI);
+    info->poisson = !info->dev;
+    info->kind = eq == GR_PSI ? KPSI : (eq == GR_APSI ? KHELM : KPOISSON);
+    info->kind32 = info->kind == KPOISSON ? KPOISSON : KHELM;
+    float *uh = c->dfu, *ul = c->dfu + N, *fh = c->dff, *fl_ = c->dff + N;
+    float *A = reinterpret_cast<float *>(c->A6), *AAh = reinterpret_cast<float *>(c->AA), *AAl = AAh + N;
+    float *wh = reinterpret_cast<float *>(c->tmp), *wl = wh + N;
+    double *fld = field_ptr(fl, eq);
+    auto aij = [&] {
+        if (c->a_fmt == 2) return;
+        // the finest level's FP64 arrays are free in this mode: scratch for the pairs of V and U
+        float *const scratch[4] = {reinterpret_cast<float *>(F.u), reinterpret_cast<float *>(F.f),
+                                   reinterpret_cast<float *>(F.c0), reinterpret_cast<float *>(F.c1)};
+        gr::dfs_aij(n, 0.5 / c->h, 1.0 / (c->h * c->h), fl->V[0], fl->V[1], fl->V[2], fl->U, scratch, A, AAh, AAl,
+                    c->st);
+        c->a_fmt = 2;
+    };
+    int g;
+    if (eq <= GR_VZ) {
+        // lap V_i = 8 pi (s_i - <s_i>)  (Eq. MG-linear-1a; mean removal of Sec. 4.3.1)
+        g = gr::dfs_sum(N, s->s[eq], c->partials, c->st);
+        gr::finalize(c->partials, g, c->dscal, c->st);
+        g = gr::dfs_mean_rhs(n, s->s[eq], c->dscal, 8.0 * kPi, fld, uh, ul, fh, fl_, c->partials, c->st);
+    } else if (eq == GR_U || eq == GR_B_SCALAR) {
+        // lap U = -1/4 div V ; lap b = -1/4 div B  (Eqs. MG-linear-1, MG-linear-2)
+        double *const *Fv = eq == GR_U ? fl->V : fl->B;
+        g = gr::dfs_div_rhs(n, -0.25 * (0.5 / c->h), Fv[0], Fv[1], Fv[2], fld, uh, ul, fh, fl_, c->partials, c->st);
+    } else if (eq == GR_PSI) {
+        aij();
+        g = gr::dfs_psi(n, fl->psi, s->s0, AAh, AAl, uh, ul, c->dfa, c->dfa + N, c->dfb, c->dfb + N, fh, fl_,
+                        c->partials, c->st);
+    } else if (eq == GR_APSI) {
+        aij();
+        g = gr::dfs_apsi(n, F.h2, fl->psi, fl->apsi, s->s0, s->sigma, AAh, AAl, K2, Kdot, uh, ul, c->dfa, c->dfa + N,
+                         fh, fl_, F.m, F.inv, c->partials, c->st);
+    } else {
+        // lap B^i = 2 d_j (alpha psi^-6 A^ij)  (Eqs. MDC-CF, MG-linear-2a)
+        aij();
+        if (c->w_fmt != 2) gr::dfs_weight(n, fl->psi, fl->apsi, wh, wl, c->st);
+        c->w_fmt = 2;
+        g = gr::dfs_shift_rhs(n, 2.0 * (0.5 / c->h), A, wh, wl, eq - GR_BX, fld, uh, ul, fh, fl_, c->partials,
+                              c->st);
+    }
+    gr::finalize(c->partials, g, c->dscal, c->st);
+    double a, q;
+    gr_status st = read_scalars(c, &a, &q);
+    if (st != GR_OK) return st;
+    if (info->poisson) {
+        const double mean = a / N;
+        info->ref = std::sqrt(std::fmax(q / N - mean * mean, 0.0));
+    } else {
+        info->ref = (eq == GR_PSI ? 2.0 * kPi : 1.0) * std::sqrt(q / N);
+    }
     if (!(info->ref >= 1e-300)) info->ref = 1.0;
     return cuda_check("setup");
 }
@@ -360,8 +431,12 @@ void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
     timed(c, GR_PROF_SWEEP64, [&] { smooth(F, nu2); });
 }
 
-// one FP32 correction V-cycle on lev[*].e with fine right-hand side lev[fine].r
-void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
+// one FP32 correction V-cycle on lev[*].e with fine right-hand side lev[fine].r;
+// red_done: the fine residual kernel already made the first red relaxation
+// from e = 0 (then the black cells of e are not read before they are written).
+// uh, ul not null (needs nu2 >= 1 and a finest level of at least 8^3): the
+// last black pass also adds e to the double-float unknown (uh, ul).
+void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh = nullptr, float *ul = nullptr)
 {
     const int top = c->nlev - 1;
     Level &F = c->lev[top];
@@ -372,11 +447,21 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
     };
     auto down = [&](int l) {
         Level &A = c->lev[l], &C = c->lev[l - 1];
-        gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+        if (nu1 > 0)  // the last pre-smoothing pass was black
+            gr::resid_restrict_red(kind32, A.n, A.e, A.r, A.m, A.ih2, C.e, C.r, c->st);
+        else
+            gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
     };
     auto up = [&](int l) { gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st); };
-    cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
-    timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu1); });
+    timed(c, GR_PROF_SWEEP32, [&] {
+        if (red_done && nu1 > 0) {
+            gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st);
+            smooth(F, nu1 - 1);
+        } else {
+            cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
+            smooth(F, nu1);
+        }
+    });
     timed(c, GR_PROF_RESTRICT, [&] { down(top); });
     // levels up to 16^3 run in one block (coarse_tail) when the grid is finer than that
     const int tail = (top > 3 && c->tail_on) ? 3 : 0;
@@ -407,7 +492,16 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2)
         }
     });
     timed(c, GR_PROF_PROLONG, [&] { up(top); });
-    timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu2); });
+    if (!uh) {
+        timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu2); });
+        return;
+    }
+    timed(c, GR_PROF_SWEEP32, [&] {
+        smooth(F, nu2 - 1);
+        gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 0, c->st);
+    });
+    timed(c, GR_PROF_MIXED_UPDATE,
+          [&] { gr::df_black_update(kind32, F.n, F.e, F.r, F.inv, F.h2, uh, ul, c->st); });
 }
 
 gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, double *r)
@@ -425,14 +519,17 @@ gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, d
     return st;
 }
 
-gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
+// fine residual norm in double-float; with red != 0 also the first red
+// relaxation of the next correction cycle (into lev[fine].e)
+gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r)
 {
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
     int g = 0;
     timed(c, GR_PROF_MIXED_RESID, [&] {
         g = gr::df_resid(in.kind, F.n, c->dfu, c->dfu + N, c->dff, c->dff + N, c->dfa, c->dfa + N, c->dfb,
-                         c->dfb + N, F.ih2, rho, F.h2, in.ref, F.r, F.m, F.inv, c->partials, c->st);
+                         c->dfb + N, F.ih2, rho, F.h2, in.ref, F.r, F.m, F.inv, F.inv, red ? F.e : nullptr,
+                         c->partials, c->st);
     });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;
@@ -465,11 +562,17 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
 {
     EqInfo in;
     gr_status st = GR_OK;
-    timed(c, GR_PROF_SETUP, [&] { st = setup_eq(c, eq, s, fl, rho, S_hat, &in); });
+    const bool dfm = o->prec == GR_PREC_MIXED_DF;
+    timed(c, GR_PROF_SETUP, [&] {
+        st = dfm ? setup_eq_df(c, eq, s, fl, rho, S_hat, &in) : setup_eq(c, eq, s, fl, rho, S_hat, &in);
+    });
     if (st != GR_OK) return st;
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
-    const bool dfm = o->prec == GR_PREC_MIXED_DF;
+    // the double-float residual also makes the first red pass of the next
+    // cycle, and the last black pass adds the correction to u
+    const bool red = dfm && o->nu1 > 0;
+    const bool fuse_update = dfm && o->nu2 > 0 && F.n >= 8;
     // residual of the plain guess (unknown 0: psi = alpha psi = 1, vectors 0),
     // the bar a given guess must beat after its first cycle
     double r_plain = NAN;
@@ -479,6 +582,13 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         if (in.kind == KPOISSON) {
             // u = 0 leaves eps = -f, and ref is RMS(f): the plain guess's relative residual is 1
             r_plain = 1.0;
+        } else if (dfm) {
+            // the pair array (2N floats) fits the FP64 scratch level array
+            cudaMemcpyAsync(F.ur, c->dfu, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+            cudaMemsetAsync(c->dfu, 0, N * sizeof(double), c->st);
+            st = df_norm(c, in, rho, false, &r_plain);
+            if (st != GR_OK) return st;
+            cudaMemcpyAsync(c->dfu, F.ur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
         } else {
             cudaMemcpyAsync(F.ur, F.u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
             cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
@@ -491,22 +601,17 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
     if (mixed) {
         if (in.kind == KHELM) {
-            gr::to_float(N, F.c0, F.m, c->st);
-            gr::helm_invdiag<float>(F.n, F.m, F.inv, F.h2, c->st);
+            if (!dfm) {  // the double-float set-up wrote m and its inverse diagonal
+                gr::to_float(N, F.c0, F.m, c->st);
+                gr::helm_invdiag<float>(F.n, F.m, F.inv, F.h2, c->st);
+            }
             restrict_coefs32(c);
         }
-        if (dfm)
-            timed(c, GR_PROF_SETUP, [&] {
-                gr::df_split(N, F.u, c->dfu, c->dfu + N, c->st);
-                gr::df_split(N, F.f, c->dff, c->dff + N, c->st);
-                if (in.kind != KPOISSON) gr::df_split(N, F.c0, c->dfa, c->dfa + N, c->st);
-                if (in.kind == KPSI) gr::df_split(N, F.c1, c->dfb, c->dfb + N, c->st);
-            });
     } else {
         restrict_coefs64(c, in.kind);
     }
     auto fine_norm = [&](double *r) {
-        if (dfm) return df_norm(c, in, rho, r);
+        if (dfm) return df_norm(c, in, rho, red, r);
         if (mixed) return mixed_norm(c, in, rho, r);
         return norm64(c, in.kind, rho, in.ref, nullptr, r);
     };
@@ -529,11 +634,15 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     while (st == GR_OK && r > tol && cyc < max_cycles) {
         if (mixed) {
             if (in.kind == KPSI) restrict_coefs32(c);
-            vcycle32(c, in.kind32, o->nu1, o->nu2);
-            timed(c, GR_PROF_MIXED_UPDATE, [&] {
-                if (dfm) gr::df_update(F.n, c->dfu, c->dfu + N, F.e, c->st);
-                else gr::mixed_update(F.n, F.u, F.e, c->st);
-            });
+            if (fuse_update) {
+                vcycle32(c, in.kind32, o->nu1, o->nu2, red, c->dfu, c->dfu + N);
+            } else {
+                vcycle32(c, in.kind32, o->nu1, o->nu2, red);
+                timed(c, GR_PROF_MIXED_UPDATE, [&] {
+                    if (dfm) gr::df_update(F.n, c->dfu, c->dfu + N, F.e, c->st);
+                    else gr::mixed_update(F.n, F.u, F.e, c->st);
+                });
+            }
         } else {
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
         }
@@ -550,15 +659,16 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     if (res) *res = r;
     // write back: +1 for the deviation unknowns, zero mean for Poisson-type
     // (the FP64 norm kernels leave the sum of u in dscal[1])
-    const double *usum = in.poisson ? c->dscal + 1 : nullptr;
     if (dfm) {
-        gr::df_join(N, c->dfu, c->dfu + N, F.u, c->st);
         if (in.poisson) {
-            dsum(c, N, F.u);
-            usum = c->dscal;
+            const int g = gr::dfs_pair_sum(N, c->dfu, c->dfu + N, c->partials, c->st);
+            gr::finalize(c->partials, g, c->dscal, c->st);
         }
+        gr::dfs_store(F.n, c->dfu, c->dfu + N, in.poisson ? c->dscal : nullptr, in.dev, field_ptr(fl, eq), c->st);
+    } else {
+        const double *usum = in.poisson ? c->dscal + 1 : nullptr;
+        gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
     }
-    gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
     gr_status cs = cuda_check("write back");
     if (cs != GR_OK) return cs;
     if (st == GR_OK && tol >= 0 && r > tol)
@@ -701,15 +811,15 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     memset(&R, 0, sizeof(R));
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = gr::g_launches.load();
-    c->a_valid = false;
-    c->w_valid = false;
+    c->a_fmt = 0;
+    c->w_fmt = 0;
     c->prof_on = o->profile != 0;
     memset(c->prof_launches, 0, sizeof(c->prof_launches));
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
     gr_status worst = GR_OK;
     std::string first_err;
     for (int eq = 0; eq < GR_NEQ; eq++) {
-        if (eq == GR_PSI) c->a_valid = false;  // V and U are final now
+        if (eq == GR_PSI) c->a_fmt = 0;  // V and U are final now
         cudaEventRecord(c->ev0, c->st);
         st = solve_eq(c, eq, s, fl, o, rho, S_hat, o->tol, o->max_cycles, &R.cycles[eq], &R.res0[eq], &R.res[eq],
                       &R.cell_updates, &R.guess_rejected[eq]);
@@ -754,8 +864,8 @@ gr_status gr_vcycle(gr_ctx *c, gr_eq eq, const gr_sources *s, gr_fields *fl, con
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
     if (st != GR_OK) return st;
-    c->a_valid = false;
-    c->w_valid = false;
+    c->a_fmt = 0;
+    c->w_fmt = 0;
     double r = NAN;
     st = solve_eq(c, eq, s, fl, o, rho, S_hat, -1.0, 1, nullptr, nullptr, &r, nullptr);
     if (res_after) *res_after = r;
@@ -773,8 +883,8 @@ gr_status gr_residual(gr_ctx *c, gr_eq eq, const gr_sources *s, const gr_fields 
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
     if (st != GR_OK) return st;
-    c->a_valid = false;
-    c->w_valid = false;
+    c->a_fmt = 0;
+    c->w_fmt = 0;
     EqInfo in;
     st = setup_eq(c, eq, s, fl, rho, S_hat, &in);
     if (st != GR_OK) return st;

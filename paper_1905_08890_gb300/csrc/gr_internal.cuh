@@ -44,6 +44,34 @@ constexpr int kBlock = 256;
 constexpr int kMaxRedBlocks = 152 * 16;  // blocks of the norm/mean reductions (16 per SM)
 constexpr int kCoarsestSweeps = 32;  // red-black sweeps on the 2^3 level
 
+#ifdef __CUDACC__
+// Block sums of a and b (blockDim.x == kBlock) into out[2 blockIdx.x + 0/1],
+// in a fixed order.
+__device__ __forceinline__ void block_sum2(double a, double b, double *out)
+{
+    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int q = 0; q < kBlock / 32; q++) {
+            ta += sa[q];
+            tb += sb[q];
+        }
+        out[2 * blockIdx.x] = ta;
+        out[2 * blockIdx.x + 1] = tb;
+    }
+}
+#endif
+
 // ---- multigrid kernels (templated on the working precision T) ---------------
 // One Gauss-Seidel pass over colour `color` of a level.  KPOISSON: f;
 // KHELM: f and c1 = 1/(6 + h^2 m); KPSI (double only): f, c0 = s0, c1 = AA,
@@ -58,6 +86,11 @@ void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, d
 template <typename T>
 void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const T *c1, double ih2, double rho, T *uc,
                     T *fc, T *urc, int fas, cudaStream_t st);
+// FP32 correction form of the same (KPOISSON or KHELM with m) right after a
+// black relaxation pass: only the red children's residuals enter the average,
+// the black ones being zero up to rounding.
+void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
+                        float *rc, cudaStream_t st);
 
 // FAS coarse right-hand side: fc = N(uc) - fc (KPSI, double).
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
@@ -111,15 +144,51 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
 
 // ---- double-float fine level (df_kernels.cu) -------------------------------
 // hi/lo = a split into FP32 pairs; a = hi + lo.
-void df_split(int64_t cnt, const double *a, float *hi, float *lo, cudaStream_t st);
-void df_join(int64_t cnt, const float *hi, const float *lo, double *a, cudaStream_t st);
 // Fine residual in double-float: r32 = -eps, KPSI also m32/inv32 (Newton
-// coefficient and FP32 inverse diagonal); a = c0, b = c1 pairs; partials:
-// block sums of (eps/ref)^2.  Returns the block count.
+// coefficient and FP32 inverse diagonal); a = c0, b = c1 pairs.  When e32 is
+// not null it also writes the first red relaxation of the correction cycle
+// from e = 0 (inv_in: the KHELM inverse diagonal).  Partials: block sums of
+// (eps/ref)^2.  Returns the block count.
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double ih2, double rho, double h2, double ref,
-             float *r32, float *m32, float *inv32, double *partials, cudaStream_t st);
+             float *r32, float *m32, float *inv32, const float *inv_in, float *e32, double *partials,
+             cudaStream_t st);
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st);
+// last black pass of the FP32 correction cycle (KPOISSON or KHELM, n >= 8)
+// fused with u += e on both colours; e's black half is left unwritten
+void df_black_update(int kind, int n, const float *e, const float *r, const float *inv, double h2, float *uh,
+                     float *ul, cudaStream_t st);
+
+// ---- double-float set-up and write-back (df_setup.cu) -----------------------
+// Natural FP64 inputs -> split-layout hi/lo pairs.  The int-returning ones
+// leave block partials (sum, sum of squares of the high parts) of the
+// quantity named and return the block count for finalize().
+int dfs_sum(int64_t cnt, const double *a, double *partials, cudaStream_t st);                      // a
+int dfs_pair_sum(int64_t cnt, const float *h, const float *l, double *partials, cudaStream_t st);  // h + l
+// f = scale (s - sum[0]/n^3), u = fld; partials of f
+int dfs_mean_rhs(int n, const double *s, const double *sum, double scale, const double *fld, float *uh, float *ul,
+                 float *fh, float *fl, double *partials, cudaStream_t st);
+// f = scale sum_l (F_l(+l) - F_l(-l)), u = fld; partials of f
+int dfs_div_rhs(int n, double scale, const double *Fx, const double *Fy, const double *Fz, const double *fld,
+                float *uh, float *ul, float *fh, float *fl, double *partials, cudaStream_t st);
+// f = scale sum_l ((A^{comp l} w)(+l) - (A^{comp l} w)(-l)), u = fld; partials of f
+int dfs_shift_rhs(int n, double scale, const float *A, const float *wh, const float *wl, int comp, const double *fld,
+                  float *uh, float *ul, float *fh, float *fl, double *partials, cudaStream_t st);
+// A_ij (12 n^3 floats: component c hi at A + 2c n^3, lo at A + (2c+1) n^3) and AA pairs, natural layout;
+// scratch: four arrays of 2 n^3 floats for the pairs of V_x, V_y, V_z, U
+void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy, const double *Vz, const double *U,
+             float *const scratch[4], float *A, float *AAh, float *AAl, cudaStream_t st);
+// psi: u = psi - 1, a = s0, b = AA, f = 0; partials of s0
+int dfs_psi(int n, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh, float *ul,
+            float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials, cudaStream_t st);
+// alpha psi: u = alpha psi - 1, a = m, f = m - psi^5 Kdot, m32, inv32; partials of psi^5 Kdot
+int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const double *s0, const double *sig,
+             const float *AAh, const float *AAl, double K2, double Kdot, float *uh, float *ul, float *ah, float *al,
+             float *fh, float *fl, float *m32, float *inv32, double *partials, cudaStream_t st);
+// w = alpha psi psi^-7 pairs, natural layout
+void dfs_weight(int n, const double *psi, const double *apsi, float *wh, float *wl, cudaStream_t st);
+// out (natural) = hi + lo - sum[0]/n^3 (sum may be null) + (dev ? 1 : 0)
+void dfs_store(int n, const float *uh, const float *ul, const double *sum, int dev, double *out, cudaStream_t st);
 
 // ---- sources, coefficients, layouts (field_kernels.cu) ---------------------
 void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,

@@ -185,7 +185,11 @@ __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ 
 // k = 2K, 2K + 1, which are loaded once into registers.  In a fine row (i, j)
 // the value at k = 2K + c has colour (i + j + c) & 1 and half-index K - 1,
 // K, K or K + 1 for c = -1, 0, 1, 2.
-template <typename T, int KIND, int FAS>
+// RED = 1: right after a black Gauss-Seidel pass of a linear equation the
+// black cells' residuals are zero up to rounding, so only the four red
+// children are evaluated (the black ones count as zero in the average); the
+// loads that only black children need are then dead and dropped.
+template <typename T, int KIND, int FAS, int RED = 0>
 __global__ void __launch_bounds__(kBlock)
     k_resid_restrict(int lgf, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
                      const T *__restrict__ c1, T ih2, T rho, T *__restrict__ uc, T *__restrict__ fc,
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(kBlock)
                 const int row = (((2 * I + a) << lgf) + 2 * J + b) << lgc;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
+                    if (RED && ((a + b + c) & 1)) continue;
                     const int id = (((a + b + c) & 1) ? half : 0) + row + K;
                     const T uc0 = v[a + 1][b + 1][c + 1];
                     const T nb = v[a + 2][b + 1][c + 1] + v[a][b + 1][c + 1] + v[a + 1][b + 2][c + 1] +
@@ -265,49 +270,79 @@ __global__ void k_fas_diff(int64_t cnt, double *__restrict__ uc, const double *_
 }
 
 // ---------------------------------------------------------------- prolongation
-// One thread per coarse cell: the 27 coarse values around (I, J, K) give its
-// 8 children by separable trilinear interpolation (3/4 from the parent, 1/4
-// from the neighbour on the child's side, per axis).  The children of
-// (I, J, K) are at half-index K of the fine rows (2I + a, 2J + b), colour
-// (a + b + c) & 1, so consecutive threads write consecutive addresses.
+// One thread per pair of coarse cells K = 2Q, 2Q + 1 of coarse row (I, J):
+// the 3 x 3 coarse rows around it, at K - 1 .. K + 2, give the 16 children by
+// separable trilinear interpolation (3/4 from the parent, 1/4 from the
+// neighbour on the child's side, per axis).  The children lie at fine
+// k = 4Q .. 4Q + 3 of the fine rows (2I + a, 2J + b); per fine row the two
+// red and the two black children are adjacent half-indices 2Q, 2Q + 1 of
+// their colour, so each colour takes one two-element vector update.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
 {
-    const int lgc = lgf - 1, mc = (1 << lgc) - 1;
-    const int half = 1 << (3 * lgf - 1);
-    const int ncells = 1 << (3 * lgc);
+    using V2 = typename Vec2<T>::type;
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1, hc = lgc - 1, mq = (1 << hc) - 1;
+    const int halfc = 1 << (3 * lgc - 1), halff = 1 << (3 * lgf - 1);
     const T w0 = T(0.25), w1 = T(0.75);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
-        const int K = t & mc, J = (t >> lgc) & mc, I = t >> (2 * lgc);
-        const int Km = (K - 1) & mc, Kp = (K + 1) & mc;
-        T z[3][3][2];  // interpolated along k: children c = 0, 1
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < halfc; t += gridDim.x * blockDim.x) {
+        const int Q = t & mq, J = (t >> hc) & mc, I = t >> (hc + lgc);
+        const int Qm = (Q - 1) & mq, Qp = (Q + 1) & mq;
+        T z[3][3][4];  // interpolated along k: fine k = 4Q + m
 #pragma unroll
         for (int x = 0; x < 3; x++)
 #pragma unroll
             for (int y = 0; y < 3; y++) {
                 const int Ii = (I + x - 1) & mc, Jj = (J + y - 1) & mc;
-                const T cm = uc[sidx32(lgc, Ii, Jj, Km)];
-                const T c0 = uc[sidx32(lgc, Ii, Jj, K)];
-                const T cp = uc[sidx32(lgc, Ii, Jj, Kp)];
+                const int base = ((Ii << lgc) + Jj) << hc;
+                const int ce = ((Ii + Jj) & 1) ? halfc : 0;  // colour array of the even coarse k
+                const int co = halfc - ce;
+                const T cm = uc[co + base + Qm];   // K - 1 = 2Q - 1
+                const T c0 = uc[ce + base + Q];    // 2Q
+                const T c1 = uc[co + base + Q];    // 2Q + 1
+                const T cp = uc[ce + base + Qp];   // 2Q + 2
                 z[x][y][0] = w0 * cm + w1 * c0;
-                z[x][y][1] = w1 * c0 + w0 * cp;
+                z[x][y][1] = w1 * c0 + w0 * c1;
+                z[x][y][2] = w0 * c0 + w1 * c1;
+                z[x][y][3] = w1 * c1 + w0 * cp;
             }
 #pragma unroll
-        for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) {
+            T yv[3][4];  // along j
 #pragma unroll
-            for (int b = 0; b < 2; b++) {
-                const int row = (((2 * I + a) << lgf) + 2 * J + b) << lgc;
+            for (int x = 0; x < 3; x++)
 #pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    // along j, then along i
-                    T yv[3];
+                for (int m = 0; m < 4; m++)
+                    yv[x][m] = b ? (w1 * z[x][1][m] + w0 * z[x][2][m]) : (w0 * z[x][0][m] + w1 * z[x][1][m]);
 #pragma unroll
-                    for (int x = 0; x < 3; x++)
-                        yv[x] = b ? (w1 * z[x][1][c] + w0 * z[x][2][c]) : (w0 * z[x][0][c] + w1 * z[x][1][c]);
-                    const T val = a ? (w1 * yv[1] + w0 * yv[2]) : (w0 * yv[0] + w1 * yv[1]);
-                    u[(((a + b + c) & 1) ? half : 0) + row + K] += val;
-                }
+            for (int a = 0; a < 2; a++) {
+                T val[4];  // along i
+#pragma unroll
+                for (int m = 0; m < 4; m++) val[m] = a ? (w1 * yv[1][m] + w0 * yv[2][m]) : (w0 * yv[0][m] + w1 * yv[1][m]);
+                const int row = (((2 * I + a) << lgf) + 2 * J + b) << (lgf - 1);
+                // fine cell 4Q + m has colour (a + b + m) & 1 and half-index 2Q + (m >> 1)
+                const int p = (a + b) & 1;
+                V2 *red = reinterpret_cast<V2 *>(u + row + 2 * Q);
+                V2 *blk = reinterpret_cast<V2 *>(u + halff + row + 2 * Q);
+                V2 r = *red, k = *blk;
+                r.x += val[p];
+                r.y += val[2 + p];
+                k.x += val[1 - p];
+                k.y += val[3 - p];
+                *red = r;
+                *blk = k;
             }
+        }
     }
 }
 
@@ -408,30 +443,6 @@ __global__ void k_helm_invdiag(int64_t cnt, const T *__restrict__ c0, T *__restr
 }
 
 // ---------------------------------------------------------------- reductions
-__device__ __forceinline__ void block_sum2(double a, double b, double *out)
-{
-    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sa[w] = a;
-        sb[w] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tb = 0.0;
-        for (int q = 0; q < kBlock / 32; q++) {
-            ta += sa[q];
-            tb += sb[q];
-        }
-        out[2 * blockIdx.x] = ta;
-        out[2 * blockIdx.x + 1] = tb;
-    }
-}
-
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock)
     k_resid_norm(int lgn, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
@@ -451,22 +462,16 @@ __global__ void __launch_bounds__(kBlock)
     block_sum2(s2, su, partials);
 }
 
-__global__ void k_finalize(const double *__restrict__ partials, int nblk, double *__restrict__ out)
+__global__ void __launch_bounds__(kBlock) k_finalize(const double *__restrict__ partials, int nblk,
+                                                     double *__restrict__ out)
 {
-    // one warp, fixed summation order
+    // one block, fixed summation order: out[0], out[1] = block_sum2's slots of block 0
     double a = 0.0, b = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += 32) {
+    for (int q = threadIdx.x; q < nblk; q += kBlock) {
         a += partials[2 * q];
         b += partials[2 * q + 1];
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    if (threadIdx.x == 0) {
-        out[0] = a;
-        out[1] = b;
-    }
+    block_sum2(a, b, out);
 }
 
 // ---------------------------------------------------------------- mixed precision
@@ -552,6 +557,19 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
         GR_LAUNCH((k_resid_restrict<T, KPSI, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
 }
 
+void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
+                        float *rc, cudaStream_t st)
+{
+    const int lgf = log2i(nf);
+    const int g = grid_for((int64_t)nf * nf * nf / 8);
+    if (kind == KPOISSON)
+        GR_LAUNCH((k_resid_restrict<float, KPOISSON, 0, 1>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f,
+                  ec, rc, nullptr);
+    else
+        GR_LAUNCH((k_resid_restrict<float, KHELM, 0, 1>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec,
+                  rc, nullptr);
+}
+
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
              cudaStream_t st)
 {
@@ -567,7 +585,7 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
 {
-    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf / 8), kBlock, st, log2i(nf), u, uc);
+    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u, uc);
 }
 
 template <typename T>
@@ -621,7 +639,7 @@ int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1
 
 void finalize(const double *partials, int nblk, double *out, cudaStream_t st)
 {
-    GR_LAUNCH(k_finalize, 1, 32, st, partials, nblk, out);
+    GR_LAUNCH(k_finalize, 1, kBlock, st, partials, nblk, out);
 }
 
 int mixed_resid(int kind, int n, const double *u, const double *f, const double *c0, const double *c1, double ih2,
