@@ -89,6 +89,18 @@ __device__ __forceinline__ df df_recip(df a)
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// The FP64 versions of the split and the join, for the rare operands outside
+// the integer paths' range.  Not inlined: as inline code the compiler may
+// predicate them into the common path, where their FP64 conversions would
+// occupy GB300's narrow FP64 pipe on every element.
+static __device__ __noinline__ df split_double_fp64(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+static __device__ __noinline__ double join_double_fp64(df v) { return (double)v.hi + (double)v.lo; }
+
 // Split a double into hi + lo FP32 with integer operations only (GB300's
 // FP64 and conversion pipes are slow): hi keeps the sign, the exponent and the
 // top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32
@@ -102,10 +114,7 @@ __device__ __forceinline__ df split_double(double x)
     const unsigned hi32 = (unsigned)__double2hiint(x), lo32 = (unsigned)__double2loint(x);
     if (((hi32 << 1) | lo32) == 0u) return {__uint_as_float(hi32), 0.0f};  // +-0
     const int ex = (int)((hi32 >> 20) & 0x7ffu) - 1023;
-    if ((unsigned)(ex + 74) > 201u) {  // ex < -74 or ex > 127
-        const float h = (float)x;
-        return {h, (float)(x - (double)h)};
-    }
+    if ((unsigned)(ex + 74) > 201u) return split_double_fp64(x);  // ex < -74 or ex > 127
     const unsigned sign = hi32 & 0x80000000u;
     // top 23 stored mantissa bits: 20 from hi32, 3 from lo32
     const unsigned hib = sign | ((unsigned)(ex + 127) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
@@ -115,37 +124,40 @@ __device__ __forceinline__ df split_double(double x)
     return fast_two_sum(__uint_as_float(hib), lo);
 }
 
-// hi + lo rounded to the nearest double, with integer operations only: both
-// significands are placed in one 64-bit integer in units of 2^-38 ulp(hi),
-// added or subtracted, and the sum is rounded to 53 bits (ties to even).  Bits
-// of lo below 2^-38 ulp(hi) are dropped first, so in rare near-tie cases the
-// result can differ from the correctly rounded one by one unit in the last
-// place.  Needs a renormalised pair (|lo| <= ulp(hi)/2, as fast_two_sum
-// leaves it) and a normal, finite hi; anything else takes the FP64 sum.
+// hi + lo rounded to the nearest double (ties to even), with 32-bit integer
+// operations only: lo, which lies below one unit in the last place of hi, is
+// rounded to a whole number of units in the last place of double(hi) (at
+// most 2^29 of them) and added to or subtracted from double(hi)'s bit
+// pattern; the sum cannot leave hi's binade except upwards onto the next
+// power of two, which the bit pattern carries correctly.  Needs |lo| < ulp(hi)
+// (a renormalised pair) and a normal, finite hi; a power-of-two hi with lo
+// of the other sign (the sum would drop a binade) and anything else take the
+// FP64 sum.
 __device__ __forceinline__ double join_double(df v)
 {
     const unsigned bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
     const int e1 = (int)((bh >> 23) & 0xffu), e2 = (int)((bl >> 23) & 0xffu);
-    const int d = e1 - (e2 ? e2 : 1);  // lo is below 2^(24 - d) ulp(hi)
-    if (e1 == 0 || e1 == 255 || e2 == 255 || d < 24) return (double)v.hi + (double)v.lo;
-    const unsigned long long m1 = (unsigned long long)((bh & 0x7fffffu) | 0x800000u);
-    const unsigned long long m2 = (unsigned long long)((bl & 0x7fffffu) | (e2 ? 0x800000u : 0u));
-    const int sh = 38 - d;  // <= 14
-    const unsigned long long x2 = sh >= 0 ? (m2 << sh) : (-sh < 64 ? (m2 >> -sh) : 0ull);
-    const unsigned long long x1 = m1 << 38;  // in [2^61, 2^62)
-    const unsigned long long x = ((bh ^ bl) >> 31) ? x1 - x2 : x1 + x2;  // value = x 2^(e1 - 188)
-    const int s = 63 - __clzll((long long)x) - 52;  // 8, 9 or 10
-    unsigned long long m = x >> s;
-    const unsigned long long rem = x & ((1ull << s) - 1ull), half = 1ull << (s - 1);
-    if (rem > half || (rem == half && (m & 1ull))) ++m;
-    int k = e1 - 188 + s;  // value = m 2^k
-    if (m >> 53) {
-        m >>= 1;
-        ++k;
+    const unsigned mh = bh & 0x7fffffu;
+    const int d = e1 - (e2 ? e2 : 1);  // lo < 2^(24 - d) ulp(hi)
+    const bool opp = ((bh ^ bl) >> 31) != 0u && (bl << 1) != 0u;
+    if (e1 == 0 || e1 == 255 || e2 == 255 || d < 24 || (opp && mh == 0u)) return join_double_fp64(v);
+    // double(hi): exponent e1 - 127 + 1023, stored mantissa mh << 29
+    const unsigned long long P = ((unsigned long long)((bh & 0x80000000u) | ((unsigned)(e1 + 896) << 20) | (mh >> 3))
+                                  << 32) |
+                                 (unsigned long long)(mh << 29);
+    // lo = m2 2^(29 - d) units of ulp(double(hi))
+    const unsigned m2 = (bl & 0x7fffffu) | (e2 ? 0x800000u : 0u);
+    const int sh = d - 29;
+    unsigned r;
+    if (sh <= 0) {
+        r = m2 << (-sh);
+    } else if (sh >= 25) {
+        r = 0u;
+    } else {
+        const unsigned fm = m2 >> sh, rem = m2 & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        r = fm + ((rem > half || (rem == half && (fm & 1u))) ? 1u : 0u);
     }
-    const unsigned long long bits = ((unsigned long long)(bh >> 31) << 63) |
-                                    ((unsigned long long)(k + 52 + 1023) << 52) | (m & ((1ull << 52) - 1ull));
-    return __longlong_as_double((long long)bits);
+    return __longlong_as_double((long long)(opp ? P - r : P + r));
 }
 
 // host-side split of a double constant into a double-float

@@ -28,23 +28,33 @@ inline int log2i(int n)
     return l;
 }
 
-// L(u) - f at one cell from the compensated neighbour sum (Sum2 of Ogita,
-// Rump and Oishi 2005: the high parts through a two-sum chain, the chain's
-// errors and all low parts added in FP32, which suffices since they are
-// 2^-24 smaller).  nh/nl: the six neighbours' high and low parts.
+// h^2 (L(u) - f) at one cell from the compensated sum of the seven stencil
+// terms and -h^2 f (Sum2 of Ogita, Rump and Oishi 2005: the high parts
+// through a two-sum chain, the chain's errors and all low parts added in
+// FP32, which suffices since they are 2^-24 smaller).  The right-hand side and
+// the coefficients arrive premultiplied by h^2 (f' = h^2 f; KHELM a' = h^2 m;
+// KPSI a' = 2 pi h^2 s0, b' = h^2 AA / 8, cpr = 2 pi rho h^2), so no
+// double-float scaling by 1/h^2 is needed; nh/nl are the six neighbours'
+// high and low parts.  KPSI also returns h^2 times the Newton coefficient and
+// 1/(6 + h^2 m).
 template <int KIND>
-__device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df f, df a, df b, df ih2, df two_pi,
-                                      df two_pi_rho, float rho10pi, float h2, float *mj_out, float *inv_out)
+__device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df f, df a, df b, df cpr, float c5,
+                                      float *mj_out, float *inv_out)
 {
     const df p6 = two_prod(u.hi, -6.0f);
     float s = p6.hi, sig = __fmaf_rn(u.lo, -6.0f, p6.lo);
+    {
+        const df q = two_sum(s, -f.hi);
+        s = q.hi;
+        sig = __fadd_rn(sig, __fsub_rn(q.lo, f.lo));
+    }
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const df q = two_sum(s, nh[k]);
         s = q.hi;
         sig = __fadd_rn(sig, __fadd_rn(q.lo, nl[k]));
     }
-    df e = df_mul(fast_two_sum(s, sig), ih2);
+    df e = fast_two_sum(s, sig);
     if (KIND == KHELM) {
         e = df_sub(e, df_mul(a, u));
     } else if (KIND == KPSI) {
@@ -52,14 +62,14 @@ __device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df
         const df iv = df_recip(v);
         const df iv2 = df_mul(iv, iv), iv4 = df_mul(iv2, iv2);
         const df v2 = df_mul(v, v), v4 = df_mul(v2, v2);
-        e = df_add(e, df_mul(df_mul(a, iv), two_pi));
-        e = df_add(e, df_mulf(df_mul(b, df_mul(df_mul(iv4, iv2), iv)), 0.125f));
-        e = df_sub(e, df_mul(df_mul(v4, v), two_pi_rho));
-        const float mj = two_pi.hi * a.hi * iv2.hi + 0.875f * b.hi * (iv4.hi * iv4.hi) + rho10pi * v4.hi;
-        *mj_out = mj;
-        *inv_out = 1.0f / (6.0f + h2 * mj);
+        e = df_add(e, df_mul(a, iv));
+        e = df_add(e, df_mul(b, df_mul(df_mul(iv4, iv2), iv)));
+        e = df_sub(e, df_mul(df_mul(v4, v), cpr));
+        const float mjh2 = a.hi * iv2.hi + 7.0f * b.hi * (iv4.hi * iv4.hi) + c5 * v4.hi;
+        *mj_out = mjh2;
+        *inv_out = 1.0f / (6.0f + mjh2);
     }
-    return df_sub(e, f);
+    return e;
 }
 
 // eps = L(u) - f on the finest level; writes r32 = -eps and, for the psi
@@ -68,15 +78,14 @@ __device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df
 // there: each needs the other colour at the same q in rows (i +- 1, j),
 // (i, j +- 1) and at q, q +- 1 in its own row, so every array element is
 // read once as a cell and, close in time, as its neighbours' neighbour.
-// Block partials: sum of (eps / ref)^2.
+// f, a, b: the h^2-premultiplied pairs of df_cell.
 template <int KIND>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, KIND == KPOISSON ? 5 : (KIND == KHELM ? 4 : 3))
     k_df_resid(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const float *__restrict__ fh,
                const float *__restrict__ fl, const float *__restrict__ ah, const float *__restrict__ al,
-               const float *__restrict__ bh, const float *__restrict__ bl, df ih2, df two_pi, df two_pi_rho,
-               float rho10pi, float h2, float inv_ref, float *__restrict__ r32, float *__restrict__ m32,
-               float *__restrict__ inv32, const float *__restrict__ inv_in, float *__restrict__ e32,
-               double *__restrict__ partials)
+               const float *__restrict__ bh, const float *__restrict__ bl, df cpr, float c5, float ih2,
+               float ih2_ref, float *__restrict__ r32, float *__restrict__ m32, float *__restrict__ inv32,
+               const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials)
 {
     // Two neighbouring half-indices q0, q0 + 1 of one row per thread (float2
     // loads), both colours: four cells.  32-bit offsets: grids up to 1024^3.
@@ -128,7 +137,7 @@ __global__ void __launch_bounds__(kBlock)
                 b2l = *reinterpret_cast<const float2 *>(bl + own);
             }
             float mj[2] = {0.0f, 0.0f}, iv[2] = {0.0f, 0.0f};
-            float rr[2];
+            float rr[2], sh[2];
 #pragma unroll
             for (int e = 0; e < 2; e++) {
                 float h6[6], l6[6];
@@ -149,31 +158,27 @@ __global__ void __launch_bounds__(kBlock)
                 const df f = {e ? f2h.y : f2h.x, e ? f2l.y : f2l.x};
                 const df a = {e ? a2h.y : a2h.x, e ? a2l.y : a2l.x};
                 const df b = {e ? b2h.y : b2h.x, e ? b2l.y : b2l.x};
-                const df r = df_cell<KIND>(h6, l6, u, f, a, b, ih2, two_pi, two_pi_rho, rho10pi, h2, &mj[e], &iv[e]);
-                rr[e] = -(r.hi + r.lo);
-                const float z = r.hi * inv_ref;
+                const df r = df_cell<KIND>(h6, l6, u, f, a, b, cpr, c5, &mj[e], &iv[e]);  // h^2 eps
+                sh[e] = r.hi + r.lo;
+                rr[e] = -sh[e] * ih2;
+                const float z = r.hi * ih2_ref;
                 acc = __fmaf_rn(z, z, acc);
             }
             *reinterpret_cast<float2 *>(r32 + own) = make_float2(rr[0], rr[1]);
             if (KIND == KPSI) {
-                *reinterpret_cast<float2 *>(m32 + own) = make_float2(mj[0], mj[1]);
+                *reinterpret_cast<float2 *>(m32 + own) = make_float2(mj[0] * ih2, mj[1] * ih2);
                 *reinterpret_cast<float2 *>(inv32 + own) = make_float2(iv[0], iv[1]);
             }
             if (c == 0 && e32) {
-                float2 d;
-                if (KIND == KPOISSON) {
-                    d = make_float2(-h2 * rr[0] * (1.0f / 6.0f), -h2 * rr[1] * (1.0f / 6.0f));
-                } else if (KIND == KHELM) {
-                    const float2 g = *reinterpret_cast<const float2 *>(inv_in + own);
-                    d = make_float2(-h2 * rr[0] * g.x, -h2 * rr[1] * g.y);
-                } else {
-                    d = make_float2(-h2 * rr[0] * iv[0], -h2 * rr[1] * iv[1]);
-                }
-                *reinterpret_cast<float2 *>(e32 + own) = d;
+                float2 g;
+                if (KIND == KPOISSON) g = make_float2(1.0f / 6.0f, 1.0f / 6.0f);
+                else if (KIND == KHELM) g = *reinterpret_cast<const float2 *>(inv_in + own);
+                else g = make_float2(iv[0], iv[1]);
+                *reinterpret_cast<float2 *>(e32 + own) = make_float2(sh[0] * g.x, sh[1] * g.y);
             }
         }
     }
-    block_sum2((double)acc, 0.0, partials);
+    block_sum2f(acc, 0.0f, partials);
 }
 
 // (hi, lo) + e, renormalised
@@ -253,25 +258,23 @@ __global__ void __launch_bounds__(kBlock)
 }  // namespace
 
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
-             const float *al, const float *bh, const float *bl, double ih2, double rho, double h2, double ref,
-             float *r32, float *m32, float *inv32, const float *inv_in, float *e32, double *partials,
-             cudaStream_t st)
+             const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
     int g = grid_for((int64_t)n * n * n / 4);
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
-    const df dih2 = df_from_double_host(ih2), d2pi = df_from_double_host(2.0 * kPi),
-             d2pr = df_from_double_host(2.0 * kPi * rho);
-    const float r10 = (float)(10.0 * kPi * rho), fh2 = (float)h2, iref = (float)(1.0 / ref);
+    const df cpr = df_from_double_host(2.0 * kPi * rho * h2);
+    const float c5 = (float)(10.0 * kPi * rho * h2), ih2 = (float)(1.0 / h2), ih2_ref = (float)(1.0 / (h2 * ref));
     if (kind == KPOISSON)
-        GR_LAUNCH(k_df_resid<KPOISSON>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10,
-                  fh2, iref, r32, m32, inv32, inv_in, e32, partials);
+        GR_LAUNCH(k_df_resid<KPOISSON>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref,
+                  r32, m32, inv32, inv_in, e32, partials);
     else if (kind == KHELM)
-        GR_LAUNCH(k_df_resid<KHELM>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10, fh2,
-                  iref, r32, m32, inv32, inv_in, e32, partials);
+        GR_LAUNCH(k_df_resid<KHELM>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32,
+                  m32, inv32, inv_in, e32, partials);
     else
-        GR_LAUNCH(k_df_resid<KPSI>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, dih2, d2pi, d2pr, r10, fh2,
-                  iref, r32, m32, inv32, inv_in, e32, partials);
+        GR_LAUNCH(k_df_resid<KPSI>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32,
+                  m32, inv32, inv_in, e32, partials);
     return g;
 }
 

@@ -86,9 +86,33 @@ struct Acc {
         s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, x.lo));
         q = __fmaf_rn(x.hi, x.hi, q);
     }
+    // block partials: the warp sums in double-float (FP32) arithmetic, the
+    // eight warp totals in FP64
     __device__ __forceinline__ void flush(double *partials) const
     {
-        block_sum2((double)s.hi + (double)s.lo, (double)q, partials);
+        __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+        df a = s;
+        float b = q;
+        for (int o = 16; o > 0; o >>= 1) {
+            const df t = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+            a = df_add(a, t);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) {
+            sa[w] = (double)a.hi + (double)a.lo;
+            sb[w] = (double)b;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0, tb = 0.0;
+            for (int k = 0; k < kBlock / 32; k++) {
+                ta += sa[k];
+                tb += sb[k];
+            }
+            partials[2 * blockIdx.x] = ta;
+            partials[2 * blockIdx.x + 1] = tb;
+        }
     }
 };
 
@@ -135,7 +159,7 @@ struct PoissonArgs {
 };
 
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
+__global__ void __launch_bounds__(kBlock, 3) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
 {
     const int mn = (1 << lgn) - 1;
     const int64_t N = (int64_t)1 << (3 * lgn);
@@ -262,12 +286,13 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // ---------------------------------------------------------------- psi, alpha psi
-// psi (Eq. MG-nonlinear): unknown psi - 1, c0 = s0, c1 = AA, f = 0; sums of s0^2
+// psi (Eq. MG-nonlinear): unknown psi - 1, a' = 2 pi h^2 s0, b' = h^2 AA / 8,
+// f = 0 (the premultiplied coefficients of the residual kernel); sums of s0^2
 __global__ void __launch_bounds__(kBlock)
-    k_dfs_psi(int lgn, const double *__restrict__ psi, const double *__restrict__ s0, const float *__restrict__ AAh,
-              const float *__restrict__ AAl, float *__restrict__ uh, float *__restrict__ ul, float *__restrict__ ah,
-              float *__restrict__ al, float *__restrict__ bh, float *__restrict__ bl, float *__restrict__ fh,
-              float *__restrict__ fl, double *partials)
+    k_dfs_psi(int lgn, df a_scale, df b_scale, const double *__restrict__ psi, const double *__restrict__ s0,
+              const float *__restrict__ AAh, const float *__restrict__ AAl, float *__restrict__ uh,
+              float *__restrict__ ul, float *__restrict__ ah, float *__restrict__ al, float *__restrict__ bh,
+              float *__restrict__ bl, float *__restrict__ fh, float *__restrict__ fl, double *partials)
 {
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df m1 = {-1.0f, 0.0f};
@@ -280,8 +305,8 @@ __global__ void __launch_bounds__(kBlock)
             const int64_t id = nat(lgn, p.i, p.j, p.k0 + e), sid = p.split(e);
             const df s = ld(s0, id);
             stp(uh, ul, sid, df_add_acc(ld(psi, id), m1));
-            stp(ah, al, sid, s);
-            stp(bh, bl, sid, ldp(AAh, AAl, id));
+            stp(ah, al, sid, df_mul(s, a_scale));
+            stp(bh, bl, sid, df_mul(ldp(AAh, AAl, id), b_scale));
             stp(fh, fl, sid, df{0.0f, 0.0f});
             acc.add(s);
         }
@@ -292,10 +317,10 @@ __global__ void __launch_bounds__(kBlock)
 // lapse equation for phi = alpha psi (Eq. sol-scheme-CMC with s = psi^-4 sigma),
 // unknown phi - 1:  lap(phi - 1) - m (phi - 1) = m - psi^5 Kdot, with
 // m = 2 pi psi^-2 (s0 + 2 sigma psi^-4) + 7/8 AA psi^-8 + 5/12 K^2 psi^4.
-// Writes u, c0 = m and f as pairs, m and 1/(6 + h^2 m) in FP32; sums of
-// (psi^5 Kdot)^2.  k2c = 5/12 K^2.
+// Writes u, a' = h^2 m and f' = h^2 (m - psi^5 Kdot) as pairs, m and
+// 1/(6 + h^2 m) in FP32; sums of (psi^5 Kdot)^2.  k2c = 5/12 K^2.
 __global__ void __launch_bounds__(kBlock)
-    k_dfs_apsi(int lgn, float h2, const double *__restrict__ psi, const double *__restrict__ apsi,
+    k_dfs_apsi(int lgn, float h2, df h2d, const double *__restrict__ psi, const double *__restrict__ apsi,
                const double *__restrict__ s0, const double *__restrict__ sig, const float *__restrict__ AAh,
                const float *__restrict__ AAl, df two_pi, df k2c, df kdot, float *__restrict__ uh,
                float *__restrict__ ul, float *__restrict__ ah, float *__restrict__ al, float *__restrict__ fh,
@@ -319,8 +344,8 @@ __global__ void __launch_bounds__(kBlock)
                                  df_mul(p4, k2c));
             const df src = df_mul(p5, kdot);
             stp(uh, ul, sid, df_add_acc(ld(apsi, id), m1));
-            stp(ah, al, sid, mm);
-            stp(fh, fl, sid, df_add(mm, df_neg(src)));
+            stp(ah, al, sid, df_mul(mm, h2d));
+            stp(fh, fl, sid, df_mul(df_add(mm, df_neg(src)), h2d));
             m32[sid] = mm.hi;
             inv32[sid] = 1.0f / (6.0f + h2 * mm.hi);
             acc.add(src);
@@ -449,12 +474,14 @@ void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy
               scratch[0], scratch[1], scratch[2], scratch[3], A, AAh, AAl);
 }
 
-int dfs_psi(int n, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh, float *ul,
-            float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials, cudaStream_t st)
+int dfs_psi(int n, double h2, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh,
+            float *ul, float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials,
+            cudaStream_t st)
 {
     const int lgn = log2i(n);
     const int g = grid_for((int64_t)n * n * n / 2);
-    GR_LAUNCH(k_dfs_psi, g, kBlock, st, lgn, psi, s0, AAh, AAl, uh, ul, ah, al, bh, bl, fh, fl, partials);
+    GR_LAUNCH(k_dfs_psi, g, kBlock, st, lgn, df_from_double_host(2.0 * kPi * h2), df_from_double_host(0.125 * h2),
+              psi, s0, AAh, AAl, uh, ul, ah, al, bh, bl, fh, fl, partials);
     return g;
 }
 
@@ -464,7 +491,7 @@ int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const doub
 {
     const int lgn = log2i(n);
     const int g = grid_for((int64_t)n * n * n / 2);
-    GR_LAUNCH(k_dfs_apsi, g, kBlock, st, lgn, (float)h2, psi, apsi, s0, sig, AAh, AAl,
+    GR_LAUNCH(k_dfs_apsi, g, kBlock, st, lgn, (float)h2, df_from_double_host(h2), psi, apsi, s0, sig, AAh, AAl,
               df_from_double_host(2.0 * kPi), df_from_double_host(5.0 / 12.0 * K2), df_from_double_host(Kdot), uh,
               ul, ah, al, fh, fl, m32, inv32, partials);
     return g;

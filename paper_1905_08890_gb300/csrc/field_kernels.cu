@@ -51,45 +51,55 @@ __device__ __forceinline__ double at(const double *__restrict__ f, int lgn, int 
 
 // ---------------------------------------------------------------- CIC deposit
 // Sec. 4.1.2: the particle at x_p lies between centres x_i <= x_p < x_{i+1};
-// cell i takes f+ = (x_{i+1} - x_p)/h, cell i+1 takes 1 - f+.
+// cell i takes f+ = (x_{i+1} - x_p)/h, cell i+1 takes 1 - f+.  The kernel is
+// bound by GB300's FP64 pipe, so it keeps FP64 operations few: the periodic
+// wrap is folded into the integer cell index (t = x/h - 1/2 shifted by a
+// multiple of n changes f+ only by rounding), one reciprocal square root gives
+// both W = sqrt(1 + u^2) and u^2/W, and the eight corner weights are formed
+// once and shared by the five quantities.
 __global__ void __launch_bounds__(kBlock)
-    k_deposit(int lgn, double L, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u,
-              double q, double *__restrict__ s0, double *__restrict__ sx, double *__restrict__ sy,
-              double *__restrict__ sz, double *__restrict__ sig)
+    k_deposit(int lgn, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u, double q,
+              double *__restrict__ s0, double *__restrict__ sx, double *__restrict__ sy, double *__restrict__ sz,
+              double *__restrict__ sig)
 {
     const int m = (1 << lgn) - 1;
-    const double invL = 1.0 / L;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
         int lo[3];
-        double fp[3];
+        double fw[3][2];  // weights of the lower and the upper cell per axis
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            double xp = x[d * np + p];
-            xp -= L * floor(xp * invL);
-            const double t = xp * invh - 0.5;
+            const double t = fma(x[d * np + p], invh, -0.5);
             const double fl = floor(t);
-            fp[d] = 1.0 - (t - fl);
-            lo[d] = ((int)fl) & m;
+            const double fr = t - fl;
+            fw[d][0] = 1.0 - fr;
+            fw[d][1] = fr;
+            lo[d] = (int)((long long)fl & m);
         }
         const double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
-        const double u2 = ux * ux + uy * uy + uz * uz;
-        const double W = sqrt(1.0 + u2);
-        const double q0 = q * W, qx = q * ux, qy = q * uy, qz = q * uz, qs = q * u2 / W;
+        const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+        const double w2 = 1.0 + u2;
+        const double rw = rsqrt(w2);  // 1/W
+        const double Q[5] = {q * (w2 * rw), q * ux, q * uy, q * uz, (q * u2) * rw};
+        double* const out[5] = {s0, sx, sy, sz, sig};
+        double w[8];
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
             for (int b = 0; b < 2; b++) {
-                const double wab = (a ? 1.0 - fp[0] : fp[0]) * (b ? 1.0 - fp[1] : fp[1]);
+                const double wab = fw[0][a] * fw[1][b];
+                w[4 * a + 2 * b] = wab * fw[2][0];
+                w[4 * a + 2 * b + 1] = wab * fw[2][1];
+            }
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
                 const int64_t row = (((int64_t)((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m)) << lgn;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const double w = wab * (c ? 1.0 - fp[2] : fp[2]);
                     const int64_t id = row + ((lo[2] + c) & m);
-                    atomicAdd(s0 + id, q0 * w);
-                    atomicAdd(sx + id, qx * w);
-                    atomicAdd(sy + id, qy * w);
-                    atomicAdd(sz + id, qz * w);
-                    atomicAdd(sig + id, qs * w);
+#pragma unroll
+                    for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, Q[k] * w[4 * a + 2 * b + c]);
                 }
             }
     }
@@ -286,7 +296,12 @@ void deposit(int n, double L, int64_t np, const double *x, const double *u, doub
     if (np <= 0) return;
     const double h = L / n;
     const double q = mass / (h * h * h);
-    GR_LAUNCH(k_deposit, grid_for(np), kBlock, st, log2i(n), L, 1.0 / h, np, x, u, q, s0, sx, sy, sz, sig);
+    // one thread per particle, no grid-stride loop: blocks start in index
+    // order, so the particles in flight stay a contiguous index window and,
+    // for lattice-ordered particles, their cells a few planes that L2 holds
+    const int64_t blocks = (np + kBlock - 1) / kBlock;
+    const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
+    GR_LAUNCH(k_deposit, g, kBlock, st, log2i(n), 1.0 / h, np, x, u, q, s0, sx, sy, sz, sig);
 }
 
 int sum_sq(int64_t cnt, const double *a, double *partials, cudaStream_t st)

@@ -298,7 +298,8 @@ gr_status setup_eq(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, 
 
 // Double-float set-up of equation eq: unknown, right-hand side and
 // coefficients as split-layout pairs in dfu, dff, dfa, dfb (and, for alpha psi,
-// lev[fine].m and .inv), from the natural FP64 sources and fields.  The same
+// lev[fine].m and .inv), from the natural FP64 sources and fields; the
+// right-hand side and coefficients premultiplied by h^2 as df_resid takes them.  The same
 // equations as setup_eq; the Poisson right-hand sides lose their mean once in
 // double-float, which leaves it at the double-float rounding level.
 gr_status setup_eq_df(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *fl, double rho, double S_hat,
@@ -330,14 +331,15 @@ gr_status setup_eq_df(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *f
         // lap V_i = 8 pi (s_i - <s_i>)  (Eq. MG-linear-1a; mean removal of Sec. 4.3.1)
         g = gr::dfs_sum(N, s->s[eq], c->partials, c->st);
         gr::finalize(c->partials, g, c->dscal, c->st);
-        g = gr::dfs_mean_rhs(n, s->s[eq], c->dscal, 8.0 * kPi, fld, uh, ul, fh, fl_, c->partials, c->st);
+        g = gr::dfs_mean_rhs(n, s->s[eq], c->dscal, 8.0 * kPi * F.h2, fld, uh, ul, fh, fl_, c->partials, c->st);
     } else if (eq == GR_U || eq == GR_B_SCALAR) {
         // lap U = -1/4 div V ; lap b = -1/4 div B  (Eqs. MG-linear-1, MG-linear-2)
         double *const *Fv = eq == GR_U ? fl->V : fl->B;
-        g = gr::dfs_div_rhs(n, -0.25 * (0.5 / c->h), Fv[0], Fv[1], Fv[2], fld, uh, ul, fh, fl_, c->partials, c->st);
+        g = gr::dfs_div_rhs(n, -0.25 * (0.5 / c->h) * F.h2, Fv[0], Fv[1], Fv[2], fld, uh, ul, fh, fl_, c->partials,
+                            c->st);
     } else if (eq == GR_PSI) {
         aij();
-        g = gr::dfs_psi(n, fl->psi, s->s0, AAh, AAl, uh, ul, c->dfa, c->dfa + N, c->dfb, c->dfb + N, fh, fl_,
+        g = gr::dfs_psi(n, F.h2, fl->psi, s->s0, AAh, AAl, uh, ul, c->dfa, c->dfa + N, c->dfb, c->dfb + N, fh, fl_,
                         c->partials, c->st);
     } else if (eq == GR_APSI) {
         aij();
@@ -348,16 +350,16 @@ gr_status setup_eq_df(gr_ctx *c, int eq, const gr_sources *s, const gr_fields *f
         aij();
         if (c->w_fmt != 2) gr::dfs_weight(n, fl->psi, fl->apsi, wh, wl, c->st);
         c->w_fmt = 2;
-        g = gr::dfs_shift_rhs(n, 2.0 * (0.5 / c->h), A, wh, wl, eq - GR_BX, fld, uh, ul, fh, fl_, c->partials,
-                              c->st);
+        g = gr::dfs_shift_rhs(n, 2.0 * (0.5 / c->h) * F.h2, A, wh, wl, eq - GR_BX, fld, uh, ul, fh, fl_,
+                              c->partials, c->st);
     }
     gr::finalize(c->partials, g, c->dscal, c->st);
     double a, q;
     gr_status st = read_scalars(c, &a, &q);
     if (st != GR_OK) return st;
-    if (info->poisson) {
+    if (info->poisson) {  // the sums are of h^2 f
         const double mean = a / N;
-        info->ref = std::sqrt(std::fmax(q / N - mean * mean, 0.0));
+        info->ref = std::sqrt(std::fmax(q / N - mean * mean, 0.0)) / F.h2;
     } else {
         info->ref = (eq == GR_PSI ? 2.0 * kPi : 1.0) * std::sqrt(q / N);
     }
@@ -528,8 +530,8 @@ gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r)
     int g = 0;
     timed(c, GR_PROF_MIXED_RESID, [&] {
         g = gr::df_resid(in.kind, F.n, c->dfu, c->dfu + N, c->dff, c->dff + N, c->dfa, c->dfa + N, c->dfb,
-                         c->dfb + N, F.ih2, rho, F.h2, in.ref, F.r, F.m, F.inv, F.inv, red ? F.e : nullptr,
-                         c->partials, c->st);
+                         c->dfb + N, F.h2, rho, in.ref, F.r, F.m, F.inv, F.inv, red ? F.e : nullptr, c->partials,
+                         c->st);
     });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;

@@ -70,6 +70,34 @@ __device__ __forceinline__ void block_sum2(double a, double b, double *out)
         out[2 * blockIdx.x + 1] = tb;
     }
 }
+
+// The same for FP32 inputs: warp sums in FP32 (for norms, where the rounding
+// of partial sums is harmless), the per-warp totals in FP64.  GB300's FP64
+// pipe is narrow enough that a full FP64 warp reduction per thread costs a
+// noticeable share of a memory-sized kernel.
+__device__ __forceinline__ void block_sum2f(float a, float b, double *out)
+{
+    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = (double)a;
+        sb[w] = (double)b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int q = 0; q < kBlock / 32; q++) {
+            ta += sa[q];
+            tb += sb[q];
+        }
+        out[2 * blockIdx.x] = ta;
+        out[2 * blockIdx.x + 1] = tb;
+    }
+}
 #endif
 
 // ---- multigrid kernels (templated on the working precision T) ---------------
@@ -145,14 +173,15 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
 // ---- double-float fine level (df_kernels.cu) -------------------------------
 // hi/lo = a split into FP32 pairs; a = hi + lo.
 // Fine residual in double-float: r32 = -eps, KPSI also m32/inv32 (Newton
-// coefficient and FP32 inverse diagonal); a = c0, b = c1 pairs.  When e32 is
-// not null it also writes the first red relaxation of the correction cycle
-// from e = 0 (inv_in: the KHELM inverse diagonal).  Partials: block sums of
-// (eps/ref)^2.  Returns the block count.
+// coefficient and FP32 inverse diagonal).  f, a = c0, b = c1 are pairs
+// premultiplied by h^2 (KPOISSON, KHELM: h^2 f, h^2 m; KPSI: f' = h^2 f,
+// a' = 2 pi h^2 s0, b' = h^2 AA / 8).  When e32 is not null it also writes the
+// first red relaxation of the correction cycle from e = 0 (inv_in: the KHELM
+// inverse diagonal).  Partials: block sums of (eps/ref)^2.  Returns the block
+// count.
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
-             const float *al, const float *bh, const float *bl, double ih2, double rho, double h2, double ref,
-             float *r32, float *m32, float *inv32, const float *inv_in, float *e32, double *partials,
-             cudaStream_t st);
+             const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st);
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st);
 // last black pass of the FP32 correction cycle (KPOISSON or KHELM, n >= 8)
 // fused with u += e on both colours; e's black half is left unwritten
@@ -160,7 +189,9 @@ void df_black_update(int kind, int n, const float *e, const float *r, const floa
                      float *ul, cudaStream_t st);
 
 // ---- double-float set-up and write-back (df_setup.cu) -----------------------
-// Natural FP64 inputs -> split-layout hi/lo pairs.  The int-returning ones
+// Natural FP64 inputs -> split-layout hi/lo pairs, right-hand sides and
+// coefficients premultiplied by h^2 as df_resid takes them (the callers pass
+// the scales with h^2 folded in).  The int-returning ones
 // leave block partials (sum, sum of squares of the high parts) of the
 // quantity named and return the block count for finalize().
 int dfs_sum(int64_t cnt, const double *a, double *partials, cudaStream_t st);                      // a
@@ -178,10 +209,11 @@ int dfs_shift_rhs(int n, double scale, const float *A, const float *wh, const fl
 // scratch: four arrays of 2 n^3 floats for the pairs of V_x, V_y, V_z, U
 void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy, const double *Vz, const double *U,
              float *const scratch[4], float *A, float *AAh, float *AAl, cudaStream_t st);
-// psi: u = psi - 1, a = s0, b = AA, f = 0; partials of s0
-int dfs_psi(int n, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh, float *ul,
-            float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials, cudaStream_t st);
-// alpha psi: u = alpha psi - 1, a = m, f = m - psi^5 Kdot, m32, inv32; partials of psi^5 Kdot
+// psi: u = psi - 1, a = 2 pi h^2 s0, b = h^2 AA / 8, f = 0; partials of s0
+int dfs_psi(int n, double h2, const double *psi, const double *s0, const float *AAh, const float *AAl, float *uh,
+            float *ul, float *ah, float *al, float *bh, float *bl, float *fh, float *fl, double *partials,
+            cudaStream_t st);
+// alpha psi: u = alpha psi - 1, a = h^2 m, f = h^2 (m - psi^5 Kdot), m32, inv32; partials of psi^5 Kdot
 int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const double *s0, const double *sig,
              const float *AAh, const float *AAl, double K2, double Kdot, float *uh, float *ul, float *ah, float *al,
              float *fh, float *fl, float *m32, float *inv32, double *partials, cudaStream_t st);
