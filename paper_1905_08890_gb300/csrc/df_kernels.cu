@@ -72,109 +72,136 @@ __device__ __forceinline__ df df_cell(const float *nh, const float *nl, df u, df
     return e;
 }
 
+// W consecutive floats (W = 2 or 4) as one vector access
+template <int W>
+__device__ __forceinline__ void ldv(const float *p, float (&v)[W])
+{
+    if (W == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void stv(float *p, const float (&v)[W])
+{
+    if (W == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// blocks per SM the residual kernel is compiled for (registers per thread)
+template <int KIND, int W>
+constexpr int resid_min_blocks()
+{
+    return W == 4 ? (KIND == KPSI ? 2 : 3) : (KIND == KPOISSON ? 5 : (KIND == KHELM ? 4 : 3));
+}
+
 // eps = L(u) - f on the finest level; writes r32 = -eps and, for the psi
 // kind, the Newton coefficient m32 = -dN/du with its FP32 inverse diagonal.
-// One thread per row position (i, j, q) handles the red and the black cell
-// there: each needs the other colour at the same q in rows (i +- 1, j),
-// (i, j +- 1) and at q, q +- 1 in its own row, so every array element is
-// read once as a cell and, close in time, as its neighbours' neighbour.
-// f, a, b: the h^2-premultiplied pairs of df_cell.
-template <int KIND>
-__global__ void __launch_bounds__(kBlock, KIND == KPOISSON ? 5 : (KIND == KHELM ? 4 : 3))
+// One thread per chunk of W consecutive half-indices q0 .. q0 + W - 1 of a row
+// (i, j) handles the red and the black cells there (2W cells): each needs the
+// other colour at the same half-indices in rows (i +- 1, j), (i, j +- 1) and
+// at q, q +- 1 in its own row, which are W-wide vector loads plus one scalar
+// for the own-row neighbour outside the chunk.  W = 4 (n >= 8) gives each
+// thread enough independent loads to keep HBM busy; W = 2 serves n = 4.
+// f, a, b: the h^2-premultiplied pairs of df_cell.  32-bit offsets: grids up
+// to 1024^3.  Also the first red relaxation of the FP32 correction cycle,
+// which starts from e = 0: e_red = -h^2 r / 6 (Poisson) or -h^2 r / (6 + h^2 m).
+template <int KIND, int W>
+__global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
     k_df_resid(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const float *__restrict__ fh,
                const float *__restrict__ fl, const float *__restrict__ ah, const float *__restrict__ al,
                const float *__restrict__ bh, const float *__restrict__ bl, df cpr, float c5, float ih2,
                float ih2_ref, float *__restrict__ r32, float *__restrict__ m32, float *__restrict__ inv32,
                const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials)
 {
-    // Two neighbouring half-indices q0, q0 + 1 of one row per thread (float2
-    // loads), both colours: four cells.  32-bit offsets: grids up to 1024^3.
-    // Also the first red relaxation of the FP32 correction cycle, which starts
-    // from e = 0: e_red = -h^2 r / 6 (Poisson) or -h^2 r / (6 + h^2 m).
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
-    for (int tp = blockIdx.x * blockDim.x + threadIdx.x; tp < (half >> 1); tp += gridDim.x * blockDim.x) {
-        const int t = tp << 1;  // even: q0 = t & mh
+    for (int tp = blockIdx.x * blockDim.x + threadIdx.x; tp < half / W; tp += gridDim.x * blockDim.x) {
+        const int t = tp * W;  // q0 = t & mh, a multiple of W
         const int q = t & mh;
         const int j = (t >> lgh) & mn;
         const int i = t >> (lgh + lgn);
         const int r0 = t - q;
         const int ri = j << lgh;
-        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri + q;
-        const int rim = (((i - 1) & mn) << (lgn + lgh)) + ri + q;
         const int rj = i << (lgn + lgh);
-        const int rjp = rj + (((j + 1) & mn) << lgh) + q;
-        const int rjm = rj + (((j - 1) & mn) << lgh) + q;
+        const int rows[5] = {(((i + 1) & mn) << (lgn + lgh)) + ri + q, (((i - 1) & mn) << (lgn + lgh)) + ri + q,
+                             rj + (((j + 1) & mn) << lgh) + q, rj + (((j - 1) & mn) << lgh) + q, t};
         const int pr = (i + j) & 1;  // k parity of the red cells in this row
-        // the own-row neighbour outside the pair: q0 + 2 (shift +1) or q0 - 1 (shift -1)
-        const int xp = r0 + ((q + 2) & mh), xm = r0 + ((q - 1) & mh);
+        // the own-row neighbour outside the chunk: q0 + W (shift +1) or q0 - 1 (shift -1)
+        const int xp = r0 + ((q + W) & mh), xm = r0 + ((q - 1) & mh);
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const int own = (c ? half : 0) + t;
             const int oth = c ? 0 : half;
             const int up = c ? !pr : pr;  // this colour's shift is +1 when its k parity is 1
-            float2 nh[5], nl[5];
-            const int rows[5] = {rip, rim, rjp, rjm, t};
+            float nh[5][W], nl[5][W];
 #pragma unroll
             for (int k = 0; k < 5; k++) {
-                nh[k] = *reinterpret_cast<const float2 *>(uh + oth + rows[k]);
-                nl[k] = *reinterpret_cast<const float2 *>(ul + oth + rows[k]);
+                ldv<W>(uh + oth + rows[k], nh[k]);
+                ldv<W>(ul + oth + rows[k], nl[k]);
             }
             const int xi = oth + (up ? xp : xm);
             const float xh = uh[xi], xl = ul[xi];
-            const float2 u2h = *reinterpret_cast<const float2 *>(uh + own);
-            const float2 u2l = *reinterpret_cast<const float2 *>(ul + own);
-            const float2 f2h = *reinterpret_cast<const float2 *>(fh + own);
-            const float2 f2l = *reinterpret_cast<const float2 *>(fl + own);
-            float2 a2h = {0.0f, 0.0f}, a2l = {0.0f, 0.0f}, b2h = {0.0f, 0.0f}, b2l = {0.0f, 0.0f};
+            float u_h[W], u_l[W], f_h[W], f_l[W], a_h[W] = {}, a_l[W] = {}, b_h[W] = {}, b_l[W] = {};
+            ldv<W>(uh + own, u_h);
+            ldv<W>(ul + own, u_l);
+            ldv<W>(fh + own, f_h);
+            ldv<W>(fl + own, f_l);
             if (KIND != KPOISSON) {
-                a2h = *reinterpret_cast<const float2 *>(ah + own);
-                a2l = *reinterpret_cast<const float2 *>(al + own);
+                ldv<W>(ah + own, a_h);
+                ldv<W>(al + own, a_l);
             }
             if (KIND == KPSI) {
-                b2h = *reinterpret_cast<const float2 *>(bh + own);
-                b2l = *reinterpret_cast<const float2 *>(bl + own);
+                ldv<W>(bh + own, b_h);
+                ldv<W>(bl + own, b_l);
             }
-            float mj[2] = {0.0f, 0.0f}, iv[2] = {0.0f, 0.0f};
-            float rr[2], sh[2];
+            float mj[W] = {}, iv[W] = {}, rr[W], sh[W];
 #pragma unroll
-            for (int e = 0; e < 2; e++) {
+            for (int e = 0; e < W; e++) {
                 float h6[6], l6[6];
 #pragma unroll
                 for (int k = 0; k < 5; k++) {
-                    h6[k] = e ? nh[k].y : nh[k].x;
-                    l6[k] = e ? nl[k].y : nl[k].x;
+                    h6[k] = nh[k][e];
+                    l6[k] = nl[k][e];
                 }
                 // shifted neighbour of cell q0 + e in the other colour's own row
                 if (up) {
-                    h6[5] = e ? xh : nh[4].y;
-                    l6[5] = e ? xl : nl[4].y;
+                    h6[5] = e == W - 1 ? xh : nh[4][e + 1 < W ? e + 1 : 0];
+                    l6[5] = e == W - 1 ? xl : nl[4][e + 1 < W ? e + 1 : 0];
                 } else {
-                    h6[5] = e ? nh[4].x : xh;
-                    l6[5] = e ? nl[4].x : xl;
+                    h6[5] = e == 0 ? xh : nh[4][e > 0 ? e - 1 : 0];
+                    l6[5] = e == 0 ? xl : nl[4][e > 0 ? e - 1 : 0];
                 }
-                const df u = {e ? u2h.y : u2h.x, e ? u2l.y : u2l.x};
-                const df f = {e ? f2h.y : f2h.x, e ? f2l.y : f2l.x};
-                const df a = {e ? a2h.y : a2h.x, e ? a2l.y : a2l.x};
-                const df b = {e ? b2h.y : b2h.x, e ? b2l.y : b2l.x};
-                const df r = df_cell<KIND>(h6, l6, u, f, a, b, cpr, c5, &mj[e], &iv[e]);  // h^2 eps
+                const df r = df_cell<KIND>(h6, l6, {u_h[e], u_l[e]}, {f_h[e], f_l[e]}, {a_h[e], a_l[e]},
+                                           {b_h[e], b_l[e]}, cpr, c5, &mj[e], &iv[e]);  // h^2 eps
                 sh[e] = r.hi + r.lo;
                 rr[e] = -sh[e] * ih2;
                 const float z = r.hi * ih2_ref;
                 acc = __fmaf_rn(z, z, acc);
             }
-            *reinterpret_cast<float2 *>(r32 + own) = make_float2(rr[0], rr[1]);
+            stv<W>(r32 + own, rr);
             if (KIND == KPSI) {
-                *reinterpret_cast<float2 *>(m32 + own) = make_float2(mj[0] * ih2, mj[1] * ih2);
-                *reinterpret_cast<float2 *>(inv32 + own) = make_float2(iv[0], iv[1]);
+#pragma unroll
+                for (int e = 0; e < W; e++) mj[e] *= ih2;
+                stv<W>(m32 + own, mj);
+                stv<W>(inv32 + own, iv);
             }
             if (c == 0 && e32) {
-                float2 g;
-                if (KIND == KPOISSON) g = make_float2(1.0f / 6.0f, 1.0f / 6.0f);
-                else if (KIND == KHELM) g = *reinterpret_cast<const float2 *>(inv_in + own);
-                else g = make_float2(iv[0], iv[1]);
-                *reinterpret_cast<float2 *>(e32 + own) = make_float2(sh[0] * g.x, sh[1] * g.y);
+                float g[W];
+                if (KIND == KHELM) {
+                    ldv<W>(inv_in + own, g);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W; e++) g[e] = KIND == KPOISSON ? 1.0f / 6.0f : iv[e];
+                }
+#pragma unroll
+                for (int e = 0; e < W; e++) g[e] *= sh[e];
+                stv<W>(e32 + own, g);
             }
         }
     }
@@ -262,19 +289,25 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
              float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    int g = grid_for((int64_t)n * n * n / 4);
+    const int w = n >= 8 ? 4 : 2;
+    int g = grid_for((int64_t)n * n * n / (2 * w));
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
     const df cpr = df_from_double_host(2.0 * kPi * rho * h2);
     const float c5 = (float)(10.0 * kPi * rho * h2), ih2 = (float)(1.0 / h2), ih2_ref = (float)(1.0 / (h2 * ref));
-    if (kind == KPOISSON)
-        GR_LAUNCH(k_df_resid<KPOISSON>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref,
-                  r32, m32, inv32, inv_in, e32, partials);
-    else if (kind == KHELM)
-        GR_LAUNCH(k_df_resid<KHELM>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32,
-                  m32, inv32, inv_in, e32, partials);
-    else
-        GR_LAUNCH(k_df_resid<KPSI>, g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32,
-                  m32, inv32, inv_in, e32, partials);
+#define GR_DF_RESID(K, W)                                                                                       \
+    GR_LAUNCH((k_df_resid<K, W>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32, \
+              m32, inv32, inv_in, e32, partials)
+    if (kind == KPOISSON) {
+        if (w == 4) GR_DF_RESID(KPOISSON, 4);
+        else GR_DF_RESID(KPOISSON, 2);
+    } else if (kind == KHELM) {
+        if (w == 4) GR_DF_RESID(KHELM, 4);
+        else GR_DF_RESID(KHELM, 2);
+    } else {
+        if (w == 4) GR_DF_RESID(KPSI, 4);
+        else GR_DF_RESID(KPSI, 2);
+    }
+#undef GR_DF_RESID
     return g;
 }
 

@@ -35,10 +35,8 @@ inline int log2i(int n)
     return l;
 }
 
-__device__ __forceinline__ int64_t nat(int lgn, int i, int j, int k)
-{
-    return ((((int64_t)i << lgn) + j) << lgn) + k;
-}
+// natural index; 32-bit since n <= 1024
+__device__ __forceinline__ int nat(int lgn, int i, int j, int k) { return (((i << lgn) + j) << lgn) + k; }
 
 __device__ __forceinline__ df ld(const double *__restrict__ a, int64_t id) { return split_double(a[id]); }
 
@@ -179,8 +177,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_dfs_poisson(int lgn, PoissonArgs 
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             const int i = p.i, j = p.j, k = p.k0 + e;
-            const int64_t id = nat(lgn, i, j, k);
-            const int64_t nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
+            const int id = nat(lgn, i, j, k);
+            const int nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
                                       {nat(lgn, i, (j + 1) & mn, k), nat(lgn, i, (j - 1) & mn, k)},
                                       {nat(lgn, i, j, (k + 1) & mn), nat(lgn, i, j, (k - 1) & mn)}};
             df f;
@@ -241,13 +239,13 @@ __global__ void __launch_bounds__(kBlock)
     const int m = (1 << lgn) - 1;
     const float *V[3] = {Pvx, Pvy, Pvz};
     const df qih2 = df_scale2(ih2, 0.25f);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t & m), j = (int)((t >> lgn) & m), i = (int)(t >> (2 * lgn));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)N; t += gridDim.x * blockDim.x) {
+        const int k = t & m, j = (t >> lgn) & m, i = t >> (2 * lgn);
         const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m, kp = (k + 1) & m,
                   km = (k - 1) & m;
-        const int64_t plus[3] = {nat(lgn, ip, j, k), nat(lgn, i, jp, k), nat(lgn, i, j, kp)};
-        const int64_t minus[3] = {nat(lgn, im, j, k), nat(lgn, i, jm, k), nat(lgn, i, j, km)};
-        auto P = [&](const float *f, int64_t id) { return ldp(f, f + N, id); };
+        const int plus[3] = {nat(lgn, ip, j, k), nat(lgn, i, jp, k), nat(lgn, i, j, kp)};
+        const int minus[3] = {nat(lgn, im, j, k), nat(lgn, i, jm, k), nat(lgn, i, j, km)};
+        auto P = [&](const float *f, int id) { return ldp(f, f + N, id); };
         auto diff = [&](df a, df b) { return df_add(a, df_neg(b)); };
         df D[3][3];
 #pragma unroll
@@ -302,7 +300,8 @@ __global__ void __launch_bounds__(kBlock)
         const PairPos p = pair_pos(lgn, t);
 #pragma unroll
         for (int e = 0; e < 2; e++) {
-            const int64_t id = nat(lgn, p.i, p.j, p.k0 + e), sid = p.split(e);
+            const int id = nat(lgn, p.i, p.j, p.k0 + e);
+            const int64_t sid = p.split(e);
             const df s = ld(s0, id);
             stp(uh, ul, sid, df_add_acc(ld(psi, id), m1));
             stp(ah, al, sid, df_mul(s, a_scale));
@@ -334,7 +333,8 @@ __global__ void __launch_bounds__(kBlock)
         const PairPos p = pair_pos(lgn, t);
 #pragma unroll
         for (int e = 0; e < 2; e++) {
-            const int64_t id = nat(lgn, p.i, p.j, p.k0 + e), sid = p.split(e);
+            const int id = nat(lgn, p.i, p.j, p.k0 + e);
+            const int64_t sid = p.split(e);
             const df ps = ld(psi, id);
             const df ip = df_recip(ps);
             const df ip2 = df_mul(ip, ip), ip4 = df_mul(ip2, ip2), ip8 = df_mul(ip4, ip4);

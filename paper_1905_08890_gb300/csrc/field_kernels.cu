@@ -4,6 +4,7 @@
 // level arrays use the red-black split layout (gr_internal.cuh).  Derivatives
 // (Sec. 4.3.1): D_a f = (f_{+a} - f_{-a})/2h, D_aa f = (f_{+a} - 2f + f_{-a})/h^2,
 // D_ab f = (f_{++} + f_{--} - f_{-+} - f_{+-})/4h^2 (Eq. U-cross-deriv).
+#include "df64.cuh"
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -51,12 +52,14 @@ __device__ __forceinline__ double at(const double *__restrict__ f, int lgn, int 
 
 // ---------------------------------------------------------------- CIC deposit
 // Sec. 4.1.2: the particle at x_p lies between centres x_i <= x_p < x_{i+1};
-// cell i takes f+ = (x_{i+1} - x_p)/h, cell i+1 takes 1 - f+.  The kernel is
-// bound by GB300's FP64 pipe, so it keeps FP64 operations few: the periodic
-// wrap is folded into the integer cell index (t = x/h - 1/2 shifted by a
-// multiple of n changes f+ only by rounding), one reciprocal square root gives
-// both W = sqrt(1 + u^2) and u^2/W, and the eight corner weights are formed
-// once and shared by the five quantities.
+// cell i takes f+ = (x_{i+1} - x_p)/h, cell i+1 takes 1 - f+.  GB300's narrow
+// FP64 pipe bounds this kernel, so FP64 is kept to the positions, the charges
+// and the eight corner weights: the periodic wrap is folded into the integer
+// cell index (t = x/h - 1/2 shifted by a multiple of n changes f+ only by
+// rounding), one reciprocal square root gives both W = sqrt(1 + u^2) and
+// u^2/W, and the forty products charge x weight are double-float products
+// (relative error about 2^-46) of the split operands, joined back to doubles
+// with integer operations for the FP64 atomic adds.
 __global__ void __launch_bounds__(kBlock)
     k_deposit(int lgn, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u, double q,
               double *__restrict__ s0, double *__restrict__ sx, double *__restrict__ sy, double *__restrict__ sz,
@@ -79,27 +82,21 @@ __global__ void __launch_bounds__(kBlock)
         const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
         const double w2 = 1.0 + u2;
         const double rw = rsqrt(w2);  // 1/W
-        const double Q[5] = {q * (w2 * rw), q * ux, q * uy, q * uz, (q * u2) * rw};
-        double* const out[5] = {s0, sx, sy, sz, sig};
-        double w[8];
+        const df Q[5] = {split_double(q * (w2 * rw)), split_double(q * ux), split_double(q * uy),
+                         split_double(q * uz), split_double((q * u2) * rw)};
+        double *const out[5] = {s0, sx, sy, sz, sig};
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
             for (int b = 0; b < 2; b++) {
                 const double wab = fw[0][a] * fw[1][b];
-                w[4 * a + 2 * b] = wab * fw[2][0];
-                w[4 * a + 2 * b + 1] = wab * fw[2][1];
-            }
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int b = 0; b < 2; b++) {
-                const int64_t row = (((int64_t)((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m)) << lgn;
+                const int row = ((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m)) << lgn;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const int64_t id = row + ((lo[2] + c) & m);
+                    const df w = split_double(wab * fw[2][c]);
+                    const int id = row + ((lo[2] + c) & m);
 #pragma unroll
-                    for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, Q[k] * w[4 * a + 2 * b + c]);
+                    for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, join_double(df_mul(Q[k], w)));
                 }
             }
     }

@@ -1,6 +1,7 @@
 """Host logic of the multi-GPU bench (independent replicas, weak scaling) on
 CPU with two gloo ranks: distinct seeds per rank, and the job throughput =
 cell updates summed over ranks / slowest rank's time."""
+import datetime
 import os
 import socket
 
@@ -23,7 +24,7 @@ def _free_port():
 def _worker(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
     updates = [3_000_000, 5_000_000][rank]
     ms = [100.0, 250.0][rank]
     value, ms_max = bench.job_throughput(updates, ms, dist, "cpu")
@@ -39,10 +40,15 @@ def test_two_gloo_ranks_aggregate_throughput_and_distinct_seeds():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    res = sorted(q.get(timeout=120) for _ in procs)
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
+    try:
+        res = sorted(q.get(timeout=120) for _ in procs)
+        for p in procs:
+            p.join(timeout=60)
+            assert p.exitcode == 0
+    finally:
+        for p in procs:
+            if p.is_alive():
+                p.kill()
     (r0, s0, v0, m0), (r1, s1, v1, m1) = res
     assert s0 != s1
     assert m0 == m1 == 250.0
