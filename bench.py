@@ -38,7 +38,7 @@ BYTES = {
     "resid_restrict32": {"poisson": 9.0, "helm": 13.0},
     "resid_restrict32_red": {"poisson": 7.0, "helm": 9.0},  # red children only, after a black pass
     "resid_restrict64": {"poisson": 18.0, "helm": 26.0, "psi": 35.0},
-    "prolong32": {"any": 8.5},
+    "prolong32": {"any": 4.5},  # black children only (a red pass follows)
     "prolong64": {"any": 17.0},
     "mixed_resid": {"poisson": 20.0, "helm": 28.0, "psi": 44.0},
     "df_resid": {"poisson": 22.0, "helm": 32.0, "psi": 46.0},  # + the first red pass of the next cycle

@@ -447,14 +447,36 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh 
             for (int col = 0; col < 2; col++)
                 gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
     };
+    // levels up to 16^3 run in one block (coarse_tail) when the grid is finer than that
+    const int tail = (top > 3 && c->tail_on) ? 3 : 0;
+    // after a black pre-smoothing pass only red residuals are restricted; a
+    // coarse level relaxed by separate launches (above the tail, not the 2^3
+    // solve) also gets its first red pass from the restriction
+    auto first_red_from_restrict = [&](int lc) { return nu1 > 0 && lc >= 1 && lc > (tail ? tail : 0); };
     auto down = [&](int l) {
         Level &A = c->lev[l], &C = c->lev[l - 1];
-        if (nu1 > 0)  // the last pre-smoothing pass was black
-            gr::resid_restrict_red(kind32, A.n, A.e, A.r, A.m, A.ih2, C.e, C.r, c->st);
-        else
+        if (nu1 > 0) {
+            const bool fr = first_red_from_restrict(l - 1);
+            gr::resid_restrict_red(kind32, A.n, A.e, A.r, A.m, A.ih2, C.e, C.r, fr ? C.inv : nullptr, fr ? C.h2 : 0.0,
+                                   c->st);
+        } else {
             gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
+        }
     };
-    auto up = [&](int l) { gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st); };
+    // pre-smoothing of a coarse level whose first red pass the restriction made
+    auto smooth_after_restrict = [&](Level &A, int lc) {
+        if (!first_red_from_restrict(lc)) {
+            smooth(A, nu1);
+            return;
+        }
+        gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, 1, c->st);
+        smooth(A, nu1 - 1);
+    };
+    // a red pass follows each prolongation when nu2 > 0: only black cells need the correction
+    auto up = [&](int l) {
+        if (nu2 > 0) gr::prolong_add_black(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
+        else gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
+    };
     timed(c, GR_PROF_SWEEP32, [&] {
         if (red_done && nu1 > 0) {
             gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st);
@@ -465,11 +487,9 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh 
         }
     });
     timed(c, GR_PROF_RESTRICT, [&] { down(top); });
-    // levels up to 16^3 run in one block (coarse_tail) when the grid is finer than that
-    const int tail = (top > 3 && c->tail_on) ? 3 : 0;
     timed(c, GR_PROF_COARSE, [&] {
         for (int l = top - 1; l >= (tail ? tail + 1 : 1); l--) {
-            smooth(c->lev[l], nu1);
+            smooth_after_restrict(c->lev[l], l);
             down(l);
         }
         if (tail) {

@@ -116,9 +116,11 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
                     T *fc, T *urc, int fas, cudaStream_t st);
 // FP32 correction form of the same (KPOISSON or KHELM with m) right after a
 // black relaxation pass: only the red children's residuals enter the average,
-// the black ones being zero up to rounding.
+// the black ones being zero up to rounding.  h2c > 0: the coarse correction
+// ec receives the coarse level's first red relaxation from zero instead of
+// zeros (cinv: the coarse KHELM inverse diagonal), so that pass is skipped.
 void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
-                        float *rc, cudaStream_t st);
+                        float *rc, const float *cinv, double h2c, cudaStream_t st);
 
 // FAS coarse right-hand side: fc = N(uc) - fc (KPSI, double).
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
@@ -129,6 +131,8 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st);
 // Fine u += P(uc), cell-centred trilinear.
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st);
+// FP32, black children only (a red relaxation of a linear equation follows)
+void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st);
 
 // The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage);
 // Poisson: source mean removed before and solution mean after.  KHELM reads

@@ -189,11 +189,15 @@ __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ 
 // black cells' residuals are zero up to rounding, so only the four red
 // children are evaluated (the black ones count as zero in the average); the
 // loads that only black children need are then dead and dropped.
-template <typename T, int KIND, int FAS, int RED = 0>
+// FIRST = 1 (correction form): instead of zeroing the coarse correction, write
+// the result of the coarse level's first red relaxation from zero,
+// -h_c^2 fc / 6 (KPOISSON) or -h_c^2 fc cinv (KHELM, cinv = 1/(6 + h_c^2 m_c)),
+// on red coarse cells and 0 on black ones, so that pass can be skipped.
+template <typename T, int KIND, int FAS, int RED = 0, int FIRST = 0>
 __global__ void __launch_bounds__(kBlock)
     k_resid_restrict(int lgf, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
                      const T *__restrict__ c1, T ih2, T rho, T *__restrict__ uc, T *__restrict__ fc,
-                     T *__restrict__ urc)
+                     T *__restrict__ urc, const T *__restrict__ cinv = nullptr, T h2c = T(0))
 {
     const int lgc = lgf - 1;
     const int mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
@@ -244,8 +248,11 @@ __global__ void __launch_bounds__(kBlock)
             uc[cid] = T(0.125) * su;
             urc[cid] = T(0.125) * su;
         } else {
-            fc[cid] = -(T(0.125) * s);
-            uc[cid] = T(0);
+            const T rc = -(T(0.125) * s);
+            fc[cid] = rc;
+            T e0 = T(0);
+            if (FIRST && !((I + J + K) & 1)) e0 = -h2c * rc * (KIND == KHELM ? cinv[cid] : T(1.0 / 6.0));
+            uc[cid] = e0;
         }
     }
 }
@@ -288,7 +295,11 @@ struct Vec2<double> {
     using type = double2;
 };
 
-template <typename T>
+// BLACK = 1 corrects the black children only: when a red Gauss-Seidel pass of
+// a linear equation follows, the red values are overwritten without being
+// read (the point update does not use the old value), so their correction
+// would be dead work.
+template <typename T, int BLACK = 0>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
 {
     using V2 = typename Vec2<T>::type;
@@ -332,15 +343,18 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__
                 const int row = (((2 * I + a) << lgf) + 2 * J + b) << (lgf - 1);
                 // fine cell 4Q + m has colour (a + b + m) & 1 and half-index 2Q + (m >> 1)
                 const int p = (a + b) & 1;
-                V2 *red = reinterpret_cast<V2 *>(u + row + 2 * Q);
                 V2 *blk = reinterpret_cast<V2 *>(u + halff + row + 2 * Q);
-                V2 r = *red, k = *blk;
-                r.x += val[p];
-                r.y += val[2 + p];
+                V2 k = *blk;
                 k.x += val[1 - p];
                 k.y += val[3 - p];
-                *red = r;
                 *blk = k;
+                if (!BLACK) {
+                    V2 *red = reinterpret_cast<V2 *>(u + row + 2 * Q);
+                    V2 r = *red;
+                    r.x += val[p];
+                    r.y += val[2 + p];
+                    *red = r;
+                }
             }
         }
     }
@@ -558,16 +572,22 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
 }
 
 void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
-                        float *rc, cudaStream_t st)
+                        float *rc, const float *cinv, double h2c, cudaStream_t st)
 {
     const int lgf = log2i(nf);
     const int g = grid_for((int64_t)nf * nf * nf / 8);
-    if (kind == KPOISSON)
-        GR_LAUNCH((k_resid_restrict<float, KPOISSON, 0, 1>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f,
-                  ec, rc, nullptr);
-    else
-        GR_LAUNCH((k_resid_restrict<float, KHELM, 0, 1>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec,
-                  rc, nullptr);
+    const float hc = (float)h2c;
+#define GR_RR(K, F)                                                                                          \
+    GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, \
+              rc, nullptr, cinv, hc)
+    if (kind == KPOISSON) {
+        if (cinv || h2c > 0) GR_RR(KPOISSON, 1);
+        else GR_RR(KPOISSON, 0);
+    } else {
+        if (h2c > 0) GR_RR(KHELM, 1);
+        else GR_RR(KHELM, 0);
+    }
+#undef GR_RR
 }
 
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
@@ -580,6 +600,11 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)nc * nc * nc;
     GR_LAUNCH(k_fas_diff, grid_for(cnt), kBlock, st, cnt, uc, urc);
+}
+
+void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st)
+{
+    GR_LAUNCH((k_prolong_add<float, 1>), grid_for((int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u, uc);
 }
 
 template <typename T>
