@@ -4,10 +4,13 @@ One step = deposit of the resident particles, reset of the ten fields to the
 plain guess (psi = alpha psi = 1, vectors 0) and the full solve.  The
 headline path is the mixed-precision solve (defect correction with the fine
 residual in double-float, FP32 correction V-cycles); the plain FP64 GPU
-solve of the same step is timed next to it.  Multi-GPU runs are independent replicas (one problem per rank,
-different seeds: weak scaling, no collective on the data path).
+solve of the same step is timed next to it, and so is the same solve started by
+one full multigrid cycle per equation (a classical non-learned warm start).
+Multi-GPU runs are independent replicas (one problem per rank, different
+seeds: weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec mixed_df|mixed|fp64]
+                    [--no-fp64] [--no-fmg] [--no-e2e] [--no-learned] [--no-cpu]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 """
 from __future__ import annotations
@@ -160,6 +163,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--prec", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
+    ap.add_argument("--no-fmg", action="store_true", help="skip the full multigrid start comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -310,6 +314,9 @@ def main():
                        "max_rel_linf_mixed_vs_fp64": max(diff.values())}
         del fld64, mixed_fields
 
+    if rank == 0 and not args.no_fmg and mixed:
+        out["fmg_start"] = fmg_measure(ctx, x, u, p, src, fld, opts)
+
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 2))
 
@@ -382,6 +389,31 @@ def e2e_measure(ctx, p, n, opts, world, steps):
             "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3)}
 
 
+def fmg_measure(ctx, x, u, p, src, fld, opts):
+    """The same workload with the full multigrid start (gr_opts.fmg, a
+    classical non-learned warm start): one untimed and one timed solve from
+    the plain guess, CUDA events; fields compared with the headline solve's."""
+    import torch
+
+    ref = {k: v.clone() for k, v in fld.items()}
+    o = dict(opts, fmg=1)
+    for it in range(2):
+        ctx.deposit(x, u, p.mass, src)
+        f2 = ctx.initial_fields()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        rep = ctx.solve(src, f2, **o)
+        t1.record()
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    diff = max(float((f2[k] - ref[k]).abs().max() / ref[k].abs().max().clamp_min(1e-300)) for k in ref)
+    del f2, ref
+    return {"time_to_residual_ms": round(ms, 3), "cycles": rep["cycles"],
+            "gcell_updates_per_s": round(rep["cell_updates"] / (ms * 1e-3) / 1e9, 3),
+            "max_rel_linf_vs_headline": diff}
+
+
 def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
     """The learned initial guess on its own workload (128^3, lognormal rms
     delta U[0.3, 3], held-out seeds): time to residual 1e-8 and V-cycles from
@@ -398,13 +430,13 @@ def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
     src = ctx.new_sources()
     kw = dict(prec=prec)
     res = {"plain_ms": 0.0, "learned_ms": 0.0, "inference_ms": 0.0, "cycles_plain": 0, "cycles_learned": 0,
-           "rejected": 0}
+           "rejected": 0, "fmg_ms": 0.0, "cycles_fmg": 0}
     for rep_i in range(2):  # first pass warms up
         for k in res:
             res[k] = 0
         for seed in seeds:
             src, rho = learn.sources(ctx, seed, src)
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
             e[0].record()
             _, rp = learn.solve(ctx, src, rho, **kw)
             e[1].record()
@@ -412,9 +444,14 @@ def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
             e[2].record()
             _, rw, t_inf = learn.warm_solve(ctx, net, src, rho, **kw)
             e[3].record()
+            e[4].record()
+            _, rf = learn.solve(ctx, src, rho, fmg=1, **kw)
+            e[5].record()
             torch.cuda.synchronize()
             res["plain_ms"] += e[0].elapsed_time(e[1])
             res["learned_ms"] += e[2].elapsed_time(e[3])
+            res["fmg_ms"] += e[4].elapsed_time(e[5])
+            res["cycles_fmg"] += sum(rf["cycles"])
             res["inference_ms"] += 1e3 * t_inf
             res["cycles_plain"] += sum(rp["cycles"])
             res["cycles_learned"] += sum(rw["cycles"])
@@ -426,7 +463,9 @@ def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
            "time_to_residual_ms_learned": round(res["learned_ms"] / k, 3),
            "inference_ms": round(res["inference_ms"] / k, 3),
            "vcycles_plain": res["cycles_plain"] / k, "vcycles_learned": res["cycles_learned"] / k,
-           "guesses_rejected": res["rejected"], "path": prec}
+           "guesses_rejected": res["rejected"],
+           "time_to_residual_ms_fmg_start": round(res["fmg_ms"] / k, 3), "cycles_fmg_start": res["cycles_fmg"] / k,
+           "path": prec}
     net.close()
     ctx.close()
     return out

@@ -106,6 +106,12 @@ typedef struct {
     int check_guess;  /* nonzero: per equation, drop the given guess for the plain one (psi = alpha psi = 1,
                          vectors 0) when its residual is not finite or, after the first cycle, still above
                          the plain guess's initial residual (gr_report.guess_rejected) */
+    int fmg;          /* nonzero (mixed modes, n >= 32): the first correction of every equation is a full
+                         multigrid cycle (nested iteration) instead of a V-cycle: the fine residual is
+                         averaged down to 16^3, solved there by two V-cycles, and each finer level starts
+                         from the trilinear prolongation of the coarser solution and takes one V-cycle.
+                         A classical non-learned warm start; the paper's solver uses V-cycles only
+                         (Sec. 4.3.1), so the default is 0.  Ignored by GR_PREC_FP64. */
 } gr_opts;
 
 /* Finest-level kernel classes timed when gr_opts.profile is set. */
@@ -137,7 +143,7 @@ typedef struct {
 } gr_report;
 
 /* Fill *o with the defaults: tol 1e-10, max_cycles 50, V(2,2), FP64,
-   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0, check_guess 0. */
+   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0, check_guess 0, fmg 0. */
 void gr_default_opts(gr_opts *o);
 
 /* Create a context for an n^3 grid of box side L.  n must be a power of two,

@@ -59,43 +59,32 @@ __device__ __forceinline__ double at(const double *__restrict__ f, int lgn, int 
 // rounding), one reciprocal square root gives both W = sqrt(1 + u^2) and
 // u^2/W, and the forty products charge x weight are double-float products
 // (relative error about 2^-46) of the split operands, joined back to doubles
-// with integer operations for the FP64 atomic adds.
-// Neighbouring lanes of a warp hold consecutive particles; when lane l's
-// upper-k corner cell is lane l+1's lower-k corner cell (particles ordered
-// along k, as a lattice-ordered set mostly is), lane l+1 adds lane l's five
-// contributions to its own before the atomics, which halves the atomics of
-// such pairs.  Any particle order gives the same sums.
+// with integer operations for the FP64 atomic adds.  With the products moved
+// off the FP64 pipe, issue (71%) and the FP64 pipe (55%) bound it together.
 __global__ void __launch_bounds__(kBlock)
     k_deposit(int lgn, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u, double q,
               double *__restrict__ s0, double *__restrict__ sx, double *__restrict__ sy, double *__restrict__ sz,
               double *__restrict__ sig)
 {
     const int m = (1 << lgn) - 1;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform loop: every lane runs every iteration, lanes past np carry no charge
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-        const int64_t p = base + lane;
-        const bool valid = p < np;
-        const int64_t pc = valid ? p : np - 1;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
         int lo[3];
         double fw[3][2];  // weights of the lower and the upper cell per axis
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double t = fma(x[d * np + pc], invh, -0.5);
+            const double t = fma(x[d * np + p], invh, -0.5);
             const double fl = floor(t);
             const double fr = t - fl;
             fw[d][0] = 1.0 - fr;
             fw[d][1] = fr;
             lo[d] = (int)((long long)fl & m);
         }
-        const double ux = u[pc], uy = u[np + pc], uz = u[2 * np + pc];
+        const double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
         const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
         const double w2 = 1.0 + u2;
         const double rw = rsqrt(w2);  // 1/W
-        const double qq = valid ? q : 0.0;
-        const df Q[5] = {split_double(qq * (w2 * rw)), split_double(qq * ux), split_double(qq * uy),
-                         split_double(qq * uz), split_double((qq * u2) * rw)};
+        const df Q[5] = {split_double(q * (w2 * rw)), split_double(q * ux), split_double(q * uy),
+                         split_double(q * uz), split_double((q * u2) * rw)};
         double *const out[5] = {s0, sx, sy, sz, sig};
 #pragma unroll
         for (int a = 0; a < 2; a++)
@@ -103,24 +92,12 @@ __global__ void __launch_bounds__(kBlock)
             for (int b = 0; b < 2; b++) {
                 const double wab = fw[0][a] * fw[1][b];
                 const int row = ((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m)) << lgn;
-                const int id0 = row + lo[2], id1 = row + ((lo[2] + 1) & m);
-                const df w0 = split_double(wab * fw[2][0]), w1 = split_double(wab * fw[2][1]);
-                // pair with the neighbouring lanes: take lane-1's upper corner, give ours to lane+1
-                const int prev_id1 = __shfl_up_sync(0xffffffffu, id1, 1);
-                const int next_id0 = __shfl_down_sync(0xffffffffu, id0, 1);
-                const bool next_valid = __shfl_down_sync(0xffffffffu, valid, 1);
-                const bool take = lane > 0 && prev_id1 == id0;
-                const bool give = lane < 31 && next_valid && next_id0 == id1;
 #pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    df c0 = df_mul(Q[k], w0);
-                    const df c1 = df_mul(Q[k], w1);
-                    const df pc1 = {__shfl_up_sync(0xffffffffu, c1.hi, 1), __shfl_up_sync(0xffffffffu, c1.lo, 1)};
-                    if (take) c0 = df_add(c0, pc1);
-                    if (valid) {
-                        atomicAdd(out[k] + id0, join_double(c0));
-                        if (!give) atomicAdd(out[k] + id1, join_double(c1));
-                    }
+                for (int c = 0; c < 2; c++) {
+                    const df w = split_double(wab * fw[2][c]);
+                    const int id = row + ((lo[2] + c) & m);
+#pragma unroll
+                    for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, join_double(df_mul(Q[k], w)));
                 }
             }
     }

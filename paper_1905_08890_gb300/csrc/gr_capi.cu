@@ -384,11 +384,21 @@ void restrict_coefs32(gr_ctx *c)
     }
 }
 
-long long vcycle_cells(const gr_ctx *c, int nu1, int nu2)
+// cells relaxed by one V-cycle whose top is level top (default: the finest)
+long long vcycle_cells(const gr_ctx *c, int nu1, int nu2, int top = -1)
 {
+    if (top < 0) top = c->nlev - 1;
     long long s = 0;
-    for (int l = 1; l < c->nlev; l++) s += (long long)(nu1 + nu2) * c->lev[l].n * c->lev[l].n * c->lev[l].n;
+    for (int l = 1; l <= top; l++) s += (long long)(nu1 + nu2) * c->lev[l].n * c->lev[l].n * c->lev[l].n;
     return s + (long long)kCoarsestSweeps * 8;
+}
+
+// cells relaxed by one full multigrid cycle (fmg32)
+long long fmg_cells(const gr_ctx *c, int nu1, int nu2)
+{
+    long long s = 2 * vcycle_cells(c, nu1, nu2, 3);
+    for (int l = 4; l < c->nlev; l++) s += vcycle_cells(c, nu1, nu2, l);
+    return s;
 }
 
 // Relaxation and transfers of one V-cycle.  With profiling, the finest
@@ -433,21 +443,30 @@ void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
     timed(c, GR_PROF_SWEEP64, [&] { smooth(F, nu2); });
 }
 
-// one FP32 correction V-cycle on lev[*].e with fine right-hand side lev[fine].r;
-// red_done: the fine residual kernel already made the first red relaxation
-// from e = 0 (then the black cells of e are not read before they are written).
-// uh, ul not null (needs nu2 >= 1 and a finest level of at least 8^3): the
-// last black pass also adds e to the double-float unknown (uh, ul).
-void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh = nullptr, float *ul = nullptr)
+// How a correction V-cycle finds its top level's e: zero (cleared here), the
+// first red relaxation from zero already made (by the fine residual kernel;
+// the black cells are then not read before they are written), or a given
+// initial e (full multigrid).
+enum Start { START_ZERO = 0, START_RED_DONE = 1, START_GIVEN = 2 };
+
+// One FP32 correction V-cycle on lev[*].e with right-hand side lev[top].r,
+// top = the finest level unless given (full multigrid's coarser cycles, all
+// timed as GR_PROF_COARSE).  uh, ul not null (needs nu2 >= 1 and a top level
+// of at least 8^3): the last black pass also adds e to the double-float
+// unknown (uh, ul).
+void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = nullptr, float *ul = nullptr,
+              int top = -1)
 {
-    const int top = c->nlev - 1;
+    if (top < 0) top = c->nlev - 1;
+    const bool fine = top == c->nlev - 1;
+    auto cls = [&](int k) { return fine ? k : (int)GR_PROF_COARSE; };
     Level &F = c->lev[top];
     auto smooth = [&](Level &A, int nu) {
         for (int s = 0; s < nu; s++)
             for (int col = 0; col < 2; col++)
                 gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
     };
-    // levels up to 16^3 run in one block (coarse_tail) when the grid is finer than that
+    // levels up to 16^3 run in one block (coarse_tail) when the top is finer than that
     const int tail = (top > 3 && c->tail_on) ? 3 : 0;
     // after a black pre-smoothing pass only red residuals are restricted; a
     // coarse level relaxed by separate launches (above the tail, not the 2^3
@@ -477,16 +496,16 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh 
         if (nu2 > 0) gr::prolong_add_black(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
         else gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
     };
-    timed(c, GR_PROF_SWEEP32, [&] {
-        if (red_done && nu1 > 0) {
+    timed(c, cls(GR_PROF_SWEEP32), [&] {
+        if (start == START_RED_DONE && nu1 > 0) {
             gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st);
             smooth(F, nu1 - 1);
         } else {
-            cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
+            if (start != START_GIVEN) cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
             smooth(F, nu1);
         }
     });
-    timed(c, GR_PROF_RESTRICT, [&] { down(top); });
+    timed(c, cls(GR_PROF_RESTRICT), [&] { down(top); });
     timed(c, GR_PROF_COARSE, [&] {
         for (int l = top - 1; l >= (tail ? tail + 1 : 1); l--) {
             smooth_after_restrict(c->lev[l], l);
@@ -513,9 +532,9 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh 
             smooth(c->lev[l], nu2);
         }
     });
-    timed(c, GR_PROF_PROLONG, [&] { up(top); });
+    timed(c, cls(GR_PROF_PROLONG), [&] { up(top); });
     if (!uh) {
-        timed(c, GR_PROF_SWEEP32, [&] { smooth(F, nu2); });
+        timed(c, cls(GR_PROF_SWEEP32), [&] { smooth(F, nu2); });
         return;
     }
     timed(c, GR_PROF_SWEEP32, [&] {
@@ -524,6 +543,43 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, bool red_done, float *uh 
     });
     timed(c, GR_PROF_MIXED_UPDATE,
           [&] { gr::df_black_update(kind32, F.n, F.e, F.r, F.inv, F.h2, uh, ul, c->st); });
+}
+
+// Full multigrid correction cycle (nested iteration) on the FP32 correction
+// equation with fine right-hand side lev[fine].r: the right-hand side is
+// averaged down to 16^3, solved there by two V-cycles from zero (the coarse
+// tail), and every finer level starts from the trilinear prolongation of the
+// coarser level's solution and takes one V-cycle; the finest cycle may add
+// its result to (uh, ul) as vcycle32 does.  Needs the coarse tail (fine
+// level of at least 32^3).
+void fmg32(gr_ctx *c, int kind32, int nu1, int nu2, float *uh, float *ul)
+{
+    const int top = c->nlev - 1;
+    timed(c, GR_PROF_COARSE, [&] {
+        for (int l = top; l > 3; l--) gr::restrict_avg(c->lev[l].n, c->lev[l].r, c->lev[l - 1].r, c->st);
+        float *e[4], *r[4];
+        const float *m[4], *iv[4];
+        double h2[4];
+        for (int l = 0; l < 4; l++) {
+            e[l] = c->lev[l].e;
+            r[l] = c->lev[l].r;
+            m[l] = c->lev[l].m;
+            iv[l] = c->lev[l].inv;
+            h2[l] = c->lev[l].h2;
+        }
+        cudaMemsetAsync(c->lev[3].e, 0, sizeof(float) * 16 * 16 * 16, c->st);
+        gr::coarse_tail(kind32, e, r, m, iv, h2, nu1, nu2, c->st);
+        gr::coarse_tail(kind32, e, r, m, iv, h2, nu1, nu2, c->st);
+    });
+    for (int l = 4; l <= top; l++) {
+        Level &A = c->lev[l];
+        timed(c, l == top ? (int)GR_PROF_PROLONG : (int)GR_PROF_COARSE, [&] {
+            cudaMemsetAsync(A.e, 0, sizeof(float) * (size_t)A.n * A.n * A.n, c->st);
+            gr::prolong_add<float>(A.n, A.e, c->lev[l - 1].e, c->st);
+        });
+        if (l < top) vcycle32(c, kind32, nu1, nu2, START_GIVEN, nullptr, nullptr, l);
+        else vcycle32(c, kind32, nu1, nu2, START_GIVEN, uh, ul);
+    }
 }
 
 gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, double *r)
@@ -595,6 +651,8 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     // cycle, and the last black pass adds the correction to u
     const bool red = dfm && o->nu1 > 0;
     const bool fuse_update = dfm && o->nu2 > 0 && F.n >= 8;
+    // full multigrid start: the first correction of the equation (mixed modes, coarse tail present)
+    const bool fmg = o->fmg != 0 && (o->prec == GR_PREC_MIXED || dfm) && c->nlev - 1 > 3 && c->tail_on;
     // residual of the plain guess (unknown 0: psi = alpha psi = 1, vectors 0),
     // the bar a given guess must beat after its first cycle
     double r_plain = NAN;
@@ -656,15 +714,20 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     while (st == GR_OK && r > tol && cyc < max_cycles) {
         if (mixed) {
             if (in.kind == KPSI) restrict_coefs32(c);
+            const bool full = fmg && cyc == 0;
+            const Start start = red ? START_RED_DONE : START_ZERO;
             if (fuse_update) {
-                vcycle32(c, in.kind32, o->nu1, o->nu2, red, c->dfu, c->dfu + N);
+                if (full) fmg32(c, in.kind32, o->nu1, o->nu2, c->dfu, c->dfu + N);
+                else vcycle32(c, in.kind32, o->nu1, o->nu2, start, c->dfu, c->dfu + N);
             } else {
-                vcycle32(c, in.kind32, o->nu1, o->nu2, red);
+                if (full) fmg32(c, in.kind32, o->nu1, o->nu2, nullptr, nullptr);
+                else vcycle32(c, in.kind32, o->nu1, o->nu2, start);
                 timed(c, GR_PROF_MIXED_UPDATE, [&] {
                     if (dfm) gr::df_update(F.n, c->dfu, c->dfu + N, F.e, c->st);
                     else gr::mixed_update(F.n, F.u, F.e, c->st);
                 });
             }
+            if (cells && full) *cells += fmg_cells(c, o->nu1, o->nu2) - per_cycle;
         } else {
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
         }
@@ -724,6 +787,7 @@ void gr_default_opts(gr_opts *o)
     o->verbose = 0;
     o->profile = 0;
     o->check_guess = 0;
+    o->fmg = 0;
 }
 
 const char *gr_last_error(void) { return g_err.c_str(); }

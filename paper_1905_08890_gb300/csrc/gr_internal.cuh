@@ -133,6 +133,8 @@ template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st);
 // FP32, black children only (a red relaxation of a linear equation follows)
 void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st);
+// FP32 coarse = 8-child average of fine (a right-hand side going down)
+void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st);
 
 // The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage);
 // Poisson: source mean removed before and solution mean after.  KHELM reads

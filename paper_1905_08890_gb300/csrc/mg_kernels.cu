@@ -419,6 +419,26 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
     }
 }
 
+// ---------------------------------------------------------------- plain restriction
+// coarse = 8-child average of fine (split layout), e.g. a right-hand side
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict_avg(int lgf, const T *__restrict__ fine, T *__restrict__ coarse)
+{
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1;
+    const int ncells = 1 << (3 * lgc);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lgc) & mc, I = t >> (2 * lgc);
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) s += fine[sidx32(lgf, 2 * I + a, 2 * J + b, 2 * K + c)];
+        coarse[sidx32(lgc, I, J, K)] = T(0.125) * s;
+    }
+}
+
 // ---------------------------------------------------------------- coefficients
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock) k_restrict_coef(int lgf, const T *__restrict__ c0f, const T *__restrict__ c1f,
@@ -600,6 +620,11 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st)
 {
     const int64_t cnt = (int64_t)nc * nc * nc;
     GR_LAUNCH(k_fas_diff, grid_for(cnt), kBlock, st, cnt, uc, urc);
+}
+
+void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st)
+{
+    GR_LAUNCH((k_restrict_avg<float>), grid_for((int64_t)nf * nf * nf / 8), kBlock, st, log2i(nf), fine, coarse);
 }
 
 void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st)

@@ -39,7 +39,8 @@ class gr_fields(ctypes.Structure):
 class gr_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
-                ("verbose", ctypes.c_int), ("profile", ctypes.c_int), ("check_guess", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("profile", ctypes.c_int), ("check_guess", ctypes.c_int),
+                ("fmg", ctypes.c_int)]
 
 
 class gr_report(ctypes.Structure):
@@ -164,7 +165,7 @@ def make_fields(fld: dict) -> gr_fields:
 
 
 def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
-              profile=0, check_guess=0) -> gr_opts:
+              profile=0, check_guess=0, fmg=0) -> gr_opts:
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
@@ -172,6 +173,7 @@ def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, 
               if isinstance(prec, str) else int(prec))
     o.rho_hat, o.S_hat, o.verbose, o.profile = rho_hat, S_hat, verbose, int(profile)
     o.check_guess = int(check_guess)
+    o.fmg = int(fmg)
     return o
 
 
