@@ -275,7 +275,7 @@ def main():
     if dom and os.path.exists(tpath):
         tj = json.load(open(tpath))
         ent = tj.get(dom)
-        if ent and ent.get("n") == n and ent.get("source_hash") == _source_hash():
+        if ent and ent.get("n") == n and ent.get("source_hash") == _source_hash(ent.get("files"), ent.get("function")):
             traffic = ent["bytes_per_launch"]
     roofline = None
     if dom:
@@ -471,13 +471,23 @@ def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
     return out
 
 
-def _source_hash():
+def _source_hash(files=None, kernel=None):
+    """Hash of the CUDA sources a profile was taken with: the named files
+    under csrc/ (all of them by default), or only the definition of one
+    kernel in them.  A traffic figure is used only while that text is
+    unchanged."""
     import hashlib
 
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1905_08890_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    for f in sorted(files or os.listdir(d)):
+        text = open(os.path.join(d, f), "rb").read()
+        if kernel:
+            k = text.find(f"{kernel}(".encode())
+            if k < 0:
+                continue
+            text = text[k:text.find(b"\n}\n", k) + 3]
+        h.update(text)
     return h.hexdigest()[:12]
 
 

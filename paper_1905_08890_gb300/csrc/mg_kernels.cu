@@ -824,44 +824,47 @@ __device__ void tail_up(const TailLevel &A, const TailLevel &C)
     __syncthreads();
 }
 
-// FP64 solve of the 2^3 level (same steps as k_coarsest)
+// FP64 solve of the 2^3 level (same steps as k_coarsest), by the first warp
+// alone so that its 64 half-sweeps need warp, not block, barriers
 template <int KIND>
 __device__ void tail_coarsest(const TailLevel &Z)
 {
     __shared__ double su[8], sf[8], sm[8];
     const int t = threadIdx.x;
-    if (t < 8) {
-        su[t] = Z.e[t];
-        sf[t] = Z.r[t];
-        sm[t] = KIND == KPOISSON ? 0.0 : (double)Z.m[t];
-    }
-    __syncthreads();
-    if (KIND == KPOISSON && t == 0) {
-        double m = 0.0;
-        for (int q = 0; q < 8; q++) m += sf[q];
-        m *= 0.125;
-        for (int q = 0; q < 8; q++) sf[q] -= m;
-    }
-    __syncthreads();
-    const double h2 = (double)Z.h2;
-    for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
-        for (int color = 0; color < 2; color++) {
-            if (t < 4) {
-                const int i = t >> 1, j = t & 1, id = 4 * color + t, o = 4 * (color ^ 1);
-                const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                su[id] = KIND == KPOISSON ? (nb - h2 * sf[id]) / 6.0 : (nb - h2 * sf[id]) / (6.0 + h2 * sm[id]);
-            }
-            __syncthreads();
+    if (t < 32) {
+        if (t < 8) {
+            su[t] = Z.e[t];
+            sf[t] = Z.r[t];
+            sm[t] = KIND == KPOISSON ? 0.0 : (double)Z.m[t];
         }
+        __syncwarp();
+        if (KIND == KPOISSON && t == 0) {
+            double m = 0.0;
+            for (int q = 0; q < 8; q++) m += sf[q];
+            m *= 0.125;
+            for (int q = 0; q < 8; q++) sf[q] -= m;
+        }
+        __syncwarp();
+        const double h2 = (double)Z.h2;
+        for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
+            for (int color = 0; color < 2; color++) {
+                if (t < 4) {
+                    const int i = t >> 1, j = t & 1, id = 4 * color + t, o = 4 * (color ^ 1);
+                    const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
+                    su[id] = KIND == KPOISSON ? (nb - h2 * sf[id]) / 6.0 : (nb - h2 * sf[id]) / (6.0 + h2 * sm[id]);
+                }
+                __syncwarp();
+            }
+        }
+        if (KIND == KPOISSON && t == 0) {
+            double m = 0.0;
+            for (int q = 0; q < 8; q++) m += su[q];
+            m *= 0.125;
+            for (int q = 0; q < 8; q++) su[q] -= m;
+        }
+        __syncwarp();
+        if (t < 8) Z.e[t] = (float)su[t];
     }
-    if (KIND == KPOISSON && t == 0) {
-        double m = 0.0;
-        for (int q = 0; q < 8; q++) m += su[q];
-        m *= 0.125;
-        for (int q = 0; q < 8; q++) su[q] -= m;
-    }
-    __syncthreads();
-    if (t < 8) Z.e[t] = (float)su[t];
     __syncthreads();
 }
 
