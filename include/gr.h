@@ -112,6 +112,11 @@ typedef struct {
                          from the trilinear prolongation of the coarser solution and takes one V-cycle.
                          A classical non-learned warm start; the paper's solver uses V-cycles only
                          (Sec. 4.3.1), so the default is 0.  Ignored by GR_PREC_FP64. */
+    const gr_fields *host_out; /* gr_solve_constraints only, may be NULL: ten arrays of n^3 doubles (host memory,
+                         pinned for overlap, or any memory cudaMemcpyAsync accepts), caller-owned.  Each field
+                         is copied there as soon as its equation is solved, on a copy stream of the context,
+                         so the copies overlap the remaining equations; the call's stream waits for the last
+                         copy before the call returns, so a synchronisation of that stream covers them. */
 } gr_opts;
 
 /* Finest-level kernel classes timed when gr_opts.profile is set. */
@@ -157,9 +162,16 @@ gr_status gr_create(int n, double L, void *cuda_stream, gr_ctx **out);
 void gr_destroy(gr_ctx *ctx);
 
 /* Cloud-in-cell deposit (Sec. 4.1.2, Eqs. s0/si/sij-code-unit-cic) of np
-   identical particles of rest mass `mass`.  x and u are device arrays in
+   identical particles of rest mass `mass`.  x and u are arrays in
    structure-of-arrays layout [3][np]: positions (wrapped periodically into
-   [0, L)) and lower-index 4-velocities u_l.  Each particle adds, with CIC
+   [0, L)) and lower-index 4-velocities u_l.  Both device memory, or both host
+   memory: host arrays (pinned for full speed) are copied in chunks of
+   GR_HOST_CHUNK particles (environment, read at gr_create; default 4M)
+   through two device staging buffers that the context allocates at first
+   use, each chunk's copy overlapping the previous chunk's deposit on a copy
+   stream of the context; the call returns once the copies are queued, and the
+   host arrays must stay valid until the context's stream has passed them.
+   A mix of host and device pointers is GR_ERR_ARG.  Each particle adds, with CIC
    weight w over the 8 surrounding cell centres, m W w/h^3 to s0,
    m u_l w/h^3 to s_l and m |u|^2/W w/h^3 to sigma, W = sqrt(1 + |u|^2)
    (the conformal factor is taken as 1 in the Lorentz factor).  The five

@@ -282,15 +282,9 @@ __global__ void __launch_bounds__(kBlock)
 }  // namespace
 
 // ================================================================ launchers
-void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
-             double *sy, double *sz, double *sig, cudaStream_t st)
+void deposit_add(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
+                 double *sy, double *sz, double *sig, cudaStream_t st)
 {
-    const size_t bytes = (size_t)n * n * n * sizeof(double);
-    cudaMemsetAsync(s0, 0, bytes, st);
-    cudaMemsetAsync(sx, 0, bytes, st);
-    cudaMemsetAsync(sy, 0, bytes, st);
-    cudaMemsetAsync(sz, 0, bytes, st);
-    cudaMemsetAsync(sig, 0, bytes, st);
     if (np <= 0) return;
     const double h = L / n;
     const double q = mass / (h * h * h);
@@ -300,6 +294,18 @@ void deposit(int n, double L, int64_t np, const double *x, const double *u, doub
     const int64_t blocks = (np + kBlock - 1) / kBlock;
     const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
     GR_LAUNCH(k_deposit, g, kBlock, st, log2i(n), 1.0 / h, np, x, u, q, s0, sx, sy, sz, sig);
+}
+
+void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
+             double *sy, double *sz, double *sig, cudaStream_t st)
+{
+    const size_t bytes = (size_t)n * n * n * sizeof(double);
+    cudaMemsetAsync(s0, 0, bytes, st);
+    cudaMemsetAsync(sx, 0, bytes, st);
+    cudaMemsetAsync(sy, 0, bytes, st);
+    cudaMemsetAsync(sz, 0, bytes, st);
+    cudaMemsetAsync(sig, 0, bytes, st);
+    deposit_add(n, L, np, x, u, mass, s0, sx, sy, sz, sig, st);
 }
 
 int sum_sq(int64_t cnt, const double *a, double *partials, cudaStream_t st)

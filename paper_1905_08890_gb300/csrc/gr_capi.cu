@@ -75,6 +75,12 @@ struct gr_ctx {
     int w_fmt = 0;
     bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // host-buffer I/O: a copy stream, its events and two particle staging buffers
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready[2] = {}, used[2] = {}, xfer = nullptr;
+    double *stage[2] = {};
+    int64_t stage_cap = 0;            // particles per staging buffer
+    int64_t host_chunk = 4 << 20;     // particles per host chunk (GR_HOST_CHUNK)
     std::vector<void *> allocs;
     // finest-level kernel timing (gr_opts.profile)
     bool prof_on = false;
@@ -769,6 +775,76 @@ gr_status resolve_bg(gr_ctx *c, const gr_opts *o, double *rho, double *S_hat)
     return GR_OK;
 }
 
+// true for memory the host addresses directly (pinned or pageable), false
+// for device (or managed) memory
+bool host_memory(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// the copy stream and events of host-buffer I/O, created at first use
+gr_status ensure_copy_stream(gr_ctx *c)
+{
+    if (c->cs) return GR_OK;
+    if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cs = nullptr;
+        return fail(GR_ERR_CUDA, "cudaStreamCreate");
+    }
+    bool ok = cudaEventCreateWithFlags(&c->xfer, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; b++)
+        ok = cudaEventCreateWithFlags(&c->ready[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->used[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(GR_ERR_CUDA, "cudaEventCreate");
+    }
+    return GR_OK;
+}
+
+// Deposit from host arrays: chunks of particles go through two staging
+// buffers; chunk i's six copies (x and u, three components each) run on the
+// copy stream while chunk i-1 deposits on the context's stream.
+gr_status deposit_from_host(gr_ctx *c, int64_t np, const double *x, const double *u, double mass,
+                            const gr_sources *out)
+{
+    gr_status st = ensure_copy_stream(c);
+    if (st != GR_OK) return st;
+    const int64_t chunk = np < c->host_chunk ? np : c->host_chunk;
+    if (c->stage_cap < chunk) {
+        for (int b = 0; b < 2; b++) {
+            st = dalloc(c, &c->stage[b], (size_t)6 * chunk);  // kept until gr_destroy
+            if (st != GR_OK) return st;
+        }
+        c->stage_cap = chunk;
+    }
+    const size_t bytes = (size_t)c->n * c->n * c->n * sizeof(double);
+    double *f[5] = {out->s0, out->s[0], out->s[1], out->s[2], out->sigma};
+    for (int k = 0; k < 5; k++) cudaMemsetAsync(f[k], 0, bytes, c->st);
+    // the staging buffers may still be read by the previous call's last chunks
+    for (int b = 0; b < 2; b++) cudaEventRecord(c->used[b], c->st);
+    int b = 0;
+    for (int64_t p0 = 0; p0 < np; p0 += chunk, b ^= 1) {
+        const int64_t m = np - p0 < chunk ? np - p0 : chunk;
+        double *xs = c->stage[b], *us = c->stage[b] + 3 * m;
+        cudaStreamWaitEvent(c->cs, c->used[b], 0);
+        for (int d = 0; d < 3; d++) {
+            cudaMemcpyAsync(xs + d * m, x + d * np + p0, m * sizeof(double), cudaMemcpyDefault, c->cs);
+            cudaMemcpyAsync(us + d * m, u + d * np + p0, m * sizeof(double), cudaMemcpyDefault, c->cs);
+        }
+        cudaEventRecord(c->ready[b], c->cs);
+        cudaStreamWaitEvent(c->st, c->ready[b], 0);
+        gr::deposit_add(c->n, c->L, m, xs, us, mass, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
+        cudaEventRecord(c->used[b], c->st);
+    }
+    return GR_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -788,6 +864,7 @@ void gr_default_opts(gr_opts *o)
     o->profile = 0;
     o->check_guess = 0;
     o->fmg = 0;
+    o->host_out = nullptr;
 }
 
 const char *gr_last_error(void) { return g_err.c_str(); }
@@ -801,8 +878,15 @@ void gr_destroy(gr_ctx *c)
     else cudaDeviceSynchronize();
     for (void *p : c->allocs) cudaFree(p);
     if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->cs) cudaStreamSynchronize(c->cs);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (int b = 0; b < 2; b++) {
+        if (c->ready[b]) cudaEventDestroy(c->ready[b]);
+        if (c->used[b]) cudaEventDestroy(c->used[b]);
+    }
+    if (c->xfer) cudaEventDestroy(c->xfer);
+    if (c->cs) cudaStreamDestroy(c->cs);
     for (auto &p : c->pending) {
         c->ev_pool.push_back(p.a);
         c->ev_pool.push_back(p.b);
@@ -823,6 +907,10 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     c->n = n;
     c->L = L;
     if (const char *env = getenv("GR_COARSE_TAIL")) c->tail_on = env[0] != '0';
+    if (const char *env = getenv("GR_HOST_CHUNK")) {
+        const long long v = atoll(env);
+        if (v > 0) c->host_chunk = v;
+    }
     c->h = L / n;
     c->st = (cudaStream_t)stream;
     c->nlev = log2i(n);
@@ -879,7 +967,14 @@ gr_status gr_deposit(gr_ctx *c, int64_t np, const double *x, const double *u, do
     if (np > 0 && (!x || !u)) return fail(GR_ERR_ARG, "x or u is NULL");
     if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL");
     if (!(mass >= 0) || !std::isfinite(mass)) return fail(GR_ERR_ARG, "mass must be finite and >= 0");
-    gr::deposit(c->n, c->L, np, x, u, mass, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
+    const bool hx = np > 0 && host_memory(x), hu = np > 0 && host_memory(u);
+    if (hx != hu) return fail(GR_ERR_ARG, "x and u must both be device or both host memory");
+    if (hx) {
+        gr_status st = deposit_from_host(c, np, x, u, mass, out);
+        if (st != GR_OK) return st;
+    } else {
+        gr::deposit(c->n, c->L, np, x, u, mass, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
+    }
     c->rho_dep = mass * (double)np / (c->L * c->L * c->L);
     return cuda_check("gr_deposit");
 }
@@ -904,11 +999,22 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
     gr_status worst = GR_OK;
     std::string first_err;
+    if (o->host_out) {
+        st = ensure_copy_stream(c);
+        if (st != GR_OK) return st;
+    }
+    const size_t field_bytes = (size_t)c->n * c->n * c->n * sizeof(double);
     for (int eq = 0; eq < GR_NEQ; eq++) {
         if (eq == GR_PSI) c->a_fmt = 0;  // V and U are final now
         cudaEventRecord(c->ev0, c->st);
         st = solve_eq(c, eq, s, fl, o, rho, S_hat, o->tol, o->max_cycles, &R.cycles[eq], &R.res0[eq], &R.res[eq],
                       &R.cell_updates, &R.guess_rejected[eq]);
+        if (o->host_out && (st == GR_OK || st == GR_ERR_NOCONV)) {
+            // this field is final: copy it out while the next equations solve
+            cudaEventRecord(c->xfer, c->st);
+            cudaStreamWaitEvent(c->cs, c->xfer, 0);
+            cudaMemcpyAsync(field_ptr(o->host_out, eq), field_ptr(fl, eq), field_bytes, cudaMemcpyDefault, c->cs);
+        }
         cudaEventRecord(c->ev1, c->st);
         cudaEventSynchronize(c->ev1);
         float ms = 0;
@@ -923,6 +1029,10 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
             first_err = g_err;
         }
         if (st != GR_OK && st != GR_ERR_NOCONV) break;
+    }
+    if (o->host_out) {  // the call's stream waits for the last copy
+        cudaEventRecord(c->xfer, c->cs);
+        cudaStreamWaitEvent(c->st, c->xfer, 0);
     }
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (c->prof_on) {

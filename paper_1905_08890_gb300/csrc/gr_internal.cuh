@@ -231,6 +231,10 @@ void dfs_store(int n, const float *uh, const float *ul, const double *sum, int d
 // ---- sources, coefficients, layouts (field_kernels.cu) ---------------------
 void deposit(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
              double *sy, double *sz, double *sig, cudaStream_t st);
+// the deposit kernel alone, adding to the five arrays (no zeroing): for
+// particles arriving in chunks
+void deposit_add(int n, double L, int64_t np, const double *x, const double *u, double mass, double *s0, double *sx,
+                 double *sy, double *sz, double *sig, cudaStream_t st);
 // Partial sums of a and a^2 over cnt doubles; returns the block count.
 int sum_sq(int64_t cnt, const double *a, double *partials, cudaStream_t st);
 // a[i] = scale * (a[i] - s[0] / cnt_total), s a device scalar (a sum).

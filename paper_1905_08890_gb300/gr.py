@@ -40,7 +40,7 @@ class gr_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
                 ("verbose", ctypes.c_int), ("profile", ctypes.c_int), ("check_guess", ctypes.c_int),
-                ("fmg", ctypes.c_int)]
+                ("fmg", ctypes.c_int), ("host_out", ctypes.POINTER(gr_fields))]
 
 
 class gr_report(ctypes.Structure):
@@ -132,13 +132,15 @@ def _check(st: int, where: str, allow=()):
     return st
 
 
-def _ptr(t):
+def _ptr(t, host_ok=False):
+    """Address of a contiguous float64 tensor: CUDA, or also CPU (host
+    memory, preferably pinned) where the C call accepts host arrays."""
     if t is None:
         return None
     import torch
 
-    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if not (t.dtype == torch.float64 and t.is_contiguous() and (t.is_cuda or (host_ok and t.device.type == "cpu"))):
+        raise ValueError("expected a contiguous float64 CUDA tensor" + (" or CPU tensor" if host_ok else ""))
     return t.data_ptr()
 
 
@@ -151,21 +153,23 @@ def make_sources(src: dict) -> gr_sources:
     return s
 
 
-def make_fields(fld: dict) -> gr_fields:
+def make_fields(fld: dict, host_ok=False) -> gr_fields:
     f = gr_fields()
-    f.psi = _ptr(fld["psi"])
-    f.apsi = _ptr(fld["apsi"])
+    f.psi = _ptr(fld["psi"], host_ok)
+    f.apsi = _ptr(fld["apsi"], host_ok)
     for d, k in enumerate(("Vx", "Vy", "Vz")):
-        f.V[d] = _ptr(fld[k])
-    f.U = _ptr(fld["U"])
+        f.V[d] = _ptr(fld[k], host_ok)
+    f.U = _ptr(fld["U"], host_ok)
     for d, k in enumerate(("Bx", "By", "Bz")):
-        f.B[d] = _ptr(fld[k])
-    f.b = _ptr(fld["b"])
+        f.B[d] = _ptr(fld[k], host_ok)
+    f.b = _ptr(fld["b"], host_ok)
     return f
 
 
 def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
-              profile=0, check_guess=0, fmg=0) -> gr_opts:
+              profile=0, check_guess=0, fmg=0, host_out=None) -> gr_opts:
+    """host_out: optional dict of ten CPU (pinned) float64 tensors that each
+    solved field is copied into while the later equations solve."""
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
@@ -174,6 +178,9 @@ def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, 
     o.rho_hat, o.S_hat, o.verbose, o.profile = rho_hat, S_hat, verbose, int(profile)
     o.check_guess = int(check_guess)
     o.fmg = int(fmg)
+    if host_out is not None:
+        o._host_out = make_fields(host_out, host_ok=True)  # kept alive with the options
+        o.host_out = ctypes.pointer(o._host_out)
     return o
 
 
@@ -200,7 +207,7 @@ def gr_destroy(ctx):
 def gr_deposit(ctx, x, u, mass: float, src: dict):
     npart = x.shape[1] if x.numel() else 0
     s = make_sources(src)
-    _check(lib().gr_deposit(ctx, npart, _ptr(x) if npart else None, _ptr(u) if npart else None, mass,
+    _check(lib().gr_deposit(ctx, npart, _ptr(x, True) if npart else None, _ptr(u, True) if npart else None, mass,
                             ctypes.byref(s)), "gr_deposit")
 
 
