@@ -51,12 +51,17 @@ __device__ __forceinline__ void stp(float *__restrict__ h, float *__restrict__ l
     l[id] = v.lo;
 }
 
-// cell pair of split offset t: row (i, j), columns k0 = 2q and k0 + 1; the
-// cell k0 + e has colour c0 ^ e and split index (c0 ^ e) * n^3/2 + t
+// Threads of the split-layout kernels own kChunk consecutive half-indices
+// t .. t + kChunk - 1 of a row (i, j), that is the 2 kChunk cells
+// k = k0 .. k0 + 2 kChunk - 1 with k0 = 2 (t mod n/2); cell k0 + e has colour
+// c0 ^ (e & 1) and split index (c0 ^ (e & 1)) n^3/2 + t + e/2.  Several cells
+// per thread keep more independent loads in flight.
+constexpr int kChunk = 2;
+
 struct PairPos {
     int i, j, k0, c0;
     int64_t t, half;
-    __device__ __forceinline__ int64_t split(int e) const { return ((c0 ^ e) ? half : 0) + t; }
+    __device__ __forceinline__ int64_t split(int e) const { return ((c0 ^ (e & 1)) ? half : 0) + t + (e >> 1); }
 };
 
 __device__ __forceinline__ PairPos pair_pos(int lgn, int64_t t)
@@ -157,7 +162,7 @@ struct PoissonArgs {
 };
 
 template <int SRC>
-__global__ void __launch_bounds__(kBlock, 3) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
+__global__ void __launch_bounds__(kBlock, SRC == SRC_SHIFT ? 2 : 3) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
 {
     const int mn = (1 << lgn) - 1;
     const int64_t N = (int64_t)1 << (3 * lgn);
@@ -171,11 +176,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_dfs_poisson(int lgn, PoissonArgs 
         for (int l = 0; l < 3; l++) tab[l] = rows[a.comp][l];
     }
     Acc acc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const PairPos p = pair_pos(lgn, t);
+    for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
+         tc += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, tc * kChunk);
 #pragma unroll
-        for (int e = 0; e < 2; e++) {
+        for (int e = 0; e < 2 * kChunk; e++) {
             const int i = p.i, j = p.j, k = p.k0 + e;
             const int id = nat(lgn, i, j, k);
             const int nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
@@ -295,11 +300,11 @@ __global__ void __launch_bounds__(kBlock)
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df m1 = {-1.0f, 0.0f};
     Acc acc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const PairPos p = pair_pos(lgn, t);
+    for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
+         tc += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, tc * kChunk);
 #pragma unroll
-        for (int e = 0; e < 2; e++) {
+        for (int e = 0; e < 2 * kChunk; e++) {
             const int id = nat(lgn, p.i, p.j, p.k0 + e);
             const int64_t sid = p.split(e);
             const df s = ld(s0, id);
@@ -328,11 +333,11 @@ __global__ void __launch_bounds__(kBlock)
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df m1 = {-1.0f, 0.0f};
     Acc acc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const PairPos p = pair_pos(lgn, t);
+    for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
+         tc += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, tc * kChunk);
 #pragma unroll
-        for (int e = 0; e < 2; e++) {
+        for (int e = 0; e < 2 * kChunk; e++) {
             const int id = nat(lgn, p.i, p.j, p.k0 + e);
             const int64_t sid = p.split(e);
             const df ps = ld(psi, id);
@@ -374,11 +379,11 @@ __global__ void __launch_bounds__(kBlock)
 {
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df nmu = sum ? df_neg(split_double(sum[0] * inv_cnt)) : df{0.0f, 0.0f};
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (N >> 1);
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const PairPos p = pair_pos(lgn, t);
+    for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
+         tc += (int64_t)gridDim.x * blockDim.x) {
+        const PairPos p = pair_pos(lgn, tc * kChunk);
 #pragma unroll
-        for (int e = 0; e < 2; e++) {
+        for (int e = 0; e < 2 * kChunk; e++) {
             df v = ldp(uh, ul, p.split(e));
             if (sum) v = df_add_acc(v, nmu);
             double d = join_double(v);
@@ -419,7 +424,7 @@ int dfs_mean_rhs(int n, const double *s, const double *sum, double scale, const 
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / 2);
+    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_MEAN>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -438,7 +443,7 @@ int dfs_div_rhs(int n, double scale, const double *Fx, const double *Fy, const d
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / 2);
+    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_DIV>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -458,7 +463,7 @@ int dfs_shift_rhs(int n, double scale, const float *A, const float *wh, const fl
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / 2);
+    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_SHIFT>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -479,7 +484,7 @@ int dfs_psi(int n, double h2, const double *psi, const double *s0, const float *
             cudaStream_t st)
 {
     const int lgn = log2i(n);
-    const int g = grid_for((int64_t)n * n * n / 2);
+    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_psi, g, kBlock, st, lgn, df_from_double_host(2.0 * kPi * h2), df_from_double_host(0.125 * h2),
               psi, s0, AAh, AAl, uh, ul, ah, al, bh, bl, fh, fl, partials);
     return g;
@@ -490,7 +495,7 @@ int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const doub
              float *fh, float *fl, float *m32, float *inv32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    const int g = grid_for((int64_t)n * n * n / 2);
+    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_apsi, g, kBlock, st, lgn, (float)h2, df_from_double_host(h2), psi, apsi, s0, sig, AAh, AAl,
               df_from_double_host(2.0 * kPi), df_from_double_host(5.0 / 12.0 * K2), df_from_double_host(Kdot), uh,
               ul, ah, al, fh, fl, m32, inv32, partials);
@@ -507,7 +512,7 @@ void dfs_store(int n, const float *uh, const float *ul, const double *sum, int d
 {
     const int lgn = log2i(n);
     const int64_t N = (int64_t)n * n * n;
-    GR_LAUNCH(k_dfs_store, grid_for(N / 2), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, dev, out);
+    GR_LAUNCH(k_dfs_store, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, dev, out);
 }
 
 }  // namespace gr
