@@ -304,3 +304,23 @@ def test_coarse_tail_block_matches_per_level_kernels(monkeypatch):
     assert ra["kernel_launches"] < rb["kernel_launches"]
     for k in oracle.FIELDS:
         assert rel_linf(fa[k], fb[k]) <= 1e-9, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("n", [4, 8])
+def test_smallest_grids_match_oracle(n, prec):
+    """The degenerate end of the hierarchy: n = 4 (two levels, the two-wide
+    double-float residual, scalar colour passes) and n = 8, every precision
+    mode, against the converged oracle."""
+    p, src = _problem(n, seed=8, sigma=0.5, v_rms=0.01, lognormal=True)
+    ofld = oracle.initial_fields(n)
+    ost, _ = oracle.solve_constraints(src, ofld, p.rho_hat, tol=1e-12, max_cycles=200)
+    assert ost == 0
+    ctx = gr.Context(n)
+    gf = _fields_to_gpu(oracle.initial_fields(n))
+    rep = ctx.solve(_fields_to_gpu(src), gf, tol=1e-11, max_cycles=200, prec=prec, rho_hat=p.rho_hat)
+    assert rep["status_code"] == gr.GR_OK, rep
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    for k in oracle.FIELDS:
+        assert rel_linf(_np(gf[k]), ofld[k]) <= tol, (k, rel_linf(_np(gf[k]), ofld[k]))
+    ctx.close()
