@@ -373,9 +373,12 @@ __global__ void __launch_bounds__(kBlock) k_dfs_weight(int64_t cnt, const double
 
 // ---------------------------------------------------------------- write-back
 // nat = join(u - <u>) (+ 1 for the deviation unknowns), <u> = sum[0] inv_cnt
+// DEV as a template parameter: a runtime flag would leave a predicated FP64
+// add on every element, which still occupies the narrow FP64 pipe
+template <int DEV>
 __global__ void __launch_bounds__(kBlock)
     k_dfs_store(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const double *__restrict__ sum,
-                double inv_cnt, int dev, double *__restrict__ out)
+                double inv_cnt, double *__restrict__ out)
 {
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df nmu = sum ? df_neg(split_double(sum[0] * inv_cnt)) : df{0.0f, 0.0f};
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kBlock)
             df v = ldp(uh, ul, p.split(e));
             if (sum) v = df_add_acc(v, nmu);
             double d = join_double(v);
-            if (dev) d += 1.0;
+            if (DEV) d += 1.0;
             out[nat(lgn, p.i, p.j, p.k0 + e)] = d;
         }
     }
@@ -512,7 +515,8 @@ void dfs_store(int n, const float *uh, const float *ul, const double *sum, int d
 {
     const int lgn = log2i(n);
     const int64_t N = (int64_t)n * n * n;
-    GR_LAUNCH(k_dfs_store, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, dev, out);
+    if (dev) GR_LAUNCH(k_dfs_store<1>, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, out);
+    else GR_LAUNCH(k_dfs_store<0>, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, out);
 }
 
 }  // namespace gr
