@@ -375,6 +375,20 @@ def e2e_measure(ctx, p, n, opts, world, steps):
     src = ctx.new_sources()
     fld = ctx.initial_fields()  # device fields, reset to the plain guess in every step
     o = dict(opts, host_out=host_out)
+    # host link rates seen by this run (the copies share the machine's host links with other jobs)
+    probe_d = torch.empty_like(host_out["psi"], device="cuda")
+    rates = {}
+    for name, (dst, srcb) in {"h2d_GBps": (probe_d, host_out["psi"]), "d2h_GBps": (host_out["psi"], probe_d)}.items():
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(srcb, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            best = max(best, dst.numel() * 8 / (a.elapsed_time(b) * 1e-3) / 1e9)
+        rates[name] = round(best, 1)
+    del probe_d
     ctx.deposit(xh, uh, p.mass, src)  # untimed: the context allocates its staging buffers on first use
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -390,7 +404,8 @@ def e2e_measure(ctx, p, n, opts, world, steps):
         torch.cuda.current_stream().synchronize()
     dt = time.perf_counter() - t0
     return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
-            "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3)}
+            "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3),
+            "link_rates_before_steps": rates}
 
 
 def fmg_measure(ctx, x, u, p, src, fld, opts):
