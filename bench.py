@@ -295,7 +295,7 @@ def main():
 
     # the end-to-end measurement runs first, on the state the timed steps left
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 2))
+        out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 3))
 
     if rank == 0 and not args.no_fp64 and mixed:
         mixed_fields = {k: v.clone() for k, v in fld.items()}
@@ -393,7 +393,9 @@ def e2e_measure(ctx, p, n, opts, world, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     updates = 0
+    per_step = []
     for _ in range(steps):
+        ts = time.perf_counter()
         ctx.deposit(xh, uh, p.mass, src)
         fld["psi"].fill_(1.0)
         fld["apsi"].fill_(1.0)
@@ -402,10 +404,11 @@ def e2e_measure(ctx, p, n, opts, world, steps):
         r = ctx.solve(src, fld, **o)
         updates += r["cell_updates"]
         torch.cuda.current_stream().synchronize()
+        per_step.append(round(1e3 * (time.perf_counter() - ts), 1))
     dt = time.perf_counter() - t0
     return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
             "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3),
-            "link_rates_before_steps": rates}
+            "ms_each_step": per_step, "link_rates_before_steps": rates}
 
 
 def fmg_measure(ctx, x, u, p, src, fld, opts):

@@ -290,13 +290,16 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
 {
     const int lgn = log2i(n);
     const int w = n >= 8 ? 4 : 2;
-    int g = grid_for((int64_t)n * n * n / (2 * w));
-    if (g > kMaxRedBlocks) g = kMaxRedBlocks;
+    const int64_t threads = (int64_t)n * n * n / (2 * w);
     const df cpr = df_from_double_host(2.0 * kPi * rho * h2);
     const float c5 = (float)(10.0 * kPi * rho * h2), ih2 = (float)(1.0 / h2), ih2_ref = (float)(1.0 / (h2 * ref));
-#define GR_DF_RESID(K, W)                                                                                       \
-    GR_LAUNCH((k_df_resid<K, W>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, r32, \
-              m32, inv32, inv_in, e32, partials)
+    int g = 0;
+#define GR_DF_RESID(K, W)                                                                                        \
+    do {                                                                                                         \
+        g = wave_grid(k_df_resid<K, W>, threads);                                                                \
+        GR_LAUNCH((k_df_resid<K, W>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, \
+                  r32, m32, inv32, inv_in, e32, partials);                                                       \
+    } while (0)
     if (kind == KPOISSON) {
         if (w == 4) GR_DF_RESID(KPOISSON, 4);
         else GR_DF_RESID(KPOISSON, 2);
@@ -315,11 +318,13 @@ void df_black_update(int kind, int n, const float *e, const float *r, const floa
                      float *ul, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    const int g = grid_for((int64_t)n * n * n / 8);
+    const int64_t threads = (int64_t)n * n * n / 8;
     if (kind == KPOISSON)
-        GR_LAUNCH(k_df_black_update<KPOISSON>, g, kBlock, st, lgn, e, r, inv, (float)h2, uh, ul);
+        GR_LAUNCH(k_df_black_update<KPOISSON>, wave_grid(k_df_black_update<KPOISSON>, threads), kBlock, st, lgn, e, r,
+                  inv, (float)h2, uh, ul);
     else
-        GR_LAUNCH(k_df_black_update<KHELM>, g, kBlock, st, lgn, e, r, inv, (float)h2, uh, ul);
+        GR_LAUNCH(k_df_black_update<KHELM>, wave_grid(k_df_black_update<KHELM>, threads), kBlock, st, lgn, e, r, inv,
+                  (float)h2, uh, ul);
 }
 
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st)

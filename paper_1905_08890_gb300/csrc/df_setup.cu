@@ -427,7 +427,7 @@ int dfs_mean_rhs(int n, const double *s, const double *sum, double scale, const 
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
+    const int g = wave_grid(k_dfs_poisson<SRC_MEAN>, (int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_MEAN>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -446,7 +446,7 @@ int dfs_div_rhs(int n, double scale, const double *Fx, const double *Fy, const d
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
+    const int g = wave_grid(k_dfs_poisson<SRC_DIV>, (int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_DIV>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -466,7 +466,7 @@ int dfs_shift_rhs(int n, double scale, const float *A, const float *wh, const fl
     a.ul = ul;
     a.fh = fh;
     a.fl = fl;
-    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
+    const int g = wave_grid(k_dfs_poisson<SRC_SHIFT>, (int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_poisson<SRC_SHIFT>, g, kBlock, st, lgn, a, partials);
     return g;
 }
@@ -478,7 +478,7 @@ void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy
     const int64_t N = (int64_t)n * n * n;
     GR_LAUNCH(k_dfs_split4, grid_for(N), kBlock, st, N, Vx, Vy, Vz, U, scratch[0], scratch[1], scratch[2],
               scratch[3]);
-    GR_LAUNCH(k_dfs_aij, grid_for(N), kBlock, st, lgn, df_from_double_host(inv2h), df_from_double_host(ih2),
+    GR_LAUNCH(k_dfs_aij, wave_grid(k_dfs_aij, N), kBlock, st, lgn, df_from_double_host(inv2h), df_from_double_host(ih2),
               scratch[0], scratch[1], scratch[2], scratch[3], A, AAh, AAl);
 }
 
@@ -487,7 +487,7 @@ int dfs_psi(int n, double h2, const double *psi, const double *s0, const float *
             cudaStream_t st)
 {
     const int lgn = log2i(n);
-    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
+    const int g = wave_grid(k_dfs_psi, (int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_psi, g, kBlock, st, lgn, df_from_double_host(2.0 * kPi * h2), df_from_double_host(0.125 * h2),
               psi, s0, AAh, AAl, uh, ul, ah, al, bh, bl, fh, fl, partials);
     return g;
@@ -498,7 +498,7 @@ int dfs_apsi(int n, double h2, const double *psi, const double *apsi, const doub
              float *fh, float *fl, float *m32, float *inv32, double *partials, cudaStream_t st)
 {
     const int lgn = log2i(n);
-    const int g = grid_for((int64_t)n * n * n / (2 * kChunk));
+    const int g = wave_grid(k_dfs_apsi, (int64_t)n * n * n / (2 * kChunk));
     GR_LAUNCH(k_dfs_apsi, g, kBlock, st, lgn, (float)h2, df_from_double_host(h2), psi, apsi, s0, sig, AAh, AAl,
               df_from_double_host(2.0 * kPi), df_from_double_host(5.0 / 12.0 * K2), df_from_double_host(Kdot), uh,
               ul, ah, al, fh, fl, m32, inv32, partials);
@@ -515,8 +515,13 @@ void dfs_store(int n, const float *uh, const float *ul, const double *sum, int d
 {
     const int lgn = log2i(n);
     const int64_t N = (int64_t)n * n * n;
-    if (dev) GR_LAUNCH(k_dfs_store<1>, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, out);
-    else GR_LAUNCH(k_dfs_store<0>, grid_for(N / (2 * kChunk)), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N, out);
+    const int64_t threads = N / (2 * kChunk);
+    if (dev)
+        GR_LAUNCH(k_dfs_store<1>, wave_grid(k_dfs_store<1>, threads), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N,
+                  out);
+    else
+        GR_LAUNCH(k_dfs_store<0>, wave_grid(k_dfs_store<0>, threads), kBlock, st, lgn, uh, ul, sum, 1.0 / (double)N,
+                  out);
 }
 
 }  // namespace gr

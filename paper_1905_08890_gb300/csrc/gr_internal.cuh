@@ -17,6 +17,8 @@
 #include <cstdint>
 
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 namespace gr {
 
@@ -32,6 +34,47 @@ extern std::atomic<long long> g_launches;
         kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);         \
         ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
     } while (0)
+
+// Blocks for a grid-stride kernel over `threads` threads: one full wave (as
+// many blocks per SM as the kernel's registers allow, on every SM) or fewer
+// when the work is smaller.  Every block then takes the same number of
+// grid-stride iterations to within one, where a fixed block count that is not
+// a multiple of the wave leaves a partial last wave with most SMs idle.
+inline int wave_grid_of(const void *kernel, int64_t threads, int block)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> per_sm;
+    static int sms = 0;
+    int b = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 1;
+        }
+        auto it = per_sm.find(kernel);
+        if (it == per_sm.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, 0) != cudaSuccess || b <= 0) {
+                cudaGetLastError();
+                b = 1;
+            }
+            per_sm[kernel] = b;
+        } else {
+            b = it->second;
+        }
+    }
+    const int64_t need = (threads + block - 1) / block;
+    const int64_t wave = (int64_t)sms * b;
+    return (int)(need < 1 ? 1 : (need < wave ? need : wave));
+}
+
+template <class Kernel>
+int wave_grid(Kernel kernel, int64_t threads, int block = 256)
+{
+    return wave_grid_of(reinterpret_cast<const void *>(kernel), threads, block);
+}
 
 // sets the thread's message returned by gr_last_error()
 void set_last_error(const char *msg);

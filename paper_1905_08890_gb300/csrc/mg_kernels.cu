@@ -559,11 +559,13 @@ void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, d
     if (sizeof(T) == 4 && n >= 8 && kind != KPSI) {
         float *uf = (float *)u;
         const float *ff = (const float *)f, *cf = (const float *)c1;
-        const int gv = grid_for((int64_t)n * n * n / 8);
+        const int64_t threads = (int64_t)n * n * n / 8;
         if (kind == KPOISSON)
-            GR_LAUNCH(k_sweep4<KPOISSON>, gv, kBlock, st, lgn, uf, ff, cf, (float)h2, color);
+            GR_LAUNCH(k_sweep4<KPOISSON>, wave_grid(k_sweep4<KPOISSON>, threads), kBlock, st, lgn, uf, ff, cf,
+                      (float)h2, color);
         else
-            GR_LAUNCH(k_sweep4<KHELM>, gv, kBlock, st, lgn, uf, ff, cf, (float)h2, color);
+            GR_LAUNCH(k_sweep4<KHELM>, wave_grid(k_sweep4<KHELM>, threads), kBlock, st, lgn, uf, ff, cf, (float)h2,
+                      color);
         return;
     }
     const int g = grid_for((int64_t)n * n * n / 2);
@@ -595,11 +597,11 @@ void resid_restrict_red(int kind, int nf, const float *e, const float *r, const 
                         float *rc, const float *cinv, double h2c, cudaStream_t st)
 {
     const int lgf = log2i(nf);
-    const int g = grid_for((int64_t)nf * nf * nf / 8);
+    const int64_t threads = (int64_t)nf * nf * nf / 8;
     const float hc = (float)h2c;
 #define GR_RR(K, F)                                                                                          \
-    GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, \
-              rc, nullptr, cinv, hc)
+    GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), wave_grid(k_resid_restrict<float, K, 0, 1, F>, threads),  \
+              kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, rc, nullptr, cinv, hc)
     if (kind == KPOISSON) {
         if (cinv || h2c > 0) GR_RR(KPOISSON, 1);
         else GR_RR(KPOISSON, 0);
@@ -629,13 +631,15 @@ void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st)
 
 void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st)
 {
-    GR_LAUNCH((k_prolong_add<float, 1>), grid_for((int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u, uc);
+    GR_LAUNCH((k_prolong_add<float, 1>), wave_grid(k_prolong_add<float, 1>, (int64_t)nf * nf * nf / 16), kBlock, st,
+              log2i(nf), u, uc);
 }
 
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
 {
-    GR_LAUNCH((k_prolong_add<T>), grid_for((int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u, uc);
+    GR_LAUNCH((k_prolong_add<T>), wave_grid(k_prolong_add<T>, (int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u,
+              uc);
 }
 
 template <typename T>
