@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
                const float *__restrict__ fl, const float *__restrict__ ah, const float *__restrict__ al,
                const float *__restrict__ bh, const float *__restrict__ bl, df cpr, float c5, float ih2,
                float ih2_ref, float *__restrict__ r32, float *__restrict__ m32, float *__restrict__ inv32,
-               const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials)
+               const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials, int rev)
 {
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
     for (int tp = blockIdx.x * blockDim.x + threadIdx.x; tp < half / W; tp += gridDim.x * blockDim.x) {
-        const int t = tp * W;  // q0 = t & mh, a multiple of W
+        const int t = (rev ? half / W - 1 - tp : tp) * W;  // q0 = t & mh, a multiple of W
         const int q = t & mh;
         const int j = (t >> lgh) & mn;
         const int i = t >> (lgh + lgn);
@@ -235,12 +235,12 @@ __global__ void k_df_update(int64_t cnt, float *__restrict__ uh, float *__restri
 template <int KIND>
 __global__ void __launch_bounds__(kBlock)
     k_df_black_update(int lgn, const float *__restrict__ e, const float *__restrict__ r, const float *__restrict__ inv,
-                      float h2, float *__restrict__ uh, float *__restrict__ ul)
+                      float h2, float *__restrict__ uh, float *__restrict__ ul, int rev)
 {
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (half >> 2); v += gridDim.x * blockDim.x) {
-        const int t = v << 2;
+        const int t = (rev ? (half >> 2) - 1 - v : v) << 2;
         const int q = t & mh;
         const int j = (t >> lgh) & mn;
         const int i = t >> (lgh + lgn);
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kBlock)
 
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
-             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st)
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev)
 {
     const int lgn = log2i(n);
     const int w = n >= 8 ? 4 : 2;
@@ -298,7 +298,7 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
     do {                                                                                                         \
         g = wave_grid(k_df_resid<K, W>, threads);                                                                \
         GR_LAUNCH((k_df_resid<K, W>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, \
-                  r32, m32, inv32, inv_in, e32, partials);                                                       \
+                  r32, m32, inv32, inv_in, e32, partials, rev);                                                  \
     } while (0)
     if (kind == KPOISSON) {
         if (w == 4) GR_DF_RESID(KPOISSON, 4);
@@ -315,16 +315,16 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
 }
 
 void df_black_update(int kind, int n, const float *e, const float *r, const float *inv, double h2, float *uh,
-                     float *ul, cudaStream_t st)
+                     float *ul, cudaStream_t st, int rev)
 {
     const int lgn = log2i(n);
     const int64_t threads = (int64_t)n * n * n / 8;
     if (kind == KPOISSON)
         GR_LAUNCH(k_df_black_update<KPOISSON>, wave_grid(k_df_black_update<KPOISSON>, threads), kBlock, st, lgn, e, r,
-                  inv, (float)h2, uh, ul);
+                  inv, (float)h2, uh, ul, rev);
     else
         GR_LAUNCH(k_df_black_update<KHELM>, wave_grid(k_df_black_update<KHELM>, threads), kBlock, st, lgn, e, r, inv,
-                  (float)h2, uh, ul);
+                  (float)h2, uh, ul, rev);
 }
 
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st)

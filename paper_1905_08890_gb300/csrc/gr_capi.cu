@@ -74,6 +74,7 @@ struct gr_ctx {
     int a_fmt = 0;
     int w_fmt = 0;
     bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
+    int dir = 0;           // traversal direction of the next finest-level launch (alternates)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // host-buffer I/O: a copy stream, its events and two particle staging buffers
     cudaStream_t cs = nullptr;
@@ -449,6 +450,15 @@ void vcycle64(gr_ctx *c, int kind, double rho, int nu1, int nu2)
     timed(c, GR_PROF_SWEEP64, [&] { smooth(F, nu2); });
 }
 
+// direction for the next finest-level launch; consecutive launches alternate
+// so that each starts on the data its predecessor touched last
+int next_dir(gr_ctx *c)
+{
+    const int d = c->dir;
+    c->dir ^= 1;
+    return d;
+}
+
 // How a correction V-cycle finds its top level's e: zero (cleared here), the
 // first red relaxation from zero already made (by the fine residual kernel;
 // the black cells are then not read before they are written), or a given
@@ -467,10 +477,12 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
     const bool fine = top == c->nlev - 1;
     auto cls = [&](int k) { return fine ? k : (int)GR_PROF_COARSE; };
     Level &F = c->lev[top];
+    // finest-level launches alternate their traversal direction
+    auto dir_of = [&](const Level &A) { return (fine && &A == &F) ? next_dir(c) : 0; };
     auto smooth = [&](Level &A, int nu) {
         for (int s = 0; s < nu; s++)
             for (int col = 0; col < 2; col++)
-                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st);
+                gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, col, c->st, dir_of(A));
     };
     // levels up to 16^3 run in one block (coarse_tail) when the top is finer than that
     const int tail = (top > 3 && c->tail_on) ? 3 : 0;
@@ -483,7 +495,7 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
         if (nu1 > 0) {
             const bool fr = first_red_from_restrict(l - 1);
             gr::resid_restrict_red(kind32, A.n, A.e, A.r, A.m, A.ih2, C.e, C.r, fr ? C.inv : nullptr, fr ? C.h2 : 0.0,
-                                   c->st);
+                                   c->st, dir_of(A));
         } else {
             gr::resid_restrict<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.ih2, 0.0, C.e, C.r, nullptr, 0, c->st);
         }
@@ -494,17 +506,17 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
             smooth(A, nu1);
             return;
         }
-        gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, 1, c->st);
+        gr::sweep_colour<float>(kind32, A.n, A.e, A.r, A.m, A.inv, A.h2, A.ih2, 0.0, 1, c->st, dir_of(A));
         smooth(A, nu1 - 1);
     };
     // a red pass follows each prolongation when nu2 > 0: only black cells need the correction
     auto up = [&](int l) {
-        if (nu2 > 0) gr::prolong_add_black(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
+        if (nu2 > 0) gr::prolong_add_black(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st, dir_of(c->lev[l]));
         else gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
     };
     timed(c, cls(GR_PROF_SWEEP32), [&] {
         if (start == START_RED_DONE && nu1 > 0) {
-            gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st);
+            gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st, dir_of(F));
             smooth(F, nu1 - 1);
         } else {
             if (start != START_GIVEN) cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
@@ -545,10 +557,10 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
     }
     timed(c, GR_PROF_SWEEP32, [&] {
         smooth(F, nu2 - 1);
-        gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 0, c->st);
+        gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 0, c->st, dir_of(F));
     });
     timed(c, GR_PROF_MIXED_UPDATE,
-          [&] { gr::df_black_update(kind32, F.n, F.e, F.r, F.inv, F.h2, uh, ul, c->st); });
+          [&] { gr::df_black_update(kind32, F.n, F.e, F.r, F.inv, F.h2, uh, ul, c->st, dir_of(F)); });
 }
 
 // Full multigrid correction cycle (nested iteration) on the FP32 correction
@@ -613,7 +625,7 @@ gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r)
     timed(c, GR_PROF_MIXED_RESID, [&] {
         g = gr::df_resid(in.kind, F.n, c->dfu, c->dfu + N, c->dff, c->dff + N, c->dfa, c->dfa + N, c->dfb,
                          c->dfb + N, F.h2, rho, in.ref, F.r, F.m, F.inv, F.inv, red ? F.e : nullptr, c->partials,
-                         c->st);
+                         c->st, next_dir(c));
     });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;

@@ -35,6 +35,10 @@ extern std::atomic<long long> g_launches;
         ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
     } while (0)
 
+// Kernels of the finest level take `rev`: nonzero walks their index range
+// from the end, so a launch that follows one walking forward starts where it
+// stopped, on data still in L2.
+
 // Blocks for a grid-stride kernel over `threads` threads: one full wave (as
 // many blocks per SM as the kernel's registers allow, on every SM) or fewer
 // when the work is smaller.  Every block then takes the same number of
@@ -149,7 +153,7 @@ __device__ __forceinline__ void block_sum2f(float a, float b, double *out)
 // unknown u = psi - 1, one Newton step per cell.
 template <typename T>
 void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, double h2, double ih2, double rho,
-                  int color, cudaStream_t st);
+                  int color, cudaStream_t st, int rev = 0);
 
 // Residual eps = L(u) - f of the fine level restricted to the coarse level.
 // Correction form (fas = 0): fc = -R eps, uc = 0.  FAS (fas = 1, KPSI):
@@ -163,7 +167,7 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
 // ec receives the coarse level's first red relaxation from zero instead of
 // zeros (cinv: the coarse KHELM inverse diagonal), so that pass is skipped.
 void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
-                        float *rc, const float *cinv, double h2c, cudaStream_t st);
+                        float *rc, const float *cinv, double h2c, cudaStream_t st, int rev = 0);
 
 // FAS coarse right-hand side: fc = N(uc) - fc (KPSI, double).
 void fas_rhs(int nc, const double *uc, double *fc, const double *c0, const double *c1, double ih2, double rho,
@@ -175,7 +179,7 @@ void fas_diff(int nc, double *uc, const double *urc, cudaStream_t st);
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st);
 // FP32, black children only (a red relaxation of a linear equation follows)
-void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st);
+void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st, int rev = 0);
 // FP32 coarse = 8-child average of fine (a right-hand side going down)
 void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st);
 
@@ -230,12 +234,12 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
 // count.
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
-             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st);
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev = 0);
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st);
 // last black pass of the FP32 correction cycle (KPOISSON or KHELM, n >= 8)
 // fused with u += e on both colours; e's black half is left unwritten
 void df_black_update(int kind, int n, const float *e, const float *r, const float *inv, double h2, float *uh,
-                     float *ul, cudaStream_t st);
+                     float *ul, cudaStream_t st, int rev = 0);
 
 // ---- double-float set-up and write-back (df_setup.cu) -----------------------
 // Natural FP64 inputs -> split-layout hi/lo pairs, right-hand sides and

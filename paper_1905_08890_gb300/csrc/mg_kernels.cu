@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kBlock)
 // scalar load.  Needs n >= 8 (rows of at least four half-indices).
 template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ u, const float *__restrict__ f,
-                                                   const float *__restrict__ c1, float h2, int color)
+                                                   const float *__restrict__ c1, float h2, int color, int rev)
 {
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int64_t half = (int64_t)1 << (3 * lgn - 1);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ 
     const float *__restrict__ oth = u + (half - off);
     const int64_t nvec = half >> 2;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvec; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = v << 2;
+        const int64_t t = (rev ? nvec - 1 - v : v) << 2;
         const int q = (int)(t & mh);
         const int j = (int)((t >> lgh) & mn);
         const int i = (int)(t >> (lgh + lgn));
@@ -197,13 +197,14 @@ template <typename T, int KIND, int FAS, int RED = 0, int FIRST = 0>
 __global__ void __launch_bounds__(kBlock)
     k_resid_restrict(int lgf, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
                      const T *__restrict__ c1, T ih2, T rho, T *__restrict__ uc, T *__restrict__ fc,
-                     T *__restrict__ urc, const T *__restrict__ cinv = nullptr, T h2c = T(0))
+                     T *__restrict__ urc, const T *__restrict__ cinv = nullptr, T h2c = T(0), int rev = 0)
 {
     const int lgc = lgf - 1;
     const int mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
     const int half = 1 << (3 * lgf - 1);
     const int ncells = 1 << (3 * lgc);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < ncells; tt += gridDim.x * blockDim.x) {
+        const int t = rev ? ncells - 1 - tt : tt;
         const int K = t & mc, J = (t >> lgc) & mc, I = t >> (2 * lgc);
         const int qm = (K - 1) & mc, qp = (K + 1) & mc;
         T v[4][4][4];  // v[a + 1][b + 1][c + 1]
@@ -300,13 +301,14 @@ struct Vec2<double> {
 // read (the point update does not use the old value), so their correction
 // would be dead work.
 template <typename T, int BLACK = 0>
-__global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc)
+__global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc, int rev = 0)
 {
     using V2 = typename Vec2<T>::type;
     const int lgc = lgf - 1, mc = (1 << lgc) - 1, hc = lgc - 1, mq = (1 << hc) - 1;
     const int halfc = 1 << (3 * lgc - 1), halff = 1 << (3 * lgf - 1);
     const T w0 = T(0.25), w1 = T(0.75);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < halfc; t += gridDim.x * blockDim.x) {
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < halfc; tt += gridDim.x * blockDim.x) {
+        const int t = rev ? halfc - 1 - tt : tt;
         const int Q = t & mq, J = (t >> hc) & mc, I = t >> (hc + lgc);
         const int Qm = (Q - 1) & mq, Qp = (Q + 1) & mq;
         T z[3][3][4];  // interpolated along k: fine k = 4Q + m
@@ -553,7 +555,7 @@ __global__ void k_to_float(int64_t cnt, const double *__restrict__ a, float *__r
 // ================================================================ launchers
 template <typename T>
 void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, double h2, double ih2, double rho,
-                  int color, cudaStream_t st)
+                  int color, cudaStream_t st, int rev)
 {
     const int lgn = log2i(n);
     if (sizeof(T) == 4 && n >= 8 && kind != KPSI) {
@@ -562,10 +564,10 @@ void sweep_colour(int kind, int n, T *u, const T *f, const T *c0, const T *c1, d
         const int64_t threads = (int64_t)n * n * n / 8;
         if (kind == KPOISSON)
             GR_LAUNCH(k_sweep4<KPOISSON>, wave_grid(k_sweep4<KPOISSON>, threads), kBlock, st, lgn, uf, ff, cf,
-                      (float)h2, color);
+                      (float)h2, color, rev);
         else
             GR_LAUNCH(k_sweep4<KHELM>, wave_grid(k_sweep4<KHELM>, threads), kBlock, st, lgn, uf, ff, cf, (float)h2,
-                      color);
+                      color, rev);
         return;
     }
     const int g = grid_for((int64_t)n * n * n / 2);
@@ -594,14 +596,16 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
 }
 
 void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
-                        float *rc, const float *cinv, double h2c, cudaStream_t st)
+                        float *rc, const float *cinv, double h2c, cudaStream_t st, int rev)
 {
     const int lgf = log2i(nf);
     const int64_t threads = (int64_t)nf * nf * nf / 8;
     const float hc = (float)h2c;
+    // a fixed 16 blocks per SM: measured faster here than a single wave
+    const int g = grid_for(threads);
 #define GR_RR(K, F)                                                                                          \
-    GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), wave_grid(k_resid_restrict<float, K, 0, 1, F>, threads),  \
-              kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, rc, nullptr, cinv, hc)
+    GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, \
+              rc, nullptr, cinv, hc, rev)
     if (kind == KPOISSON) {
         if (cinv || h2c > 0) GR_RR(KPOISSON, 1);
         else GR_RR(KPOISSON, 0);
@@ -629,17 +633,17 @@ void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st)
     GR_LAUNCH((k_restrict_avg<float>), grid_for((int64_t)nf * nf * nf / 8), kBlock, st, log2i(nf), fine, coarse);
 }
 
-void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st)
+void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st, int rev)
 {
     GR_LAUNCH((k_prolong_add<float, 1>), wave_grid(k_prolong_add<float, 1>, (int64_t)nf * nf * nf / 16), kBlock, st,
-              log2i(nf), u, uc);
+              log2i(nf), u, uc, rev);
 }
 
 template <typename T>
 void prolong_add(int nf, T *u, const T *uc, cudaStream_t st)
 {
     GR_LAUNCH((k_prolong_add<T>), wave_grid(k_prolong_add<T>, (int64_t)nf * nf * nf / 16), kBlock, st, log2i(nf), u,
-              uc);
+              uc, 0);
 }
 
 template <typename T>
@@ -723,7 +727,7 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st)
 
 #define GR_INST(T)                                                                                                  \
     template void sweep_colour<T>(int, int, T *, const T *, const T *, const T *, double, double, double, int,     \
-                                  cudaStream_t);                                                                   \
+                                  cudaStream_t, int);                                                              \
     template void resid_restrict<T>(int, int, const T *, const T *, const T *, const T *, double, double, T *, T *, \
                                     T *, int, cudaStream_t);                                                       \
     template void prolong_add<T>(int, T *, const T *, cudaStream_t);                                               \
