@@ -125,11 +125,12 @@ typedef enum {
     GR_PROF_SWEEP32,       /* FP32 red-black colour pass (mixed) */
     GR_PROF_RESTRICT,      /* residual fused with restriction (FP64 or FP32) */
     GR_PROF_PROLONG,       /* trilinear prolongation + correction (FP64 or FP32) */
-    GR_PROF_MIXED_RESID,   /* FP64 residual feeding the FP32 correction (mixed) */
-    GR_PROF_MIXED_UPDATE,  /* FP64 += FP32 correction (mixed) */
+    GR_PROF_MIXED_RESID,   /* fine residual feeding the FP32 correction (mixed: FP64; mixed_df: double-float,
+                              with the correction's first red pass) */
+    GR_PROF_MIXED_UPDATE,  /* u += FP32 correction (mixed_df: fused with the last black pass) */
     GR_PROF_NORM64,        /* FP64 residual norm (FP64 path) */
     GR_PROF_SETUP,         /* sources, coefficients and layout changes of the finest level */
-    GR_PROF_COARSE,        /* every multigrid kernel below the finest level */
+    GR_PROF_COARSE,        /* every multigrid kernel below the finest level (and full multigrid's coarser cycles) */
     GR_NPROF
 } gr_prof_class;
 
