@@ -68,8 +68,10 @@ typedef enum {
     GR_PREC_FP64 = 0,     /* every sweep, transfer and residual in FP64 */
     GR_PREC_MIXED = 1,    /* FP64 fine residual and update; FP32 correction V-cycle
                              (psi: on the Newton linearisation); FP64 2^3 level */
-    GR_PREC_MIXED_DF = 2  /* as GR_PREC_MIXED, but the fine residual and update in
-                             double-float (pairs of FP32, 48-bit significand) */
+    GR_PREC_MIXED_DF = 2  /* as GR_PREC_MIXED, but the finest level's set-up, residual,
+                             update and write-back in double-float (pairs of FP32,
+                             48-bit significand); results agree with GR_PREC_FP64 to
+                             the tolerance */
 } gr_prec;
 
 typedef struct gr_ctx gr_ctx; /* opaque */
