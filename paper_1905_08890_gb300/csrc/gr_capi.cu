@@ -3,11 +3,14 @@
 // Each equation is solved on a hierarchy of levels n, n/2, ..., 2 (Sec. 4.3.1,
 // last paragraph) held in red-black split layout.  FP64 path: V(nu1, nu2)
 // cycles, correction form for the linear equations (Eq. GR-linear-coarse),
-// full approximation scheme for psi (Sec. 4.3.2.1).  Mixed path: an FP64
+// full approximation scheme for psi (Sec. 4.3.2.1).  Mixed paths: a
 // defect-correction loop whose correction equation lap e - m e = -eps is
 // relaxed by one FP32 V-cycle per iteration (for psi, m is the Newton
-// linearisation of the Hamiltonian-constraint operator); the 2^3 level and
-// all reductions stay FP64.
+// linearisation of the Hamiltonian-constraint operator; optionally a full
+// multigrid cycle for the first iteration); the fine residual and update are
+// FP64 (GR_PREC_MIXED) or double-float, with the finest level's set-up and
+// write-back too (GR_PREC_MIXED_DF); the 2^3 level and all reductions' last
+// stages stay FP64.  Host-buffer I/O runs on a copy stream of the context.
 #include <cuda_runtime.h>
 
 #include <atomic>
