@@ -258,6 +258,100 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
+// FP32 red-children restriction (correction form, after a black pass), one
+// thread per pair of coarse cells K = 2Q, 2Q + 1 of coarse row (I, J): their
+// red children lie at fine k = 4Q + d, d = 0..3, of the four central fine rows
+// (2I + a, 2J + b).  Per central row the six values at d = -1 .. 4 are two
+// two-element vectors and two scalars (one colour holds even, the other odd k);
+// each of the eight side rows (a or b in {-1, 2}) contributes the two black
+// values facing the red children of its central neighbour, one vector.  About
+// half the loads and a third of the index arithmetic of one thread per coarse
+// cell.  FIRST as in k_resid_restrict.
+template <int KIND, int FIRST>
+__global__ void __launch_bounds__(kBlock)
+    k_restrict_red2(int lgf, const float *__restrict__ e, const float *__restrict__ r, const float *__restrict__ m,
+                    float ih2, float *__restrict__ ec, float *__restrict__ rc, const float *__restrict__ cinv,
+                    float h2c, int rev)
+{
+    using V2 = float2;
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1, hcl = lgc - 1, mq = (1 << hcl) - 1;
+    const int mf = (1 << lgf) - 1, mhf = (1 << (lgf - 1)) - 1;
+    const int halff = 1 << (3 * lgf - 1), halfc = 1 << (3 * lgc - 1);
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < halfc; tt += gridDim.x * blockDim.x) {
+        const int t = rev ? halfc - 1 - tt : tt;
+        const int Q = t & mq, J = (t >> hcl) & mc, I = t >> (hcl + lgc);
+        const int h0 = 2 * Q;  // fine half-index of k = 4Q
+        auto base = [&](int a, int b) {
+            const int fi = (2 * I + a) & mf, fj = (2 * J + b) & mf;
+            return ((fi << lgf) + fj) << (lgf - 1);
+        };
+        // central rows: c[a][b][d + 1] = e at k = 4Q + d, d = -1 .. 4
+        float c[2][2][6];
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const int rb = base(a, b);
+                const int pr = (a + b) & 1;  // colour of even k in this row
+                const int ev = pr ? halff : 0, od = halff - ev;
+                const V2 E = *reinterpret_cast<const V2 *>(e + ev + rb + h0);  // k = 4Q, 4Q + 2
+                const V2 O = *reinterpret_cast<const V2 *>(e + od + rb + h0);  // k = 4Q + 1, 4Q + 3
+                c[a][b][1] = E.x;
+                c[a][b][3] = E.y;
+                c[a][b][2] = O.x;
+                c[a][b][4] = O.y;
+                c[a][b][0] = e[od + rb + ((h0 - 1) & mhf)];  // k = 4Q - 1
+                c[a][b][5] = e[ev + rb + ((h0 + 2) & mhf)];  // k = 4Q + 4
+            }
+        // side rows: the black values at the red children's k of the adjacent central row
+        // si[b][0]: row (-1, b), si[b][1]: row (2, b); sj[a][0]: row (a, -1), sj[a][1]: row (a, 2)
+        V2 si[2][2], sj[2][2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            si[q][0] = *reinterpret_cast<const V2 *>(e + halff + base(-1, q) + h0);
+            si[q][1] = *reinterpret_cast<const V2 *>(e + halff + base(2, q) + h0);
+            sj[q][0] = *reinterpret_cast<const V2 *>(e + halff + base(q, -1) + h0);
+            sj[q][1] = *reinterpret_cast<const V2 *>(e + halff + base(q, 2) + h0);
+        }
+        float s[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const int pr = (a + b) & 1;  // red children of this row: d = pr, pr + 2
+                const int rb = base(a, b);
+                const V2 R = *reinterpret_cast<const V2 *>(r + rb + h0);  // red r at d = pr, pr + 2
+                V2 M = make_float2(0.0f, 0.0f);
+                if (KIND == KHELM) M = *reinterpret_cast<const V2 *>(m + rb + h0);
+#pragma unroll
+                for (int w = 0; w < 2; w++) {
+                    const int d = pr + 2 * w;
+                    const float uc = c[a][b][d + 1];
+                    // i neighbours: a - 1 and a + 1 (a side row when outside 0..1)
+                    const float ia = a == 0 ? (w ? si[b][0].y : si[b][0].x) : c[0][b][d + 1];
+                    const float ib = a == 1 ? (w ? si[b][1].y : si[b][1].x) : c[1][b][d + 1];
+                    const float ja = b == 0 ? (w ? sj[a][0].y : sj[a][0].x) : c[a][0][d + 1];
+                    const float jb = b == 1 ? (w ? sj[a][1].y : sj[a][1].x) : c[a][1][d + 1];
+                    const float nb = ia + ib + ja + jb + c[a][b][d] + c[a][b][d + 2];
+                    float lap = (nb - 6.0f * uc) * ih2;
+                    if (KIND == KHELM) lap -= (w ? M.y : M.x) * uc;
+                    s[w] += lap - (w ? R.y : R.x);
+                }
+            }
+        const int off = ((I << lgc) + J) << hcl;
+        const int c0 = (I + J) & 1;  // colour of coarse K = 2Q
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+            const int cid = ((c0 ^ w) ? halfc : 0) + off + Q;
+            const float rcv = -(0.125f * s[w]);
+            rc[cid] = rcv;
+            float e0 = 0.0f;
+            if (FIRST && !(c0 ^ w)) e0 = -h2c * rcv * (KIND == KHELM ? cinv[cid] : (1.0f / 6.0f));
+            ec[cid] = e0;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBlock)
     k_fas_rhs(int lgc, const double *__restrict__ uc, double *__restrict__ fc, const double *__restrict__ c0,
               const double *__restrict__ c1, double ih2, double rho)
@@ -603,6 +697,20 @@ void resid_restrict_red(int kind, int nf, const float *e, const float *r, const 
     const float hc = (float)h2c;
     // a fixed 16 blocks per SM: measured faster here than a single wave
     const int g = grid_for(threads);
+    if (nf >= 8) {  // two coarse cells per thread
+        const int g2 = grid_for(threads / 2);
+#define GR_RR2(K, F) \
+    GR_LAUNCH((k_restrict_red2<K, F>), g2, kBlock, st, lgf, e, r, m, (float)ih2, ec, rc, cinv, hc, rev)
+        if (kind == KPOISSON) {
+            if (cinv || h2c > 0) GR_RR2(KPOISSON, 1);
+            else GR_RR2(KPOISSON, 0);
+        } else {
+            if (h2c > 0) GR_RR2(KHELM, 1);
+            else GR_RR2(KHELM, 0);
+        }
+#undef GR_RR2
+        return;
+    }
 #define GR_RR(K, F)                                                                                          \
     GR_LAUNCH((k_resid_restrict<float, K, 0, 1, F>), g, kBlock, st, lgf, e, r, m, nullptr, (float)ih2, 0.0f, ec, \
               rc, nullptr, cinv, hc, rev)

@@ -223,23 +223,26 @@ def test_homogeneous_background_from_random_guesses():
 
 
 # ------------------------------------------------------------------ errors
-def test_nonfinite_source_is_reported():
-    n = 8
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("field", ["s0", "sx"])
+def test_nonfinite_source_is_reported(field, prec):
+    n = 32
     p, src = _problem(n)
-    src["s0"][1, 2, 3] = np.nan
+    src[field][1, 2, 3] = np.nan
     ctx = gr.Context(n)
     with pytest.raises(gr.GRError) as ei:
-        ctx.solve(_fields_to_gpu(src), _fields_to_gpu(oracle.initial_fields(n)), rho_hat=p.rho_hat)
+        ctx.solve(_fields_to_gpu(src), _fields_to_gpu(oracle.initial_fields(n)), rho_hat=p.rho_hat, prec=prec)
     assert ei.value.status == gr.GR_ERR_NONFINITE
     ctx.close()
 
 
-def test_max_cycles_reports_noconv_with_report():
+@pytest.mark.parametrize("prec", ["fp64", "mixed_df"])
+def test_max_cycles_reports_noconv_with_report(prec):
     n = 16
     p, src = _problem(n)
     ctx = gr.Context(n)
     rep = ctx.solve(_fields_to_gpu(src), _fields_to_gpu(oracle.initial_fields(n)), tol=1e-14, max_cycles=1,
-                    rho_hat=p.rho_hat, allow_noconv=True)
+                    rho_hat=p.rho_hat, allow_noconv=True, prec=prec)
     assert rep["status_code"] == gr.GR_ERR_NOCONV
     assert rep["cycles"] == [1] * 10
     assert all(s == gr.GR_ERR_NOCONV for s in rep["status"])
