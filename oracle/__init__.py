@@ -14,6 +14,10 @@ Equation kinds: POISSON (lap u = f), HELMHOLTZ (lap u - c0 u = f) and PSI
 (lap u + 2 pi c0/psi + c1/(8 psi^7) - 2 pi rho psi^5 = f with psi = 1 + u:
 the unknown of the psi kind is the deviation psi - 1).
 
+Static nested refinement patches: ``deposit_window``/``deposit_patches``,
+``composite_eq`` (one equation) and ``solve_composite`` (the ten) on a chain
+of patches given as dicts {"n": cells per side, "origin": [3 parent cells]}.
+
 Field order used throughout: psi, alpha psi, V_x, V_y, V_z, U, B^x, B^y, B^z, b.
 Equation (solve) order: V_x, V_y, V_z, U, psi, alpha psi, B^x, B^y, B^z, b
 (Sec. 2.4 solution sequence; Sec. 4.3.1 equations MG-linear-1a ... 2).
@@ -90,6 +94,12 @@ def lib():
             L.orc_solve_constraints.restype = I
             L.orc_residual_at.argtypes = [I, I, P, P, D, D, I64, P, P, P]
             L.orc_residual_at.restype = None
+            L.orc_deposit_window.argtypes = [I, P, I, I64, P, P, D, P, P, P, P, P]
+            L.orc_deposit_window.restype = None
+            L.orc_composite_eq.argtypes = [I, I, I, P, P, D, P, P, P, P, P, P, P, P, P, D, I, I, I, P, P, P]
+            L.orc_composite_eq.restype = I
+            L.orc_solve_composite.argtypes = [I, I, P, P, P, P, P, P, D, D, D, I, I, I, P, P, P]
+            L.orc_solve_composite.restype = I
             _lib = L
     return _lib
 
@@ -299,3 +309,98 @@ def residual_at(eq: int, src: dict, fld: dict, rho_hat: float, cells, S_hat: flo
     f = np.empty(idx.size)
     lib().orc_residual_at(eq, n, sp, fp, rho_hat, S_hat, idx.size, idx.ctypes.data, eps.ctypes.data, f.ctypes.data)
     return eps, f
+
+
+# ---------------------------------------------------------------- patches
+# A chain of static patches: patch p (1-based) has n_p cells per side at
+# spacing h0 / 2^p and refines the parent block origin_p .. origin_p + n_p/2 - 1
+# (parent cells per axis; patch 1's block may wrap on the periodic base).
+def patch_window(n0: int, patches, p: int):
+    """(N, O): the resolution N = n0 2^p and the origin O (cells of that
+    resolution, per axis) of patch p (1-based) of the chain."""
+    O = [0, 0, 0]
+    for q in range(1, p + 1):
+        O = [2 * (O[d] + patches[q - 1]["origin"][d]) for d in range(3)]
+    N = n0 << p
+    return N, [o % N for o in O]
+
+
+def deposit_window(N: int, O, nw: int, x: np.ndarray, u: np.ndarray, mass: float) -> dict:
+    """CIC sources at resolution N on the nw^3 window of cells O + a (mod N)."""
+    x = _f64(x)
+    u = _f64(u)
+    npart = x.shape[1] if x.ndim == 2 else 0
+    out = {k: np.zeros((nw, nw, nw)) for k in SOURCES}
+    Oa = (ctypes.c_int * 3)(*[int(o) for o in O])
+    lib().orc_deposit_window(N, Oa, nw, npart, _p(x), _p(u), mass, *[_p(out[k]) for k in SOURCES])
+    return out
+
+
+def deposit_patches(n0: int, patches, x, u, mass: float):
+    """Sources of every patch of the chain (list of dicts)."""
+    out = []
+    for p in range(1, len(patches) + 1):
+        N, O = patch_window(n0, patches, p)
+        out.append(deposit_window(N, O, patches[p - 1]["n"], x, u, mass))
+    return out
+
+
+def _chain(patches):
+    pn = (ctypes.c_int * max(1, len(patches)))(*[int(q["n"]) for q in patches])
+    po = (ctypes.c_int * max(3, 3 * len(patches)))(*[int(o) for q in patches for o in q["origin"]])
+    return pn, po
+
+
+def composite_eq(kind, u0, f0, patches, up, fp, c00=None, c10=None, c0p=None, c1p=None, rho=0.0, refs=None,
+                 tol=1e-10, max_cycles=50, nu1=2, nu2=2):
+    """Composite solve of one equation, in place on u0 (base, n0^3) and the
+    patch interiors up[p] (n_p^3); fp, c0p, c1p: per-patch arrays (or None).
+    Returns (status, cycles, res0, res) with per-level residual lists."""
+    n0 = u0.shape[0]
+    np_ = len(patches)
+    f0 = _f64(f0)
+    c00 = None if c00 is None else _f64(c00)
+    c10 = None if c10 is None else _f64(c10)
+    for a in up:
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    fp = [_f64(a) for a in fp]
+    c0p = [None if a is None else _f64(a) for a in (c0p or [None] * np_)]
+    c1p = [None if a is None else _f64(a) for a in (c1p or [None] * np_)]
+    arr = lambda lst: (ctypes.c_void_p * max(1, np_))(*[None if a is None else a.ctypes.data for a in lst])
+    pn, po = _chain(patches)
+    rf = (ctypes.c_double * (np_ + 1))(*([0.0] * (np_ + 1) if refs is None else refs))
+    cyc = ctypes.c_int(0)
+    r0 = (ctypes.c_double * (np_ + 1))()
+    r = (ctypes.c_double * (np_ + 1))()
+    st = lib().orc_composite_eq(kind, n0, np_, pn, po, rho, _p(u0), _p(f0), _p(c00), _p(c10), arr(up), arr(fp),
+                                arr(c0p), arr(c1p), rf, tol, max_cycles, nu1, nu2, ctypes.byref(cyc), r0, r)
+    return st, cyc.value, list(r0), list(r)
+
+
+def initial_patch_fields(patches):
+    return [initial_fields(q["n"]) for q in patches]
+
+
+def solve_composite(src0: dict, srcp, fld0: dict, fldp, patches, rho_hat: float, S_hat: float = 0.0, tol=1e-10,
+                    max_cycles=50, nu1=2, nu2=2):
+    """Ten-equation composite solve, in place on fld0 (base) and fldp (one
+    field dict per patch).  Returns (status, report): per-equation cycles and
+    status in solve order, res[e][l] the final residual of level l."""
+    n0 = src0["s0"].shape[0]
+    np_ = len(patches)
+    s0 = [_f64(src0[k]) for k in SOURCES]
+    sp = [_f64(d[k]) for d in srcp for k in SOURCES]
+    for d in [fld0] + list(fldp):
+        for k in FIELDS:
+            assert d[k].dtype == np.float64 and d[k].flags.c_contiguous
+    f0 = [fld0[k] for k in FIELDS]
+    fpl = [d[k] for d in fldp for k in FIELDS]
+    vp = lambda lst: (ctypes.c_void_p * max(1, len(lst)))(*[a.ctypes.data for a in lst])
+    pn, po = _chain(patches)
+    cyc = (ctypes.c_int * 10)()
+    r = (ctypes.c_double * (10 * (np_ + 1)))()
+    sts = (ctypes.c_int * 10)()
+    st = lib().orc_solve_composite(n0, np_, pn, po, vp(s0), vp(sp), vp(f0), vp(fpl), rho_hat, S_hat, tol,
+                                   max_cycles, nu1, nu2, cyc, r, sts)
+    res = [list(r[e * (np_ + 1):(e + 1) * (np_ + 1)]) for e in range(10)]
+    return st, {"cycles": list(cyc), "res": res, "status": list(sts)}

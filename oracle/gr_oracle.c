@@ -35,6 +35,10 @@
  *
  * Background scalars: K^2 = 24 pi rho_hat, Kdot = 12 pi rho_hat + 4 pi S_hat
  * (Eqs. 1-Friedmann, 2-Friedmann with rho_Lambda = 0).
+ *
+ * Static nested refinement patches (the last part of this file): the same
+ * equations on a chain of cubic patches, each refining its parent by 2,
+ * coupled to the base by composite-grid FAS with flux matching.
  */
 #include <math.h>
 #include <stdint.h>
@@ -857,4 +861,820 @@ void orc_residual_at(int eq, int n, const double *const *src, const double *cons
         eps[c] = e;
         fscale[c] = f;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Static nested refinement patches: composite-grid FAS                */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper solves its equations on the adaptive grid of its host code
+ * (Sec. 3, Sec. 4.3) without stating how a refined region couples to its
+ * parent.  This part takes the multilevel FAS reading (Brandt's multilevel
+ * adaptive technique) for static cubic patches: patch p refines a block of
+ * n_p/2 cells per side of its parent by 2 per axis; patch 1 lies in the
+ * periodic base (its block may wrap), patch p + 1 inside patch p with at
+ * least two parent cells to spare on every side.
+ *
+ *   - A patch solves its own equation on its interior cells.  Its two ghost
+ *     layers hold the trilinear interpolation P of the parent (Dirichlet
+ *     data; the same weights as the prolongation, 3/4 and 1/4 per axis).
+ *   - After the patch's relaxation the parent takes, on the cells the patch
+ *     covers, u = R u_patch and the right-hand side L_parent(u) - R eps_patch
+ *     (eps = L(u) - f of the patch, R the 8-child average), so that the
+ *     parent converges to the restricted patch solution there (FAS,
+ *     Sec. 4.3.2.1, applied across levels of different extent).
+ *   - After the parent's solve the patch interior takes P(u_new - u_old) of
+ *     the parent's change and its ghosts are interpolated afresh.
+ *   - Flux matching: on each uncovered parent cell that shares a face with
+ *     the covered block, the coarse flux (u_in - u_out)/h_c through that face
+ *     is replaced by the mean of the four fine fluxes (u_inner - u_ghost)/h_f
+ *     through it, as the right-hand side change -(T_fine - T_coarse)/h_c
+ *     taken at each injection.  The composite operator is then conservative
+ *     (its volume-weighted sum telescopes), and with the trilinear ghosts the
+ *     composite solution is second-order accurate; without it the flux
+ *     mismatch acts as a spurious source.
+ *
+ * One composite cycle: base V-cycle, then for p = 1..P the correction and
+ * nu2 sweeps of patch p, then for p = P..1 nu1 sweeps of patch p, its
+ * residual and the injection into its parent.  The residual of level l is
+ * RMS(eps_l) over all its cells after that injection (on covered cells it is
+ * R eps of the finer level), relative to the level's own reference; a solve
+ * converges when every level is at or below tol.
+ *
+ * Periodic Poisson-type equations: the coupled system is solvable only if
+ * the volume-weighted sum of its right-hand sides vanishes, and a patch's
+ * sources (deposited at its own resolution) need not sum to the base's over
+ * the same region.  The system carries a scalar lambda added to the
+ * source of every cell that no finer level covers, on every level (lambda
+ * starts at 0).  After each injection into the base, m = mean of the base
+ * right-hand side; every base cell loses m and lambda becomes lambda - m, so
+ * the base stays mean-free and the patches see the same constant (on covered
+ * cells it arrives through R eps).  The solution's mean is removed from every
+ * level once, at the end.
+ */
+#define PG 2          /* ghost layers of a patch */
+#define ORC_MAXP 4    /* patches in a chain */
+
+static inline int64_t gx(int m, int i, int j, int k) { return ((int64_t)(i + PG) * m + (j + PG)) * m + (k + PG); }
+static inline int wrapi(int i, int n) { return ((i % n) + n) % n; }
+static inline int fdiv2(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
+
+/* One level seen as arrays with a common index map: the periodic base
+   (natural n^3, indices wrap) or a patch (ghosted (n + 2 PG)^3). */
+typedef struct {
+    int n, ghosted;
+    double *u, *f, *c0, *c1;
+    double h2, ih2;
+} view_t;
+
+static inline int64_t vidx(const view_t *v, int i, int j, int k)
+{
+    if (v->ghosted) return gx(v->n + 2 * PG, i, j, k);
+    return ix(v->n, wrapi(i, v->n), wrapi(j, v->n), wrapi(k, v->n));
+}
+
+static inline double vnb(const view_t *v, const double *a, int i, int j, int k)
+{
+    return a[vidx(v, i + 1, j, k)] + a[vidx(v, i - 1, j, k)] + a[vidx(v, i, j + 1, k)] + a[vidx(v, i, j - 1, k)] +
+           a[vidx(v, i, j, k + 1)] + a[vidx(v, i, j, k - 1)];
+}
+
+/* L(u) of the level at one cell */
+static inline double vop(int kind, const view_t *v, double rho, int i, int j, int k)
+{
+    const int64_t c = vidx(v, i, j, k);
+    const double c0 = v->c0 ? v->c0[c] : 0.0, c1 = v->c1 ? v->c1[c] : 0.0;
+    return op_point(kind, v->u[c], vnb(v, v->u, i, j, k), v->ih2, c0, c1, rho);
+}
+
+typedef struct {
+    view_t v;              /* ghosted arrays of this patch */
+    int o[3];              /* origin in parent cells */
+    int nc, w;             /* covered parent cells per side (n / 2), window side (nc + 4) */
+    double *eps, *win, *old, *Ru, *Re;
+    double *flux;          /* the flux correction in force on each of the 6 nc^2 parent cells next to the block */
+    double ref;
+} patch_t;
+
+/* parent cells o - 2 .. o + nc + 1 per axis into a w^3 window */
+static void gather_window(const view_t *par, const patch_t *P, const double *a, double *win)
+{
+    const int w = P->w;
+    for (int x = 0; x < w; x++)
+        for (int y = 0; y < w; y++)
+            for (int z = 0; z < w; z++)
+                win[((int64_t)x * w + y) * w + z] = a[vidx(par, P->o[0] - 2 + x, P->o[1] - 2 + y, P->o[2] - 2 + z)];
+}
+
+/* trilinear interpolation of a window at patch cell (i, j, k), -PG <= i < n + PG:
+   fine cell i sits in parent cell floor(i/2) and leans towards its neighbour
+   on the side of i's half (weights 3/4, 1/4 per axis) */
+static double interp_window(const double *win, int w, int i, int j, int k)
+{
+    int I[2], J[2], K[2];
+    I[0] = fdiv2(i) + 2; I[1] = I[0] + ((i & 1) ? 1 : -1);
+    J[0] = fdiv2(j) + 2; J[1] = J[0] + ((j & 1) ? 1 : -1);
+    K[0] = fdiv2(k) + 2; K[1] = K[0] + ((k & 1) ? 1 : -1);
+    const double wt[2] = {0.75, 0.25};
+    double s = 0.0;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int c = 0; c < 2; c++) s += wt[a] * wt[b] * wt[c] * win[((int64_t)I[a] * w + J[b]) * w + K[c]];
+    return s;
+}
+
+static inline int is_interior(int n, int i, int j, int k)
+{
+    return i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n;
+}
+
+/* ghost cells of a (ghosted m^3) patch array from the parent window */
+static void fill_ghosts(const patch_t *P, const double *win, double *a)
+{
+    const int n = P->v.n, m = n + 2 * PG;
+    for (int i = -PG; i < n + PG; i++)
+        for (int j = -PG; j < n + PG; j++)
+            for (int k = -PG; k < n + PG; k++)
+                if (!is_interior(n, i, j, k)) a[gx(m, i, j, k)] = interp_window(win, P->w, i, j, k);
+}
+
+/* the block of a patch's cells that its child patch covers (co = NULL: no child) */
+typedef struct {
+    const int *co;
+    int nc;
+    double lam;
+} cover_t;
+
+/* right-hand side of a patch cell: f, plus lambda where no child covers it */
+static inline double rhs_at(const view_t *v, const cover_t *cv, int i, int j, int k)
+{
+    const double f = v->f[vidx(v, i, j, k)];
+    if (cv->co && i - cv->co[0] >= 0 && i - cv->co[0] < cv->nc && j - cv->co[1] >= 0 && j - cv->co[1] < cv->nc &&
+        k - cv->co[2] >= 0 && k - cv->co[2] < cv->nc)
+        return f;
+    return f + cv->lam;
+}
+
+/* one red-black Gauss-Seidel colour over the patch interior (local colour
+   (i + j + k) % 2), the same point update as gs_colour */
+static void patch_gs(int kind, double rho, const view_t *v, const cover_t *cv, int color)
+{
+    const int n = v->n;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = (i + j + color) & 1; k < n; k += 2) {
+                const int64_t c = vidx(v, i, j, k);
+                const double nb = vnb(v, v->u, i, j, k);
+                const double f = rhs_at(v, cv, i, j, k);
+                double *u = v->u;
+                if (kind == ORC_POISSON) {
+                    u[c] = (nb - v->h2 * f) / 6.0;
+                } else if (kind == ORC_HELMHOLTZ) {
+                    u[c] = (nb - v->h2 * f) / (6.0 + v->h2 * v->c0[c]);
+                } else {
+                    double w = 1.0 + u[c], w2 = w * w, w4 = w2 * w2;
+                    double g = op_point(ORC_PSI, u[c], nb, v->ih2, v->c0[c], v->c1[c], rho) - f;
+                    double dg = -6.0 * v->ih2 - 2.0 * PI * v->c0[c] / w2 - 7.0 * v->c1[c] / (8.0 * w4 * w4) -
+                                10.0 * PI * rho * w4;
+                    u[c] -= g / dg;
+                }
+            }
+}
+
+/* eps = L(u) - f over the patch interior; returns RMS(eps) */
+static double patch_residual(int kind, double rho, const patch_t *P, const cover_t *cv)
+{
+    const int n = P->v.n;
+    double s = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) {
+                const int64_t c = vidx(&P->v, i, j, k);
+                const double e = vop(kind, &P->v, rho, i, j, k) - rhs_at(&P->v, cv, i, j, k);
+                P->eps[c] = e;
+                s += e * e;
+            }
+    return sqrt(s / (double)cells(n));
+}
+
+/* Ru, Re: 8-child averages of the patch's u and eps (nc^3, natural) */
+static void patch_restrict(const patch_t *P)
+{
+    const int nc = P->nc;
+    for (int I = 0; I < nc; I++)
+        for (int J = 0; J < nc; J++)
+            for (int K = 0; K < nc; K++) {
+                double su = 0.0, se = 0.0;
+                for (int a = 0; a < 2; a++)
+                    for (int b = 0; b < 2; b++)
+                        for (int c = 0; c < 2; c++) {
+                            const int64_t id = vidx(&P->v, 2 * I + a, 2 * J + b, 2 * K + c);
+                            su += P->v.u[id];
+                            se += P->eps[id];
+                        }
+                P->Ru[ix(nc, I, J, K)] = 0.125 * su;
+                P->Re[ix(nc, I, J, K)] = 0.125 * se;
+            }
+}
+
+typedef struct {
+    int kind, np, nu1, nu2, n0;
+    double rho;
+    hier_t H;                    /* base hierarchy; its finest f is the working right-hand side */
+    view_t base;                 /* finest base level */
+    double *forig;               /* the base right-hand side as set up */
+    patch_t P[ORC_MAXP + 1];     /* P[1..np] */
+    double ref[ORC_MAXP + 1];
+    double lambda;               /* the Poisson solvability constant */
+} comp_t;
+
+static view_t *parent_of(comp_t *C, int p) { return p == 1 ? &C->base : &C->P[p - 1].v; }
+
+static cover_t cover_of(const comp_t *C, int p)
+{
+    cover_t cv = {NULL, 0, C->lambda};
+    if (p < C->np) {
+        cv.co = C->P[p + 1].o;
+        cv.nc = C->P[p + 1].nc;
+    }
+    return cv;
+}
+
+/* u = R u_patch and f = L(u) - R eps on the parent cells patch p covers;
+   the parent window after the injection becomes the patch's u_old */
+static void inject(comp_t *C, int p)
+{
+    patch_t *P = &C->P[p];
+    view_t *par = parent_of(C, p);
+    const int nc = P->nc;
+    patch_restrict(P);
+    for (int I = 0; I < nc; I++)
+        for (int J = 0; J < nc; J++)
+            for (int K = 0; K < nc; K++)
+                par->u[vidx(par, P->o[0] + I, P->o[1] + J, P->o[2] + K)] = P->Ru[ix(nc, I, J, K)];
+    gather_window(par, P, par->u, P->old);
+    for (int I = 0; I < nc; I++)
+        for (int J = 0; J < nc; J++)
+            for (int K = 0; K < nc; K++) {
+                const int a = P->o[0] + I, b = P->o[1] + J, c = P->o[2] + K;
+                par->f[vidx(par, a, b, c)] = vop(C->kind, par, C->rho, a, b, c) - P->Re[ix(nc, I, J, K)];
+            }
+    {
+        /* parent cells next to the block: the coarse flux through the shared face
+           replaced by the mean of the four fine fluxes (as a right-hand side change) */
+        const int n = P->v.n, m = n + 2 * PG;
+        const double hc = sqrt(par->h2), hf = 0.5 * hc;
+        int q = 0;
+        for (int ax = 0; ax < 3; ax++)
+            for (int sd = -1; sd <= 1; sd += 2)
+                for (int t1 = 0; t1 < nc; t1++)
+                    for (int t2 = 0; t2 < nc; t2++, q++) {
+                        const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+                        int in[3], out[3];
+                        in[ax] = sd < 0 ? 0 : nc - 1;
+                        in[b1] = t1;
+                        in[b2] = t2;
+                        for (int d = 0; d < 3; d++) out[d] = in[d] + (d == ax ? sd : 0);
+                        const double uin = par->u[vidx(par, P->o[0] + in[0], P->o[1] + in[1], P->o[2] + in[2])];
+                        const double uout = par->u[vidx(par, P->o[0] + out[0], P->o[1] + out[1], P->o[2] + out[2])];
+                        const double Tc = (uin - uout) / hc;
+                        double Tf = 0.0;
+                        for (int e1 = 0; e1 < 2; e1++)
+                            for (int e2 = 0; e2 < 2; e2++) {
+                                int fi[3], fg[3];
+                                fi[ax] = sd < 0 ? 0 : n - 1;
+                                fg[ax] = sd < 0 ? -1 : n;
+                                fi[b1] = fg[b1] = 2 * t1 + e1;
+                                fi[b2] = fg[b2] = 2 * t2 + e2;
+                                Tf += (P->v.u[gx(m, fi[0], fi[1], fi[2])] - P->v.u[gx(m, fg[0], fg[1], fg[2])]) / hf;
+                            }
+                        Tf *= 0.25;
+                        const double corr = -(Tf - Tc) / hc;
+                        par->f[vidx(par, P->o[0] + out[0], P->o[1] + out[1], P->o[2] + out[2])] += corr - P->flux[q];
+                        P->flux[q] = corr;
+                    }
+    }
+    if (p == 1 && C->kind == ORC_POISSON) {
+        /* the base loses the mean of its right-hand side; lambda follows */
+        const int64_t N = cells(C->n0);
+        double *f = C->base.f;
+        double m = 0.0;
+        for (int64_t q = 0; q < N; q++) m += f[q];
+        m /= (double)N;
+        for (int64_t q = 0; q < N; q++) f[q] -= m;
+        C->lambda -= m;
+    }
+}
+
+/* patches P..1: nu sweeps, residual, injection; then the base residual.
+   res[l] = relative residual of level l */
+static void comp_down(comp_t *C, int nu, double *res)
+{
+    for (int p = C->np; p >= 1; p--) {
+        patch_t *P = &C->P[p];
+        const cover_t cv = cover_of(C, p);
+        for (int s = 0; s < nu; s++) {
+            patch_gs(C->kind, C->rho, &P->v, &cv, 0);
+            patch_gs(C->kind, C->rho, &P->v, &cv, 1);
+        }
+        res[p] = patch_residual(C->kind, C->rho, P, &cv) / C->ref[p];
+        inject(C, p);
+    }
+    res[0] = orc_residual(C->kind, C->n0, C->base.u, C->base.f, C->base.c0, C->base.c1, C->rho, NULL) / C->ref[0];
+}
+
+/* patches 1..P: the parent's correction P(u_new - u_old) on the interior,
+   fresh ghosts, nu sweeps */
+static void comp_up(comp_t *C, int nu)
+{
+    for (int p = 1; p <= C->np; p++) {
+        patch_t *P = &C->P[p];
+        view_t *par = parent_of(C, p);
+        const int n = P->v.n, m = n + 2 * PG;
+        gather_window(par, P, par->u, P->win);
+        const int64_t W = (int64_t)P->w * P->w * P->w;
+        for (int64_t q = 0; q < W; q++) P->old[q] = P->win[q] - P->old[q];  /* old := new - old */
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++)
+                for (int k = 0; k < n; k++) P->v.u[gx(m, i, j, k)] += interp_window(P->old, P->w, i, j, k);
+        fill_ghosts(P, P->win, P->v.u);
+        const cover_t cv = cover_of(C, p);
+        for (int s = 0; s < nu; s++) {
+            patch_gs(C->kind, C->rho, &P->v, &cv, 0);
+            patch_gs(C->kind, C->rho, &P->v, &cv, 1);
+        }
+    }
+}
+
+static void comp_free(comp_t *C)
+{
+    for (int p = 1; p <= C->np; p++) {
+        patch_t *P = &C->P[p];
+        free(P->eps); free(P->win); free(P->old); free(P->Ru); free(P->Re); free(P->flux);
+        P->eps = P->win = P->old = P->Ru = P->Re = P->flux = NULL;
+    }
+    free(C->forig);
+    C->forig = NULL;
+    hier_free(&C->H);
+}
+
+static int patch_chain_valid(int n0, int np, const int *pn, const int *po)
+{
+    if (!valid_n(n0) || np < 0 || np > ORC_MAXP) return 0;
+    int npar = n0;
+    for (int p = 0; p < np; p++) {
+        const int n = pn[p];
+        if (!valid_n(n) || n < 8) return 0;
+        for (int d = 0; d < 3; d++) {
+            const int o = po[3 * p + d];
+            if (p == 0) {
+                if (o < 0 || o >= n0 || n / 2 + 4 > n0) return 0;
+            } else if (o < 2 || o + n / 2 + 2 > npar) {
+                return 0;
+            }
+        }
+        npar = n;
+    }
+    return 1;
+}
+
+/* largest of the levels' residuals, NaN if one is not finite */
+static double worst_of(const double *r, int nl)
+{
+    double w = 0.0;
+    for (int l = 0; l < nl; l++) {
+        if (!isfinite(r[l])) return NAN;
+        if (r[l] > w) w = r[l];
+    }
+    return w;
+}
+
+/* The composite solve of one equation on ghosted patch arrays already in
+   C->P[p].v (u with interior guess, f, c0, c1) and the base arrays. */
+static int comp_solve(comp_t *C, double tol, int max_cycles, int *cycles, double *res0, double *res)
+{
+    double r[ORC_MAXP + 1];
+    /* ghosts of the guesses, coarse to fine */
+    for (int p = 1; p <= C->np; p++) {
+        gather_window(parent_of(C, p), &C->P[p], parent_of(C, p)->u, C->P[p].win);
+        fill_ghosts(&C->P[p], C->P[p].win, C->P[p].v.u);
+    }
+    comp_down(C, 0, r);
+    if (res0)
+        for (int l = 0; l <= C->np; l++) res0[l] = r[l];
+    int st = ORC_OK, cyc = 0;
+    double worst = worst_of(r, C->np + 1);
+    if (!isfinite(worst)) st = ORC_ERR_NONFINITE;
+    while (st == ORC_OK && worst > tol && cyc < max_cycles) {
+        vcycle_level(&C->H, C->H.nlev - 1);
+        comp_up(C, C->nu2);
+        comp_down(C, C->nu1, r);
+        cyc++;
+        worst = worst_of(r, C->np + 1);
+        if (!isfinite(worst)) st = ORC_ERR_NONFINITE;
+    }
+    if (st == ORC_OK && worst > tol) st = ORC_ERR_NOCONV;
+    if (C->kind == ORC_POISSON) {
+        /* the solution's mean off every level */
+        const double m = orc_mean(C->n0, C->base.u);
+        for (int64_t q = 0; q < cells(C->n0); q++) C->base.u[q] -= m;
+        for (int p = 1; p <= C->np; p++) {
+            const int mm = C->P[p].v.n + 2 * PG;
+            for (int64_t q = 0; q < (int64_t)mm * mm * mm; q++) C->P[p].v.u[q] -= m;
+        }
+    }
+    if (cycles) *cycles = cyc;
+    if (res)
+        for (int l = 0; l <= C->np; l++) res[l] = r[l];
+    return st;
+}
+
+/* set up the base hierarchy and the patch work arrays of C (patch u, f, c0,
+   c1 must be set by the caller afterwards or before: they are not touched) */
+static int comp_init(comp_t *C, int kind, int n0, int np, const int *pn, const int *po, double rho, double *u0,
+                     const double *f0, const double *c00, const double *c10, int nu1, int nu2)
+{
+    C->kind = kind; C->np = np; C->nu1 = nu1; C->nu2 = nu2; C->n0 = n0; C->rho = rho;
+    const int64_t N0 = cells(n0);
+    C->forig = (double *)malloc(N0 * sizeof(double));
+    if (!C->forig) return ORC_ERR_NOMEM;
+    memcpy(C->forig, f0, N0 * sizeof(double));
+    if (kind == ORC_POISSON) subtract_mean(n0, C->forig);
+    int st = hier_build(&C->H, kind, n0, u0, C->forig, c00, c10, rho, nu1, nu2);
+    if (st != ORC_OK) return st;
+    level_t *F = &C->H.lev[C->H.nlev - 1];
+    C->base.n = n0; C->base.ghosted = 0;
+    C->base.u = u0; C->base.f = F->f; C->base.c0 = (double *)c00; C->base.c1 = (double *)c10;
+    C->base.h2 = 1.0 / ((double)n0 * n0); C->base.ih2 = (double)n0 * n0;
+    for (int p = 1; p <= np; p++) {
+        patch_t *P = &C->P[p];
+        const int n = pn[p - 1];
+        const double nh = (double)n0 * (double)(1 << p); /* 1/h of this patch */
+        P->v.n = n; P->v.ghosted = 1;
+        P->v.h2 = 1.0 / (nh * nh); P->v.ih2 = nh * nh;
+        for (int d = 0; d < 3; d++) P->o[d] = po[3 * (p - 1) + d];
+        P->nc = n / 2; P->w = n / 2 + 4;
+        const int64_t M = (int64_t)(n + 2 * PG) * (n + 2 * PG) * (n + 2 * PG);
+        const int64_t W = (int64_t)P->w * P->w * P->w, Nc = cells(P->nc);
+        P->eps = (double *)calloc(M, sizeof(double));
+        P->win = (double *)calloc(W, sizeof(double));
+        P->old = (double *)calloc(W, sizeof(double));
+        P->Ru = (double *)calloc(Nc, sizeof(double));
+        P->Re = (double *)calloc(Nc, sizeof(double));
+        P->flux = (double *)calloc(6 * P->nc * P->nc, sizeof(double));
+        if (!P->eps || !P->win || !P->old || !P->Ru || !P->Re || !P->flux) return ORC_ERR_NOMEM;
+    }
+    return ORC_OK;
+}
+
+static double rms_interior(int n, const double *a)
+{
+    const int m = n + 2 * PG;
+    double s = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) s += a[gx(m, i, j, k)] * a[gx(m, i, j, k)];
+    return sqrt(s / (double)cells(n));
+}
+
+/* interior n^3 (natural) <-> ghosted (n + 2 PG)^3 */
+static void to_ghosted(int n, const double *in, double *out, double add)
+{
+    const int m = n + 2 * PG;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) out[gx(m, i, j, k)] = in[ix(n, i, j, k)] + add;
+}
+
+static void from_ghosted(int n, const double *in, double *out, double add)
+{
+    const int m = n + 2 * PG;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) out[ix(n, i, j, k)] = in[gx(m, i, j, k)] + add;
+}
+
+/* Composite solve of one equation (kind, rho as orc_solve_eq) on the base
+   (u0, f0, c00, c10: n0^3 natural) and a chain of np patches: pn[p] cells
+   per side, origins po[3p..3p+2] in parent cells; up/fp/c0p/c1p: interior
+   pn^3 natural arrays (c0p, c1p entries may be NULL where the kind has no
+   such coefficient).  refs[l] (np + 1 values) are the levels' reference
+   norms, <= 0 for RMS(f) of the level (the base's after mean removal for
+   Poisson).  res0/res receive the np + 1 relative residuals (base first). */
+int orc_composite_eq(int kind, int n0, int np, const int *pn, const int *po, double rho, double *u0,
+                     const double *f0, const double *c00, const double *c10, double *const *up,
+                     const double *const *fp, const double *const *c0p, const double *const *c1p, const double *refs,
+                     double tol, int max_cycles, int nu1, int nu2, int *cycles, double *res0, double *res)
+{
+    if (!patch_chain_valid(n0, np, pn, po) || max_cycles < 0 || nu1 < 0 || nu2 < 0) return ORC_ERR_ARG;
+    comp_t C;
+    memset(&C, 0, sizeof(C));
+    int st = comp_init(&C, kind, n0, np, pn, po, rho, u0, f0, c00, c10, nu1, nu2);
+    double *store[ORC_MAXP + 1][4];
+    memset(store, 0, sizeof(store));
+    for (int p = 1; p <= np && st == ORC_OK; p++) {
+        const int n = pn[p - 1];
+        const int64_t M = (int64_t)(n + 2 * PG) * (n + 2 * PG) * (n + 2 * PG);
+        for (int q = 0; q < 4; q++) {
+            store[p][q] = (double *)calloc(M, sizeof(double));
+            if (!store[p][q]) st = ORC_ERR_NOMEM;
+        }
+        if (st != ORC_OK) break;
+        view_t *v = &C.P[p].v;
+        v->u = store[p][0]; v->f = store[p][1];
+        v->c0 = c0p && c0p[p - 1] ? store[p][2] : NULL;
+        v->c1 = c1p && c1p[p - 1] ? store[p][3] : NULL;
+        to_ghosted(n, up[p - 1], v->u, 0.0);
+        to_ghosted(n, fp[p - 1], v->f, 0.0);
+        if (v->c0) to_ghosted(n, c0p[p - 1], v->c0, 0.0);
+        if (v->c1) to_ghosted(n, c1p[p - 1], v->c1, 0.0);
+    }
+    if (st == ORC_OK) {
+        C.ref[0] = (refs && refs[0] > 0) ? refs[0] : orc_rms(n0, C.forig);
+        for (int p = 1; p <= np; p++)
+            C.ref[p] = (refs && refs[p] > 0) ? refs[p] : rms_interior(pn[p - 1], C.P[p].v.f);
+        for (int l = 0; l <= np; l++)
+            if (!(C.ref[l] >= 1e-300)) C.ref[l] = 1.0;
+        st = comp_solve(&C, tol, max_cycles, cycles, res0, res);
+        for (int p = 1; p <= np; p++) from_ghosted(pn[p - 1], C.P[p].v.u, up[p - 1], 0.0);
+    }
+    for (int p = 1; p <= np; p++)
+        for (int q = 0; q < 4; q++) free(store[p][q]);
+    comp_free(&C);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sources and the ten-equation solve on a patch chain                 */
+/* ------------------------------------------------------------------ */
+
+/* CIC at resolution N (spacing 1/N: the arithmetic of orc_deposit with
+   n = N), kept on the nw^3 window of cells O + a (mod N), 0 <= a < nw.
+   A patch at level p of a base n0 is the window N = n0 2^p, O = its origin
+   in cells of that resolution. */
+void orc_deposit_window(int N, const int *O, int nw, int64_t np, const double *x, const double *u, double mass,
+                        double *s0, double *sx, double *sy, double *sz, double *sigma)
+{
+    const double h = 1.0 / N, vol = h * h * h;
+    const int64_t M = cells(nw);
+    memset(s0, 0, M * sizeof(double));
+    memset(sx, 0, M * sizeof(double));
+    memset(sy, 0, M * sizeof(double));
+    memset(sz, 0, M * sizeof(double));
+    memset(sigma, 0, M * sizeof(double));
+    for (int64_t p = 0; p < np; p++) {
+        int lo[3];
+        double fplus[3];
+        for (int d = 0; d < 3; d++) {
+            double xp = x[d * np + p];
+            xp -= floor(xp);
+            double t = xp / h - 0.5;
+            double fl = floor(t);
+            fplus[d] = 1.0 - (t - fl);
+            int i = (int)fl;
+            lo[d] = (i % N + N) % N;
+        }
+        double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
+        double u2 = ux * ux + uy * uy + uz * uz;
+        double W = sqrt(1.0 + u2);
+        double q0 = mass * W / vol, qx = mass * ux / vol, qy = mass * uy / vol, qz = mass * uz / vol;
+        double qs = mass * u2 / W / vol;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                for (int c = 0; c < 2; c++) {
+                    const int ra = wrapi((lo[0] + a) % N - O[0], N), rb = wrapi((lo[1] + b) % N - O[1], N),
+                              rc = wrapi((lo[2] + c) % N - O[2], N);
+                    if (ra >= nw || rb >= nw || rc >= nw) continue;
+                    double w = (a ? 1.0 - fplus[0] : fplus[0]) * (b ? 1.0 - fplus[1] : fplus[1]) *
+                               (c ? 1.0 - fplus[2] : fplus[2]);
+                    int64_t id = ix(nw, ra, rb, rc);
+                    s0[id] += q0 * w;
+                    sx[id] += qx * w;
+                    sy[id] += qy * w;
+                    sz[id] += qz * w;
+                    sigma[id] += qs * w;
+                }
+    }
+}
+
+static inline int64_t gxs(int m, int i, int j, int k, int a, int s)
+{
+    int c[3] = {i, j, k};
+    c[a] += s;
+    return gx(m, c[0], c[1], c[2]);
+}
+
+/* A_ij (xx yy zz xy xz yz) at a patch cell from ghosted V, U (the stencils
+   of orc_aij; 1/h = nh) */
+static void aij_ghosted(int m, const double *const *V, const double *U, double nh, int i, int j, int k, double A[6])
+{
+    const double i2h = 0.5 * nh, ih2 = nh * nh;
+    double D[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int l = 0; l < 3; l++) D[a][l] = (V[l][gxs(m, i, j, k, a, 1)] - V[l][gxs(m, i, j, k, a, -1)]) * i2h;
+    const double divV = D[0][0] + D[1][1] + D[2][2];
+    const double u0 = U[gx(m, i, j, k)];
+    for (int a = 0; a < 3; a++) {
+        const double Uaa = (U[gxs(m, i, j, k, a, 1)] - 2.0 * u0 + U[gxs(m, i, j, k, a, -1)]) * ih2;
+        A[a] = 2.0 * D[a][a] - 0.5 * divV + 2.0 * Uaa;
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int p = 0; p < 3; p++) {
+        const int a = pa[p], b = pb[p];
+        double s = 0.0;
+        for (int sa = -1; sa <= 1; sa += 2)
+            for (int sb = -1; sb <= 1; sb += 2) {
+                int c[3] = {i, j, k};
+                c[a] += sa;
+                c[b] += sb;
+                s += (double)(sa * sb) * U[gx(m, c[0], c[1], c[2])];
+            }
+        A[3 + p] = D[a][b] + D[b][a] + 2.0 * s * 0.25 * ih2;
+    }
+}
+
+/* Right-hand side, coefficients (ghosted arrays, interior written) and
+   reference of equation e on a patch of n cells at 1/h = nh: the formulas of
+   orc_eq_setup with derivatives taken on the ghosted fields G (setup order
+   V_x V_y V_z U psi apsi B^x B^y B^z b; the entries the equation reads are
+   filled).  The momentum sources lose the base mean smean of s_i (the
+   homogeneous background); the divergence sources of U, b and B^i keep
+   theirs (on the periodic base it vanishes up to rounding). */
+static int patch_eq_setup(int e, int n, double nh, const double *const *src, const double *const *G, double smean,
+                          double rho_hat, double S_hat, double *f, double *c0, double *c1, double *ref)
+{
+    const int m = n + 2 * PG;
+    const double K2 = 24.0 * PI * rho_hat, Kdot = 12.0 * PI * rho_hat + 4.0 * PI * S_hat, i2h = 0.5 * nh;
+    double s2 = 0.0;
+    int kind = ORC_POISSON;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) {
+                const int64_t g = gx(m, i, j, k), id = ix(n, i, j, k);
+                if (e <= 2) {
+                    f[g] = 8.0 * PI * (src[1 + e][id] - smean);
+                    s2 += f[g] * f[g];
+                } else if (e == 3 || e == 9) {
+                    const double *const *F = G + (e == 3 ? 0 : 6);
+                    double s = 0.0;
+                    for (int a = 0; a < 3; a++) s += F[a][gxs(m, i, j, k, a, 1)] - F[a][gxs(m, i, j, k, a, -1)];
+                    f[g] = -0.25 * s * i2h;
+                    s2 += f[g] * f[g];
+                } else if (e == 4) {
+                    double A[6];
+                    aij_ghosted(m, G, G[3], nh, i, j, k, A);
+                    c1[g] = aa_of(A);
+                    c0[g] = src[0][id];
+                    f[g] = 0.0;
+                    s2 += src[0][id] * src[0][id];
+                    kind = ORC_PSI;
+                } else if (e == 5) {
+                    double A[6];
+                    aij_ghosted(m, G, G[3], nh, i, j, k, A);
+                    const double aa = aa_of(A);
+                    const double p = G[4][g], p2 = p * p, p4 = p2 * p2, p8 = p4 * p4;
+                    c0[g] = 2.0 * PI / p2 * (src[0][id] + 2.0 * src[4][id] / p4) + 0.875 * aa / p8 +
+                            (5.0 / 12.0) * p4 * K2;
+                    const double fk = -p4 * p * Kdot;
+                    s2 += fk * fk;
+                    f[g] = fk + c0[g];
+                    kind = ORC_HELMHOLTZ;
+                } else {
+                    const int tab[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+                    double s = 0.0;
+                    for (int l = 0; l < 3; l++)
+                        for (int sg = -1; sg <= 1; sg += 2) {
+                            int c[3] = {i, j, k};
+                            c[l] += sg;
+                            double A[6];
+                            aij_ghosted(m, G, G[3], nh, c[0], c[1], c[2], A);
+                            const int64_t q = gx(m, c[0], c[1], c[2]);
+                            const double p = G[4][q], p2 = p * p, p4 = p2 * p2;
+                            s += (double)sg * G[5][q] / (p4 * p2 * p) * A[tab[e - 6][l]];
+                        }
+                    f[g] = 2.0 * s * i2h;
+                    s2 += f[g] * f[g];
+                }
+            }
+    *ref = sqrt(s2 / (double)cells(n));
+    if (e == 4) *ref *= 2.0 * PI;
+    if (!(*ref >= 1e-300)) *ref = 1.0;
+    return kind;
+}
+
+/* Ten-equation composite solve (the order of orc_solve_constraints) on the
+   base (src0: 5 arrays, fld0: 10 fields in field order, n0^3) and a patch
+   chain (pn, po as orc_composite_eq; srcp[5p + q], fldp[10p + q]: pn^3
+   natural arrays, q in the base's order).  cycles[e], status[e] per
+   equation in solve order; res[e (np + 1) + l] the final relative residual
+   of level l (0 = base). */
+int orc_solve_composite(int n0, int np, const int *pn, const int *po, const double *const *src0,
+                        const double *const *srcp, double *const *fld0, double *const *fldp, double rho_hat,
+                        double S_hat, double tol, int max_cycles, int nu1, int nu2, int *cycles, double *res,
+                        int *status)
+{
+    if (!patch_chain_valid(n0, np, pn, po) || max_cycles < 0 || nu1 < 0 || nu2 < 0) return ORC_ERR_ARG;
+    const int64_t N0 = cells(n0);
+    /* setup order V_x V_y V_z U psi apsi B^x B^y B^z b -> field index */
+    static const int fidx[10] = {2, 3, 4, 5, 0, 1, 6, 7, 8, 9};
+    double *f = (double *)malloc(N0 * sizeof(double));
+    double *c0 = (double *)malloc(N0 * sizeof(double));
+    double *c1 = (double *)malloc(N0 * sizeof(double));
+    double *G[ORC_MAXP + 1][10];
+    double *wk[ORC_MAXP + 1][4];
+    double *win[ORC_MAXP + 1];
+    memset(G, 0, sizeof(G));
+    memset(wk, 0, sizeof(wk));
+    memset(win, 0, sizeof(win));
+    int worst = (f && c0 && c1) ? ORC_OK : ORC_ERR_NOMEM;
+    for (int p = 1; p <= np && worst == ORC_OK; p++) {
+        const int n = pn[p - 1], w = n / 2 + 4;
+        const int64_t M = (int64_t)(n + 2 * PG) * (n + 2 * PG) * (n + 2 * PG);
+        for (int q = 0; q < 10; q++)
+            if (!(G[p][q] = (double *)calloc(M, sizeof(double)))) worst = ORC_ERR_NOMEM;
+        for (int q = 0; q < 4; q++)
+            if (!(wk[p][q] = (double *)calloc(M, sizeof(double)))) worst = ORC_ERR_NOMEM;
+        if (!(win[p] = (double *)calloc((int64_t)w * w * w, sizeof(double)))) worst = ORC_ERR_NOMEM;
+    }
+    const double *setup0[10];
+    for (int q = 0; q < 10; q++) setup0[q] = fld0[fidx[q]];
+    for (int e = 0; e < 10 && worst == ORC_OK; e++) {
+        /* ghosted copies of the solved fields the equation reads, coarse to fine */
+        int need[10] = {0};
+        if (e == 3) need[0] = need[1] = need[2] = 1;
+        if (e == 4 || e == 5) need[0] = need[1] = need[2] = need[3] = 1;
+        if (e == 5) need[4] = 1;
+        if (e >= 6 && e <= 8) need[0] = need[1] = need[2] = need[3] = need[4] = need[5] = 1;
+        if (e == 9) need[6] = need[7] = need[8] = 1;
+        for (int p = 1; p <= np; p++) {
+            const int n = pn[p - 1];
+            patch_t P;
+            memset(&P, 0, sizeof(P));
+            P.v.n = n; P.nc = n / 2; P.w = n / 2 + 4;
+            for (int d = 0; d < 3; d++) P.o[d] = po[3 * (p - 1) + d];
+            view_t par;
+            memset(&par, 0, sizeof(par));
+            if (p == 1) { par.n = n0; par.ghosted = 0; }
+            else { par.n = pn[p - 2]; par.ghosted = 1; }
+            for (int q = 0; q < 10; q++) {
+                if (!need[q]) continue;
+                to_ghosted(n, fldp[10 * (p - 1) + fidx[q]], G[p][q], 0.0);
+                gather_window(&par, &P, p == 1 ? setup0[q] : G[p - 1][q], win[p]);
+                fill_ghosts(&P, win[p], G[p][q]);
+            }
+        }
+        double ref0 = 1.0;
+        const int kind = orc_eq_setup(e, n0, src0, setup0, rho_hat, S_hat, f, c0, c1, &ref0);
+        if (kind < 0) {
+            worst = ORC_ERR_NOMEM;
+            break;
+        }
+        const int dev = (e == 4 || e == 5);
+        double refs[ORC_MAXP + 1];
+        refs[0] = ref0 >= 1e-300 ? ref0 : 1.0;
+        comp_t C;
+        memset(&C, 0, sizeof(C));
+        double *u0 = fld0[fidx[e]];
+        if (dev)
+            for (int64_t q = 0; q < N0; q++) u0[q] -= 1.0;
+        int st = comp_init(&C, kind, n0, np, pn, po, rho_hat, u0, f, kind == ORC_POISSON ? NULL : c0,
+                           kind == ORC_PSI ? c1 : NULL, nu1, nu2);
+        for (int p = 1; p <= np && st == ORC_OK; p++) {
+            const int n = pn[p - 1];
+            const double smean = e <= 2 ? orc_mean(n0, src0[1 + e]) : 0.0;
+            view_t *v = &C.P[p].v;
+            v->u = wk[p][0]; v->f = wk[p][1];
+            v->c0 = kind == ORC_POISSON ? NULL : wk[p][2];
+            v->c1 = kind == ORC_PSI ? wk[p][3] : NULL;
+            patch_eq_setup(e, n, (double)n0 * (double)(1 << p), srcp + 5 * (p - 1), (const double *const *)G[p],
+                           smean, rho_hat, S_hat, v->f, wk[p][2], wk[p][3], &refs[p]);
+            to_ghosted(n, fldp[10 * (p - 1) + fidx[e]], v->u, dev ? -1.0 : 0.0);
+        }
+        if (st == ORC_OK) {
+            for (int l = 0; l <= np; l++) C.ref[l] = refs[l];
+            double r[ORC_MAXP + 1];
+            int cyc = 0;
+            st = comp_solve(&C, tol, max_cycles, &cyc, NULL, r);
+            if (cycles) cycles[e] = cyc;
+            if (res)
+                for (int l = 0; l <= np; l++) res[e * (np + 1) + l] = r[l];
+            for (int p = 1; p <= np; p++)
+                from_ghosted(pn[p - 1], C.P[p].v.u, fldp[10 * (p - 1) + fidx[e]], dev ? 1.0 : 0.0);
+        }
+        if (dev)
+            for (int64_t q = 0; q < N0; q++) u0[q] += 1.0;
+        comp_free(&C);
+        if (status) status[e] = st;
+        if (st != ORC_OK && worst == ORC_OK) worst = st;
+        if (st == ORC_ERR_NOMEM || st == ORC_ERR_NONFINITE) break;
+    }
+    for (int p = 1; p <= np; p++) {
+        for (int q = 0; q < 10; q++) free(G[p][q]);
+        for (int q = 0; q < 4; q++) free(wk[p][q]);
+        free(win[p]);
+    }
+    free(f);
+    free(c0);
+    free(c1);
+    return worst;
 }
