@@ -96,6 +96,25 @@ typedef struct {
     double *b;
 } gr_fields;
 
+/* Static nested refinement patches (the paper's solver runs on an adaptive
+   grid, Sec. 3 and Sec. 4.3; this library offers a chain of static cubic
+   patches).  patch[0] refines the periodic base; patch[p] refines
+   patch[p - 1].  Patch p has n cells per side at spacing h / 2^(p + 1) and
+   covers the parent cells origin .. origin + n/2 - 1 per axis (parent cell
+   units; patch[0]'s block may wrap around the periodic base).  Constraints:
+   n a power of two, 8 <= n <= 512; patch[0]: 0 <= origin < base n and
+   n/2 + 4 <= base n; patch[p > 0]: origin >= 2 and origin + n/2 + 2 <= the
+   parent's n.  src and fld are caller-owned device arrays of n^3 doubles,
+   natural layout (index (i n + j) n + k within the patch): src as
+   gr_deposit_patches writes it, fld the guesses in and the solutions out. */
+#define GR_MAX_PATCHES 4
+typedef struct {
+    int n;
+    int origin[3];
+    gr_sources src;
+    gr_fields fld;
+} gr_patch;
+
 typedef struct {
     double tol;       /* stop an equation when RMS(eps)/ref <= tol (see gr_solve_constraints) */
     int max_cycles;   /* per equation; >= 0 */
@@ -119,6 +138,15 @@ typedef struct {
                          is copied there as soon as its equation is solved, on a copy stream of the context,
                          so the copies overlap the remaining equations; the call's stream waits for the last
                          copy before the call returns, so a synchronisation of that stream covers them. */
+    int npatch;       /* gr_solve_constraints only: 0 (default) solves the periodic base alone; 1..GR_MAX_PATCHES
+                         solves the composite problem on the base and the chain patch[0..npatch-1] (composite-grid
+                         FAS: a patch's ghost layers take the trilinear interpolation of its parent, the parent
+                         takes the restricted patch solution and residual on the cells the patch covers, and the
+                         coarse flux through each face of a covered block is replaced by the mean of the four
+                         fine fluxes).  Every equation then stops when the base and every patch are at or below
+                         tol, each relative to its own reference.  Patches relax in FP64 whatever the precision
+                         mode; check_guess is ignored. */
+    const gr_patch *patch;
 } gr_opts;
 
 /* Finest-level kernel classes timed when gr_opts.profile is set. */
@@ -148,10 +176,13 @@ typedef struct {
     int prof_launches[GR_NPROF];  /* with gr_opts.profile: launches per gr_prof_class */
     double prof_ms[GR_NPROF];     /* with gr_opts.profile: summed CUDA-event time per class */
     int guess_rejected[GR_NEQ];   /* with gr_opts.check_guess: 1 where the plain guess replaced the given one */
+    double res_level[GR_NEQ][GR_MAX_PATCHES + 1]; /* with patches: relative residual at exit of the base (0) and of
+                                                     patch p (p + 1); res is their maximum */
 } gr_report;
 
 /* Fill *o with the defaults: tol 1e-10, max_cycles 50, V(2,2), FP64,
-   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0, check_guess 0, fmg 0. */
+   rho_hat and S_hat from the deposit / dust, verbose 0, profile 0, check_guess 0, fmg 0, no host_out,
+   no patches. */
 void gr_default_opts(gr_opts *o);
 
 /* Create a context for an n^3 grid of box side L.  n must be a power of two,
@@ -195,6 +226,16 @@ gr_status gr_deposit(gr_ctx *ctx, int64_t np, const double *x, const double *u, 
    or the first failing equation's status (NOCONV: fields keep the last
    iterate and the remaining equations are still solved; NONFINITE: stops).
    rep (host, may be NULL) receives per-equation cycles and residuals. */
+/* Cloud-in-cell sources of every patch of a chain (gr_opts.patch): each
+   patch's five src arrays are overwritten with the deposit of the np
+   particles at the patch's resolution (the formulas of gr_deposit with
+   spacing h / 2^(p + 1)), restricted to the patch's cells; particles whose
+   cloud misses the patch add nothing.  x, u: device arrays as in gr_deposit
+   (host memory returns GR_ERR_ARG).  Queued on the context's stream.
+   GR_ERR_ARG for an invalid chain or a NULL array. */
+gr_status gr_deposit_patches(gr_ctx *ctx, int npatch, const gr_patch *patch, int64_t np, const double *x,
+                             const double *u, double mass);
+
 gr_status gr_solve_constraints(gr_ctx *ctx, const gr_sources *src, gr_fields *inout, const gr_opts *opts,
                                gr_report *rep);
 

@@ -110,17 +110,22 @@ constexpr int resid_min_blocks()
 // f, a, b: the h^2-premultiplied pairs of df_cell.  32-bit offsets: grids up
 // to 1024^3.  Also the first red relaxation of the FP32 correction cycle,
 // which starts from e = 0: e_red = -h^2 r / 6 (Poisson) or -h^2 r / (6 + h^2 m).
-template <int KIND, int W>
+// SHIFT (Poisson with nested patches): every cell's right-hand side is
+// f + fshift[0] (the solvability constant), i.e. h^2 f + fshift[0] * fsh_scale.
+template <int KIND, int W, bool SHIFT = false>
 __global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
     k_df_resid(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const float *__restrict__ fh,
                const float *__restrict__ fl, const float *__restrict__ ah, const float *__restrict__ al,
                const float *__restrict__ bh, const float *__restrict__ bl, df cpr, float c5, float ih2,
                float ih2_ref, float *__restrict__ r32, float *__restrict__ m32, float *__restrict__ inv32,
-               const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials, int rev)
+               const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials, int rev,
+               const double *__restrict__ fshift, double fsh_scale)
 {
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
+    df fs = {0.0f, 0.0f};
+    if (SHIFT) fs = split_double(fshift[0] * fsh_scale);
     for (int tp = blockIdx.x * blockDim.x + threadIdx.x; tp < half / W; tp += gridDim.x * blockDim.x) {
         const int t = (rev ? half / W - 1 - tp : tp) * W;  // q0 = t & mh, a multiple of W
         const int q = t & mh;
@@ -177,8 +182,9 @@ __global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
                     h6[5] = e == 0 ? xh : nh[4][e > 0 ? e - 1 : 0];
                     l6[5] = e == 0 ? xl : nl[4][e > 0 ? e - 1 : 0];
                 }
-                const df r = df_cell<KIND>(h6, l6, {u_h[e], u_l[e]}, {f_h[e], f_l[e]}, {a_h[e], a_l[e]},
-                                           {b_h[e], b_l[e]}, cpr, c5, &mj[e], &iv[e]);  // h^2 eps
+                const df fe = SHIFT ? df_add({f_h[e], f_l[e]}, fs) : df{f_h[e], f_l[e]};
+                const df r = df_cell<KIND>(h6, l6, {u_h[e], u_l[e]}, fe, {a_h[e], a_l[e]}, {b_h[e], b_l[e]}, cpr,
+                                           c5, &mj[e], &iv[e]);  // h^2 eps
                 sh[e] = r.hi + r.lo;
                 rr[e] = -sh[e] * ih2;
                 const float z = r.hi * ih2_ref;
@@ -286,7 +292,8 @@ __global__ void __launch_bounds__(kBlock)
 
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
-             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev)
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev,
+             const double *fshift)
 {
     const int lgn = log2i(n);
     const int w = n >= 8 ? 4 : 2;
@@ -294,21 +301,24 @@ int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh,
     const df cpr = df_from_double_host(2.0 * kPi * rho * h2);
     const float c5 = (float)(10.0 * kPi * rho * h2), ih2 = (float)(1.0 / h2), ih2_ref = (float)(1.0 / (h2 * ref));
     int g = 0;
-#define GR_DF_RESID(K, W)                                                                                        \
+#define GR_DF_RESID(K, W, S)                                                                                     \
     do {                                                                                                         \
-        g = wave_grid(k_df_resid<K, W>, threads);                                                                \
-        GR_LAUNCH((k_df_resid<K, W>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2, ih2_ref, \
-                  r32, m32, inv32, inv_in, e32, partials, rev);                                                  \
+        g = wave_grid(k_df_resid<K, W, S>, threads);                                                             \
+        GR_LAUNCH((k_df_resid<K, W, S>), g, kBlock, st, lgn, uh, ul, fh, fl, ah, al, bh, bl, cpr, c5, ih2,       \
+                  ih2_ref, r32, m32, inv32, inv_in, e32, partials, rev, fshift, h2);                             \
     } while (0)
-    if (kind == KPOISSON) {
-        if (w == 4) GR_DF_RESID(KPOISSON, 4);
-        else GR_DF_RESID(KPOISSON, 2);
+    if (kind == KPOISSON && fshift) {
+        if (w == 4) GR_DF_RESID(KPOISSON, 4, true);
+        else GR_DF_RESID(KPOISSON, 2, true);
+    } else if (kind == KPOISSON) {
+        if (w == 4) GR_DF_RESID(KPOISSON, 4, false);
+        else GR_DF_RESID(KPOISSON, 2, false);
     } else if (kind == KHELM) {
-        if (w == 4) GR_DF_RESID(KHELM, 4);
-        else GR_DF_RESID(KHELM, 2);
+        if (w == 4) GR_DF_RESID(KHELM, 4, false);
+        else GR_DF_RESID(KHELM, 2, false);
     } else {
-        if (w == 4) GR_DF_RESID(KPSI, 4);
-        else GR_DF_RESID(KPSI, 2);
+        if (w == 4) GR_DF_RESID(KPSI, 4, false);
+        else GR_DF_RESID(KPSI, 2, false);
     }
 #undef GR_DF_RESID
     return g;

@@ -53,6 +53,19 @@ struct Level {
     float *e = nullptr, *r = nullptr, *m = nullptr, *inv = nullptr;                 // FP32
 };
 
+// one patch of a chain (gr_patch): ghosted (n + 4)^3 FP64 work arrays
+struct PatchLevel {
+    int n = 0, lgn = 0, m = 0, nc = 0, w = 0;
+    int o[3] = {0, 0, 0};
+    double h = 0;                                     // spacing
+    double *u = nullptr, *f = nullptr, *c0 = nullptr, *c1 = nullptr, *eps = nullptr;
+    double *G[GR_NEQ] = {};                           // the fields, interior = latest solution, ghosts on demand
+    double *win = nullptr, *old = nullptr;            // parent windows, (n/2 + 4)^3
+    double *Ru = nullptr, *Re = nullptr;              // restricted u and residual, (n/2)^3
+    double *flux = nullptr;                           // flux corrections in force, 6 (n/2)^2
+    double ref = 1;
+};
+
 struct EqInfo {
     int kind;      // operator on the FP64 fine level
     int kind32;    // operator of the FP32 correction equation
@@ -96,6 +109,11 @@ struct gr_ctx {
     std::vector<Pending> pending;
     int prof_launches[GR_NPROF] = {};
     double prof_ms[GR_NPROF] = {};
+    // nested patches: work arrays of the current chain, device scalars (0: the
+    // Poisson solvability constant, 1..8: its sums, 16..: set-up sums, 32..: norms)
+    std::vector<PatchLevel> pl;
+    std::vector<void *> palloc;
+    double *pdev = nullptr, *phost = nullptr;
 };
 
 namespace {
@@ -137,7 +155,8 @@ int log2i(int n)
 bool valid_opts(const gr_opts *o)
 {
     return o && !(o->tol < 0) && o->max_cycles >= 0 && o->nu1 >= 0 && o->nu1 <= 8 && o->nu2 >= 0 && o->nu2 <= 8 &&
-           (o->prec == GR_PREC_FP64 || o->prec == GR_PREC_MIXED || o->prec == GR_PREC_MIXED_DF);
+           (o->prec == GR_PREC_FP64 || o->prec == GR_PREC_MIXED || o->prec == GR_PREC_MIXED_DF) &&
+           o->npatch >= 0 && o->npatch <= GR_MAX_PATCHES && (o->npatch == 0 || o->patch);
 }
 
 bool src_ok(const gr_sources *s)
@@ -620,7 +639,7 @@ gr_status norm64(gr_ctx *c, int kind, double rho, double ref, double *eps_nat, d
 
 // fine residual norm in double-float; with red != 0 also the first red
 // relaxation of the next correction cycle (into lev[fine].e)
-gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r)
+gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r, const double *fshift = nullptr)
 {
     Level &F = c->lev[c->nlev - 1];
     const int64_t N = (int64_t)F.n * F.n * F.n;
@@ -628,7 +647,7 @@ gr_status df_norm(gr_ctx *c, const EqInfo &in, double rho, bool red, double *r)
     timed(c, GR_PROF_MIXED_RESID, [&] {
         g = gr::df_resid(in.kind, F.n, c->dfu, c->dfu + N, c->dff, c->dff + N, c->dfa, c->dfa + N, c->dfb,
                          c->dfb + N, F.h2, rho, in.ref, F.r, F.m, F.inv, F.inv, red ? F.e : nullptr, c->partials,
-                         c->st, next_dir(c));
+                         c->st, next_dir(c), fshift);
     });
     gr::finalize(c->partials, g, c->dscal, c->st);
     double q;
@@ -653,11 +672,299 @@ gr_status mixed_norm(gr_ctx *c, const EqInfo &in, double rho, double *r)
     return st;
 }
 
+// ---------------------------------------------------------------- nested patches
+// A chain of static patches (gr_patch): composite-grid FAS with flux matching,
+// the multilevel reading of the paper's adaptive-grid solve (Sec. 3,
+// Sec. 4.3).  Per equation: set-up on every patch, then per cycle the base's
+// correction cycle, the patches' corrections and post-smoothing (coarse to
+// fine), their pre-smoothing, residuals and injections into their parents
+// (fine to coarse), and the base residual.
+
+bool chain_valid(const gr_ctx *c, int np, const gr_patch *P)
+{
+    if (np < 0 || np > GR_MAX_PATCHES || (np > 0 && !P)) return false;
+    int npar = c->n;
+    for (int p = 0; p < np; p++) {
+        const int n = P[p].n;
+        if (n < 8 || n > 512 || (n & (n - 1))) return false;
+        for (int d = 0; d < 3; d++) {
+            const int o = P[p].origin[d];
+            if (p == 0 ? (o < 0 || o >= c->n || n / 2 + 4 > c->n) : (o < 2 || o + n / 2 + 2 > npar)) return false;
+        }
+        npar = n;
+    }
+    return true;
+}
+
+void free_patches(gr_ctx *c)
+{
+    for (void *q : c->palloc) cudaFree(q);
+    c->palloc.clear();
+    c->pl.clear();
+}
+
+template <typename T>
+gr_status palloc(gr_ctx *c, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GR_ERR_NOMEM, "cudaMalloc(%zu bytes) for a patch", count * sizeof(T));
+    }
+    c->palloc.push_back(q);
+    *p = (T *)q;
+    return GR_OK;
+}
+
+// work arrays for the chain (kept while the chain's sizes stay the same)
+gr_status ensure_patches(gr_ctx *c, int np, const gr_patch *P)
+{
+    if (!c->pdev) {
+        gr_status st = dalloc(c, &c->pdev, 64);
+        if (st != GR_OK) return st;
+        if (cudaMallocHost(&c->phost, 64 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->phost = nullptr;
+            return fail(GR_ERR_NOMEM, "cudaMallocHost");
+        }
+    }
+    bool same = (int)c->pl.size() == np;
+    for (int p = 0; same && p < np; p++) same = c->pl[p].n == P[p].n;
+    if (!same) {
+        cudaStreamSynchronize(c->st);
+        free_patches(c);
+        c->pl.resize(np);
+        for (int p = 0; p < np; p++) {
+            PatchLevel &L = c->pl[p];
+            L.n = P[p].n;
+            L.lgn = log2i(L.n);
+            L.m = L.n + 4;
+            L.nc = L.n / 2;
+            L.w = L.nc + 4;
+            const size_t M = (size_t)L.m * L.m * L.m, W = (size_t)L.w * L.w * L.w, Nc = (size_t)L.nc * L.nc * L.nc;
+            gr_status st = GR_OK;
+            double **arr[5] = {&L.u, &L.f, &L.c0, &L.c1, &L.eps};
+            for (int q = 0; q < 5 && st == GR_OK; q++) st = palloc(c, arr[q], M);
+            for (int q = 0; q < GR_NEQ && st == GR_OK; q++) st = palloc(c, &L.G[q], M);
+            if (st == GR_OK) st = palloc(c, &L.win, W);
+            if (st == GR_OK) st = palloc(c, &L.old, W);
+            if (st == GR_OK) st = palloc(c, &L.Ru, Nc);
+            if (st == GR_OK) st = palloc(c, &L.Re, Nc);
+            if (st == GR_OK) st = palloc(c, &L.flux, 6 * (size_t)L.nc * L.nc);
+            if (st != GR_OK) {
+                free_patches(c);
+                return st;
+            }
+            // ghost cells never written keep defined values
+            for (int q = 0; q < 5; q++) cudaMemsetAsync(*arr[q], 0, M * sizeof(double), c->st);
+            for (int q = 0; q < GR_NEQ; q++) cudaMemsetAsync(L.G[q], 0, M * sizeof(double), c->st);
+        }
+    }
+    for (int p = 0; p < np; p++) {
+        PatchLevel &L = c->pl[p];
+        for (int d = 0; d < 3; d++) L.o[d] = P[p].origin[d];
+        L.h = c->h / (double)(2 << p);
+    }
+    return cuda_check("patch arrays");
+}
+
+gr::PBase base_view(gr_ctx *c, int fmt, double rho)
+{
+    Level &F = c->lev[c->nlev - 1];
+    const int64_t N = (int64_t)F.n * F.n * F.n;
+    gr::PBase B;
+    B.lgn = log2i(F.n);
+    B.h2 = F.h2;
+    B.ih2 = F.ih2;
+    B.rho = rho;
+    if (fmt == gr::PB_SPLIT) {
+        B.u = F.u, B.f = F.f, B.c0 = F.c0, B.c1 = F.c1;
+    } else {
+        B.uh = c->dfu, B.ul = c->dfu + N, B.fh = c->dff, B.fl = c->dff + N;
+        B.ah = c->dfa, B.al = c->dfa + N, B.bh = c->dfb, B.bl = c->dfb + N;
+    }
+    return B;
+}
+
+gr::PPatch patch_view(gr_ctx *c, int p, const EqInfo &in, double rho)
+{
+    PatchLevel &L = c->pl[p];
+    gr::PPatch V;
+    V.lgn = L.lgn;
+    V.m = L.m;
+    V.u = L.u;
+    V.f = L.f;
+    V.c0 = in.kind != KPOISSON ? L.c0 : nullptr;
+    V.c1 = in.kind == KPSI ? L.c1 : nullptr;
+    V.h2 = L.h * L.h;
+    V.ih2 = 1.0 / V.h2;
+    V.rho = rho;
+    if (p + 1 < (int)c->pl.size()) {
+        for (int d = 0; d < 3; d++) V.co[d] = c->pl[p + 1].o[d];
+        V.cnc = c->pl[p + 1].nc;
+    }
+    V.lam = in.poisson ? c->pdev : nullptr;
+    return V;
+}
+
+// parent window of patch p from the base (format fmt, or natural field nat) or patch p - 1's array a
+void parent_window(gr_ctx *c, int p, int fmt, double rho, const double *nat, const double *a, double *win)
+{
+    PatchLevel &L = c->pl[p];
+    if (p == 0) {
+        gr::PBase B = base_view(c, fmt, rho);
+        if (fmt == gr::PB_NAT) B.nat = nat;
+        gr::patch_gather_base(fmt, B, L.o, L.w, win, c->st);
+    } else {
+        gr::patch_gather_patch(a, c->pl[p - 1].n, L.o, L.w, win, c->st);
+    }
+}
+
+// Set-up of equation eq on every patch: ghosts of the solved fields it reads,
+// right-hand side, coefficients and reference, the working unknown with
+// ghosts from the parent's, and the Poisson bookkeeping.
+gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, const gr_sources *s,
+                         const gr_fields *fl, double rho, double S_hat, int fmt)
+{
+    const int np = (int)c->pl.size();
+    const int64_t N0 = (int64_t)c->n * c->n * c->n;
+    const double K2 = 24.0 * kPi * rho, Kdot = 12.0 * kPi * rho + 4.0 * kPi * S_hat;
+    bool need[GR_NEQ] = {};
+    if (eq == GR_U) need[GR_VX] = need[GR_VY] = need[GR_VZ] = true;
+    if (eq == GR_PSI || eq == GR_APSI || (eq >= GR_BX && eq <= GR_BZ))
+        need[GR_VX] = need[GR_VY] = need[GR_VZ] = need[GR_U] = true;
+    if (eq == GR_APSI || (eq >= GR_BX && eq <= GR_BZ)) need[GR_PSI] = true;
+    if (eq >= GR_BX && eq <= GR_BZ) need[GR_APSI] = true;
+    if (eq == GR_B_SCALAR) need[GR_BX] = need[GR_BY] = need[GR_BZ] = true;
+    for (int q = 0; q < GR_NEQ; q++) {
+        if (!need[q]) continue;
+        for (int p = 0; p < np; p++) {
+            PatchLevel &L = c->pl[p];
+            parent_window(c, p, gr::PB_NAT, rho, field_ptr(fl, q), p ? c->pl[p - 1].G[q] : nullptr, L.win);
+            gr::patch_interp(L.n, L.win, nullptr, L.G[q], c->st);
+        }
+    }
+    double smean = 0.0;
+    if (eq <= GR_VZ) {  // the base mean of s_i (the homogeneous background)
+        dsum(c, N0, s->s[eq]);
+        double a, q2;
+        gr_status st = read_scalars(c, &a, &q2);
+        if (st != GR_OK) return st;
+        smean = a / N0;
+    }
+    for (int p = 0; p < np; p++) {
+        PatchLevel &L = c->pl[p];
+        const gr_sources &ps = o->patch[p].src;
+        gr::PSetSrc S = {{ps.s0, ps.s[0], ps.s[1], ps.s[2], ps.sigma}};
+        gr::PSetFld G;
+        for (int q = 0; q < GR_NEQ; q++) G.g[q] = L.G[q];
+        const int g = gr::patch_setup(eq, L.n, 1.0 / L.h, S, G, smean, K2, Kdot, L.f, L.c0, L.c1, c->partials, c->st);
+        gr::finalize(c->partials, g, c->pdev + 16 + 2 * p, c->st);
+    }
+    cudaMemcpyAsync(c->phost + 16, c->pdev + 16, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check("patch set-up");
+    for (int p = 0; p < np; p++) {
+        PatchLevel &L = c->pl[p];
+        L.ref = (eq == GR_PSI ? 2.0 * kPi : 1.0) * std::sqrt(c->phost[16 + 2 * p] / ((double)L.n * L.n * L.n));
+        if (!(L.ref >= 1e-300)) L.ref = 1.0;
+        gr::patch_to_ghosted(L.n, field_ptr(&o->patch[p].fld, eq), L.u, in.dev ? -1.0 : 0.0, c->st);
+    }
+    for (int p = 0; p < np; p++) {
+        PatchLevel &L = c->pl[p];
+        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win);
+        gr::patch_interp(L.n, L.win, nullptr, L.u, c->st);
+        cudaMemsetAsync(L.flux, 0, 6 * (size_t)L.nc * L.nc * sizeof(double), c->st);
+    }
+    cudaMemsetAsync(c->pdev, 0, sizeof(double), c->st);  // lambda = 0
+    if (in.poisson) {
+        const gr::PBase B = base_view(c, fmt, rho);
+        const int g = gr::patch_sum_f_base(fmt, B, c->pl[0].o, c->pl[0].nc, c->partials, c->st);
+        gr::finalize(c->partials, g, c->pdev + 1, c->st);  // the original right-hand side over the covered cells
+    }
+    return cuda_check("patch set-up");
+}
+
+// patches fine to coarse: nu sweeps, residual (norm into pdev[32 + 2p]),
+// restriction, injection into the parent with flux matching; for Poisson the
+// solvability constant after the base injection.  Queues the norms' copy to
+// phost (the caller's next synchronisation covers it).
+void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
+{
+    const int np = (int)c->pl.size();
+    Level &F = c->lev[c->nlev - 1];
+    const int64_t N0 = (int64_t)F.n * F.n * F.n;
+    for (int p = np - 1; p >= 0; p--) {
+        PatchLevel &L = c->pl[p];
+        const gr::PPatch V = patch_view(c, p, in, rho);
+        for (int sw = 0; sw < nu; sw++) {
+            gr::patch_gs(in.kind, V, 0, c->st);
+            gr::patch_gs(in.kind, V, 1, c->st);
+        }
+        int g = gr::patch_resid(in.kind, V, L.eps, c->partials, c->st);
+        gr::finalize(c->partials, g, c->pdev + 32 + 2 * p, c->st);
+        gr::patch_restrict(L.n, L.u, L.eps, L.Ru, L.Re, c->st);
+        if (p == 0) {
+            const gr::PBase B = base_view(c, fmt, rho);
+            gr::patch_inject_u_base(fmt, B, L.o, L.nc, L.Ru, c->st);
+            gr::patch_gather_base(fmt, B, L.o, L.w, L.old, c->st);
+            g = gr::patch_inject_f_base(fmt, in.kind, B, L.o, L.nc, L.Re,
+                                        (fmt == gr::PB_DF && in.poisson) ? c->pdev : nullptr, c->partials, c->st);
+            gr::finalize(c->partials, g, c->pdev + 3, c->st);
+            gr::patch_reflux(fmt, B, gr::PPatch{}, L.o, L.n, L.u, c->h, L.flux, c->st);
+            if (in.poisson) {
+                gr::patch_lambda(c->pdev + 1, L.flux, 6 * L.nc * L.nc, (double)N0, (double)L.nc * L.nc * L.nc,
+                                 c->pdev, c->st);
+                if (fmt == gr::PB_SPLIT) gr::sub_scalar(N0, F.f, c->pdev + 5, c->st);
+            }
+        } else {
+            PatchLevel &Q = c->pl[p - 1];
+            const gr::PPatch par = patch_view(c, p - 1, in, rho);
+            gr::patch_inject_u_patch(Q.u, Q.n, L.o, L.nc, L.Ru, c->st);
+            gr::patch_gather_patch(Q.u, Q.n, L.o, L.w, L.old, c->st);
+            gr::patch_inject_f_patch(in.kind, par, L.o, L.nc, L.Re, c->st);
+            gr::patch_reflux(-1, gr::PBase{}, par, L.o, L.n, L.u, Q.h, L.flux, c->st);
+        }
+    }
+    cudaMemcpyAsync(c->phost + 32, c->pdev + 32, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+}
+
+// patches coarse to fine: the parent's correction P(u_new - u_old), fresh ghosts, nu sweeps
+void patch_up(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
+{
+    const int np = (int)c->pl.size();
+    for (int p = 0; p < np; p++) {
+        PatchLevel &L = c->pl[p];
+        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win);
+        gr::patch_interp(L.n, L.win, L.old, L.u, c->st);
+        const gr::PPatch V = patch_view(c, p, in, rho);
+        for (int sw = 0; sw < nu; sw++) {
+            gr::patch_gs(in.kind, V, 0, c->st);
+            gr::patch_gs(in.kind, V, 1, c->st);
+        }
+    }
+}
+
+// relative residuals of the patches from the last patch_down (after a synchronisation)
+void patch_norms(const gr_ctx *c, double *r)
+{
+    for (size_t p = 0; p < c->pl.size(); p++) {
+        const PatchLevel &L = c->pl[p];
+        r[p] = std::sqrt(c->phost[32 + 2 * p] / ((double)L.n * L.n * L.n)) / L.ref;
+    }
+}
+
+long long patch_cells(const gr_ctx *c, int nu)
+{
+    long long s = 0;
+    for (const PatchLevel &L : c->pl) s += (long long)nu * L.n * L.n * L.n;
+    return s;
+}
+
 // Solve (or cycle) one equation; writes the field back.  tol < 0 with
 // max_cycles = 1 performs exactly one cycle and reports OK.
 gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const gr_opts *o, double rho,
                    double S_hat, double tol, int max_cycles, int *cycles, double *res0, double *res,
-                   long long *cells, int *rejected = nullptr)
+                   long long *cells, int *rejected = nullptr, double *res_level = nullptr)
 {
     EqInfo in;
     gr_status st = GR_OK;
@@ -677,7 +984,9 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     // residual of the plain guess (unknown 0: psi = alpha psi = 1, vectors 0),
     // the bar a given guess must beat after its first cycle
     double r_plain = NAN;
-    const bool check = o->check_guess != 0 && rejected != nullptr;
+    const bool patches = o->npatch > 0;
+    const int pfmt = dfm ? gr::PB_DF : gr::PB_SPLIT;
+    const bool check = o->check_guess != 0 && rejected != nullptr && !patches;
     if (check) {
         *rejected = 0;
         if (in.kind == KPOISSON) {
@@ -711,11 +1020,25 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     } else {
         restrict_coefs64(c, in.kind);
     }
+    double rlev[GR_MAX_PATCHES + 1] = {};
+    // the base residual and, with patches, the largest of all levels' (rlev: each level's)
     auto fine_norm = [&](double *r) {
-        if (dfm) return df_norm(c, in, rho, red, r);
-        if (mixed) return mixed_norm(c, in, rho, r);
-        return norm64(c, in.kind, rho, in.ref, nullptr, r);
+        gr_status q;
+        if (dfm) q = df_norm(c, in, rho, red, r, (patches && in.poisson) ? c->pdev : nullptr);
+        else if (mixed) q = mixed_norm(c, in, rho, r);
+        else q = norm64(c, in.kind, rho, in.ref, nullptr, r);
+        rlev[0] = *r;
+        if (q == GR_OK && patches) {
+            patch_norms(c, rlev + 1);
+            for (int p = 1; p <= o->npatch; p++) *r = std::isfinite(rlev[p]) && rlev[p] <= *r ? *r : rlev[p];
+        }
+        return q;
     };
+    if (patches) {
+        st = patch_setup_eq(c, eq, o, in, s, fl, rho, S_hat, pfmt);
+        if (st != GR_OK) return st;
+        patch_down(c, in, pfmt, 0, rho);
+    }
     auto use_plain_guess = [&]() {
         cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
         if (dfm) cudaMemsetAsync(c->dfu, 0, 2 * N * sizeof(float), c->st);
@@ -752,6 +1075,11 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         } else {
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
         }
+        if (patches) {
+            patch_up(c, in, pfmt, o->nu2, rho);
+            patch_down(c, in, pfmt, o->nu1, rho);
+            if (cells) *cells += patch_cells(c, o->nu1 + o->nu2);
+        }
         st = fine_norm(&r);
         cyc++;
         if (cells) *cells += per_cycle;
@@ -774,6 +1102,14 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     } else {
         const double *usum = in.poisson ? c->dscal + 1 : nullptr;
         gr::from_split(F.n, F.u, field_ptr(fl, eq), in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
+    }
+    if (patches) {  // the same mean off every patch; the patch's copy of the field for later set-ups
+        const double *usum = in.poisson ? (dfm ? c->dscal : c->dscal + 1) : nullptr;
+        for (int p = 0; p < o->npatch; p++)
+            gr::patch_from_ghosted(c->pl[p].n, c->pl[p].u, field_ptr(&o->patch[p].fld, eq), c->pl[p].G[eq],
+                                   in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
+        if (res_level)
+            for (int p = 0; p <= o->npatch; p++) res_level[p] = rlev[p];
     }
     gr_status cs = cuda_check("write back");
     if (cs != GR_OK) return cs;
@@ -880,6 +1216,8 @@ void gr_default_opts(gr_opts *o)
     o->check_guess = 0;
     o->fmg = 0;
     o->host_out = nullptr;
+    o->npatch = 0;
+    o->patch = nullptr;
 }
 
 const char *gr_last_error(void) { return g_err.c_str(); }
@@ -892,7 +1230,9 @@ void gr_destroy(gr_ctx *c)
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     for (void *p : c->allocs) cudaFree(p);
+    free_patches(c);
     if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->phost) cudaFreeHost(c->phost);
     if (c->cs) cudaStreamSynchronize(c->cs);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1000,9 +1340,24 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
     if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
     if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
+    if (o->npatch > 0) {
+        if (!chain_valid(c, o->npatch, o->patch)) return fail(GR_ERR_ARG, "invalid patch chain");
+        for (int p = 0; p < o->npatch; p++)
+            if (!src_ok(&o->patch[p].src) || !fld_ok(&o->patch[p].fld))
+                return fail(GR_ERR_ARG, "patch %d: a source or field array is NULL", p);
+    }
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
     if (st != GR_OK) return st;
+    if (o->npatch > 0) {
+        st = ensure_patches(c, o->npatch, o->patch);
+        if (st != GR_OK) return st;
+        for (int p = 0; p < o->npatch; p++)  // every field's guess, for the set-ups of the equations before its own
+            for (int q = 0; q < GR_NEQ; q++)
+                gr::patch_to_ghosted(c->pl[p].n, field_ptr(&o->patch[p].fld, q), c->pl[p].G[q], 0.0, c->st);
+    } else if (!c->pl.empty()) {
+        free_patches(c);
+    }
     gr_report R;
     memset(&R, 0, sizeof(R));
     auto t0 = std::chrono::steady_clock::now();
@@ -1023,7 +1378,7 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
         if (eq == GR_PSI) c->a_fmt = 0;  // V and U are final now
         cudaEventRecord(c->ev0, c->st);
         st = solve_eq(c, eq, s, fl, o, rho, S_hat, o->tol, o->max_cycles, &R.cycles[eq], &R.res0[eq], &R.res[eq],
-                      &R.cell_updates, &R.guess_rejected[eq]);
+                      &R.cell_updates, &R.guess_rejected[eq], R.res_level[eq]);
         if (o->host_out && (st == GR_OK || st == GR_ERR_NOCONV)) {
             // this field is final: copy it out while the next equations solve
             cudaEventRecord(c->xfer, c->st);
@@ -1078,7 +1433,9 @@ gr_status gr_vcycle(gr_ctx *c, gr_eq eq, const gr_sources *s, gr_fields *fl, con
     c->a_fmt = 0;
     c->w_fmt = 0;
     double r = NAN;
-    st = solve_eq(c, eq, s, fl, o, rho, S_hat, -1.0, 1, nullptr, nullptr, &r, nullptr);
+    gr_opts base_only = *o;  // one cycle of the periodic base: patches are gr_solve_constraints's
+    base_only.npatch = 0;
+    st = solve_eq(c, eq, s, fl, &base_only, rho, S_hat, -1.0, 1, nullptr, nullptr, &r, nullptr);
     if (res_after) *res_after = r;
     return st;
 }
@@ -1103,6 +1460,29 @@ gr_status gr_residual(gr_ctx *c, gr_eq eq, const gr_sources *s, const gr_fields 
     st = norm64(c, in.kind, rho, in.ref, res_field, &r);
     if (rel_norm) *rel_norm = r;
     return st;
+}
+
+gr_status gr_deposit_patches(gr_ctx *c, int npatch, const gr_patch *patch, int64_t np, const double *x,
+                             const double *u, double mass)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if (npatch < 1 || !chain_valid(c, npatch, patch)) return fail(GR_ERR_ARG, "invalid patch chain");
+    if (np < 0 || (np > 0 && (!x || !u))) return fail(GR_ERR_ARG, "bad particle arrays");
+    if (np > 0 && (host_memory(x) || host_memory(u)))
+        return fail(GR_ERR_ARG, "gr_deposit_patches takes device particle arrays");
+    for (int p = 0; p < npatch; p++)
+        if (!src_ok(&patch[p].src)) return fail(GR_ERR_ARG, "patch %d: a source array is NULL", p);
+    int O[3] = {0, 0, 0};
+    for (int p = 0; p < npatch; p++) {
+        const int N = c->n << (p + 1), n = patch[p].n;
+        for (int d = 0; d < 3; d++) O[d] = (2 * (O[d] + patch[p].origin[d])) & (N - 1);
+        const gr_sources &ps = patch[p].src;
+        double *f[5] = {ps.s0, ps.s[0], ps.s[1], ps.s[2], ps.sigma};
+        for (int k = 0; k < 5; k++) cudaMemsetAsync(f[k], 0, (size_t)n * n * n * sizeof(double), c->st);
+        gr::patch_deposit(np, x, u, mass, c->L, N, O, n, gr::PSetSrc{{f[0], f[1], f[2], f[3], f[4]}}, c->st);
+    }
+    return cuda_check("gr_deposit_patches");
 }
 
 }  // extern "C"

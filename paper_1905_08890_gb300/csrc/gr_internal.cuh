@@ -234,7 +234,8 @@ void to_float(int64_t cnt, const double *a, float *b, cudaStream_t st);
 // count.
 int df_resid(int kind, int n, const float *uh, const float *ul, const float *fh, const float *fl, const float *ah,
              const float *al, const float *bh, const float *bl, double h2, double rho, double ref, float *r32,
-             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev = 0);
+             float *m32, float *inv32, const float *inv_in, float *e32, double *partials, cudaStream_t st, int rev = 0,
+             const double *fshift = nullptr);
 void df_update(int n, float *uh, float *ul, const float *e, cudaStream_t st);
 // last black pass of the FP32 correction cycle (KPOISSON or KHELM, n >= 8)
 // fused with u += e on both colours; e's black half is left unwritten
@@ -308,5 +309,61 @@ void apsi_setup(int n, double h2, const double *psi, const double *apsi, const d
 // B^i source: f (split) = 2 sum_j D_j (w A^ij), w = apsi psi^-7 (natural scratch).
 void shift_weight(int n, const double *psi, const double *apsi, double *w, cudaStream_t st);
 void shift_source(int n, double inv2h, const double *A, const double *w, int comp, double *f, cudaStream_t st);
+
+
+// ---------------------------------------------------------------- nested patches
+// Base level as the patch kernels see it: natural FP64 fields (PB_NAT, nat),
+// the FP64 split-layout arrays of a solve (PB_SPLIT: u, f, c0, c1 as the
+// FP64 relaxation uses them) or the double-float split-layout arrays
+// (PB_DF: uh/ul, fh/fl = h^2 f, ah/al, bh/bl = the h^2-scaled coefficients).
+enum PatchBaseFmt : int { PB_NAT = 0, PB_SPLIT = 1, PB_DF = 2 };
+struct PBase {
+    int lgn = 0;
+    const double *nat = nullptr;
+    double *u = nullptr, *f = nullptr;
+    const double *c0 = nullptr, *c1 = nullptr;
+    float *uh = nullptr, *ul = nullptr, *fh = nullptr, *fl = nullptr;
+    const float *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+    double h2 = 0, ih2 = 0, rho = 0;
+};
+// One patch level: ghosted (n + 4)^3 FP64 arrays; co/cnc the block its child
+// covers (cnc = 0: none); lam the Poisson solvability constant (NULL: none).
+struct PPatch {
+    int lgn = 0, m = 0;
+    double *u = nullptr, *f = nullptr;
+    const double *c0 = nullptr, *c1 = nullptr;
+    double h2 = 0, ih2 = 0, rho = 0;
+    int co[3] = {0, 0, 0}, cnc = 0;
+    const double *lam = nullptr;
+};
+struct PSetSrc {
+    double *s[5];  // s0 s_x s_y s_z sigma, natural n^3
+};
+struct PSetFld {
+    const double *g[10];  // ghosted fields, setup order V_x V_y V_z U psi apsi B^x B^y B^z b
+};
+void patch_deposit(int64_t np, const double *x, const double *u, double mass, double L, int N, const int O[3], int nw,
+                   const PSetSrc &out, cudaStream_t st);
+void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st);
+void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st);
+void patch_interp(int n, const double *win, const double *old, double *u, cudaStream_t st);
+void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st);
+int patch_resid(int kind, const PPatch &P, double *eps, double *partials, cudaStream_t st);
+void patch_restrict(int n, const double *u, const double *eps, double *Ru, double *Re, cudaStream_t st);
+void patch_inject_u_base(int fmt, const PBase &B, const int o[3], int nc, const double *Ru, cudaStream_t st);
+int patch_inject_f_base(int fmt, int kind, const PBase &B, const int o[3], int nc, const double *Re, const double *lam,
+                        double *partials, cudaStream_t st);
+int patch_sum_f_base(int fmt, const PBase &B, const int o[3], int nc, double *partials, cudaStream_t st);
+void patch_inject_u_patch(double *pu, int npar, const int o[3], int nc, const double *Ru, cudaStream_t st);
+void patch_inject_f_patch(int kind, const PPatch &par, const int o[3], int nc, const double *Re, cudaStream_t st);
+void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const int o[3], int n, const double *pu, double hc,
+                  double *flux, cudaStream_t st);
+void patch_lambda(double *sc, const double *flux, int nq, double N, double Ncov, double *lam, cudaStream_t st);
+void sub_scalar(int64_t cnt, double *a, const double *m, cudaStream_t st);
+void patch_to_ghosted(int n, const double *in, double *out, double add, cudaStream_t st);
+void patch_from_ghosted(int n, const double *in, double *out, double *keep, double add, const double *usum,
+                        double scale, cudaStream_t st);
+int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, double smean, double K2, double Kdot,
+                double *f, double *c0, double *c1, double *partials, cudaStream_t st);
 
 }  // namespace gr

@@ -1,0 +1,796 @@
+// patch_kernels.cu - static nested refinement patches: the kernels of the
+// composite-grid FAS solve (cloud-in-cell deposit at a patch's resolution,
+// parent windows, ghost interpolation, relaxation, residual, restriction,
+// injection into the parent with flux matching, the solvability constant of
+// the periodic Poisson-type equations, and the per-equation set-up).
+//
+// A patch of n^3 cells is stored natural-layout with two ghost layers,
+// (n + 4)^3 doubles, index ((i + 2) m + (j + 2)) m + (k + 2), m = n + 4,
+// -2 <= i, j, k < n + 2.  It refines the parent block o .. o + n/2 - 1 (per
+// axis) by 2; the parent window is the (n/2 + 4)^3 block of parent cells
+// o - 2 .. o + n/2 + 1, which every interpolation and correction of the
+// patch reads.  FP64 throughout: the patches hold a few percent of the cells
+// of a solve, and their relaxation is latency-bound, not bandwidth-bound.
+//
+// The paper runs its solver on an adaptive grid (Sec. 3, Sec. 4.3) without
+// stating how a refined region couples to its parent; these kernels follow
+// the multilevel FAS reading: ghosts = trilinear interpolation of the parent,
+// the parent takes u = R u_patch and f = L(u) - R eps_patch on the covered
+// cells (FAS, Sec. 4.3.2.1), the coarse flux through each face of the
+// covered block is replaced by the mean of the four fine fluxes, and the
+// patch takes the parent's correction P(u_new - u_old).
+#include "df64.cuh"
+#include "gr_internal.cuh"
+
+namespace gr {
+namespace {
+
+constexpr int PG = 2;  // ghost layers
+
+__device__ __forceinline__ int64_t gxi(int m, int i, int j, int k)
+{
+    return ((int64_t)(i + PG) * m + (j + PG)) * m + (k + PG);
+}
+
+// natural and split-layout indices on the periodic base (n = 2^lgn; the
+// coordinates wrap)
+__device__ __forceinline__ int64_t bnat(int lgn, int i, int j, int k)
+{
+    const int mk = (1 << lgn) - 1;
+    return ((((int64_t)(i & mk) << lgn) + (j & mk)) << lgn) + (k & mk);
+}
+
+__device__ __forceinline__ int64_t bsplit(int lgn, int i, int j, int k)
+{
+    const int mk = (1 << lgn) - 1;
+    i &= mk, j &= mk, k &= mk;
+    return ((int64_t)((i + j + k) & 1) << (3 * lgn - 1)) + ((((int64_t)i << lgn) + j) << (lgn - 1)) + (k >> 1);
+}
+
+// ---------------------------------------------------------------- base access
+template <int FMT>
+__device__ __forceinline__ double b_u(const PBase &B, int i, int j, int k)
+{
+    if (FMT == PB_NAT) return B.nat[bnat(B.lgn, i, j, k)];
+    const int64_t s = bsplit(B.lgn, i, j, k);
+    if (FMT == PB_SPLIT) return B.u[s];
+    return join_double({B.uh[s], B.ul[s]});
+}
+
+template <int FMT>
+__device__ __forceinline__ void b_set_u(const PBase &B, int i, int j, int k, double v)
+{
+    const int64_t s = bsplit(B.lgn, i, j, k);
+    if (FMT == PB_SPLIT) {
+        B.u[s] = v;
+    } else {
+        const df d = split_double(v);
+        B.uh[s] = d.hi;
+        B.ul[s] = d.lo;
+    }
+}
+
+// the base right-hand side at a split index, unscaled (the double-float
+// arrays hold h^2 f)
+template <int FMT>
+__device__ __forceinline__ double b_f(const PBase &B, int64_t s)
+{
+    if (FMT == PB_SPLIT) return B.f[s];
+    return join_double({B.fh[s], B.fl[s]}) * B.ih2;
+}
+
+template <int FMT>
+__device__ __forceinline__ void b_set_f(const PBase &B, int64_t s, double v)
+{
+    if (FMT == PB_SPLIT) {
+        B.f[s] = v;
+    } else {
+        const df d = split_double(v * B.h2);
+        B.fh[s] = d.hi;
+        B.fl[s] = d.lo;
+    }
+}
+
+// L(u) of the base equation at one cell (the oracle's operator: Poisson
+// lap u; Helmholtz lap u - m u; psi lap u + 2 pi s0/psi + AA/(8 psi^7) -
+// 2 pi rho psi^5 with psi = 1 + u); the double-float arrays hold the
+// h^2-scaled coefficients a' = h^2 m or 2 pi h^2 s0 and b' = h^2 AA / 8
+template <int FMT, int KIND>
+__device__ __forceinline__ double b_op(const PBase &B, int i, int j, int k)
+{
+    const double u = b_u<FMT>(B, i, j, k);
+    const double nb = b_u<FMT>(B, i + 1, j, k) + b_u<FMT>(B, i - 1, j, k) + b_u<FMT>(B, i, j + 1, k) +
+                      b_u<FMT>(B, i, j - 1, k) + b_u<FMT>(B, i, j, k + 1) + b_u<FMT>(B, i, j, k - 1);
+    const int64_t s = bsplit(B.lgn, i, j, k);
+    if (FMT == PB_SPLIT) {
+        const double lap = (nb - 6.0 * u) * B.ih2;
+        if (KIND == KPOISSON) return lap;
+        if (KIND == KHELM) return lap - B.c0[s] * u;
+        const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2;
+        return lap + 2.0 * kPi * B.c0[s] / v + B.c1[s] / (8.0 * v4 * v2 * v) - 2.0 * kPi * B.rho * v4 * v;
+    }
+    double S = nb - 6.0 * u;
+    if (KIND == KHELM) {
+        S -= join_double({B.ah[s], B.al[s]}) * u;
+    } else if (KIND == KPSI) {
+        const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2;
+        S += join_double({B.ah[s], B.al[s]}) / v + join_double({B.bh[s], B.bl[s]}) / (v4 * v2 * v) -
+             2.0 * kPi * B.rho * B.h2 * v4 * v;
+    }
+    return S * B.ih2;
+}
+
+// ---------------------------------------------------------------- patch access
+__device__ __forceinline__ double p_nb(const double *u, int m, int i, int j, int k)
+{
+    return u[gxi(m, i + 1, j, k)] + u[gxi(m, i - 1, j, k)] + u[gxi(m, i, j + 1, k)] + u[gxi(m, i, j - 1, k)] +
+           u[gxi(m, i, j, k + 1)] + u[gxi(m, i, j, k - 1)];
+}
+
+template <int KIND>
+__device__ __forceinline__ double p_op(const PPatch &P, int i, int j, int k)
+{
+    const int64_t c = gxi(P.m, i, j, k);
+    const double u = P.u[c];
+    const double lap = (p_nb(P.u, P.m, i, j, k) - 6.0 * u) * P.ih2;
+    if (KIND == KPOISSON) return lap;
+    if (KIND == KHELM) return lap - P.c0[c] * u;
+    const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2;
+    return lap + 2.0 * kPi * P.c0[c] / v + P.c1[c] / (8.0 * v4 * v2 * v) - 2.0 * kPi * P.rho * v4 * v;
+}
+
+// right-hand side of a patch cell: f, plus the solvability constant lambda
+// where the child patch does not cover the cell
+__device__ __forceinline__ double p_rhs(const PPatch &P, int i, int j, int k)
+{
+    const double f = P.f[gxi(P.m, i, j, k)];
+    if (!P.lam) return f;
+    const bool cov = P.cnc > 0 && (unsigned)(i - P.co[0]) < (unsigned)P.cnc &&
+                     (unsigned)(j - P.co[1]) < (unsigned)P.cnc && (unsigned)(k - P.co[2]) < (unsigned)P.cnc;
+    return cov ? f : f + *P.lam;
+}
+
+// interior cell t (0 <= t < n^3) of an n^3 patch, n = 2^lgn
+__device__ __forceinline__ void p_cell(int lgn, int64_t t, int &i, int &j, int &k)
+{
+    const int mk = (1 << lgn) - 1;
+    k = (int)(t & mk);
+    j = (int)((t >> lgn) & mk);
+    i = (int)(t >> (2 * lgn));
+}
+
+// trilinear interpolation of a w^3 window at patch cell (i, j, k): fine
+// cell i sits in parent cell floor(i/2) (window index floor(i/2) + 2) and
+// leans 1/4 towards the neighbour on the side of its half; with `old`, of
+// the difference win - old
+__device__ __forceinline__ double interp(const double *win, const double *old, int w, int i, int j, int k)
+{
+    int I[2], J[2], K[2];
+    I[0] = (i >> 1) + 2;
+    I[1] = I[0] + ((i & 1) ? 1 : -1);
+    J[0] = (j >> 1) + 2;
+    J[1] = J[0] + ((j & 1) ? 1 : -1);
+    K[0] = (k >> 1) + 2;
+    K[1] = K[0] + ((k & 1) ? 1 : -1);
+    const double wt[2] = {0.75, 0.25};
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int64_t q = ((int64_t)I[a] * w + J[b]) * w + K[c];
+                const double v = old ? win[q] - old[q] : win[q];
+                s += wt[a] * wt[b] * wt[c] * v;
+            }
+    return s;
+}
+
+// ---------------------------------------------------------------- deposit
+// CIC at resolution N (spacing L/N; the base deposit's formulas in plain
+// FP64) onto the nw^3 window of cells O + a (mod N); one thread per particle.
+__global__ void __launch_bounds__(kBlock)
+    k_pdeposit(int64_t np, const double *__restrict__ x, const double *__restrict__ u, double mass, double L, int N,
+               int O0, int O1, int O2, int nw, double *__restrict__ s0, double *__restrict__ sx,
+               double *__restrict__ sy, double *__restrict__ sz, double *__restrict__ sig)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double h = L / N, vol = h * h * h;
+    const int O[3] = {O0, O1, O2};
+    int r[3];
+    double fplus[3];
+    bool near = true;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double xp = x[d * np + p];
+        xp -= L * floor(xp / L);
+        const double t = xp / h - 0.5;
+        const double fl = floor(t);
+        fplus[d] = 1.0 - (t - fl);
+        r[d] = ((int)fl - O[d]) & (N - 1);  // window coordinate of the lower cloud cell
+        near = near && (r[d] < nw || ((r[d] + 1) & (N - 1)) < nw);
+    }
+    if (!near) return;
+    const double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    const double W = sqrt(1.0 + u2);
+    const double q0 = mass * W / vol, qx = mass * ux / vol, qy = mass * uy / vol, qz = mass * uz / vol;
+    const double qs = mass * u2 / W / vol;
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const int ra = (r[0] + a) & (N - 1);
+        if (ra >= nw) continue;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int rb = (r[1] + b) & (N - 1);
+            if (rb >= nw) continue;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int rc = (r[2] + c) & (N - 1);
+                if (rc >= nw) continue;
+                const double w =
+                    (a ? 1.0 - fplus[0] : fplus[0]) * (b ? 1.0 - fplus[1] : fplus[1]) * (c ? 1.0 - fplus[2] : fplus[2]);
+                const int64_t id = ((int64_t)ra * nw + rb) * nw + rc;
+                atomicAdd(s0 + id, q0 * w);
+                atomicAdd(sx + id, qx * w);
+                atomicAdd(sy + id, qy * w);
+                atomicAdd(sz + id, qz * w);
+                atomicAdd(sig + id, qs * w);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- windows
+template <int FMT>
+__global__ void __launch_bounds__(kBlock) k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win)
+{
+    const int64_t W = (int64_t)w * w * w;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W; t += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(t % w), y = (int)((t / w) % w), x = (int)(t / ((int64_t)w * w));
+        win[t] = b_u<FMT>(B, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_gather_patch(const double *__restrict__ pu, int mpar, int o0, int o1, int o2, int w, double *__restrict__ win)
+{
+    const int64_t W = (int64_t)w * w * w;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W; t += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(t % w), y = (int)((t / w) % w), x = (int)(t / ((int64_t)w * w));
+        win[t] = pu[gxi(mpar, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z)];
+    }
+}
+
+// every cell of a ghosted patch array: ghosts = P(win); interior += P(win - old)
+// when old is given, else untouched
+__global__ void __launch_bounds__(kBlock)
+    k_interp(int n, const double *__restrict__ win, const double *__restrict__ old, int w, double *__restrict__ u)
+{
+    const int m = n + 2 * PG;
+    const int64_t M = (int64_t)m * m * m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % m) - PG, j = (int)((t / m) % m) - PG, i = (int)(t / ((int64_t)m * m)) - PG;
+        const bool inside = (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n && (unsigned)k < (unsigned)n;
+        if (!inside) u[t] = interp(win, nullptr, w, i, j, k);
+        else if (old) u[t] += interp(win, old, w, i, j, k);
+    }
+}
+
+// ---------------------------------------------------------------- relaxation, residual
+// one red-black colour over the interior (local colour (i + j + k) & 1): the
+// point update of the base relaxation (Newton step for psi)
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
+{
+    const int64_t half = (int64_t)1 << (3 * P.lgn - 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < half; t += (int64_t)gridDim.x * blockDim.x) {
+        const int h = (1 << P.lgn) >> 1;
+        const int kk = (int)(t % h), j = (int)((t / h) & ((1 << P.lgn) - 1)), i = (int)(t >> (2 * P.lgn - 1));
+        const int k = 2 * kk + ((i + j + color) & 1);
+        const int64_t c = gxi(P.m, i, j, k);
+        const double nb = p_nb(P.u, P.m, i, j, k);
+        const double f = p_rhs(P, i, j, k);
+        if (KIND == KPOISSON) {
+            P.u[c] = (nb - P.h2 * f) / 6.0;
+        } else if (KIND == KHELM) {
+            P.u[c] = (nb - P.h2 * f) / (6.0 + P.h2 * P.c0[c]);
+        } else {
+            const double u = P.u[c], w = 1.0 + u, w2 = w * w, w4 = w2 * w2;
+            const double g = p_op<KPSI>(P, i, j, k) - f;
+            const double dg = -6.0 * P.ih2 - 2.0 * kPi * P.c0[c] / w2 - 7.0 * P.c1[c] / (8.0 * w4 * w4) -
+                              10.0 * kPi * P.rho * w4;
+            P.u[c] = u - g / dg;
+        }
+    }
+}
+
+// eps = L(u) - f on the interior (ghosted eps array) and block sums of eps^2
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_presid(PPatch P, double *__restrict__ eps, double *__restrict__ partials)
+{
+    const int64_t N = (int64_t)1 << (3 * P.lgn);
+    double s2 = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(P.lgn, t, i, j, k);
+        const double e = p_op<KIND>(P, i, j, k) - p_rhs(P, i, j, k);
+        eps[gxi(P.m, i, j, k)] = e;
+        s2 += e * e;
+    }
+    block_sum2(s2, 0.0, partials);
+}
+
+// 8-child averages of u and eps over the nc^3 parent cells the patch covers
+__global__ void __launch_bounds__(kBlock) k_prestrict(int n, const double *__restrict__ u, const double *__restrict__ eps,
+                                                      double *__restrict__ Ru, double *__restrict__ Re)
+{
+    const int nc = n / 2, m = n + 2 * PG;
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        double su = 0.0, se = 0.0;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int64_t id = gxi(m, 2 * I + a, 2 * J + b, 2 * K + c);
+                    su += u[id];
+                    se += eps[id];
+                }
+        Ru[t] = 0.125 * su;
+        Re[t] = 0.125 * se;
+    }
+}
+
+// ---------------------------------------------------------------- injection
+template <int FMT>
+__global__ void __launch_bounds__(kBlock) k_inject_u_base(PBase B, int o0, int o1, int o2, int nc, const double *__restrict__ Ru)
+{
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        b_set_u<FMT>(B, o0 + I, o1 + J, o2 + K, Ru[t]);
+    }
+}
+
+// f = L(u) - R eps on the covered base cells (the double-float arrays store
+// h^2 (f - lambda) so that the residual kernel's uniform + lambda restores
+// it); block sums of f for the mean of the Poisson right-hand side
+template <int FMT, int KIND>
+__global__ void __launch_bounds__(kBlock) k_inject_f_base(PBase B, int o0, int o1, int o2, int nc,
+                                                          const double *__restrict__ Re, const double *__restrict__ lam,
+                                                          double *__restrict__ partials)
+{
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    const double l = (FMT == PB_DF && lam) ? *lam : 0.0;
+    double sf = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        const int i = o0 + I, j = o1 + J, k = o2 + K;
+        const double f = b_op<FMT, KIND>(B, i, j, k) - Re[t];
+        b_set_f<FMT>(B, bsplit(B.lgn, i, j, k), f - l);
+        sf += f;
+    }
+    if (partials) block_sum2(sf, 0.0, partials);
+}
+
+// the base right-hand side summed over the covered cells (unscaled)
+template <int FMT>
+__global__ void __launch_bounds__(kBlock) k_sum_f_base(PBase B, int o0, int o1, int o2, int nc, double *__restrict__ partials)
+{
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    double sf = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        sf += b_f<FMT>(B, bsplit(B.lgn, o0 + I, o1 + J, o2 + K));
+    }
+    block_sum2(sf, 0.0, partials);
+}
+
+__global__ void __launch_bounds__(kBlock) k_inject_u_patch(double *__restrict__ pu, int mpar, int o0, int o1, int o2,
+                                                           int nc, const double *__restrict__ Ru)
+{
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        pu[gxi(mpar, o0 + I, o1 + J, o2 + K)] = Ru[t];
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, int o1, int o2, int nc,
+                                                           const double *__restrict__ Re)
+{
+    const int64_t Nc = (int64_t)nc * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+        const int i = o0 + I, j = o1 + J, k = o2 + K;
+        par.f[gxi(par.m, i, j, k)] = p_op<KIND>(par, i, j, k) - Re[t];
+    }
+}
+
+// Flux matching on the 6 nc^2 parent cells next to the covered block: the
+// coarse flux (u_in - u_out)/h_c through the shared face is replaced by the
+// mean of the four fine fluxes (u_inner - u_ghost)/h_f, as the change
+// corr = -(T_f - T_c)/h_c of the parent's right-hand side there; flux[q]
+// keeps the correction in force.  PARENT: 0 a patch (ghosted arrays in par),
+// else the base in format PARENT.
+__device__ __forceinline__ void shell_cell(int q, int nc, int n, int in[3], int out[3], int fi[4][3], int fg[4][3])
+{
+    const int per = nc * nc;
+    const int face = q / per, r = q % per;
+    const int ax = face >> 1, sd = (face & 1) ? 1 : -1;
+    const int t1 = r / nc, t2 = r % nc;
+    const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+    in[ax] = sd < 0 ? 0 : nc - 1;
+    in[b1] = t1;
+    in[b2] = t2;
+    for (int d = 0; d < 3; d++) out[d] = in[d] + (d == ax ? sd : 0);
+    for (int e = 0; e < 4; e++) {
+        fi[e][ax] = sd < 0 ? 0 : n - 1;
+        fg[e][ax] = sd < 0 ? -1 : n;
+        fi[e][b1] = fg[e][b1] = 2 * t1 + (e >> 1);
+        fi[e][b2] = fg[e][b2] = 2 * t2 + (e & 1);
+    }
+}
+
+template <int PARENT>
+__global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, int o0, int o1, int o2, int n,
+                                                   const double *__restrict__ pu, double hc, double *__restrict__ flux)
+{
+    const int nc = n / 2, m = n + 2 * PG;
+    const int nq = 6 * nc * nc;
+    const double hf = 0.5 * hc;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        int in[3], out[3], fi[4][3], fg[4][3];
+        shell_cell(q, nc, n, in, out, fi, fg);
+        const int ii = o0 + in[0], ij = o1 + in[1], ik = o2 + in[2];
+        const int oi = o0 + out[0], oj = o1 + out[1], ok = o2 + out[2];
+        double uin, uout;
+        if (PARENT == 0) {
+            uin = par.u[gxi(par.m, ii, ij, ik)];
+            uout = par.u[gxi(par.m, oi, oj, ok)];
+        } else {
+            uin = b_u<PARENT>(B, ii, ij, ik);
+            uout = b_u<PARENT>(B, oi, oj, ok);
+        }
+        const double Tc = (uin - uout) / hc;
+        double Tf = 0.0;
+        for (int e = 0; e < 4; e++)
+            Tf += (pu[gxi(m, fi[e][0], fi[e][1], fi[e][2])] - pu[gxi(m, fg[e][0], fg[e][1], fg[e][2])]) / hf;
+        Tf *= 0.25;
+        const double corr = -(Tf - Tc) / hc;
+        const double d = corr - flux[q];
+        flux[q] = corr;
+        if (PARENT == 0) {
+            par.f[gxi(par.m, oi, oj, ok)] += d;
+        } else {
+            const int64_t s = bsplit(B.lgn, oi, oj, ok);
+            b_set_f<PARENT>(B, s, b_f<PARENT>(B, s) + d);
+        }
+    }
+}
+
+// The Poisson solvability constant after an injection into the base:
+// m = mean of the base right-hand side with the patches at lambda, i.e.
+// (sum_cov f' - sum_cov f_orig + sum_shell corr + (N - N_cov) lambda) / N
+// (the original right-hand side is mean-free); lambda -= m.  sc[0] = sum_cov
+// f_orig, sc[2] = sum_cov f' (finalized block sums); m goes to sc[4].
+__global__ void __launch_bounds__(kBlock) k_lambda(double *__restrict__ sc, const double *__restrict__ flux, int nq,
+                                                   double N, double Ncov, double *__restrict__ lam)
+{
+    double s = 0.0;
+    for (int q = threadIdx.x; q < nq; q += kBlock) s += flux[q];
+    block_sum2(s, 0.0, sc + 6);  // sc[6] = sum of the shell corrections
+    if (threadIdx.x == 0) {
+        const double l = *lam;
+        const double m = (sc[2] - sc[0] + sc[6] + (N - Ncov) * l) / N;
+        sc[4] = m;
+        *lam = l - m;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sub_scalar(int64_t cnt, double *__restrict__ a, const double *__restrict__ m)
+{
+    const double v = *m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        a[t] -= v;
+}
+
+// ---------------------------------------------------------------- copies
+// ghosted interior <- natural n^3 (+ add)
+__global__ void __launch_bounds__(kBlock) k_to_ghosted(int lgn, const double *__restrict__ in, double *__restrict__ out, double add)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const int m = (1 << lgn) + 2 * PG;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(lgn, t, i, j, k);
+        out[gxi(m, i, j, k)] = in[t] + add;
+    }
+}
+
+// natural n^3 (and, if keep, a second ghosted array's interior) <- ghosted
+// interior + add - usum[0] * scale (usum may be NULL)
+__global__ void __launch_bounds__(kBlock) k_from_ghosted(int lgn, const double *__restrict__ in, double *__restrict__ out,
+                                                         double *__restrict__ keep, double add,
+                                                         const double *__restrict__ usum, double scale)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const int m = (1 << lgn) + 2 * PG;
+    const double sh = add - (usum ? usum[0] * scale : 0.0);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(lgn, t, i, j, k);
+        const int64_t g = gxi(m, i, j, k);
+        const double v = in[g] + sh;
+        out[t] = v;
+        if (keep) keep[g] = v;
+    }
+}
+
+// ---------------------------------------------------------------- set-up
+__device__ __forceinline__ int64_t gxs(int m, int i, int j, int k, int a, int s)
+{
+    return gxi(m, i + (a == 0 ? s : 0), j + (a == 1 ? s : 0), k + (a == 2 ? s : 0));
+}
+
+// A_ij (xx yy zz xy xz yz) at a patch cell from ghosted V, U (the base's
+// stencils: 3-point first derivatives, 3-point second difference on the
+// diagonal, 4-cell cross derivative; Eqs. Aij-discrete-2, U-cross-deriv)
+__device__ void aij_at(int m, const double *const V[3], const double *U, double nh, int i, int j, int k, double A[6])
+{
+    const double i2h = 0.5 * nh, ih2 = nh * nh;
+    double D[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int l = 0; l < 3; l++) D[a][l] = (V[l][gxs(m, i, j, k, a, 1)] - V[l][gxs(m, i, j, k, a, -1)]) * i2h;
+    const double divV = D[0][0] + D[1][1] + D[2][2];
+    const double u0 = U[gxi(m, i, j, k)];
+    for (int a = 0; a < 3; a++) {
+        const double Uaa = (U[gxs(m, i, j, k, a, 1)] - 2.0 * u0 + U[gxs(m, i, j, k, a, -1)]) * ih2;
+        A[a] = 2.0 * D[a][a] - 0.5 * divV + 2.0 * Uaa;
+    }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int p = 0; p < 3; p++) {
+        const int a = pa[p], b = pb[p];
+        double s = 0.0;
+        for (int sa = -1; sa <= 1; sa += 2)
+            for (int sb = -1; sb <= 1; sb += 2) {
+                int c[3] = {i, j, k};
+                c[a] += sa;
+                c[b] += sb;
+                s += (double)(sa * sb) * U[gxi(m, c[0], c[1], c[2])];
+            }
+        A[3 + p] = D[a][b] + D[b][a] + 2.0 * s * 0.25 * ih2;
+    }
+}
+
+__device__ __forceinline__ double aa_of(const double A[6])
+{
+    return A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + 2.0 * (A[3] * A[3] + A[4] * A[4] + A[5] * A[5]);
+}
+
+// Right-hand side and coefficients of equation eq (solve order) on a patch's
+// interior (ghosted f, c0, c1), with block sums of the square of the
+// reference quantity: the momentum sources 8 pi (s_i - smean); the
+// divergence sources -div/4; psi: c0 = s0, c1 = AA, f = 0 (reference s0);
+// alpha psi: c0 = m, f = m - psi^5 Kdot (reference psi^5 Kdot); B^i:
+// 2 d_j (alpha psi psi^-7 A^ij).  G: ghosted fields in the order V_x V_y V_z
+// U psi apsi B^x B^y B^z b.
+__global__ void __launch_bounds__(kBlock)
+    k_pset(int eq, int lgn, double nh, PSetSrc S, PSetFld G, double smean, double K2, double Kdot,
+           double *__restrict__ f, double *__restrict__ c0, double *__restrict__ c1, double *__restrict__ partials)
+{
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    const int m = (1 << lgn) + 2 * PG;
+    const double i2h = 0.5 * nh;
+    const double *V[3] = {G.g[0], G.g[1], G.g[2]};
+    double s2 = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(lgn, t, i, j, k);
+        const int64_t g = gxi(m, i, j, k);
+        if (eq <= 2) {
+            f[g] = 8.0 * kPi * (S.s[1 + eq][t] - smean);
+            s2 += f[g] * f[g];
+        } else if (eq == 3 || eq == 9) {
+            const int b = eq == 3 ? 0 : 6;
+            double s = 0.0;
+            for (int a = 0; a < 3; a++) s += G.g[b + a][gxs(m, i, j, k, a, 1)] - G.g[b + a][gxs(m, i, j, k, a, -1)];
+            f[g] = -0.25 * s * i2h;
+            s2 += f[g] * f[g];
+        } else if (eq == 4) {
+            double A[6];
+            aij_at(m, V, G.g[3], nh, i, j, k, A);
+            c1[g] = aa_of(A);
+            c0[g] = S.s[0][t];
+            f[g] = 0.0;
+            s2 += S.s[0][t] * S.s[0][t];
+        } else if (eq == 5) {
+            double A[6];
+            aij_at(m, V, G.g[3], nh, i, j, k, A);
+            const double aa = aa_of(A);
+            const double p = G.g[4][g], p2 = p * p, p4 = p2 * p2, p8 = p4 * p4;
+            c0[g] = 2.0 * kPi / p2 * (S.s[0][t] + 2.0 * S.s[4][t] / p4) + 0.875 * aa / p8 + (5.0 / 12.0) * p4 * K2;
+            const double fk = -p4 * p * Kdot;
+            s2 += fk * fk;
+            f[g] = fk + c0[g];
+        } else {
+            const int tab[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+            double s = 0.0;
+            for (int l = 0; l < 3; l++)
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int c[3] = {i, j, k};
+                    c[l] += sg;
+                    double A[6];
+                    aij_at(m, V, G.g[3], nh, c[0], c[1], c[2], A);
+                    const int64_t q = gxi(m, c[0], c[1], c[2]);
+                    const double p = G.g[4][q], p2 = p * p, p4 = p2 * p2;
+                    s += (double)sg * G.g[5][q] / (p4 * p2 * p) * A[tab[eq - 6][l]];
+                }
+            f[g] = 2.0 * s * i2h;
+            s2 += f[g] * f[g];
+        }
+    }
+    block_sum2(s2, 0.0, partials);
+}
+
+inline int blocks_for(int64_t work, int cap = kMaxRedBlocks)
+{
+    int64_t b = (work + kBlock - 1) / kBlock;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+inline int lg2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+void patch_deposit(int64_t np, const double *x, const double *u, double mass, double L, int N, const int O[3], int nw,
+                   const PSetSrc &out, cudaStream_t st)
+{
+    if (np <= 0) return;
+    const int64_t g = (np + kBlock - 1) / kBlock;
+    GR_LAUNCH(k_pdeposit, (unsigned)g, kBlock, st, np, x, u, mass, L, N, O[0], O[1], O[2], nw, out.s[0], out.s[1],
+              out.s[2], out.s[3], out.s[4]);
+}
+
+void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)w * w * w);
+    if (fmt == PB_NAT) GR_LAUNCH(k_gather_base<PB_NAT>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
+    else if (fmt == PB_SPLIT) GR_LAUNCH(k_gather_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
+    else GR_LAUNCH(k_gather_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
+}
+
+void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st)
+{
+    GR_LAUNCH(k_gather_patch, blocks_for((int64_t)w * w * w), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], w, win);
+}
+
+void patch_interp(int n, const double *win, const double *old, double *u, cudaStream_t st)
+{
+    const int m = n + 2 * PG;
+    GR_LAUNCH(k_interp, blocks_for((int64_t)m * m * m), kBlock, st, n, win, old, n / 2 + 4, u);
+}
+
+void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)1 << (3 * P.lgn - 1));
+    if (kind == KPOISSON) GR_LAUNCH(k_pgs<KPOISSON>, g, kBlock, st, P, color);
+    else if (kind == KHELM) GR_LAUNCH(k_pgs<KHELM>, g, kBlock, st, P, color);
+    else GR_LAUNCH(k_pgs<KPSI>, g, kBlock, st, P, color);
+}
+
+int patch_resid(int kind, const PPatch &P, double *eps, double *partials, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)1 << (3 * P.lgn));
+    if (kind == KPOISSON) GR_LAUNCH(k_presid<KPOISSON>, g, kBlock, st, P, eps, partials);
+    else if (kind == KHELM) GR_LAUNCH(k_presid<KHELM>, g, kBlock, st, P, eps, partials);
+    else GR_LAUNCH(k_presid<KPSI>, g, kBlock, st, P, eps, partials);
+    return g;
+}
+
+void patch_restrict(int n, const double *u, const double *eps, double *Ru, double *Re, cudaStream_t st)
+{
+    const int nc = n / 2;
+    GR_LAUNCH(k_prestrict, blocks_for((int64_t)nc * nc * nc), kBlock, st, n, u, eps, Ru, Re);
+}
+
+void patch_inject_u_base(int fmt, const PBase &B, const int o[3], int nc, const double *Ru, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)nc * nc * nc);
+    if (fmt == PB_SPLIT) GR_LAUNCH(k_inject_u_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], nc, Ru);
+    else GR_LAUNCH(k_inject_u_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], nc, Ru);
+}
+
+int patch_inject_f_base(int fmt, int kind, const PBase &B, const int o[3], int nc, const double *Re, const double *lam,
+                        double *partials, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)nc * nc * nc);
+#define GR_INJ(F, K) GR_LAUNCH((k_inject_f_base<F, K>), g, kBlock, st, B, o[0], o[1], o[2], nc, Re, lam, partials)
+    if (fmt == PB_SPLIT) {
+        if (kind == KPOISSON) GR_INJ(PB_SPLIT, KPOISSON);
+        else if (kind == KHELM) GR_INJ(PB_SPLIT, KHELM);
+        else GR_INJ(PB_SPLIT, KPSI);
+    } else {
+        if (kind == KPOISSON) GR_INJ(PB_DF, KPOISSON);
+        else if (kind == KHELM) GR_INJ(PB_DF, KHELM);
+        else GR_INJ(PB_DF, KPSI);
+    }
+#undef GR_INJ
+    return g;
+}
+
+int patch_sum_f_base(int fmt, const PBase &B, const int o[3], int nc, double *partials, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)nc * nc * nc);
+    if (fmt == PB_SPLIT) GR_LAUNCH(k_sum_f_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], nc, partials);
+    else GR_LAUNCH(k_sum_f_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], nc, partials);
+    return g;
+}
+
+void patch_inject_u_patch(double *pu, int npar, const int o[3], int nc, const double *Ru, cudaStream_t st)
+{
+    GR_LAUNCH(k_inject_u_patch, blocks_for((int64_t)nc * nc * nc), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], nc,
+              Ru);
+}
+
+void patch_inject_f_patch(int kind, const PPatch &par, const int o[3], int nc, const double *Re, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)nc * nc * nc);
+    if (kind == KPOISSON) GR_LAUNCH(k_inject_f_patch<KPOISSON>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
+    else if (kind == KHELM) GR_LAUNCH(k_inject_f_patch<KHELM>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
+    else GR_LAUNCH(k_inject_f_patch<KPSI>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
+}
+
+void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const int o[3], int n, const double *pu, double hc,
+                  double *flux, cudaStream_t st)
+{
+    const int nc = n / 2;
+    const int g = blocks_for((int64_t)6 * nc * nc);
+    if (parent_fmt < 0) GR_LAUNCH(k_reflux<0>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
+    else if (parent_fmt == PB_SPLIT) GR_LAUNCH(k_reflux<PB_SPLIT>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
+    else GR_LAUNCH(k_reflux<PB_DF>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
+}
+
+void patch_lambda(double *sc, const double *flux, int nq, double N, double Ncov, double *lam, cudaStream_t st)
+{
+    GR_LAUNCH(k_lambda, 1, kBlock, st, sc, flux, nq, N, Ncov, lam);
+}
+
+void sub_scalar(int64_t cnt, double *a, const double *m, cudaStream_t st)
+{
+    GR_LAUNCH(k_sub_scalar, blocks_for(cnt), kBlock, st, cnt, a, m);
+}
+
+void patch_to_ghosted(int n, const double *in, double *out, double add, cudaStream_t st)
+{
+    GR_LAUNCH(k_to_ghosted, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), in, out, add);
+}
+
+void patch_from_ghosted(int n, const double *in, double *out, double *keep, double add, const double *usum,
+                        double scale, cudaStream_t st)
+{
+    GR_LAUNCH(k_from_ghosted, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), in, out, keep, add, usum, scale);
+}
+
+int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, double smean, double K2, double Kdot,
+                double *f, double *c0, double *c1, double *partials, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)n * n * n);
+    GR_LAUNCH(k_pset, g, kBlock, st, eq, lg2(n), nh, S, G, smean, K2, Kdot, f, c0, c1, partials);
+    return g;
+}
+
+}  // namespace gr

@@ -36,11 +36,19 @@ class gr_fields(ctypes.Structure):
     _fields_ = [("psi", _P), ("apsi", _P), ("V", _P * 3), ("U", _P), ("B", _P * 3), ("b", _P)]
 
 
+MAX_PATCHES = 4
+
+
+class gr_patch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("origin", ctypes.c_int * 3), ("src", gr_sources), ("fld", gr_fields)]
+
+
 class gr_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("prec", ctypes.c_int), ("rho_hat", ctypes.c_double), ("S_hat", ctypes.c_double),
                 ("verbose", ctypes.c_int), ("profile", ctypes.c_int), ("check_guess", ctypes.c_int),
-                ("fmg", ctypes.c_int), ("host_out", ctypes.POINTER(gr_fields))]
+                ("fmg", ctypes.c_int), ("host_out", ctypes.POINTER(gr_fields)), ("npatch", ctypes.c_int),
+                ("patch", ctypes.POINTER(gr_patch))]
 
 
 class gr_report(ctypes.Structure):
@@ -48,7 +56,7 @@ class gr_report(ctypes.Structure):
                 ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
                 ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
                 ("prof_launches", ctypes.c_int * 9), ("prof_ms", ctypes.c_double * 9),
-                ("guess_rejected", ctypes.c_int * 10)]
+                ("guess_rejected", ctypes.c_int * 10), ("res_level", (ctypes.c_double * (MAX_PATCHES + 1)) * 10)]
 
 
 PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid", "mixed_update", "norm64", "setup",
@@ -57,8 +65,8 @@ PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid"
 
 _lib = None
 _lock = threading.Lock()
-EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_solve_constraints", "gr_vcycle",
-            "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc")
+EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_deposit_patches", "gr_solve_constraints",
+            "gr_vcycle", "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc")
 
 
 def lib():
@@ -76,6 +84,9 @@ def lib():
             L.gr_destroy.restype = None
             L.gr_deposit.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.c_double, ctypes.POINTER(gr_sources)]
             L.gr_deposit.restype = ctypes.c_int
+            L.gr_deposit_patches.argtypes = [_P, ctypes.c_int, ctypes.POINTER(gr_patch), ctypes.c_int64, _P, _P,
+                                             ctypes.c_double]
+            L.gr_deposit_patches.restype = ctypes.c_int
             L.gr_solve_constraints.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
                                                ctypes.POINTER(gr_opts), ctypes.POINTER(gr_report)]
             L.gr_solve_constraints.restype = ctypes.c_int
@@ -166,10 +177,27 @@ def make_fields(fld: dict, host_ok=False) -> gr_fields:
     return f
 
 
+def make_patches(patches) -> ctypes.Array:
+    """A gr_patch array from dicts {"n", "origin", "src" (sources dict),
+    "fld" (fields dict)}; "src"/"fld" may be missing where the call does not
+    read them (they are then NULL)."""
+    arr = (gr_patch * max(1, len(patches)))()
+    for p, q in enumerate(patches):
+        arr[p].n = int(q["n"])
+        for d in range(3):
+            arr[p].origin[d] = int(q["origin"][d])
+        if q.get("src") is not None:
+            arr[p].src = make_sources(q["src"])
+        if q.get("fld") is not None:
+            arr[p].fld = make_fields(q["fld"])
+    return arr
+
+
 def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
-              profile=0, check_guess=0, fmg=0, host_out=None) -> gr_opts:
+              profile=0, check_guess=0, fmg=0, host_out=None, patches=None) -> gr_opts:
     """host_out: optional dict of ten CPU (pinned) float64 tensors that each
-    solved field is copied into while the later equations solve."""
+    solved field is copied into while the later equations solve.  patches:
+    optional list of patch dicts (see make_patches) with "src" and "fld"."""
     o = gr_opts()
     lib().gr_default_opts(ctypes.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2 = tol, max_cycles, nu1, nu2
@@ -181,6 +209,10 @@ def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, 
     if host_out is not None:
         o._host_out = make_fields(host_out, host_ok=True)  # kept alive with the options
         o.host_out = ctypes.pointer(o._host_out)
+    if patches:
+        o._patches = make_patches(patches)
+        o.npatch = len(patches)
+        o.patch = ctypes.cast(o._patches, ctypes.POINTER(gr_patch))
     return o
 
 
@@ -188,6 +220,7 @@ def report_dict(r: gr_report) -> dict:
     return {"cycles": list(r.cycles), "res0": list(r.res0), "res": list(r.res), "status": list(r.eq_status),
             "seconds": r.seconds, "eq_seconds": list(r.eq_seconds), "cell_updates": int(r.cell_updates),
             "kernel_launches": int(r.kernel_launches), "guess_rejected": list(r.guess_rejected),
+            "res_level": [list(r.res_level[e]) for e in range(10)],
             "prof": {k: {"launches": int(r.prof_launches[i]), "ms": float(r.prof_ms[i])}
                      for i, k in enumerate(PROF_CLASSES)}}
 
@@ -209,6 +242,14 @@ def gr_deposit(ctx, x, u, mass: float, src: dict):
     s = make_sources(src)
     _check(lib().gr_deposit(ctx, npart, _ptr(x, True) if npart else None, _ptr(u, True) if npart else None, mass,
                             ctypes.byref(s)), "gr_deposit")
+
+
+def gr_deposit_patches(ctx, patches, x, u, mass: float):
+    """Sources of every patch (dicts with "n", "origin", "src"); x, u CUDA tensors."""
+    npart = x.shape[1] if x.numel() else 0
+    arr = make_patches([{"n": q["n"], "origin": q["origin"], "src": q["src"]} for q in patches])
+    _check(lib().gr_deposit_patches(ctx, len(patches), arr, npart, _ptr(x) if npart else None,
+                                    _ptr(u) if npart else None, mass), "gr_deposit_patches")
 
 
 def gr_solve_constraints(ctx, src: dict, fld: dict, opts: gr_opts, allow_noconv=False) -> dict:
@@ -294,6 +335,28 @@ class Context:
         src = src if src is not None else self.new_sources()
         gr_deposit(self.h, x, u, mass, src)
         return src
+
+    def patch_grid(self, n: int) -> dict:
+        import torch
+
+        return torch.empty((n,) * 3, dtype=torch.float64, device=self.device)
+
+    def deposit_patches(self, patches, x, u, mass: float):
+        """Fill (allocating where missing) each patch dict's "src"."""
+        for q in patches:
+            if q.get("src") is None:
+                q["src"] = {k: self.patch_grid(q["n"]) for k in SOURCES}
+        gr_deposit_patches(self.h, patches, x, u, mass)
+        return patches
+
+    def initial_patch_fields(self, patches):
+        """Set each patch dict's "fld" to the plain guess."""
+        for q in patches:
+            fld = {k: self.patch_grid(q["n"]).zero_() for k in FIELDS}
+            fld["psi"].fill_(1.0)
+            fld["apsi"].fill_(1.0)
+            q["fld"] = fld
+        return patches
 
     def solve(self, src, fld, **kw) -> dict:
         allow = kw.pop("allow_noconv", False)

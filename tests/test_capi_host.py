@@ -48,3 +48,41 @@ def test_bad_box_and_null_arguments_rejected():
     assert gr.lib().gr_vcycle(None, 0, None, None, ctypes.byref(o), None) == gr.GR_ERR_ARG
     assert gr.lib().gr_residual(None, 0, None, None, ctypes.byref(o), None, None) == gr.GR_ERR_ARG
     assert gr.lib().gr_deposit(None, 0, None, None, 1.0, None) == gr.GR_ERR_ARG
+
+
+def test_patch_deposit_rejects_null_context_and_bad_chains():
+    p = gr.make_patches([{"n": 8, "origin": [0, 0, 0]}])
+    assert gr.lib().gr_deposit_patches(None, 1, p, 0, None, None, 1.0) == gr.GR_ERR_ARG
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of gr_opts, gr_report and gr_patch have the C
+    header's sizes and field offsets (compiled here with the host compiler)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    checks = {
+        "gr_opts": ["tol", "max_cycles", "prec", "rho_hat", "fmg", "host_out", "npatch", "patch"],
+        "gr_report": ["cycles", "res0", "seconds", "cell_updates", "prof_ms", "guess_rejected", "res_level"],
+        "gr_patch": ["n", "origin", "src", "fld"],
+    }
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "gr.h"', "int main(void) {"]
+    for t, fields in checks.items():
+        src.append(f'printf("{t} %zu\\n", sizeof({t}));')
+        for f in fields:
+            src.append(f'printf("{t}.{f} %zu\\n", offsetof({t}, {f}));')
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(c), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for t, fields in checks.items():
+        cls = getattr(gr, t)
+        assert int(out[t]) == ctypes.sizeof(cls), t
+        for f in fields:
+            assert int(out[f"{t}.{f}"]) == getattr(cls, f).offset, (t, f)

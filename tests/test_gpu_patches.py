@@ -1,0 +1,143 @@
+"""GPU parity of the static nested refinement patches (composite-grid FAS
+with flux matching) against the oracle: patch deposits, and the ten-equation
+composite solve on every level in every precision mode, including a chain
+whose first patch wraps around the periodic base and a single patch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_08890_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker deselects these on CPU
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1905_08890_gb300 import gr  # noqa: E402
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu(d):
+    return {k: _t(v) for k, v in d.items()}
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def centred_chain(n0, n, npatch=2):
+    out, npar = [], n0
+    for _ in range(npatch):
+        o = (npar - n // 2) // 2
+        out.append({"n": n, "origin": [o, o, o]})
+        npar = n
+    return out
+
+
+def _problem(n0, seed=3, sigma=1.0, per=1):
+    return synth.zeldovich(n0 * per, seed, sigma, 0.003, True)
+
+
+def _oracle_solve(n0, chain, p, tol=1e-12):
+    src0 = oracle.deposit(n0, p.x, p.u, p.mass)
+    srcp = oracle.deposit_patches(n0, chain, p.x, p.u, p.mass)
+    fld0, fldp = oracle.initial_fields(n0), oracle.initial_patch_fields(chain)
+    st, rep = oracle.solve_composite(src0, srcp, fld0, fldp, chain, p.rho_hat, tol=tol, max_cycles=80)
+    assert st == 0, rep
+    return src0, srcp, fld0, fldp
+
+
+def _gpu_solve(n0, chain, p, prec, tol):
+    ctx = gr.Context(n0)
+    x, u = _t(p.x), _t(p.u)
+    src = ctx.deposit(x, u, p.mass)
+    patches = [dict(q) for q in chain]
+    ctx.deposit_patches(patches, x, u, p.mass)
+    ctx.initial_patch_fields(patches)
+    fld = ctx.initial_fields()
+    rep = ctx.solve(src, fld, tol=tol, max_cycles=80, prec=prec, rho_hat=p.rho_hat, patches=patches)
+    torch.cuda.synchronize()
+    out0 = {k: v.cpu().numpy() for k, v in fld.items()}
+    outp = [{k: v.cpu().numpy() for k, v in q["fld"].items()} for q in patches]
+    srcp = [{k: v.cpu().numpy() for k, v in q["src"].items()} for q in patches]
+    ctx.close()
+    return rep, out0, outp, srcp
+
+
+def test_patch_deposit_matches_the_oracle():
+    n0 = 32
+    chain = [{"n": 16, "origin": [29, 3, 12]}, {"n": 16, "origin": [4, 2, 6]}]
+    p = _problem(n0, seed=5, sigma=2.0)
+    want = oracle.deposit_patches(n0, chain, p.x, p.u, p.mass)
+    ctx = gr.Context(n0)
+    patches = [dict(q) for q in chain]
+    ctx.deposit_patches(patches, _t(p.x), _t(p.u), p.mass)
+    torch.cuda.synchronize()
+    for q, w in zip(patches, want):
+        for k in oracle.SOURCES:
+            got = q["src"][k].cpu().numpy()
+            assert np.abs(got - w[k]).max() <= 1e-12 * max(np.abs(w[k]).max(), 1e-300), k
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8), ("mixed", 1e-10, 1e-8)])
+def test_composite_solve_matches_the_oracle(prec, tol, bar):
+    n0 = 32
+    chain = centred_chain(n0, 16)
+    p = _problem(n0)
+    src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
+    rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, prec, tol)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for e in range(10):
+        assert max(rep["res_level"][e][:3]) <= tol, (e, rep["res_level"][e])
+        assert rep["res"][e] == max(rep["res_level"][e][:3])
+    for k in oracle.FIELDS:
+        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k, rel_linf(g0[k], ofld0[k]))
+        for lvl in range(2):
+            err = rel_linf(gp[lvl][k], ofldp[lvl][k])
+            assert err <= bar, ("patch", lvl + 1, k, err)
+
+
+def test_composite_with_a_wrapping_first_patch_and_64_cubed_base():
+    """Patch 1's block wraps around two faces of the periodic base; 64^3 base
+    with 32^3 patches (several relaxation tiles per level)."""
+    n0 = 64
+    chain = [{"n": 32, "origin": [58, 60, 20]}, {"n": 32, "origin": [7, 9, 8]}]
+    p = _problem(n0, seed=7, sigma=1.5)
+    src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p, tol=1e-11)
+    rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, "mixed_df", 1e-9)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for k in oracle.FIELDS:
+        assert rel_linf(g0[k], ofld0[k]) <= 1e-8, ("base", k)
+        for lvl in range(2):
+            assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= 1e-8, ("patch", lvl + 1, k)
+
+
+def test_single_patch_fp64():
+    n0 = 16
+    chain = [{"n": 8, "origin": [3, 10, 6]}]
+    p = _problem(n0, seed=9, sigma=1.0, per=2)
+    src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
+    rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, "fp64", 1e-12)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for k in oracle.FIELDS:
+        assert rel_linf(g0[k], ofld0[k]) <= 1e-9, ("base", k)
+        assert rel_linf(gp[0][k], ofldp[0][k]) <= 1e-9, ("patch", k)
+
+
+def test_invalid_chain_is_refused():
+    n0 = 16
+    ctx = gr.Context(n0)
+    bad = [{"n": 16, "origin": [4, 4, 4]}, {"n": 16, "origin": [1, 4, 4]}]  # patch 2 at the parent's edge
+    ctx.initial_patch_fields(bad)
+    for q in bad:
+        q["src"] = {k: ctx.patch_grid(q["n"]).zero_() for k in oracle.SOURCES}
+    src = {k: ctx._grid().zero_() for k in oracle.SOURCES}
+    with pytest.raises(gr.GRError) as ei:
+        ctx.solve(src, ctx.initial_fields(), rho_hat=0.01, patches=bad)
+    assert ei.value.status == gr.GR_ERR_ARG
+    ctx.close()
