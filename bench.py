@@ -5,12 +5,14 @@ plain guess (psi = alpha psi = 1, vectors 0) and the full solve.  The
 headline path is the mixed-precision solve (defect correction with the fine
 residual in double-float, FP32 correction V-cycles); the plain FP64 GPU
 solve of the same step is timed next to it, and so is the same solve started by
-one full multigrid cycle per equation (a classical non-learned warm start).
+one full multigrid cycle per equation (a classical non-learned warm start),
+and the composite solve with two static nested refinement patches (128^3 at
+2x and 4x the base resolution, centred on the densest cell).
 Multi-GPU runs are independent replicas (one problem per rank, different
 seeds: weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec mixed_df|mixed|fp64]
-                    [--no-fp64] [--no-fmg] [--no-e2e] [--no-learned] [--no-cpu]
+                    [--no-fp64] [--no-fmg] [--no-e2e] [--no-learned] [--no-patches] [--no-cpu]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 """
 from __future__ import annotations
@@ -168,6 +170,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison at 128^3")
+    ap.add_argument("--no-patches", action="store_true",
+                    help="skip the composite solve with two nested 128^3 refinement patches")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -321,6 +325,9 @@ def main():
     if rank == 0 and not args.no_fmg and mixed:
         out["fmg_start"] = fmg_measure(ctx, x, u, p, src, fld, opts)
 
+    if rank == 0 and not args.no_patches and n >= 256:
+        out["patches"] = patches_measure(ctx, x, u, p, src, fld, opts, n)
+
     if rank == 0 and not args.no_learned:
         out["learned"] = learned_measure(args.prec)
 
@@ -434,6 +441,48 @@ def fmg_measure(ctx, x, u, p, src, fld, opts):
     return {"time_to_residual_ms": round(ms, 3), "cycles": rep["cycles"],
             "gcell_updates_per_s": round(rep["cell_updates"] / (ms * 1e-3) / 1e9, 3),
             "max_rel_linf_vs_headline": diff}
+
+
+def patches_measure(ctx, x, u, p, src, fld, opts, n, sizes=(128, 128)):
+    """The full-scale configuration with static nested refinement patches:
+    two 128^3 patches at 2x and 4x the base resolution centred on the densest
+    base cell, composite solve to the same tolerance (patches relax in FP64).
+    One untimed and one timed run from the plain guess (CUDA events), next to
+    the base-only headline solve's fields."""
+    import torch
+
+    from paper_1905_08890_gb300 import gr
+
+    ctx.deposit(x, u, p.mass, src)
+    c = int(torch.argmax(src["s0"]).item())
+    centre = (c // (n * n), (c // n) % n, c % n)
+    chain = gr.centred_chain(n, centre, sizes)
+    ctx.initial_patch_fields(chain)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for it in range(2):
+        for q in chain:
+            for k, v in q["fld"].items():
+                v.fill_(1.0 if k in ("psi", "apsi") else 0.0)
+        f2 = ctx.initial_fields()
+        torch.cuda.synchronize()
+        ev[0].record()
+        ctx.deposit_patches(chain, x, u, p.mass)
+        ev[1].record()
+        ev[2].record()
+        rep = ctx.solve(src, f2, patches=chain, **opts)
+        ev[3].record()
+        torch.cuda.synchronize()
+    dep_ms, ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    diff = max(float((f2[k] - fld[k]).abs().max() / fld[k].abs().max().clamp_min(1e-300)) for k in fld)
+    psi2 = chain[-1]["fld"]["psi"]
+    out = {"chain": [{"n": q["n"], "origin": q["origin"]} for q in chain], "centre_cell": list(centre),
+           "time_to_residual_ms": round(ms, 3), "deposit_patches_ms": round(dep_ms, 3), "cycles": rep["cycles"],
+           "res_max_per_level": [float(f"{max(r[l] for r in rep['res_level']):.3e}") for l in range(len(sizes) + 1)],
+           "base_fields_max_rel_change_vs_no_patches": diff,
+           "finest_patch_psi_range": [float(psi2.min()), float(psi2.max())],
+           "base_psi_range": [float(f2["psi"].min()), float(f2["psi"].max())]}
+    del f2, chain
+    return out
 
 
 def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):

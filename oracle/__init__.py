@@ -100,6 +100,10 @@ def lib():
             L.orc_composite_eq.restype = I
             L.orc_solve_composite.argtypes = [I, I, P, P, P, P, P, P, D, D, D, I, I, I, P, P, P]
             L.orc_solve_composite.restype = I
+            L.orc_patch_ghosted.argtypes = [I, P, I, I, P, P, P]
+            L.orc_patch_ghosted.restype = None
+            L.orc_patch_residual_at.argtypes = [I, I, D, P, P, D, D, D, I64, P, P, P]
+            L.orc_patch_residual_at.restype = None
             _lib = L
     return _lib
 
@@ -404,3 +408,32 @@ def solve_composite(src0: dict, srcp, fld0: dict, fldp, patches, rho_hat: float,
                                    max_cycles, nu1, nu2, cyc, r, sts)
     res = [list(r[e * (np_ + 1):(e + 1) * (np_ + 1)]) for e in range(10)]
     return st, {"cycles": list(cyc), "res": res, "status": list(sts)}
+
+
+def patch_ghosted(interior, origin, parent, parent_periodic: bool):
+    """(n + 4)^3 array: the patch interior with two ghost layers interpolated
+    (trilinear) from the parent (natural array; periodic for the base)."""
+    interior = _f64(interior)
+    parent = _f64(parent)
+    n = interior.shape[0]
+    out = np.zeros((n + 4,) * 3)
+    o = (ctypes.c_int * 3)(*[int(v) for v in origin])
+    lib().orc_patch_ghosted(n, o, parent.shape[0], int(parent_periodic), _p(parent), _p(interior), _p(out))
+    return out
+
+
+def patch_residual_at(eq: int, n: int, nh: float, src: dict, G: dict, smean: float, rho_hat: float, cells,
+                      S_hat: float = 0.0):
+    """(eps, fscale) of equation eq (solve order) at the natural interior
+    indices `cells` of a patch without a child; G: ghosted fields by name."""
+    order = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+    srcs = [_f64(src[k]) for k in SOURCES]
+    gs = [_f64(G[k]) for k in order]
+    sp = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in srcs])
+    gp = (ctypes.c_void_p * 10)(*[a.ctypes.data for a in gs])
+    idx = np.ascontiguousarray(cells, dtype=np.int64)
+    eps = np.empty(idx.size)
+    f = np.empty(idx.size)
+    lib().orc_patch_residual_at(eq, n, nh, sp, gp, smean, rho_hat, S_hat, idx.size, idx.ctypes.data,
+                                eps.ctypes.data, f.ctypes.data)
+    return eps, f

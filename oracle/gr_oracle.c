@@ -1678,3 +1678,98 @@ int orc_solve_composite(int n0, int np, const int *pn, const int *po, const doub
     free(c1);
     return worst;
 }
+
+/* ------------------------------------------------------------------ */
+/* Pointwise checks on a patch, for grids too large for a full oracle   */
+/* composite solve                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Ghosted (n + 2 PG)^3 array from a patch's interior (natural n^3) and its
+   parent (natural npar^3, periodic if the parent is the base): ghosts are
+   the trilinear interpolation of the parent window at origin o. */
+void orc_patch_ghosted(int n, const int *o, int npar, int parent_periodic, const double *parent,
+                       const double *interior, double *out)
+{
+    view_t par;
+    memset(&par, 0, sizeof(par));
+    par.n = npar;
+    par.ghosted = 0;
+    patch_t P;
+    memset(&P, 0, sizeof(P));
+    P.v.n = n;
+    P.nc = n / 2;
+    P.w = n / 2 + 4;
+    for (int d = 0; d < 3; d++) P.o[d] = o[d];
+    double *win = (double *)malloc((size_t)P.w * P.w * P.w * sizeof(double));
+    if (!win) return;
+    if (parent_periodic) {
+        gather_window(&par, &P, parent, win);
+    } else {
+        /* a patch parent: its interior cells o - 2 .. o + nc + 1 (the chain keeps them inside) */
+        const int w = P.w;
+        for (int x = 0; x < w; x++)
+            for (int y = 0; y < w; y++)
+                for (int z = 0; z < w; z++)
+                    win[((int64_t)x * w + y) * w + z] = parent[ix(npar, o[0] - 2 + x, o[1] - 2 + y, o[2] - 2 + z)];
+    }
+    to_ghosted(n, interior, out, 0.0);
+    fill_ghosts(&P, win, out);
+    free(win);
+}
+
+/* eps = L(u) - f of equation e (solve order) on a patch without a child, at
+   the interior cells idx[] (natural n^3 indices): the set-up of
+   patch_eq_setup from the patch's sources src (5 interior arrays) and its
+   ghosted fields G (setup order), then the operator at each cell.  fscale[c]
+   receives the local reference quantity (the right-hand side; 2 pi s0 for
+   psi; psi^5 Kdot for alpha psi).  No solvability constant is added: for the
+   Poisson-type equations eps carries the solve's uniform lambda. */
+void orc_patch_residual_at(int e, int n, double nh, const double *const *src, const double *const *G, double smean,
+                           double rho_hat, double S_hat, int64_t ncell, const int64_t *idx, double *eps,
+                           double *fscale)
+{
+    const int m = n + 2 * PG;
+    const int64_t M = (int64_t)m * m * m;
+    double *f = (double *)calloc(M, sizeof(double));
+    double *c0 = (double *)calloc(M, sizeof(double));
+    double *c1 = (double *)calloc(M, sizeof(double));
+    if (!f || !c0 || !c1) {
+        free(f); free(c0); free(c1);
+        return;
+    }
+    double ref;
+    const int kind = patch_eq_setup(e, n, nh, src, G, smean, rho_hat, S_hat, f, c0, c1, &ref);
+    const double Kdot = 12.0 * PI * rho_hat + 4.0 * PI * S_hat;
+    const int fi[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
+    const double *u = G[fi[e]];
+    view_t v;
+    memset(&v, 0, sizeof(v));
+    v.n = n;
+    v.ghosted = 1;
+    v.ih2 = nh * nh;
+    v.h2 = 1.0 / v.ih2;
+    double *ud = (double *)malloc(M * sizeof(double)); /* the equation's unknown: psi - 1, alpha psi - 1 */
+    if (!ud) {
+        free(f); free(c0); free(c1);
+        return;
+    }
+    const double sh = (e == 4 || e == 5) ? 1.0 : 0.0;
+    for (int64_t q = 0; q < M; q++) ud[q] = u[q] - sh;
+    v.u = ud;
+    v.f = f;
+    v.c0 = kind == ORC_POISSON ? NULL : c0;
+    v.c1 = kind == ORC_PSI ? c1 : NULL;
+    for (int64_t c = 0; c < ncell; c++) {
+        const int64_t id = idx[c];
+        const int k = (int)(id % n), j = (int)((id / n) % n), i = (int)(id / ((int64_t)n * n));
+        const int64_t g = gx(m, i, j, k);
+        eps[c] = vop(kind, &v, rho_hat, i, j, k) - f[g];
+        if (e == 4) fscale[c] = 2.0 * PI * src[0][id];
+        else if (e == 5) fscale[c] = pow(G[4][g], 5) * Kdot;
+        else fscale[c] = f[g];
+    }
+    free(ud);
+    free(f);
+    free(c0);
+    free(c1);
+}

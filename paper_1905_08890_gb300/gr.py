@@ -193,6 +193,24 @@ def make_patches(patches) -> ctypes.Array:
     return arr
 
 
+def centred_chain(n0: int, centre, sizes) -> list:
+    """A chain of patches (dicts with "n" and "origin") centred on base cell
+    `centre` (i, j, k): patch 1 of sizes[0] cells covers the sizes[0]/2 base
+    cells around it (its block may wrap around the periodic base), each
+    further patch sits in the middle of its parent.  Host-side arithmetic
+    only; gr_solve_constraints checks the chain."""
+    out, npar = [], n0
+    for p, n in enumerate(sizes):
+        if p == 0:
+            origin = [(int(c) - n // 4) % n0 for c in centre]
+        else:
+            o = (npar - n // 2) // 2
+            origin = [o, o, o]
+        out.append({"n": int(n), "origin": origin})
+        npar = n
+    return out
+
+
 def make_opts(tol=1e-10, max_cycles=50, nu1=2, nu2=2, prec="fp64", rho_hat=0.0, S_hat=0.0, verbose=0,
               profile=0, check_guess=0, fmg=0, host_out=None, patches=None) -> gr_opts:
     """host_out: optional dict of ten CPU (pinned) float64 tensors that each

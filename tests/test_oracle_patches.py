@@ -258,3 +258,29 @@ def test_ten_equations_on_patches_approach_the_uniform_fine_solve(orc):
         d_comp = np.abs(fldp[1][k] - fu[k][sl]).max()
         d_base = np.abs(c2[sl] - fu[k][sl]).max()
         assert d_comp <= 0.7 * d_base, (k, d_comp, d_base)
+
+
+def test_pointwise_patch_residual_of_a_converged_composite_solve(orc):
+    """The pointwise check used at full size (orc_patch_residual_at with
+    ghosts re-interpolated from the parent's final fields) sees the finest
+    patch of a converged composite solve at the tolerance's level: every
+    equation's relative RMS residual below 30 tol (Poisson-type: after the
+    uniform solvability constant, estimated by the mean, is removed)."""
+    n0, npt, tol = 16, 16, 1e-10
+    p = synth.zeldovich(2 * n0, seed=4, sigma=1.0, v_rms=0.003, lognormal=True)
+    patches = chain(n0, n=npt)
+    src0 = orc.deposit(n0, p.x, p.u, p.mass)
+    srcp = orc.deposit_patches(n0, patches, p.x, p.u, p.mass)
+    fld0, fldp = orc.initial_fields(n0), orc.initial_patch_fields(patches)
+    st, rep = orc.solve_composite(src0, srcp, fld0, fldp, patches, p.rho_hat, tol=tol, max_cycles=60)
+    assert st == 0
+    G = {k: orc.patch_ghosted(fldp[1][k], patches[1]["origin"], fldp[0][k], False) for k in orc.FIELDS}
+    cells = np.arange(npt ** 3)
+    nh = n0 * 4
+    for e, k in enumerate(orc.EQUATIONS):
+        smean = float(src0[("sx", "sy", "sz")[e]].mean()) if e <= 2 else 0.0
+        eps, f = orc.patch_residual_at(e, npt, nh, srcp[1], G, smean, p.rho_hat, cells)
+        if e not in (4, 5):
+            eps = eps - eps.mean()
+        r = np.sqrt(np.mean(eps ** 2)) / max(np.sqrt(np.mean(f ** 2)), 1e-300)
+        assert r <= 30 * tol, (k, r)
