@@ -259,7 +259,7 @@ def main():
         launches_c = sum(r["prof"][cls]["launches"] for r in reps)
         if launches_c == 0:
             continue
-        if cls in ("setup", "coarse"):
+        if cls in ("setup", "coarse", "patch"):
             kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "share_of_step": round(tot_ms / ms, 3)}
             continue
         byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, args.prec) for r in reps)
@@ -273,7 +273,8 @@ def main():
                           "algorithmic_GBps": round((48 + 40) * n ** 3 * len(dep_ev) / (dep_ms * 1e-3) / 1e9, 1),
                           "frac_hbm": round((48 + 40) * n ** 3 * len(dep_ev) / (dep_ms * 1e-3) / 1e9 / hbm, 3),
                           "share_of_step": round(dep_ms / ms, 3)}
-    dom = max((k for k in kernels if k not in ("coarse", "deposit")), key=lambda k: kernels[k]["ms"]) if kernels else None
+    dom = (max((k for k in kernels if k not in ("coarse", "deposit", "patch")), key=lambda k: kernels[k]["ms"])
+           if kernels else None)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if dom and os.path.exists(tpath):
@@ -473,10 +474,18 @@ def patches_measure(ctx, x, u, p, src, fld, opts, n, sizes=(128, 128)):
         ev[3].record()
         torch.cuda.synchronize()
     dep_ms, ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    # a third run with the per-class CUDA events, for the patches' share (not the timed number)
+    for q in chain:
+        for k, v in q["fld"].items():
+            v.fill_(1.0 if k in ("psi", "apsi") else 0.0)
+    f3 = ctx.initial_fields()
+    prof = ctx.solve(src, f3, patches=chain, profile=1, **opts)["prof"]
+    del f3
     diff = max(float((f2[k] - fld[k]).abs().max() / fld[k].abs().max().clamp_min(1e-300)) for k in fld)
     psi2 = chain[-1]["fld"]["psi"]
     out = {"chain": [{"n": q["n"], "origin": q["origin"]} for q in chain], "centre_cell": list(centre),
            "time_to_residual_ms": round(ms, 3), "deposit_patches_ms": round(dep_ms, 3), "cycles": rep["cycles"],
+           "patch_kernels_ms": round(prof["patch"]["ms"], 3), "patch_launches": prof["patch"]["launches"],
            "res_max_per_level": [float(f"{max(r[l] for r in rep['res_level']):.3e}") for l in range(len(sizes) + 1)],
            "base_fields_max_rel_change_vs_no_patches": diff,
            "finest_patch_psi_range": [float(psi2.min()), float(psi2.max())],

@@ -161,6 +161,7 @@ typedef enum {
     GR_PROF_NORM64,        /* FP64 residual norm (FP64 path) */
     GR_PROF_SETUP,         /* sources, coefficients and layout changes of the finest level */
     GR_PROF_COARSE,        /* every multigrid kernel below the finest level (and full multigrid's coarser cycles) */
+    GR_PROF_PATCH,         /* nested patches: set-up, relaxation, residual, transfers and injection */
     GR_NPROF
 } gr_prof_class;
 

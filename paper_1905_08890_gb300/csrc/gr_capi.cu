@@ -63,6 +63,7 @@ struct PatchLevel {
     double *win = nullptr, *old = nullptr;            // parent windows, (n/2 + 4)^3
     double *Ru = nullptr, *Re = nullptr;              // restricted u and residual, (n/2)^3
     double *flux = nullptr;                           // flux corrections in force, 6 (n/2)^2
+    double *A6 = nullptr;                             // A_ij of the solved V, U (6 ghosted arrays)
     double ref = 1;
 };
 
@@ -751,6 +752,7 @@ gr_status ensure_patches(gr_ctx *c, int np, const gr_patch *P)
             if (st == GR_OK) st = palloc(c, &L.Ru, Nc);
             if (st == GR_OK) st = palloc(c, &L.Re, Nc);
             if (st == GR_OK) st = palloc(c, &L.flux, 6 * (size_t)L.nc * L.nc);
+            if (st == GR_OK) st = palloc(c, &L.A6, 6 * M);
             if (st != GR_OK) {
                 free_patches(c);
                 return st;
@@ -795,7 +797,7 @@ gr::PPatch patch_view(gr_ctx *c, int p, const EqInfo &in, double rho)
     V.u = L.u;
     V.f = L.f;
     V.c0 = in.kind != KPOISSON ? L.c0 : nullptr;
-    V.c1 = in.kind == KPSI ? L.c1 : nullptr;
+    V.c1 = in.kind != KPOISSON ? L.c1 : nullptr;  // psi: AA; Helmholtz: the inverse diagonal
     V.h2 = L.h * L.h;
     V.ih2 = 1.0 / V.h2;
     V.rho = rho;
@@ -808,15 +810,16 @@ gr::PPatch patch_view(gr_ctx *c, int p, const EqInfo &in, double rho)
 }
 
 // parent window of patch p from the base (format fmt, or natural field nat) or patch p - 1's array a
-void parent_window(gr_ctx *c, int p, int fmt, double rho, const double *nat, const double *a, double *win)
+void parent_window(gr_ctx *c, int p, int fmt, double rho, const double *nat, const double *a, double *win,
+                   double *dold = nullptr)
 {
     PatchLevel &L = c->pl[p];
     if (p == 0) {
         gr::PBase B = base_view(c, fmt, rho);
         if (fmt == gr::PB_NAT) B.nat = nat;
-        gr::patch_gather_base(fmt, B, L.o, L.w, win, c->st);
+        gr::patch_gather_base(fmt, B, L.o, L.w, win, c->st, dold);
     } else {
-        gr::patch_gather_patch(a, c->pl[p - 1].n, L.o, L.w, win, c->st);
+        gr::patch_gather_patch(a, c->pl[p - 1].n, L.o, L.w, win, c->st, dold);
     }
 }
 
@@ -858,7 +861,9 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
         gr::PSetSrc S = {{ps.s0, ps.s[0], ps.s[1], ps.s[2], ps.sigma}};
         gr::PSetFld G;
         for (int q = 0; q < GR_NEQ; q++) G.g[q] = L.G[q];
-        const int g = gr::patch_setup(eq, L.n, 1.0 / L.h, S, G, smean, K2, Kdot, L.f, L.c0, L.c1, c->partials, c->st);
+        if (eq == GR_PSI) gr::patch_aij(L.n, 1.0 / L.h, G, L.A6, c->st);  // V and U are final from here on
+        const int g = gr::patch_setup(eq, L.n, 1.0 / L.h, S, G, L.A6, smean, K2, Kdot, L.f, L.c0, L.c1, c->partials,
+                                      c->st);
         gr::finalize(c->partials, g, c->pdev + 16 + 2 * p, c->st);
     }
     cudaMemcpyAsync(c->phost + 16, c->pdev + 16, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
@@ -934,7 +939,8 @@ void patch_up(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
     const int np = (int)c->pl.size();
     for (int p = 0; p < np; p++) {
         PatchLevel &L = c->pl[p];
-        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win);
+        // L.old becomes the parent's change since the injection
+        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win, L.old);
         gr::patch_interp(L.n, L.win, L.old, L.u, c->st);
         const gr::PPatch V = patch_view(c, p, in, rho);
         for (int sw = 0; sw < nu; sw++) {
@@ -1035,9 +1041,9 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         return q;
     };
     if (patches) {
-        st = patch_setup_eq(c, eq, o, in, s, fl, rho, S_hat, pfmt);
+        timed(c, GR_PROF_PATCH, [&] { st = patch_setup_eq(c, eq, o, in, s, fl, rho, S_hat, pfmt); });
         if (st != GR_OK) return st;
-        patch_down(c, in, pfmt, 0, rho);
+        timed(c, GR_PROF_PATCH, [&] { patch_down(c, in, pfmt, 0, rho); });
     }
     auto use_plain_guess = [&]() {
         cudaMemsetAsync(F.u, 0, N * sizeof(double), c->st);
@@ -1076,8 +1082,10 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
             vcycle64(c, in.kind, rho, o->nu1, o->nu2);
         }
         if (patches) {
-            patch_up(c, in, pfmt, o->nu2, rho);
-            patch_down(c, in, pfmt, o->nu1, rho);
+            timed(c, GR_PROF_PATCH, [&] {
+                patch_up(c, in, pfmt, o->nu2, rho);
+                patch_down(c, in, pfmt, o->nu1, rho);
+            });
             if (cells) *cells += patch_cells(c, o->nu1 + o->nu2);
         }
         st = fine_norm(&r);

@@ -344,9 +344,13 @@ struct PSetFld {
 };
 void patch_deposit(int64_t np, const double *x, const double *u, double mass, double L, int N, const int O[3], int nw,
                    const PSetSrc &out, cudaStream_t st);
-void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st);
-void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st);
-void patch_interp(int n, const double *win, const double *old, double *u, cudaStream_t st);
+// win = the parent's window; with dold, also dold := win - dold
+void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st,
+                       double *dold = nullptr);
+void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st,
+                        double *dold = nullptr);
+// ghosts of u = P(win); with d, the interior += P(d)
+void patch_interp(int n, const double *win, const double *d, double *u, cudaStream_t st);
 void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st);
 int patch_resid(int kind, const PPatch &P, double *eps, double *partials, cudaStream_t st);
 void patch_restrict(int n, const double *u, const double *eps, double *Ru, double *Re, cudaStream_t st);
@@ -363,7 +367,9 @@ void sub_scalar(int64_t cnt, double *a, const double *m, cudaStream_t st);
 void patch_to_ghosted(int n, const double *in, double *out, double add, cudaStream_t st);
 void patch_from_ghosted(int n, const double *in, double *out, double *keep, double add, const double *usum,
                         double scale, cudaStream_t st);
-int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, double smean, double K2, double Kdot,
-                double *f, double *c0, double *c1, double *partials, cudaStream_t st);
+// A_ij of the ghosted V, U on the interior and first ghost layer (six ghosted arrays)
+void patch_aij(int n, double nh, const PSetFld &G, double *A6, cudaStream_t st);
+int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, const double *A6, double smean,
+                double K2, double Kdot, double *f, double *c0, double *c1, double *partials, cudaStream_t st);
 
 }  // namespace gr

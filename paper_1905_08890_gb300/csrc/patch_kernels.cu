@@ -135,8 +135,8 @@ __device__ __forceinline__ double p_op(const PPatch &P, int i, int j, int k)
     const double lap = (p_nb(P.u, P.m, i, j, k) - 6.0 * u) * P.ih2;
     if (KIND == KPOISSON) return lap;
     if (KIND == KHELM) return lap - P.c0[c] * u;
-    const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2;
-    return lap + 2.0 * kPi * P.c0[c] / v + P.c1[c] / (8.0 * v4 * v2 * v) - 2.0 * kPi * P.rho * v4 * v;
+    const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2, iv = 1.0 / v, iv2 = iv * iv;
+    return lap + 2.0 * kPi * P.c0[c] * iv + 0.125 * P.c1[c] * (iv2 * iv2 * iv2 * iv) - 2.0 * kPi * P.rho * v4 * v;
 }
 
 // right-hand side of a patch cell: f, plus the solvability constant lambda
@@ -197,27 +197,28 @@ __global__ void __launch_bounds__(kBlock)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
-    const double h = L / N, vol = h * h * h;
+    // positions scaled by 1/L and N/L (multiplications: the FP64 divide is
+    // the slowest FP64 instruction, and every particle passes here)
+    const double iL = 1.0 / L, sN = (double)N / L, ivol = sN * sN * sN;
     const int O[3] = {O0, O1, O2};
     int r[3];
     double fplus[3];
-    bool near = true;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         double xp = x[d * np + p];
-        xp -= L * floor(xp / L);
-        const double t = xp / h - 0.5;
+        xp -= L * floor(xp * iL);
+        const double t = xp * sN - 0.5;
         const double fl = floor(t);
         fplus[d] = 1.0 - (t - fl);
         r[d] = ((int)fl - O[d]) & (N - 1);  // window coordinate of the lower cloud cell
-        near = near && (r[d] < nw || ((r[d] + 1) & (N - 1)) < nw);
+        if (r[d] >= nw && ((r[d] + 1) & (N - 1)) >= nw) return;  // the cloud misses the window
     }
-    if (!near) return;
     const double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
     const double u2 = ux * ux + uy * uy + uz * uz;
     const double W = sqrt(1.0 + u2);
-    const double q0 = mass * W / vol, qx = mass * ux / vol, qy = mass * uy / vol, qz = mass * uz / vol;
-    const double qs = mass * u2 / W / vol;
+    const double mv = mass * ivol;
+    const double q0 = mv * W, qx = mv * ux, qy = mv * uy, qz = mv * uz;
+    const double qs = mv * u2 / W;
 #pragma unroll
     for (int a = 0; a < 2; a++) {
         const int ra = (r[0] + a) & (N - 1);
@@ -244,38 +245,73 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // ---------------------------------------------------------------- windows
+// win = the parent's values on the window; with dold, also dold := win - dold
+// (the parent's change since dold was gathered)
 template <int FMT>
-__global__ void __launch_bounds__(kBlock) k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win)
+__global__ void __launch_bounds__(kBlock)
+    k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win, double *__restrict__ dold)
 {
-    const int64_t W = (int64_t)w * w * w;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W; t += (int64_t)gridDim.x * blockDim.x) {
-        const int z = (int)(t % w), y = (int)((t / w) % w), x = (int)(t / ((int64_t)w * w));
-        win[t] = b_u<FMT>(B, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z);
+    const int W = w * w * w;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
+        const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
+        const double v = b_u<FMT>(B, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z);
+        win[t] = v;
+        if (dold) dold[t] = v - dold[t];
     }
 }
 
-__global__ void __launch_bounds__(kBlock)
-    k_gather_patch(const double *__restrict__ pu, int mpar, int o0, int o1, int o2, int w, double *__restrict__ win)
+__global__ void __launch_bounds__(kBlock) k_gather_patch(const double *__restrict__ pu, int mpar, int o0, int o1, int o2,
+                                                         int w, double *__restrict__ win, double *__restrict__ dold)
 {
-    const int64_t W = (int64_t)w * w * w;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W; t += (int64_t)gridDim.x * blockDim.x) {
-        const int z = (int)(t % w), y = (int)((t / w) % w), x = (int)(t / ((int64_t)w * w));
-        win[t] = pu[gxi(mpar, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z)];
+    const int W = w * w * w;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
+        const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
+        const double v = pu[gxi(mpar, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z)];
+        win[t] = v;
+        if (dold) dold[t] = v - dold[t];
     }
 }
 
-// every cell of a ghosted patch array: ghosts = P(win); interior += P(win - old)
-// when old is given, else untouched
+// interior of a ghosted patch array += P(d), d the parent's change on the window
 __global__ void __launch_bounds__(kBlock)
-    k_interp(int n, const double *__restrict__ win, const double *__restrict__ old, int w, double *__restrict__ u)
+    k_interp_in(int lgn, const double *__restrict__ d, int w, double *__restrict__ u)
+{
+    const int N = 1 << (3 * lgn), m = (1 << lgn) + 2 * PG;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(lgn, t, i, j, k);
+        u[gxi(m, i, j, k)] += interp(d, nullptr, w, i, j, k);
+    }
+}
+
+// ghost cells of a ghosted patch array = P(win): the shell of the (n + 4)^3
+// block, enumerated as the six slabs i < 0, i >= n (all j, k), then 0 <= i < n
+// with j < 0 or j >= n (all k), then 0 <= i, j < n with k < 0 or k >= n
+__global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__restrict__ win, int w, double *__restrict__ u)
 {
     const int m = n + 2 * PG;
-    const int64_t M = (int64_t)m * m * m;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t % m) - PG, j = (int)((t / m) % m) - PG, i = (int)(t / ((int64_t)m * m)) - PG;
-        const bool inside = (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n && (unsigned)k < (unsigned)n;
-        if (!inside) u[t] = interp(win, nullptr, w, i, j, k);
-        else if (old) u[t] += interp(win, old, w, i, j, k);
+    const int a = 2 * PG * m * m;        // i slabs
+    const int b = n * 2 * PG * m;        // j slabs
+    const int cnt = a + b + n * n * 2 * PG;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (t < a) {
+            const int s = t / (m * m), r = t - s * m * m;
+            i = s < PG ? s - PG : n + s - PG;
+            j = r / m - PG;
+            k = r - (r / m) * m - PG;
+        } else if (t < a + b) {
+            const int q = t - a, s = q / (n * m), r = q - s * n * m;  // s in [0, 2 PG)
+            i = r / m;
+            j = s < PG ? s - PG : n + s - PG;
+            k = r - i * m - PG;
+        } else {
+            const int q = t - a - b, s = q / (n * n), r = q - s * n * n;
+            i = r / n;
+            j = r - i * n;
+            k = s < PG ? s - PG : n + s - PG;
+        }
+        u[gxi(m, i, j, k)] = interp(win, nullptr, w, i, j, k);
     }
 }
 
@@ -285,23 +321,26 @@ __global__ void __launch_bounds__(kBlock)
 template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
 {
-    const int64_t half = (int64_t)1 << (3 * P.lgn - 1);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < half; t += (int64_t)gridDim.x * blockDim.x) {
-        const int h = (1 << P.lgn) >> 1;
-        const int kk = (int)(t % h), j = (int)((t / h) & ((1 << P.lgn) - 1)), i = (int)(t >> (2 * P.lgn - 1));
+    const int half = 1 << (3 * P.lgn - 1);
+    const int lh = P.lgn - 1, mk = (1 << P.lgn) - 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < half; t += gridDim.x * blockDim.x) {
+        const int kk = t & ((1 << lh) - 1), j = (t >> lh) & mk, i = t >> (lh + P.lgn);
         const int k = 2 * kk + ((i + j + color) & 1);
         const int64_t c = gxi(P.m, i, j, k);
         const double nb = p_nb(P.u, P.m, i, j, k);
         const double f = p_rhs(P, i, j, k);
         if (KIND == KPOISSON) {
-            P.u[c] = (nb - P.h2 * f) / 6.0;
+            P.u[c] = (nb - P.h2 * f) * (1.0 / 6.0);
         } else if (KIND == KHELM) {
-            P.u[c] = (nb - P.h2 * f) / (6.0 + P.h2 * P.c0[c]);
+            P.u[c] = (nb - P.h2 * f) * P.c1[c];  // c1 = 1 / (6 + h^2 m), written by the set-up
         } else {
-            const double u = P.u[c], w = 1.0 + u, w2 = w * w, w4 = w2 * w2;
-            const double g = p_op<KPSI>(P, i, j, k) - f;
-            const double dg = -6.0 * P.ih2 - 2.0 * kPi * P.c0[c] / w2 - 7.0 * P.c1[c] / (8.0 * w4 * w4) -
-                              10.0 * kPi * P.rho * w4;
+            // one Newton step on g(u) = L(u) - f (the oracle's update, with 1/psi formed once)
+            const double u = P.u[c], w = 1.0 + u, w2 = w * w, w4 = w2 * w2, iw = 1.0 / w, iw2 = iw * iw,
+                         iw4 = iw2 * iw2;
+            const double c0 = P.c0[c], c1 = P.c1[c];
+            const double g = (nb - 6.0 * u) * P.ih2 + 2.0 * kPi * c0 * iw + 0.125 * c1 * (iw4 * iw2 * iw) -
+                             2.0 * kPi * P.rho * w4 * w - f;
+            const double dg = -6.0 * P.ih2 - 2.0 * kPi * c0 * iw2 - 0.875 * c1 * (iw4 * iw4) - 10.0 * kPi * P.rho * w4;
             P.u[c] = u - g / dg;
         }
     }
@@ -328,9 +367,9 @@ __global__ void __launch_bounds__(kBlock) k_prestrict(int n, const double *__res
                                                       double *__restrict__ Ru, double *__restrict__ Re)
 {
     const int nc = n / 2, m = n + 2 * PG;
-    const int64_t Nc = (int64_t)nc * nc * nc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         double su = 0.0, se = 0.0;
 #pragma unroll
         for (int a = 0; a < 2; a++)
@@ -351,9 +390,9 @@ __global__ void __launch_bounds__(kBlock) k_prestrict(int n, const double *__res
 template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_inject_u_base(PBase B, int o0, int o1, int o2, int nc, const double *__restrict__ Ru)
 {
-    const int64_t Nc = (int64_t)nc * nc * nc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         b_set_u<FMT>(B, o0 + I, o1 + J, o2 + K, Ru[t]);
     }
 }
@@ -366,11 +405,11 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_base(PBase B, int o0, int o
                                                           const double *__restrict__ Re, const double *__restrict__ lam,
                                                           double *__restrict__ partials)
 {
-    const int64_t Nc = (int64_t)nc * nc * nc;
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     const double l = (FMT == PB_DF && lam) ? *lam : 0.0;
     double sf = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         const int i = o0 + I, j = o1 + J, k = o2 + K;
         const double f = b_op<FMT, KIND>(B, i, j, k) - Re[t];
         b_set_f<FMT>(B, bsplit(B.lgn, i, j, k), f - l);
@@ -383,10 +422,10 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_base(PBase B, int o0, int o
 template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_sum_f_base(PBase B, int o0, int o1, int o2, int nc, double *__restrict__ partials)
 {
-    const int64_t Nc = (int64_t)nc * nc * nc;
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     double sf = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         sf += b_f<FMT>(B, bsplit(B.lgn, o0 + I, o1 + J, o2 + K));
     }
     block_sum2(sf, 0.0, partials);
@@ -395,9 +434,9 @@ __global__ void __launch_bounds__(kBlock) k_sum_f_base(PBase B, int o0, int o1, 
 __global__ void __launch_bounds__(kBlock) k_inject_u_patch(double *__restrict__ pu, int mpar, int o0, int o1, int o2,
                                                            int nc, const double *__restrict__ Ru)
 {
-    const int64_t Nc = (int64_t)nc * nc * nc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         pu[gxi(mpar, o0 + I, o1 + J, o2 + K)] = Ru[t];
     }
 }
@@ -406,9 +445,9 @@ template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, int o1, int o2, int nc,
                                                            const double *__restrict__ Re)
 {
-    const int64_t Nc = (int64_t)nc * nc * nc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Nc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int K = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((int64_t)nc * nc));
+    const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
+        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         const int i = o0 + I, j = o1 + J, k = o2 + K;
         par.f[gxi(par.m, i, j, k)] = p_op<KIND>(par, i, j, k) - Re[t];
     }
@@ -570,6 +609,22 @@ __device__ void aij_at(int m, const double *const V[3], const double *U, double 
     }
 }
 
+// A_ij on the interior and the first ghost layer (what the set-ups read),
+// six ghosted arrays A6[q * M + cell]
+__global__ void __launch_bounds__(kBlock) k_paij(int n, double nh, PSetFld G, double *__restrict__ A6)
+{
+    const int m = n + 2 * PG, e = n + 2;
+    const int64_t M = (int64_t)m * m * m;
+    const double *V[3] = {G.g[0], G.g[1], G.g[2]};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < e * e * e; t += gridDim.x * blockDim.x) {
+        const int i = t / (e * e) - 1, r = t - (i + 1) * e * e, j = r / e - 1, k = r - (j + 1) * e - 1;
+        double A[6];
+        aij_at(m, V, G.g[3], nh, i, j, k, A);
+        const int64_t g = gxi(m, i, j, k);
+        for (int q = 0; q < 6; q++) A6[q * M + g] = A[q];
+    }
+}
+
 __device__ __forceinline__ double aa_of(const double A[6])
 {
     return A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + 2.0 * (A[3] * A[3] + A[4] * A[4] + A[5] * A[5]);
@@ -579,17 +634,18 @@ __device__ __forceinline__ double aa_of(const double A[6])
 // interior (ghosted f, c0, c1), with block sums of the square of the
 // reference quantity: the momentum sources 8 pi (s_i - smean); the
 // divergence sources -div/4; psi: c0 = s0, c1 = AA, f = 0 (reference s0);
-// alpha psi: c0 = m, f = m - psi^5 Kdot (reference psi^5 Kdot); B^i:
+// alpha psi: c0 = m, c1 = 1/(6 + h^2 m), f = m - psi^5 Kdot (reference psi^5 Kdot); B^i:
 // 2 d_j (alpha psi psi^-7 A^ij).  G: ghosted fields in the order V_x V_y V_z
 // U psi apsi B^x B^y B^z b.
 __global__ void __launch_bounds__(kBlock)
-    k_pset(int eq, int lgn, double nh, PSetSrc S, PSetFld G, double smean, double K2, double Kdot,
-           double *__restrict__ f, double *__restrict__ c0, double *__restrict__ c1, double *__restrict__ partials)
+    k_pset(int eq, int lgn, double nh, PSetSrc S, PSetFld G, const double *__restrict__ A6, double smean, double K2,
+           double Kdot, double *__restrict__ f, double *__restrict__ c0, double *__restrict__ c1,
+           double *__restrict__ partials)
 {
     const int64_t N = (int64_t)1 << (3 * lgn);
     const int m = (1 << lgn) + 2 * PG;
+    const int64_t M = (int64_t)m * m * m;
     const double i2h = 0.5 * nh;
-    const double *V[3] = {G.g[0], G.g[1], G.g[2]};
     double s2 = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -606,17 +662,18 @@ __global__ void __launch_bounds__(kBlock)
             s2 += f[g] * f[g];
         } else if (eq == 4) {
             double A[6];
-            aij_at(m, V, G.g[3], nh, i, j, k, A);
+            for (int q = 0; q < 6; q++) A[q] = A6[q * M + g];
             c1[g] = aa_of(A);
             c0[g] = S.s[0][t];
             f[g] = 0.0;
             s2 += S.s[0][t] * S.s[0][t];
         } else if (eq == 5) {
             double A[6];
-            aij_at(m, V, G.g[3], nh, i, j, k, A);
+            for (int q = 0; q < 6; q++) A[q] = A6[q * M + g];
             const double aa = aa_of(A);
             const double p = G.g[4][g], p2 = p * p, p4 = p2 * p2, p8 = p4 * p4;
             c0[g] = 2.0 * kPi / p2 * (S.s[0][t] + 2.0 * S.s[4][t] / p4) + 0.875 * aa / p8 + (5.0 / 12.0) * p4 * K2;
+            c1[g] = 1.0 / (6.0 + c0[g] / (nh * nh));  // the inverse diagonal of the relaxation
             const double fk = -p4 * p * Kdot;
             s2 += fk * fk;
             f[g] = fk + c0[g];
@@ -627,11 +684,9 @@ __global__ void __launch_bounds__(kBlock)
                 for (int sg = -1; sg <= 1; sg += 2) {
                     int c[3] = {i, j, k};
                     c[l] += sg;
-                    double A[6];
-                    aij_at(m, V, G.g[3], nh, c[0], c[1], c[2], A);
                     const int64_t q = gxi(m, c[0], c[1], c[2]);
                     const double p = G.g[4][q], p2 = p * p, p4 = p2 * p2;
-                    s += (double)sg * G.g[5][q] / (p4 * p2 * p) * A[tab[eq - 6][l]];
+                    s += (double)sg * G.g[5][q] / (p4 * p2 * p) * A6[tab[eq - 6][l] * M + q];
                 }
             f[g] = 2.0 * s * i2h;
             s2 += f[g] * f[g];
@@ -665,23 +720,26 @@ void patch_deposit(int64_t np, const double *x, const double *u, double mass, do
               out.s[2], out.s[3], out.s[4]);
 }
 
-void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st)
+void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st, double *dold)
 {
     const int g = blocks_for((int64_t)w * w * w);
-    if (fmt == PB_NAT) GR_LAUNCH(k_gather_base<PB_NAT>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
-    else if (fmt == PB_SPLIT) GR_LAUNCH(k_gather_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
-    else GR_LAUNCH(k_gather_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], w, win);
+    if (fmt == PB_NAT) GR_LAUNCH(k_gather_base<PB_NAT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
+    else if (fmt == PB_SPLIT) GR_LAUNCH(k_gather_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
+    else GR_LAUNCH(k_gather_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
 }
 
-void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st)
+void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st,
+                        double *dold)
 {
-    GR_LAUNCH(k_gather_patch, blocks_for((int64_t)w * w * w), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], w, win);
+    GR_LAUNCH(k_gather_patch, blocks_for((int64_t)w * w * w), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], w, win,
+              dold);
 }
 
-void patch_interp(int n, const double *win, const double *old, double *u, cudaStream_t st)
+void patch_interp(int n, const double *win, const double *d, double *u, cudaStream_t st)
 {
     const int m = n + 2 * PG;
-    GR_LAUNCH(k_interp, blocks_for((int64_t)m * m * m), kBlock, st, n, win, old, n / 2 + 4, u);
+    if (d) GR_LAUNCH(k_interp_in, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), d, n / 2 + 4, u);
+    GR_LAUNCH(k_interp_ghost, blocks_for((int64_t)m * m * m - (int64_t)n * n * n), kBlock, st, n, win, n / 2 + 4, u);
 }
 
 void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st)
@@ -785,11 +843,16 @@ void patch_from_ghosted(int n, const double *in, double *out, double *keep, doub
     GR_LAUNCH(k_from_ghosted, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), in, out, keep, add, usum, scale);
 }
 
-int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, double smean, double K2, double Kdot,
-                double *f, double *c0, double *c1, double *partials, cudaStream_t st)
+void patch_aij(int n, double nh, const PSetFld &G, double *A6, cudaStream_t st)
+{
+    GR_LAUNCH(k_paij, blocks_for((int64_t)(n + 2) * (n + 2) * (n + 2)), kBlock, st, n, nh, G, A6);
+}
+
+int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, const double *A6, double smean,
+                double K2, double Kdot, double *f, double *c0, double *c1, double *partials, cudaStream_t st)
 {
     const int g = blocks_for((int64_t)n * n * n);
-    GR_LAUNCH(k_pset, g, kBlock, st, eq, lg2(n), nh, S, G, smean, K2, Kdot, f, c0, c1, partials);
+    GR_LAUNCH(k_pset, g, kBlock, st, eq, lg2(n), nh, S, G, A6, smean, K2, Kdot, f, c0, c1, partials);
     return g;
 }
 

@@ -55,12 +55,12 @@ class gr_report(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int * 10), ("res0", ctypes.c_double * 10), ("res", ctypes.c_double * 10),
                 ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
                 ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
-                ("prof_launches", ctypes.c_int * 9), ("prof_ms", ctypes.c_double * 9),
+                ("prof_launches", ctypes.c_int * 10), ("prof_ms", ctypes.c_double * 10),
                 ("guess_rejected", ctypes.c_int * 10), ("res_level", (ctypes.c_double * (MAX_PATCHES + 1)) * 10)]
 
 
 PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid", "mixed_update", "norm64", "setup",
-                "coarse")
+                "coarse", "patch")
 
 
 _lib = None
