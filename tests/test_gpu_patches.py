@@ -141,3 +141,37 @@ def test_invalid_chain_is_refused():
         ctx.solve(src, ctx.initial_fields(), rho_hat=0.01, patches=bad)
     assert ei.value.status == gr.GR_ERR_ARG
     ctx.close()
+
+
+def test_context_reuse_across_chains_and_without_patches():
+    """One context: a two-patch solve, a one-patch solve with other sizes (the
+    work arrays are rebuilt), then a base-only solve, which must equal a fresh
+    context's base-only solve on the same sources (to rounding: the two
+    contexts' launches alternate their traversal from different starting
+    points, which reorders the norm sums); the full multigrid start and the
+    per-class profile work with patches."""
+    n0 = 32
+    p = _problem(n0, seed=11, sigma=1.0)
+    x, u = _t(p.x), _t(p.u)
+    ctx = gr.Context(n0)
+    src = ctx.deposit(x, u, p.mass)
+    for chain, kw in ((centred_chain(n0, 16), dict(fmg=1)), ([{"n": 8, "origin": [30, 1, 17]}], dict(profile=1))):
+        patches = [dict(q) for q in chain]
+        ctx.deposit_patches(patches, x, u, p.mass)
+        ctx.initial_patch_fields(patches)
+        rep = ctx.solve(src, ctx.initial_fields(), tol=1e-9, max_cycles=60, prec="mixed_df", rho_hat=p.rho_hat,
+                        patches=patches, **kw)
+        assert rep["status_code"] == gr.GR_OK and max(rep["res"]) <= 1e-9
+        if kw.get("profile"):
+            assert rep["prof"]["patch"]["launches"] > 0 and rep["prof"]["patch"]["ms"] > 0
+    f1 = ctx.initial_fields()
+    ctx.solve(src, f1, tol=1e-9, max_cycles=60, prec="mixed_df", rho_hat=p.rho_hat)
+    ctx2 = gr.Context(n0)
+    f2 = ctx2.initial_fields()
+    ctx2.solve(src, f2, tol=1e-9, max_cycles=60, prec="mixed_df", rho_hat=p.rho_hat)
+    torch.cuda.synchronize()
+    for k in oracle.FIELDS:
+        d = float((f1[k] - f2[k]).abs().max() / f2[k].abs().max().clamp_min(1e-300))
+        assert d <= 1e-12, (k, d)
+    ctx.close()
+    ctx2.close()
