@@ -447,7 +447,7 @@ def fmg_measure(ctx, x, u, p, src, fld, opts):
 def patches_measure(ctx, x, u, p, src, fld, opts, n, sizes=(128, 128)):
     """The full-scale configuration with static nested refinement patches:
     two 128^3 patches at 2x and 4x the base resolution centred on the densest
-    base cell, composite solve to the same tolerance (patches relax in FP64).
+    base cell, composite solve to the same tolerance.
     One untimed and one timed run from the plain guess (CUDA events), next to
     the base-only headline solve's fields."""
     import torch

@@ -144,8 +144,8 @@ typedef struct {
                          takes the restricted patch solution and residual on the cells the patch covers, and the
                          coarse flux through each face of a covered block is replaced by the mean of the four
                          fine fluxes).  Every equation then stops when the base and every patch are at or below
-                         tol, each relative to its own reference.  Patches relax in FP64 whatever the precision
-                         mode; check_guess is ignored. */
+                         tol, each relative to its own reference.  Patches relax in FP64 with GR_PREC_FP64 and
+                         in double-float (pairs of FP32) in the mixed modes; check_guess is ignored. */
     const gr_patch *patch;
 } gr_opts;
 

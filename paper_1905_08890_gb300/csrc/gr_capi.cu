@@ -64,6 +64,10 @@ struct PatchLevel {
     double *Ru = nullptr, *Re = nullptr;              // restricted u and residual, (n/2)^3
     double *flux = nullptr;                           // flux corrections in force, 6 (n/2)^2
     double *A6 = nullptr;                             // A_ij of the solved V, U (6 ghosted arrays)
+    // the double-float relaxation (mixed modes): unknown, h^2 f and h^2-scaled coefficients as FP32 pairs
+    float *uh = nullptr, *ul = nullptr, *fh = nullptr, *fl = nullptr;
+    float *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+    float *d32 = nullptr;                             // the parent's change on the window, FP32
     double ref = 1;
 };
 
@@ -115,6 +119,7 @@ struct gr_ctx {
     std::vector<PatchLevel> pl;
     std::vector<void *> palloc;
     double *pdev = nullptr, *phost = nullptr;
+    bool pdf = false;  // the patches relax in double-float (mixed modes) rather than FP64
 };
 
 namespace {
@@ -753,12 +758,16 @@ gr_status ensure_patches(gr_ctx *c, int np, const gr_patch *P)
             if (st == GR_OK) st = palloc(c, &L.Re, Nc);
             if (st == GR_OK) st = palloc(c, &L.flux, 6 * (size_t)L.nc * L.nc);
             if (st == GR_OK) st = palloc(c, &L.A6, 6 * M);
+            float **fa[8] = {&L.uh, &L.ul, &L.fh, &L.fl, &L.ah, &L.al, &L.bh, &L.bl};
+            for (int q = 0; q < 8 && st == GR_OK; q++) st = palloc(c, fa[q], M);
+            if (st == GR_OK) st = palloc(c, &L.d32, W);
             if (st != GR_OK) {
                 free_patches(c);
                 return st;
             }
             // ghost cells never written keep defined values
             for (int q = 0; q < 5; q++) cudaMemsetAsync(*arr[q], 0, M * sizeof(double), c->st);
+            for (int q = 0; q < 8; q++) cudaMemsetAsync(*fa[q], 0, M * sizeof(float), c->st);
             for (int q = 0; q < GR_NEQ; q++) cudaMemsetAsync(L.G[q], 0, M * sizeof(double), c->st);
         }
     }
@@ -798,9 +807,13 @@ gr::PPatch patch_view(gr_ctx *c, int p, const EqInfo &in, double rho)
     V.f = L.f;
     V.c0 = in.kind != KPOISSON ? L.c0 : nullptr;
     V.c1 = in.kind != KPOISSON ? L.c1 : nullptr;  // psi: AA; Helmholtz: the inverse diagonal
+    V.uh = L.uh, V.ul = L.ul, V.fh = L.fh, V.fl = L.fl;
+    V.ah = L.ah, V.al = L.al, V.bh = L.bh, V.bl = L.bl;
     V.h2 = L.h * L.h;
     V.ih2 = 1.0 / V.h2;
     V.rho = rho;
+    V.cpr = gr::df_from_double_host(2.0 * kPi * rho * V.h2);
+    V.c5 = (float)(10.0 * kPi * rho * V.h2);
     if (p + 1 < (int)c->pl.size()) {
         for (int d = 0; d < 3; d++) V.co[d] = c->pl[p + 1].o[d];
         V.cnc = c->pl[p + 1].nc;
@@ -809,17 +822,31 @@ gr::PPatch patch_view(gr_ctx *c, int p, const EqInfo &in, double rho)
     return V;
 }
 
-// parent window of patch p from the base (format fmt, or natural field nat) or patch p - 1's array a
-void parent_window(gr_ctx *c, int p, int fmt, double rho, const double *nat, const double *a, double *win,
-                   double *dold = nullptr)
+// an FP64 ghosted array of patch p seen as a level (for windows of the fields)
+gr::PPatch field_view(gr_ctx *c, int p, double *a)
+{
+    gr::PPatch V;
+    V.lgn = c->pl[p].lgn;
+    V.m = c->pl[p].m;
+    V.u = a;
+    return V;
+}
+
+// parent window of patch p: from the base (format fmt; PB_NAT reads the
+// natural field nat), else from patch p - 1's working unknown (a == NULL) or
+// its FP64 ghosted array a
+void parent_window(gr_ctx *c, int p, int fmt, double rho, const double *nat, double *a, const EqInfo *in,
+                   double *win, double *dold = nullptr, float *d32 = nullptr)
 {
     PatchLevel &L = c->pl[p];
     if (p == 0) {
         gr::PBase B = base_view(c, fmt, rho);
         if (fmt == gr::PB_NAT) B.nat = nat;
-        gr::patch_gather_base(fmt, B, L.o, L.w, win, c->st, dold);
+        gr::patch_gather_base(fmt, B, L.o, L.w, win, c->st, dold, d32);
+    } else if (a) {
+        gr::patch_gather_patch(field_view(c, p - 1, a), false, L.o, L.w, win, c->st, dold, d32);
     } else {
-        gr::patch_gather_patch(a, c->pl[p - 1].n, L.o, L.w, win, c->st, dold);
+        gr::patch_gather_patch(patch_view(c, p - 1, *in, rho), c->pdf, L.o, L.w, win, c->st, dold, d32);
     }
 }
 
@@ -843,8 +870,8 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
         if (!need[q]) continue;
         for (int p = 0; p < np; p++) {
             PatchLevel &L = c->pl[p];
-            parent_window(c, p, gr::PB_NAT, rho, field_ptr(fl, q), p ? c->pl[p - 1].G[q] : nullptr, L.win);
-            gr::patch_interp(L.n, L.win, nullptr, L.G[q], c->st);
+            parent_window(c, p, gr::PB_NAT, rho, field_ptr(fl, q), p ? c->pl[p - 1].G[q] : nullptr, &in, L.win);
+            gr::patch_interp(field_view(c, p, L.G[q]), false, L.win, nullptr, nullptr, c->st);
         }
     }
     double smean = 0.0;
@@ -864,6 +891,7 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
         if (eq == GR_PSI) gr::patch_aij(L.n, 1.0 / L.h, G, L.A6, c->st);  // V and U are final from here on
         const int g = gr::patch_setup(eq, L.n, 1.0 / L.h, S, G, L.A6, smean, K2, Kdot, L.f, L.c0, L.c1, c->partials,
                                       c->st);
+        if (c->pdf) gr::patch_coef_df(in.kind, patch_view(c, p, in, rho), c->st);
         gr::finalize(c->partials, g, c->pdev + 16 + 2 * p, c->st);
     }
     cudaMemcpyAsync(c->phost + 16, c->pdev + 16, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
@@ -872,12 +900,13 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
         PatchLevel &L = c->pl[p];
         L.ref = (eq == GR_PSI ? 2.0 * kPi : 1.0) * std::sqrt(c->phost[16 + 2 * p] / ((double)L.n * L.n * L.n));
         if (!(L.ref >= 1e-300)) L.ref = 1.0;
-        gr::patch_to_ghosted(L.n, field_ptr(&o->patch[p].fld, eq), L.u, in.dev ? -1.0 : 0.0, c->st);
+        gr::patch_u_load(patch_view(c, p, in, rho), c->pdf, field_ptr(&o->patch[p].fld, eq), in.dev ? -1.0 : 0.0,
+                         c->st);
     }
     for (int p = 0; p < np; p++) {
         PatchLevel &L = c->pl[p];
-        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win);
-        gr::patch_interp(L.n, L.win, nullptr, L.u, c->st);
+        parent_window(c, p, fmt, rho, nullptr, nullptr, &in, L.win);
+        gr::patch_interp(patch_view(c, p, in, rho), c->pdf, L.win, nullptr, nullptr, c->st);
         cudaMemsetAsync(L.flux, 0, 6 * (size_t)L.nc * L.nc * sizeof(double), c->st);
     }
     cudaMemsetAsync(c->pdev, 0, sizeof(double), c->st);  // lambda = 0
@@ -902,12 +931,12 @@ void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
         PatchLevel &L = c->pl[p];
         const gr::PPatch V = patch_view(c, p, in, rho);
         for (int sw = 0; sw < nu; sw++) {
-            gr::patch_gs(in.kind, V, 0, c->st);
-            gr::patch_gs(in.kind, V, 1, c->st);
+            gr::patch_gs(in.kind, V, c->pdf, 0, c->st);
+            gr::patch_gs(in.kind, V, c->pdf, 1, c->st);
         }
-        int g = gr::patch_resid(in.kind, V, L.eps, c->partials, c->st);
+        int g = gr::patch_resid(in.kind, V, c->pdf, L.eps, c->partials, c->st);
         gr::finalize(c->partials, g, c->pdev + 32 + 2 * p, c->st);
-        gr::patch_restrict(L.n, L.u, L.eps, L.Ru, L.Re, c->st);
+        gr::patch_restrict(V, c->pdf, L.eps, L.Ru, L.Re, c->st);
         if (p == 0) {
             const gr::PBase B = base_view(c, fmt, rho);
             gr::patch_inject_u_base(fmt, B, L.o, L.nc, L.Ru, c->st);
@@ -915,7 +944,7 @@ void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
             g = gr::patch_inject_f_base(fmt, in.kind, B, L.o, L.nc, L.Re,
                                         (fmt == gr::PB_DF && in.poisson) ? c->pdev : nullptr, c->partials, c->st);
             gr::finalize(c->partials, g, c->pdev + 3, c->st);
-            gr::patch_reflux(fmt, B, gr::PPatch{}, L.o, L.n, L.u, c->h, L.flux, c->st);
+            gr::patch_reflux(fmt, B, gr::PPatch{}, V, c->pdf, L.o, c->h, L.flux, c->st);
             if (in.poisson) {
                 gr::patch_lambda(c->pdev + 1, L.flux, 6 * L.nc * L.nc, (double)N0, (double)L.nc * L.nc * L.nc,
                                  c->pdev, c->st);
@@ -924,10 +953,10 @@ void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
         } else {
             PatchLevel &Q = c->pl[p - 1];
             const gr::PPatch par = patch_view(c, p - 1, in, rho);
-            gr::patch_inject_u_patch(Q.u, Q.n, L.o, L.nc, L.Ru, c->st);
-            gr::patch_gather_patch(Q.u, Q.n, L.o, L.w, L.old, c->st);
-            gr::patch_inject_f_patch(in.kind, par, L.o, L.nc, L.Re, c->st);
-            gr::patch_reflux(-1, gr::PBase{}, par, L.o, L.n, L.u, Q.h, L.flux, c->st);
+            gr::patch_inject_u_patch(par, c->pdf, L.o, L.nc, L.Ru, c->st);
+            gr::patch_gather_patch(par, c->pdf, L.o, L.w, L.old, c->st);
+            gr::patch_inject_f_patch(in.kind, par, c->pdf, L.o, L.nc, L.Re, c->st);
+            gr::patch_reflux(-1, gr::PBase{}, par, V, c->pdf, L.o, Q.h, L.flux, c->st);
         }
     }
     cudaMemcpyAsync(c->phost + 32, c->pdev + 32, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
@@ -940,12 +969,12 @@ void patch_up(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
     for (int p = 0; p < np; p++) {
         PatchLevel &L = c->pl[p];
         // L.old becomes the parent's change since the injection
-        parent_window(c, p, fmt, rho, nullptr, p ? c->pl[p - 1].u : nullptr, L.win, L.old);
-        gr::patch_interp(L.n, L.win, L.old, L.u, c->st);
+        parent_window(c, p, fmt, rho, nullptr, nullptr, &in, L.win, L.old, c->pdf ? L.d32 : nullptr);
         const gr::PPatch V = patch_view(c, p, in, rho);
+        gr::patch_interp(V, c->pdf, L.win, L.old, L.d32, c->st);
         for (int sw = 0; sw < nu; sw++) {
-            gr::patch_gs(in.kind, V, 0, c->st);
-            gr::patch_gs(in.kind, V, 1, c->st);
+            gr::patch_gs(in.kind, V, c->pdf, 0, c->st);
+            gr::patch_gs(in.kind, V, c->pdf, 1, c->st);
         }
     }
 }
@@ -1114,8 +1143,8 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
     if (patches) {  // the same mean off every patch; the patch's copy of the field for later set-ups
         const double *usum = in.poisson ? (dfm ? c->dscal : c->dscal + 1) : nullptr;
         for (int p = 0; p < o->npatch; p++)
-            gr::patch_from_ghosted(c->pl[p].n, c->pl[p].u, field_ptr(&o->patch[p].fld, eq), c->pl[p].G[eq],
-                                   in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
+            gr::patch_u_store(patch_view(c, p, in, rho), c->pdf, field_ptr(&o->patch[p].fld, eq), c->pl[p].G[eq],
+                              in.dev ? 1.0 : 0.0, usum, 1.0 / N, c->st);
         if (res_level)
             for (int p = 0; p <= o->npatch; p++) res_level[p] = rlev[p];
     }
@@ -1360,6 +1389,7 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
     if (o->npatch > 0) {
         st = ensure_patches(c, o->npatch, o->patch);
         if (st != GR_OK) return st;
+        c->pdf = o->prec != GR_PREC_FP64;
         for (int p = 0; p < o->npatch; p++)  // every field's guess, for the set-ups of the equations before its own
             for (int q = 0; q < GR_NEQ; q++)
                 gr::patch_to_ghosted(c->pl[p].n, field_ptr(&o->patch[p].fld, q), c->pl[p].G[q], 0.0, c->st);

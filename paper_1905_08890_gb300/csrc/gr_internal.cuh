@@ -20,6 +20,8 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "df64.cuh"
+
 namespace gr {
 
 // kernels launched by this library since load; every launch goes through GR_LAUNCH
@@ -326,12 +328,21 @@ struct PBase {
     const float *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
     double h2 = 0, ih2 = 0, rho = 0;
 };
-// One patch level: ghosted (n + 4)^3 FP64 arrays; co/cnc the block its child
+// One patch level: ghosted (n + 4)^3 arrays; co/cnc the block its child
 // covers (cnc = 0: none); lam the Poisson solvability constant (NULL: none).
+// The working unknown is u (FP64) or the pair uh/ul (the double-float
+// relaxation of the mixed modes, with the h^2-scaled pairs fh/fl, ah/al,
+// bh/bl of the right-hand side and coefficients, cpr = 2 pi rho h^2 and
+// c5 = 10 pi rho h^2); f, c0, c1 are the FP64 right-hand side and
+// coefficients (Helmholtz c1: 1 / (6 + h^2 m)).
 struct PPatch {
     int lgn = 0, m = 0;
     double *u = nullptr, *f = nullptr;
     const double *c0 = nullptr, *c1 = nullptr;
+    float *uh = nullptr, *ul = nullptr, *fh = nullptr, *fl = nullptr;
+    float *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+    df cpr = {0.0f, 0.0f};
+    float c5 = 0.0f;
     double h2 = 0, ih2 = 0, rho = 0;
     int co[3] = {0, 0, 0}, cnc = 0;
     const double *lam = nullptr;
@@ -344,29 +355,32 @@ struct PSetFld {
 };
 void patch_deposit(int64_t np, const double *x, const double *u, double mass, double L, int N, const int O[3], int nw,
                    const PSetSrc &out, cudaStream_t st);
-// win = the parent's window; with dold, also dold := win - dold
+// win = the parent's window; with dold, also dold := win - dold (and d32 its FP32 copy)
 void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st,
-                       double *dold = nullptr);
-void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st,
-                        double *dold = nullptr);
-// ghosts of u = P(win); with d, the interior += P(d)
-void patch_interp(int n, const double *win, const double *d, double *u, cudaStream_t st);
-void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st);
-int patch_resid(int kind, const PPatch &P, double *eps, double *partials, cudaStream_t st);
-void patch_restrict(int n, const double *u, const double *eps, double *Ru, double *Re, cudaStream_t st);
+                       double *dold = nullptr, float *d32 = nullptr);
+void patch_gather_patch(const PPatch &par, bool pdf, const int o[3], int w, double *win, cudaStream_t st,
+                        double *dold = nullptr, float *d32 = nullptr);
+// ghosts of the unknown = P(win); with d (or its FP32 copy d32 for pdf), the interior += P(d)
+void patch_interp(const PPatch &P, bool pdf, const double *win, const double *d, const float *d32, cudaStream_t st);
+void patch_gs(int kind, const PPatch &P, bool pdf, int color, cudaStream_t st);
+int patch_resid(int kind, const PPatch &P, bool pdf, double *eps, double *partials, cudaStream_t st);
+void patch_restrict(const PPatch &P, bool pdf, const double *eps, double *Ru, double *Re, cudaStream_t st);
 void patch_inject_u_base(int fmt, const PBase &B, const int o[3], int nc, const double *Ru, cudaStream_t st);
 int patch_inject_f_base(int fmt, int kind, const PBase &B, const int o[3], int nc, const double *Re, const double *lam,
                         double *partials, cudaStream_t st);
 int patch_sum_f_base(int fmt, const PBase &B, const int o[3], int nc, double *partials, cudaStream_t st);
-void patch_inject_u_patch(double *pu, int npar, const int o[3], int nc, const double *Ru, cudaStream_t st);
-void patch_inject_f_patch(int kind, const PPatch &par, const int o[3], int nc, const double *Re, cudaStream_t st);
-void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const int o[3], int n, const double *pu, double hc,
-                  double *flux, cudaStream_t st);
+void patch_inject_u_patch(const PPatch &par, bool pdf, const int o[3], int nc, const double *Ru, cudaStream_t st);
+void patch_inject_f_patch(int kind, const PPatch &par, bool pdf, const int o[3], int nc, const double *Re,
+                          cudaStream_t st);
+void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const PPatch &ch, bool pdf, const int o[3],
+                  double hc, double *flux, cudaStream_t st);
 void patch_lambda(double *sc, const double *flux, int nq, double N, double Ncov, double *lam, cudaStream_t st);
 void sub_scalar(int64_t cnt, double *a, const double *m, cudaStream_t st);
 void patch_to_ghosted(int n, const double *in, double *out, double add, cudaStream_t st);
-void patch_from_ghosted(int n, const double *in, double *out, double *keep, double add, const double *usum,
-                        double scale, cudaStream_t st);
+void patch_u_load(const PPatch &P, bool pdf, const double *in, double add, cudaStream_t st);
+void patch_u_store(const PPatch &P, bool pdf, double *out, double *keep, double add, const double *usum, double scale,
+                   cudaStream_t st);
+void patch_coef_df(int kind, const PPatch &P, cudaStream_t st);
 // A_ij of the ghosted V, U on the interior and first ghost layer (six ghosted arrays)
 void patch_aij(int n, double nh, const PSetFld &G, double *A6, cudaStream_t st);
 int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, const double *A6, double smean,

@@ -21,6 +21,7 @@
 // patch takes the parent's correction P(u_new - u_old).
 #include "df64.cuh"
 #include "gr_internal.cuh"
+#include "df_stencil.cuh"
 
 namespace gr {
 namespace {
@@ -121,22 +122,78 @@ __device__ __forceinline__ double b_op(const PBase &B, int i, int j, int k)
 }
 
 // ---------------------------------------------------------------- patch access
-__device__ __forceinline__ double p_nb(const double *u, int m, int i, int j, int k)
+// The working unknown of a patch is FP64 (u) or, with DF, a double-float pair
+// (uh, ul: the mixed modes, where the relaxation runs in FP32 instructions).
+template <bool DF>
+__device__ __forceinline__ double pu_get(const PPatch &P, int64_t c)
 {
-    return u[gxi(m, i + 1, j, k)] + u[gxi(m, i - 1, j, k)] + u[gxi(m, i, j + 1, k)] + u[gxi(m, i, j - 1, k)] +
-           u[gxi(m, i, j, k + 1)] + u[gxi(m, i, j, k - 1)];
+    if (DF) return join_double({P.uh[c], P.ul[c]});
+    return P.u[c];
 }
 
-template <int KIND>
+template <bool DF>
+__device__ __forceinline__ void pu_set(const PPatch &P, int64_t c, double v)
+{
+    if (DF) {
+        const df d = split_double(v);
+        P.uh[c] = d.hi;
+        P.ul[c] = d.lo;
+    } else {
+        P.u[c] = v;
+    }
+}
+
+template <bool DF>
+__device__ __forceinline__ double p_nb(const PPatch &P, int i, int j, int k)
+{
+    const int m = P.m;
+    return pu_get<DF>(P, gxi(m, i + 1, j, k)) + pu_get<DF>(P, gxi(m, i - 1, j, k)) +
+           pu_get<DF>(P, gxi(m, i, j + 1, k)) + pu_get<DF>(P, gxi(m, i, j - 1, k)) +
+           pu_get<DF>(P, gxi(m, i, j, k + 1)) + pu_get<DF>(P, gxi(m, i, j, k - 1));
+}
+
+// L(u) at a patch cell in FP64 (the oracle's operator; FP64 coefficients c0, c1)
+template <int KIND, bool DF = false>
 __device__ __forceinline__ double p_op(const PPatch &P, int i, int j, int k)
 {
     const int64_t c = gxi(P.m, i, j, k);
-    const double u = P.u[c];
-    const double lap = (p_nb(P.u, P.m, i, j, k) - 6.0 * u) * P.ih2;
+    const double u = pu_get<DF>(P, c);
+    const double lap = (p_nb<DF>(P, i, j, k) - 6.0 * u) * P.ih2;
     if (KIND == KPOISSON) return lap;
     if (KIND == KHELM) return lap - P.c0[c] * u;
     const double v = 1.0 + u, v2 = v * v, v4 = v2 * v2, iv = 1.0 / v, iv2 = iv * iv;
     return lap + 2.0 * kPi * P.c0[c] * iv + 0.125 * P.c1[c] * (iv2 * iv2 * iv2 * iv) - 2.0 * kPi * P.rho * v4 * v;
+}
+
+// whether the child patch covers cell (i, j, k)
+__device__ __forceinline__ bool p_covered(const PPatch &P, int i, int j, int k)
+{
+    return P.cnc > 0 && (unsigned)(i - P.co[0]) < (unsigned)P.cnc && (unsigned)(j - P.co[1]) < (unsigned)P.cnc &&
+           (unsigned)(k - P.co[2]) < (unsigned)P.cnc;
+}
+
+// h^2 eps = h^2 (L(u) - f) at a patch cell in double-float (the base's stencil
+// operator on the pair arrays; f' = h^2 f, plus h^2 lambda where no child
+// covers the cell); KPSI also the Newton inverse diagonal
+template <int KIND>
+__device__ __forceinline__ df p_cell_df(const PPatch &P, df lam2, int i, int j, int k, float *inv)
+{
+    const int m = P.m;
+    const int64_t c = gxi(m, i, j, k);
+    const int64_t nb[6] = {gxi(m, i + 1, j, k), gxi(m, i - 1, j, k), gxi(m, i, j + 1, k),
+                           gxi(m, i, j - 1, k), gxi(m, i, j, k + 1), gxi(m, i, j, k - 1)};
+    float nh[6], nl[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        nh[q] = P.uh[nb[q]];
+        nl[q] = P.ul[nb[q]];
+    }
+    df f = {P.fh[c], P.fl[c]};
+    if (P.lam && !p_covered(P, i, j, k)) f = df_add(f, lam2);
+    const df a = KIND == KPOISSON ? df{0.0f, 0.0f} : df{P.ah[c], P.al[c]};
+    const df b = KIND == KPSI ? df{P.bh[c], P.bl[c]} : df{0.0f, 0.0f};
+    float mj = 0.0f;
+    return df_cell<KIND>(nh, nl, {P.uh[c], P.ul[c]}, f, a, b, P.cpr, P.c5, &mj, inv);
 }
 
 // right-hand side of a patch cell: f, plus the solvability constant lambda
@@ -145,9 +202,7 @@ __device__ __forceinline__ double p_rhs(const PPatch &P, int i, int j, int k)
 {
     const double f = P.f[gxi(P.m, i, j, k)];
     if (!P.lam) return f;
-    const bool cov = P.cnc > 0 && (unsigned)(i - P.co[0]) < (unsigned)P.cnc &&
-                     (unsigned)(j - P.co[1]) < (unsigned)P.cnc && (unsigned)(k - P.co[2]) < (unsigned)P.cnc;
-    return cov ? f : f + *P.lam;
+    return p_covered(P, i, j, k) ? f : f + *P.lam;
 }
 
 // interior cell t (0 <= t < n^3) of an n^3 patch, n = 2^lgn
@@ -247,47 +302,90 @@ __global__ void __launch_bounds__(kBlock)
 // ---------------------------------------------------------------- windows
 // win = the parent's values on the window; with dold, also dold := win - dold
 // (the parent's change since dold was gathered)
+// (d32, if given, receives the change rounded to FP32: the double-float
+// patches add its interpolation in FP32, since it is small)
 template <int FMT>
-__global__ void __launch_bounds__(kBlock)
-    k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win, double *__restrict__ dold)
+__global__ void __launch_bounds__(kBlock) k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win,
+                                                        double *__restrict__ dold, float *__restrict__ d32)
 {
     const int W = w * w * w;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
         const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
         const double v = b_u<FMT>(B, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z);
         win[t] = v;
-        if (dold) dold[t] = v - dold[t];
+        if (dold) {
+            const double d = v - dold[t];
+            dold[t] = d;
+            if (d32) d32[t] = (float)d;
+        }
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_gather_patch(const double *__restrict__ pu, int mpar, int o0, int o1, int o2,
-                                                         int w, double *__restrict__ win, double *__restrict__ dold)
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_gather_patch(PPatch par, int o0, int o1, int o2, int w,
+                                                         double *__restrict__ win, double *__restrict__ dold,
+                                                         float *__restrict__ d32)
 {
     const int W = w * w * w;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
         const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
-        const double v = pu[gxi(mpar, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z)];
+        const double v = pu_get<DF>(par, gxi(par.m, o0 - 2 + x, o1 - 2 + y, o2 - 2 + z));
         win[t] = v;
-        if (dold) dold[t] = v - dold[t];
+        if (dold) {
+            const double d = v - dold[t];
+            dold[t] = d;
+            if (d32) d32[t] = (float)d;
+        }
     }
 }
 
-// interior of a ghosted patch array += P(d), d the parent's change on the window
+// trilinear interpolation of a float window (the weights of interp)
+__device__ __forceinline__ float interp32(const float *d, int w, int i, int j, int k)
+{
+    int I[2], J[2], K[2];
+    I[0] = (i >> 1) + 2;
+    I[1] = I[0] + ((i & 1) ? 1 : -1);
+    J[0] = (j >> 1) + 2;
+    J[1] = J[0] + ((j & 1) ? 1 : -1);
+    K[0] = (k >> 1) + 2;
+    K[1] = K[0] + ((k & 1) ? 1 : -1);
+    const float wt[2] = {0.75f, 0.25f};
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int c = 0; c < 2; c++) s += wt[a] * wt[b] * wt[c] * d[(I[a] * w + J[b]) * w + K[c]];
+    return s;
+}
+
+// interior of the patch's unknown += P(d), d the parent's change on the
+// window (FP64 d, or its FP32 copy d32 for the double-float unknown)
+template <bool DF>
 __global__ void __launch_bounds__(kBlock)
-    k_interp_in(int lgn, const double *__restrict__ d, int w, double *__restrict__ u)
+    k_interp_in(int lgn, PPatch P, const double *__restrict__ d, const float *__restrict__ d32, int w)
 {
     const int N = 1 << (3 * lgn), m = (1 << lgn) + 2 * PG;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
         int i, j, k;
         p_cell(lgn, t, i, j, k);
-        u[gxi(m, i, j, k)] += interp(d, nullptr, w, i, j, k);
+        const int64_t c = gxi(m, i, j, k);
+        if (DF) {
+            const df s = df_plus_f(P.uh[c], P.ul[c], interp32(d32, w, i, j, k));
+            P.uh[c] = s.hi;
+            P.ul[c] = s.lo;
+        } else {
+            P.u[c] += interp(d, nullptr, w, i, j, k);
+        }
     }
 }
 
 // ghost cells of a ghosted patch array = P(win): the shell of the (n + 4)^3
 // block, enumerated as the six slabs i < 0, i >= n (all j, k), then 0 <= i < n
 // with j < 0 or j >= n (all k), then 0 <= i, j < n with k < 0 or k >= n
-__global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__restrict__ win, int w, double *__restrict__ u)
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__restrict__ win, int w, PPatch P)
 {
     const int m = n + 2 * PG;
     const int a = 2 * PG * m * m;        // i slabs
@@ -311,23 +409,37 @@ __global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__
             j = r - i * n;
             k = s < PG ? s - PG : n + s - PG;
         }
-        u[gxi(m, i, j, k)] = interp(win, nullptr, w, i, j, k);
+        pu_set<DF>(P, gxi(m, i, j, k), interp(win, nullptr, w, i, j, k));
     }
 }
 
 // ---------------------------------------------------------------- relaxation, residual
 // one red-black colour over the interior (local colour (i + j + k) & 1): the
-// point update of the base relaxation (Newton step for psi)
-template <int KIND>
+// point update of the base relaxation (Newton step for psi).  DF: the update
+// u += h^2 eps / (6 + h^2 m) of the double-float unknown, h^2 eps from the
+// stencil operator in FP32 instructions, the divisor in FP32 (it scales a
+// correction that vanishes at the fixed point)
+template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
 {
     const int half = 1 << (3 * P.lgn - 1);
     const int lh = P.lgn - 1, mk = (1 << P.lgn) - 1;
+    df lam2 = {0.0f, 0.0f};
+    if (DF && P.lam) lam2 = split_double(*P.lam * P.h2);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < half; t += gridDim.x * blockDim.x) {
         const int kk = t & ((1 << lh) - 1), j = (t >> lh) & mk, i = t >> (lh + P.lgn);
         const int k = 2 * kk + ((i + j + color) & 1);
         const int64_t c = gxi(P.m, i, j, k);
-        const double nb = p_nb(P.u, P.m, i, j, k);
+        if (DF) {
+            float inv = 1.0f / 6.0f;
+            const df e = p_cell_df<KIND>(P, lam2, i, j, k, &inv);  // h^2 eps
+            if (KIND == KHELM) inv = 1.0f / (6.0f + P.ah[c]);
+            const df s = df_plus_f(P.uh[c], P.ul[c], (e.hi + e.lo) * inv);
+            P.uh[c] = s.hi;
+            P.ul[c] = s.lo;
+            continue;
+        }
+        const double nb = p_nb<false>(P, i, j, k);
         const double f = p_rhs(P, i, j, k);
         if (KIND == KPOISSON) {
             P.u[c] = (nb - P.h2 * f) * (1.0 / 6.0);
@@ -347,15 +459,23 @@ __global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
 }
 
 // eps = L(u) - f on the interior (ghosted eps array) and block sums of eps^2
-template <int KIND>
+template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_presid(PPatch P, double *__restrict__ eps, double *__restrict__ partials)
 {
     const int64_t N = (int64_t)1 << (3 * P.lgn);
+    df lam2 = {0.0f, 0.0f};
+    if (DF && P.lam) lam2 = split_double(*P.lam * P.h2);
     double s2 = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
         p_cell(P.lgn, t, i, j, k);
-        const double e = p_op<KIND>(P, i, j, k) - p_rhs(P, i, j, k);
+        double e;
+        if (DF) {
+            float inv;
+            e = join_double(p_cell_df<KIND>(P, lam2, i, j, k, &inv)) * P.ih2;
+        } else {
+            e = p_op<KIND>(P, i, j, k) - p_rhs(P, i, j, k);
+        }
         eps[gxi(P.m, i, j, k)] = e;
         s2 += e * e;
     }
@@ -363,7 +483,8 @@ __global__ void __launch_bounds__(kBlock) k_presid(PPatch P, double *__restrict_
 }
 
 // 8-child averages of u and eps over the nc^3 parent cells the patch covers
-__global__ void __launch_bounds__(kBlock) k_prestrict(int n, const double *__restrict__ u, const double *__restrict__ eps,
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_prestrict(int n, PPatch P, const double *__restrict__ eps,
                                                       double *__restrict__ Ru, double *__restrict__ Re)
 {
     const int nc = n / 2, m = n + 2 * PG;
@@ -378,7 +499,7 @@ __global__ void __launch_bounds__(kBlock) k_prestrict(int n, const double *__res
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     const int64_t id = gxi(m, 2 * I + a, 2 * J + b, 2 * K + c);
-                    su += u[id];
+                    su += pu_get<DF>(P, id);
                     se += eps[id];
                 }
         Ru[t] = 0.125 * su;
@@ -431,17 +552,19 @@ __global__ void __launch_bounds__(kBlock) k_sum_f_base(PBase B, int o0, int o1, 
     block_sum2(sf, 0.0, partials);
 }
 
-__global__ void __launch_bounds__(kBlock) k_inject_u_patch(double *__restrict__ pu, int mpar, int o0, int o1, int o2,
-                                                           int nc, const double *__restrict__ Ru)
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_inject_u_patch(PPatch par, int o0, int o1, int o2, int nc,
+                                                           const double *__restrict__ Ru)
 {
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
-        pu[gxi(mpar, o0 + I, o1 + J, o2 + K)] = Ru[t];
+        pu_set<DF>(par, gxi(par.m, o0 + I, o1 + J, o2 + K), Ru[t]);
     }
 }
 
-template <int KIND>
+// (the double-float parent stores h^2 f as a pair)
+template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, int o1, int o2, int nc,
                                                            const double *__restrict__ Re)
 {
@@ -449,7 +572,15 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, i
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         const int i = o0 + I, j = o1 + J, k = o2 + K;
-        par.f[gxi(par.m, i, j, k)] = p_op<KIND>(par, i, j, k) - Re[t];
+        const int64_t g = gxi(par.m, i, j, k);
+        const double f = p_op<KIND, DF>(par, i, j, k) - Re[t];
+        if (DF) {
+            const df d = split_double(f * par.h2);
+            par.fh[g] = d.hi;
+            par.fl[g] = d.lo;
+        } else {
+            par.f[g] = f;
+        }
     }
 }
 
@@ -478,9 +609,9 @@ __device__ __forceinline__ void shell_cell(int q, int nc, int n, int in[3], int 
     }
 }
 
-template <int PARENT>
-__global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, int o0, int o1, int o2, int n,
-                                                   const double *__restrict__ pu, double hc, double *__restrict__ flux)
+template <int PARENT, bool DF>
+__global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, PPatch ch, int o0, int o1, int o2, int n,
+                                                   double hc, double *__restrict__ flux)
 {
     const int nc = n / 2, m = n + 2 * PG;
     const int nq = 6 * nc * nc;
@@ -492,8 +623,8 @@ __global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, int o0, 
         const int oi = o0 + out[0], oj = o1 + out[1], ok = o2 + out[2];
         double uin, uout;
         if (PARENT == 0) {
-            uin = par.u[gxi(par.m, ii, ij, ik)];
-            uout = par.u[gxi(par.m, oi, oj, ok)];
+            uin = pu_get<DF>(par, gxi(par.m, ii, ij, ik));
+            uout = pu_get<DF>(par, gxi(par.m, oi, oj, ok));
         } else {
             uin = b_u<PARENT>(B, ii, ij, ik);
             uout = b_u<PARENT>(B, oi, oj, ok);
@@ -501,13 +632,21 @@ __global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, int o0, 
         const double Tc = (uin - uout) / hc;
         double Tf = 0.0;
         for (int e = 0; e < 4; e++)
-            Tf += (pu[gxi(m, fi[e][0], fi[e][1], fi[e][2])] - pu[gxi(m, fg[e][0], fg[e][1], fg[e][2])]) / hf;
+            Tf += (pu_get<DF>(ch, gxi(m, fi[e][0], fi[e][1], fi[e][2])) -
+                   pu_get<DF>(ch, gxi(m, fg[e][0], fg[e][1], fg[e][2]))) / hf;
         Tf *= 0.25;
         const double corr = -(Tf - Tc) / hc;
         const double d = corr - flux[q];
         flux[q] = corr;
         if (PARENT == 0) {
-            par.f[gxi(par.m, oi, oj, ok)] += d;
+            const int64_t g = gxi(par.m, oi, oj, ok);
+            if (DF) {
+                const df v = split_double(join_double({par.fh[g], par.fl[g]}) + d * par.h2);
+                par.fh[g] = v.hi;
+                par.fl[g] = v.lo;
+            } else {
+                par.f[g] += d;
+            }
         } else {
             const int64_t s = bsplit(B.lgn, oi, oj, ok);
             b_set_f<PARENT>(B, s, b_f<PARENT>(B, s) + d);
@@ -554,22 +693,57 @@ __global__ void __launch_bounds__(kBlock) k_to_ghosted(int lgn, const double *__
     }
 }
 
-// natural n^3 (and, if keep, a second ghosted array's interior) <- ghosted
-// interior + add - usum[0] * scale (usum may be NULL)
-__global__ void __launch_bounds__(kBlock) k_from_ghosted(int lgn, const double *__restrict__ in, double *__restrict__ out,
-                                                         double *__restrict__ keep, double add,
-                                                         const double *__restrict__ usum, double scale)
+// the working unknown's interior <- natural n^3 (+ add)
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_u_load(int lgn, const double *__restrict__ in, PPatch P, double add)
 {
-    const int64_t N = (int64_t)1 << (3 * lgn);
-    const int m = (1 << lgn) + 2 * PG;
-    const double sh = add - (usum ? usum[0] * scale : 0.0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int N = 1 << (3 * lgn);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
         int i, j, k;
         p_cell(lgn, t, i, j, k);
-        const int64_t g = gxi(m, i, j, k);
-        const double v = in[g] + sh;
+        pu_set<DF>(P, gxi(P.m, i, j, k), in[t] + add);
+    }
+}
+
+// natural n^3 (and the interior of the ghosted FP64 copy keep) <- the working
+// unknown + add - usum[0] * scale (usum may be NULL)
+template <bool DF>
+__global__ void __launch_bounds__(kBlock) k_u_store(int lgn, PPatch P, double *__restrict__ out,
+                                                    double *__restrict__ keep, double add,
+                                                    const double *__restrict__ usum, double scale)
+{
+    const int N = 1 << (3 * lgn);
+    const double sh = add - (usum ? usum[0] * scale : 0.0);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(lgn, t, i, j, k);
+        const int64_t g = gxi(P.m, i, j, k);
+        const double v = pu_get<DF>(P, g) + sh;
         out[t] = v;
         if (keep) keep[g] = v;
+    }
+}
+
+// the double-float relaxation's right-hand side and coefficients, scaled by
+// h^2 as the stencil operator takes them: f' = h^2 f; Helmholtz a' = h^2 m;
+// psi a' = 2 pi h^2 s0, b' = h^2 AA / 8
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_pcoef_df(PPatch P)
+{
+    const int N = 1 << (3 * P.lgn);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        p_cell(P.lgn, t, i, j, k);
+        const int64_t g = gxi(P.m, i, j, k);
+        df d = split_double(P.f[g] * P.h2);
+        P.fh[g] = d.hi, P.fl[g] = d.lo;
+        if (KIND == KPOISSON) continue;
+        d = split_double(P.c0[g] * P.h2 * (KIND == KPSI ? 2.0 * kPi : 1.0));
+        P.ah[g] = d.hi, P.al[g] = d.lo;
+        if (KIND == KPSI) {
+            d = split_double(P.c1[g] * P.h2 * 0.125);
+            P.bh[g] = d.hi, P.bl[g] = d.lo;
+        }
     }
 }
 
@@ -720,49 +894,75 @@ void patch_deposit(int64_t np, const double *x, const double *u, double mass, do
               out.s[2], out.s[3], out.s[4]);
 }
 
-void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st, double *dold)
+void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st, double *dold,
+                       float *d32)
 {
     const int g = blocks_for((int64_t)w * w * w);
-    if (fmt == PB_NAT) GR_LAUNCH(k_gather_base<PB_NAT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
-    else if (fmt == PB_SPLIT) GR_LAUNCH(k_gather_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
-    else GR_LAUNCH(k_gather_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold);
+    if (fmt == PB_NAT) GR_LAUNCH(k_gather_base<PB_NAT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold, d32);
+    else if (fmt == PB_SPLIT) GR_LAUNCH(k_gather_base<PB_SPLIT>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold, d32);
+    else GR_LAUNCH(k_gather_base<PB_DF>, g, kBlock, st, B, o[0], o[1], o[2], w, win, dold, d32);
 }
 
-void patch_gather_patch(const double *pu, int npar, const int o[3], int w, double *win, cudaStream_t st,
-                        double *dold)
+void patch_gather_patch(const PPatch &par, bool pdf, const int o[3], int w, double *win, cudaStream_t st,
+                        double *dold, float *d32)
 {
-    GR_LAUNCH(k_gather_patch, blocks_for((int64_t)w * w * w), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], w, win,
-              dold);
+    const int g = blocks_for((int64_t)w * w * w);
+    if (pdf) GR_LAUNCH(k_gather_patch<true>, g, kBlock, st, par, o[0], o[1], o[2], w, win, dold, d32);
+    else GR_LAUNCH(k_gather_patch<false>, g, kBlock, st, par, o[0], o[1], o[2], w, win, dold, d32);
 }
 
-void patch_interp(int n, const double *win, const double *d, double *u, cudaStream_t st)
+void patch_interp(const PPatch &P, bool pdf, const double *win, const double *d, const float *d32, cudaStream_t st)
 {
-    const int m = n + 2 * PG;
-    if (d) GR_LAUNCH(k_interp_in, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), d, n / 2 + 4, u);
-    GR_LAUNCH(k_interp_ghost, blocks_for((int64_t)m * m * m - (int64_t)n * n * n), kBlock, st, n, win, n / 2 + 4, u);
+    const int n = 1 << P.lgn, m = n + 2 * PG, w = n / 2 + 4;
+    const int gi = blocks_for((int64_t)n * n * n), gg = blocks_for((int64_t)m * m * m - (int64_t)n * n * n);
+    if (pdf) {
+        if (d) GR_LAUNCH(k_interp_in<true>, gi, kBlock, st, P.lgn, P, d, d32, w);
+        GR_LAUNCH(k_interp_ghost<true>, gg, kBlock, st, n, win, w, P);
+    } else {
+        if (d) GR_LAUNCH(k_interp_in<false>, gi, kBlock, st, P.lgn, P, d, d32, w);
+        GR_LAUNCH(k_interp_ghost<false>, gg, kBlock, st, n, win, w, P);
+    }
 }
 
-void patch_gs(int kind, const PPatch &P, int color, cudaStream_t st)
+void patch_gs(int kind, const PPatch &P, bool pdf, int color, cudaStream_t st)
 {
     const int g = blocks_for((int64_t)1 << (3 * P.lgn - 1));
-    if (kind == KPOISSON) GR_LAUNCH(k_pgs<KPOISSON>, g, kBlock, st, P, color);
-    else if (kind == KHELM) GR_LAUNCH(k_pgs<KHELM>, g, kBlock, st, P, color);
-    else GR_LAUNCH(k_pgs<KPSI>, g, kBlock, st, P, color);
+#define GR_PGS(K, D) GR_LAUNCH((k_pgs<K, D>), g, kBlock, st, P, color)
+    if (pdf) {
+        if (kind == KPOISSON) GR_PGS(KPOISSON, true);
+        else if (kind == KHELM) GR_PGS(KHELM, true);
+        else GR_PGS(KPSI, true);
+    } else {
+        if (kind == KPOISSON) GR_PGS(KPOISSON, false);
+        else if (kind == KHELM) GR_PGS(KHELM, false);
+        else GR_PGS(KPSI, false);
+    }
+#undef GR_PGS
 }
 
-int patch_resid(int kind, const PPatch &P, double *eps, double *partials, cudaStream_t st)
+int patch_resid(int kind, const PPatch &P, bool pdf, double *eps, double *partials, cudaStream_t st)
 {
     const int g = blocks_for((int64_t)1 << (3 * P.lgn));
-    if (kind == KPOISSON) GR_LAUNCH(k_presid<KPOISSON>, g, kBlock, st, P, eps, partials);
-    else if (kind == KHELM) GR_LAUNCH(k_presid<KHELM>, g, kBlock, st, P, eps, partials);
-    else GR_LAUNCH(k_presid<KPSI>, g, kBlock, st, P, eps, partials);
+#define GR_PRES(K, D) GR_LAUNCH((k_presid<K, D>), g, kBlock, st, P, eps, partials)
+    if (pdf) {
+        if (kind == KPOISSON) GR_PRES(KPOISSON, true);
+        else if (kind == KHELM) GR_PRES(KHELM, true);
+        else GR_PRES(KPSI, true);
+    } else {
+        if (kind == KPOISSON) GR_PRES(KPOISSON, false);
+        else if (kind == KHELM) GR_PRES(KHELM, false);
+        else GR_PRES(KPSI, false);
+    }
+#undef GR_PRES
     return g;
 }
 
-void patch_restrict(int n, const double *u, const double *eps, double *Ru, double *Re, cudaStream_t st)
+void patch_restrict(const PPatch &P, bool pdf, const double *eps, double *Ru, double *Re, cudaStream_t st)
 {
-    const int nc = n / 2;
-    GR_LAUNCH(k_prestrict, blocks_for((int64_t)nc * nc * nc), kBlock, st, n, u, eps, Ru, Re);
+    const int n = 1 << P.lgn, nc = n / 2;
+    const int g = blocks_for((int64_t)nc * nc * nc);
+    if (pdf) GR_LAUNCH(k_prestrict<true>, g, kBlock, st, n, P, eps, Ru, Re);
+    else GR_LAUNCH(k_prestrict<false>, g, kBlock, st, n, P, eps, Ru, Re);
 }
 
 void patch_inject_u_base(int fmt, const PBase &B, const int o[3], int nc, const double *Ru, cudaStream_t st)
@@ -798,28 +998,46 @@ int patch_sum_f_base(int fmt, const PBase &B, const int o[3], int nc, double *pa
     return g;
 }
 
-void patch_inject_u_patch(double *pu, int npar, const int o[3], int nc, const double *Ru, cudaStream_t st)
-{
-    GR_LAUNCH(k_inject_u_patch, blocks_for((int64_t)nc * nc * nc), kBlock, st, pu, npar + 2 * PG, o[0], o[1], o[2], nc,
-              Ru);
-}
-
-void patch_inject_f_patch(int kind, const PPatch &par, const int o[3], int nc, const double *Re, cudaStream_t st)
+void patch_inject_u_patch(const PPatch &par, bool pdf, const int o[3], int nc, const double *Ru, cudaStream_t st)
 {
     const int g = blocks_for((int64_t)nc * nc * nc);
-    if (kind == KPOISSON) GR_LAUNCH(k_inject_f_patch<KPOISSON>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
-    else if (kind == KHELM) GR_LAUNCH(k_inject_f_patch<KHELM>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
-    else GR_LAUNCH(k_inject_f_patch<KPSI>, g, kBlock, st, par, o[0], o[1], o[2], nc, Re);
+    if (pdf) GR_LAUNCH(k_inject_u_patch<true>, g, kBlock, st, par, o[0], o[1], o[2], nc, Ru);
+    else GR_LAUNCH(k_inject_u_patch<false>, g, kBlock, st, par, o[0], o[1], o[2], nc, Ru);
 }
 
-void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const int o[3], int n, const double *pu, double hc,
-                  double *flux, cudaStream_t st)
+void patch_inject_f_patch(int kind, const PPatch &par, bool pdf, const int o[3], int nc, const double *Re,
+                          cudaStream_t st)
 {
-    const int nc = n / 2;
+    const int g = blocks_for((int64_t)nc * nc * nc);
+#define GR_PINJ(K, D) GR_LAUNCH((k_inject_f_patch<K, D>), g, kBlock, st, par, o[0], o[1], o[2], nc, Re)
+    if (pdf) {
+        if (kind == KPOISSON) GR_PINJ(KPOISSON, true);
+        else if (kind == KHELM) GR_PINJ(KHELM, true);
+        else GR_PINJ(KPSI, true);
+    } else {
+        if (kind == KPOISSON) GR_PINJ(KPOISSON, false);
+        else if (kind == KHELM) GR_PINJ(KHELM, false);
+        else GR_PINJ(KPSI, false);
+    }
+#undef GR_PINJ
+}
+
+void patch_reflux(int parent_fmt, const PBase &B, const PPatch &par, const PPatch &ch, bool pdf, const int o[3],
+                  double hc, double *flux, cudaStream_t st)
+{
+    const int n = 1 << ch.lgn, nc = n / 2;
     const int g = blocks_for((int64_t)6 * nc * nc);
-    if (parent_fmt < 0) GR_LAUNCH(k_reflux<0>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
-    else if (parent_fmt == PB_SPLIT) GR_LAUNCH(k_reflux<PB_SPLIT>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
-    else GR_LAUNCH(k_reflux<PB_DF>, g, kBlock, st, B, par, o[0], o[1], o[2], n, pu, hc, flux);
+#define GR_RFX(F, D) GR_LAUNCH((k_reflux<F, D>), g, kBlock, st, B, par, ch, o[0], o[1], o[2], n, hc, flux)
+    if (pdf) {
+        if (parent_fmt < 0) GR_RFX(0, true);
+        else if (parent_fmt == PB_SPLIT) GR_RFX(PB_SPLIT, true);
+        else GR_RFX(PB_DF, true);
+    } else {
+        if (parent_fmt < 0) GR_RFX(0, false);
+        else if (parent_fmt == PB_SPLIT) GR_RFX(PB_SPLIT, false);
+        else GR_RFX(PB_DF, false);
+    }
+#undef GR_RFX
 }
 
 void patch_lambda(double *sc, const double *flux, int nq, double N, double Ncov, double *lam, cudaStream_t st)
@@ -837,10 +1055,27 @@ void patch_to_ghosted(int n, const double *in, double *out, double add, cudaStre
     GR_LAUNCH(k_to_ghosted, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), in, out, add);
 }
 
-void patch_from_ghosted(int n, const double *in, double *out, double *keep, double add, const double *usum,
-                        double scale, cudaStream_t st)
+void patch_u_load(const PPatch &P, bool pdf, const double *in, double add, cudaStream_t st)
 {
-    GR_LAUNCH(k_from_ghosted, blocks_for((int64_t)n * n * n), kBlock, st, lg2(n), in, out, keep, add, usum, scale);
+    const int g = blocks_for((int64_t)1 << (3 * P.lgn));
+    if (pdf) GR_LAUNCH(k_u_load<true>, g, kBlock, st, P.lgn, in, P, add);
+    else GR_LAUNCH(k_u_load<false>, g, kBlock, st, P.lgn, in, P, add);
+}
+
+void patch_u_store(const PPatch &P, bool pdf, double *out, double *keep, double add, const double *usum, double scale,
+                   cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)1 << (3 * P.lgn));
+    if (pdf) GR_LAUNCH(k_u_store<true>, g, kBlock, st, P.lgn, P, out, keep, add, usum, scale);
+    else GR_LAUNCH(k_u_store<false>, g, kBlock, st, P.lgn, P, out, keep, add, usum, scale);
+}
+
+void patch_coef_df(int kind, const PPatch &P, cudaStream_t st)
+{
+    const int g = blocks_for((int64_t)1 << (3 * P.lgn));
+    if (kind == KPOISSON) GR_LAUNCH(k_pcoef_df<KPOISSON>, g, kBlock, st, P);
+    else if (kind == KHELM) GR_LAUNCH(k_pcoef_df<KHELM>, g, kBlock, st, P);
+    else GR_LAUNCH(k_pcoef_df<KPSI>, g, kBlock, st, P);
 }
 
 void patch_aij(int n, double nh, const PSetFld &G, double *A6, cudaStream_t st)
