@@ -9,8 +9,10 @@
 // -2 <= i, j, k < n + 2.  It refines the parent block o .. o + n/2 - 1 (per
 // axis) by 2; the parent window is the (n/2 + 4)^3 block of parent cells
 // o - 2 .. o + n/2 + 1, which every interpolation and correction of the
-// patch reads.  FP64 throughout: the patches hold a few percent of the cells
-// of a solve, and their relaxation is latency-bound, not bandwidth-bound.
+// patch reads.  The transfers and the coupling run in FP64; the relaxation
+// and the residual run in FP64 (GR_PREC_FP64) or, in the mixed modes, on
+// double-float pairs with the base's stencil operator, since GB300 issues
+// FP64 at 1/58 of the FP32 rate and an FP64 colour pass is FP64-issue bound.
 //
 // The paper runs its solver on an adaptive grid (Sec. 3, Sec. 4.3) without
 // stating how a refined region couples to its parent; these kernels follow
