@@ -175,3 +175,21 @@ def test_context_reuse_across_chains_and_without_patches():
         assert d <= 1e-12, (k, d)
     ctx.close()
     ctx2.close()
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8)])
+def test_three_patches_of_different_sizes(prec, tol, bar):
+    """A chain of three patches, 32^3, 16^3 and 8^3, off-centre in their
+    parents (eight times the base resolution at the finest)."""
+    n0 = 32
+    chain = [{"n": 32, "origin": [5, 9, 27]}, {"n": 16, "origin": [12, 3, 14]}, {"n": 8, "origin": [2, 7, 5]}]
+    p = _problem(n0, seed=13, sigma=2.0, per=2)
+    src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
+    rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, prec, tol)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for e in range(10):
+        assert max(rep["res_level"][e][:4]) <= tol
+    for k in oracle.FIELDS:
+        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k)
+        for lvl in range(3):
+            assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= bar, ("patch", lvl + 1, k, rel_linf(gp[lvl][k], ofldp[lvl][k]))
