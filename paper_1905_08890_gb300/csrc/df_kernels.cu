@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
                const float *__restrict__ inv_in, float *__restrict__ e32, double *__restrict__ partials, int rev,
                const double *__restrict__ fshift, double fsh_scale)
 {
+    pdl_begin();
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     float acc = 0.0f;
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(kBlock, (resid_min_blocks<KIND, W>()))
 // u (double-float) += e
 __global__ void k_df_update(int64_t cnt, float *__restrict__ uh, float *__restrict__ ul, const float *__restrict__ e)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const df s = df_plus_f(uh[t], ul[t], e[t]);
         uh[t] = s.hi;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(kBlock)
     k_df_black_update(int lgn, const float *__restrict__ e, const float *__restrict__ r, const float *__restrict__ inv,
                       float h2, float *__restrict__ uh, float *__restrict__ ul, int rev)
 {
+    pdl_begin();
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int half = 1 << (3 * lgn - 1);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (half >> 2); v += gridDim.x * blockDim.x) {

@@ -124,6 +124,7 @@ __device__ __forceinline__ df df_scale2(df a, float p2) { return {a.hi * p2, a.l
 // ---------------------------------------------------------------- sums
 __global__ void __launch_bounds__(kBlock) k_dfs_sum(int64_t cnt, const double *__restrict__ a, double *partials)
 {
+    pdl_begin();
     Acc acc;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         acc.add(ld(a, t));
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_dfs_sum(int64_t cnt, const double *_
 __global__ void __launch_bounds__(kBlock)
     k_dfs_pair_sum(int64_t cnt, const float *__restrict__ h, const float *__restrict__ l, double *partials)
 {
+    pdl_begin();
     Acc acc;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         acc.add(ldp(h, l, t));
@@ -164,6 +166,7 @@ struct PoissonArgs {
 template <int SRC>
 __global__ void __launch_bounds__(kBlock, SRC == SRC_SHIFT ? 2 : 3) k_dfs_poisson(int lgn, PoissonArgs a, double *partials)
 {
+    pdl_begin();
     const int mn = (1 << lgn) - 1;
     const int64_t N = (int64_t)1 << (3 * lgn);
     df mu = {0.0f, 0.0f};
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(kBlock)
                  const double *__restrict__ a2, const double *__restrict__ a3, float *__restrict__ p0,
                  float *__restrict__ p1, float *__restrict__ p2, float *__restrict__ p3)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         stp(p0, p0 + cnt, t, ld(a0, t));
         stp(p1, p1 + cnt, t, ld(a1, t));
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(kBlock)
               const float *__restrict__ Pvz, const float *__restrict__ Pu, float *__restrict__ A,
               float *__restrict__ AAh, float *__restrict__ AAl)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const int m = (1 << lgn) - 1;
     const float *V[3] = {Pvx, Pvy, Pvz};
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(kBlock)
               float *__restrict__ ul, float *__restrict__ ah, float *__restrict__ al, float *__restrict__ bh,
               float *__restrict__ bl, float *__restrict__ fh, float *__restrict__ fl, double *partials)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df m1 = {-1.0f, 0.0f};
     Acc acc;
@@ -330,6 +336,7 @@ __global__ void __launch_bounds__(kBlock)
                float *__restrict__ ul, float *__restrict__ ah, float *__restrict__ al, float *__restrict__ fh,
                float *__restrict__ fl, float *__restrict__ m32, float *__restrict__ inv32, double *partials)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df m1 = {-1.0f, 0.0f};
     Acc acc;
@@ -364,6 +371,7 @@ __global__ void __launch_bounds__(kBlock) k_dfs_weight(int64_t cnt, const double
                                                        const double *__restrict__ apsi, float *__restrict__ wh,
                                                        float *__restrict__ wl)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const df ip = df_recip(ld(psi, t));
         const df ip2 = df_mul(ip, ip), ip4 = df_mul(ip2, ip2);
@@ -380,6 +388,7 @@ __global__ void __launch_bounds__(kBlock)
     k_dfs_store(int lgn, const float *__restrict__ uh, const float *__restrict__ ul, const double *__restrict__ sum,
                 double inv_cnt, double *__restrict__ out)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const df nmu = sum ? df_neg(split_double(sum[0] * inv_cnt)) : df{0.0f, 0.0f};
     for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;

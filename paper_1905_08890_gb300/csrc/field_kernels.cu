@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kBlock)
               double *__restrict__ s0, double *__restrict__ sx, double *__restrict__ sy, double *__restrict__ sz,
               double *__restrict__ sig)
 {
+    pdl_begin();
     const int m = (1 << lgn) - 1;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
         int lo[3];
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kBlock)
 // ---------------------------------------------------------------- reductions
 __global__ void __launch_bounds__(kBlock) k_sum_sq(int64_t cnt, const double *__restrict__ a, double *__restrict__ part)
 {
+    pdl_begin();
     double s = 0.0, s2 = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const double v = a[t];
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_sum_sq(int64_t cnt, const double *__
 __global__ void k_scale_sub_mean(int64_t cnt, double *__restrict__ a, const double *__restrict__ sum, double inv_cnt,
                                  double scale)
 {
+    pdl_begin();
     const double m = sum[0] * inv_cnt;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         a[t] = scale * (a[t] - m);
@@ -127,6 +130,7 @@ __global__ void k_scale_sub_mean(int64_t cnt, double *__restrict__ a, const doub
 __global__ void __launch_bounds__(kBlock)
     k_to_split(int lgn, const double *__restrict__ nat, double *__restrict__ split, double shift)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -139,6 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_from_split(int lgn, const double *__
                                                        double *__restrict__ nat, double shift,
                                                        const double *__restrict__ sum, double inv_cnt)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     const double m = sum ? sum[0] * inv_cnt : 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(kBlock)
     k_div_to_split(int lgn, double inv2h, const double *__restrict__ Fx, const double *__restrict__ Fy,
                    const double *__restrict__ Fz, double scale, double *__restrict__ f)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -170,6 +176,7 @@ __global__ void __launch_bounds__(kBlock)
              const double *__restrict__ Vz, const double *__restrict__ U, double *__restrict__ A,
              double *__restrict__ AA)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     const int m = (1 << lgn) - 1;
     const double *V[3] = {Vx, Vy, Vz};
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(kBlock)
     k_psi_setup(int lgn, const double *__restrict__ psi, const double *__restrict__ s0, const double *__restrict__ AA,
                 double *__restrict__ u, double *__restrict__ c0, double *__restrict__ c1, double *__restrict__ f)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -232,6 +240,7 @@ __global__ void __launch_bounds__(kBlock)
                  double K2, double Kdot, double *__restrict__ u, double *__restrict__ c0, double *__restrict__ c1,
                  double *__restrict__ f, double *__restrict__ g)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -252,6 +261,7 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock) k_shift_weight(int64_t cnt, const double *__restrict__ psi,
                                                          const double *__restrict__ apsi, double *__restrict__ w)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const double p = psi[t], p2 = p * p, p4 = p2 * p2;
         w[t] = apsi[t] / (p4 * p2 * p);
@@ -263,6 +273,7 @@ __global__ void __launch_bounds__(kBlock)
     k_shift_source(int lgn, double inv2h, const double *__restrict__ A, const double *__restrict__ w, int comp,
                    double *__restrict__ f)
 {
+    pdl_begin();
     const int64_t cnt = (int64_t)1 << (3 * lgn);
     const int tab[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {

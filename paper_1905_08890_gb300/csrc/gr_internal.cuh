@@ -26,16 +26,58 @@ namespace gr {
 
 // kernels launched by this library since load; every launch goes through GR_LAUNCH
 extern std::atomic<long long> g_launches;
-#define GR_LAUNCH(kernel, grid, block, stream, ...)                         \
-    do {                                                                    \
-        kernel<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__);              \
-        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
+
+// Every kernel is launched with programmatic dependent launch: the next kernel
+// of the stream may be scheduled onto the SMs while its predecessor drains
+// (its launch latency and block start-up overlap the predecessor's last
+// blocks), and every kernel begins with pdl_begin(), which waits for the
+// predecessor's completion and memory before anything else, so the stream's
+// order of effects is that of plain launches.
+template <class T>
+struct ident {
+    using type = T;
+};
+template <typename... KArgs>
+inline void launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st,
+                       typename ident<KArgs>::type... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k, args...) != cudaSuccess) {
+        // a stream that takes no programmatic serialization (the legacy default
+        // stream may not): a plain launch, whose error, if any, stays recorded
+        cudaGetLastError();
+        cfg.numAttrs = 0;
+        cudaLaunchKernelEx(&cfg, k, args...);
+    }
+}
+#define GR_LAUNCH(kernel, grid, block, stream, ...)                              \
+    do {                                                                         \
+        ::gr::launch_pdl(kernel, (grid), (block), 0, (stream), __VA_ARGS__);      \
+        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);                \
     } while (0)
-#define GR_LAUNCH_SMEM(kernel, grid, block, smem, stream, ...)              \
-    do {                                                                    \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);         \
-        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);           \
+#define GR_LAUNCH_SMEM(kernel, grid, block, smem, stream, ...)                   \
+    do {                                                                         \
+        ::gr::launch_pdl(kernel, (grid), (block), (smem), (stream), __VA_ARGS__); \
+        ::gr::g_launches.fetch_add(1, std::memory_order_relaxed);                \
     } while (0)
+
+#ifdef __CUDACC__
+// first statement of every kernel: let the stream's next kernel launch, then
+// wait for the previous one (a no-op for a kernel launched without the attribute)
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory");
+}
+#endif
 
 // Kernels of the finest level take `rev`: nonzero walks their index range
 // from the end, so a launch that follows one walking forward starts where it

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kBlock)
     k_sweep(int lgn, T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
             T h2, T ih2, T rho, int color)
 {
+    pdl_begin();
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int64_t half = (int64_t)1 << (3 * lgn - 1);
     const int64_t off = color ? half : 0;
@@ -132,6 +133,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ u, const float *__restrict__ f,
                                                    const float *__restrict__ c1, float h2, int color, int rev)
 {
+    pdl_begin();
     const int lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
     const int64_t half = (int64_t)1 << (3 * lgn - 1);
     const int64_t off = color ? half : 0;
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(kBlock)
                      const T *__restrict__ c1, T ih2, T rho, T *__restrict__ uc, T *__restrict__ fc,
                      T *__restrict__ urc, const T *__restrict__ cinv = nullptr, T h2c = T(0), int rev = 0)
 {
+    pdl_begin();
     const int lgc = lgf - 1;
     const int mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
     const int half = 1 << (3 * lgf - 1);
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(kBlock)
                     float ih2, float *__restrict__ ec, float *__restrict__ rc, const float *__restrict__ cinv,
                     float h2c, int rev)
 {
+    pdl_begin();
     using V2 = float2;
     const int lgc = lgf - 1, mc = (1 << lgc) - 1, hcl = lgc - 1, mq = (1 << hcl) - 1;
     const int mf = (1 << lgf) - 1, mhf = (1 << (lgf - 1)) - 1;
@@ -356,6 +360,7 @@ __global__ void __launch_bounds__(kBlock)
     k_fas_rhs(int lgc, const double *__restrict__ uc, double *__restrict__ fc, const double *__restrict__ c0,
               const double *__restrict__ c1, double ih2, double rho)
 {
+    pdl_begin();
     const int64_t ncells = (int64_t)1 << (3 * lgc);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -367,6 +372,7 @@ __global__ void __launch_bounds__(kBlock)
 
 __global__ void k_fas_diff(int64_t cnt, double *__restrict__ uc, const double *__restrict__ urc)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         uc[t] -= urc[t];
 }
@@ -397,6 +403,7 @@ struct Vec2<double> {
 template <typename T, int BLACK = 0>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__ u, const T *__restrict__ uc, int rev = 0)
 {
+    pdl_begin();
     using V2 = typename Vec2<T>::type;
     const int lgc = lgf - 1, mc = (1 << lgc) - 1, hc = lgc - 1, mq = (1 << hc) - 1;
     const int halfc = 1 << (3 * lgc - 1), halff = 1 << (3 * lgf - 1);
@@ -461,6 +468,7 @@ template <typename T, int KIND>
 __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
                            double h2, double ih2, double rho)
 {
+    pdl_begin();
     __shared__ double su[8], sf[8], s0[8], s1[8];
     const int t = threadIdx.x;
     if (t < 8) {
@@ -520,6 +528,7 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_restrict_avg(int lgf, const T *__restrict__ fine, T *__restrict__ coarse)
 {
+    pdl_begin();
     const int lgc = lgf - 1, mc = (1 << lgc) - 1;
     const int ncells = 1 << (3 * lgc);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncells; t += gridDim.x * blockDim.x) {
@@ -540,6 +549,7 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock) k_restrict_coef(int lgf, const T *__restrict__ c0f, const T *__restrict__ c1f,
                                                           T *__restrict__ c0c, T *__restrict__ c1c, T h2c)
 {
+    pdl_begin();
     const int lgc = lgf - 1, mc = (1 << lgc) - 1;
     const int64_t ncells = (int64_t)1 << (3 * lgc);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
@@ -568,6 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict_coef(int lgf, const T *__re
 template <typename T>
 __global__ void k_helm_invdiag(int64_t cnt, const T *__restrict__ c0, T *__restrict__ c1, T h2)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         c1[t] = T(1) / (T(6) + h2 * c0[t]);
 }
@@ -578,6 +589,7 @@ __global__ void __launch_bounds__(kBlock)
     k_resid_norm(int lgn, const T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ c0,
                  const T *__restrict__ c1, T ih2, T rho, double *__restrict__ partials, double *__restrict__ eps_nat)
 {
+    pdl_begin();
     const int64_t ncells = (int64_t)1 << (3 * lgn);
     double s2 = 0.0, su = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
@@ -595,6 +607,7 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock) k_finalize(const double *__restrict__ partials, int nblk,
                                                      double *__restrict__ out)
 {
+    pdl_begin();
     // one block, fixed summation order: out[0], out[1] = block_sum2's slots of block 0
     double a = 0.0, b = 0.0;
     for (int q = threadIdx.x; q < nblk; q += kBlock) {
@@ -611,6 +624,7 @@ __global__ void __launch_bounds__(kBlock)
                   const double *__restrict__ c1, double ih2, double h2, double rho, float *__restrict__ r32,
                   float *__restrict__ m32, float *__restrict__ inv32, double *__restrict__ partials)
 {
+    pdl_begin();
     const int64_t ncells = (int64_t)1 << (3 * lgn);
     double s2 = 0.0, su = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells;
@@ -634,12 +648,14 @@ __global__ void __launch_bounds__(kBlock)
 
 __global__ void k_mixed_update(int64_t cnt, double *__restrict__ u, const float *__restrict__ e)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         u[t] += (double)e[t];
 }
 
 __global__ void k_to_float(int64_t cnt, const double *__restrict__ a, float *__restrict__ b)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         b[t] = (float)a[t];
 }
@@ -680,13 +696,13 @@ void resid_restrict(int kind, int nf, const T *u, const T *f, const T *c0, const
     const int lgf = log2i(nf);
     const int g = grid_for((int64_t)nf * nf * nf / 8);
     if (kind == KPOISSON)
-        GR_LAUNCH((k_resid_restrict<T, KPOISSON, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPOISSON, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc, nullptr, T(0), 0);
     else if (kind == KHELM)
-        GR_LAUNCH((k_resid_restrict<T, KHELM, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KHELM, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc, nullptr, T(0), 0);
     else if (fas)
-        GR_LAUNCH((k_resid_restrict<T, KPSI, 1>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPSI, 1>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc, nullptr, T(0), 0);
     else
-        GR_LAUNCH((k_resid_restrict<T, KPSI, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc);
+        GR_LAUNCH((k_resid_restrict<T, KPSI, 0>), g, kBlock, st, lgf, u, f, c0, c1, (T)ih2, (T)rho, uc, fc, urc, nullptr, T(0), 0);
 }
 
 void resid_restrict_red(int kind, int nf, const float *e, const float *r, const float *m, double ih2, float *ec,
@@ -995,6 +1011,7 @@ struct TailArgs {
 template <int KIND>
 __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs g, int nu1, int nu2)
 {
+    pdl_begin();
     extern __shared__ float sh[];
     TailLevel L[4];
     float *p = sh;

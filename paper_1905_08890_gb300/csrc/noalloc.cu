@@ -61,6 +61,7 @@ __device__ __forceinline__ void na_block_sum2(double a, double b, double *out)
 __global__ void __launch_bounds__(kNaThreads)
     k_na_sum(const double *__restrict__ s, int64_t cells, double *__restrict__ scratch)
 {
+    gr::pdl_begin();
     const int64_t base = (int64_t)blockIdx.x * kNaCellsPerBlock + threadIdx.x;
     double a = 0.0;
 #pragma unroll
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kNaThreads)
 // totals of the block partials, fixed order, into scratch[dst], scratch[dst + 1]
 __global__ void k_na_total(double *__restrict__ scratch, int nblk, int dst)
 {
+    gr::pdl_begin();
     double a = 0.0, b = 0.0;
     for (int q = threadIdx.x; q < nblk; q += 32) {
         a += scratch[2 * q];
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(kNaThreads)
     k_na_resid(int lgn, double ih2, const double *__restrict__ u, const double *__restrict__ s,
                double *__restrict__ res, double *__restrict__ scratch, int64_t tot_s)
 {
+    gr::pdl_begin();
     const int m = (1 << lgn) - 1;
     const int64_t cells = (int64_t)1 << (3 * lgn);
     const double mean = scratch[tot_s] / (double)cells;

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kBlock)
                int O0, int O1, int O2, int nw, double *__restrict__ s0, double *__restrict__ sx,
                double *__restrict__ sy, double *__restrict__ sz, double *__restrict__ sig)
 {
+    pdl_begin();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
     // positions scaled by 1/L and N/L (multiplications: the FP64 divide is
@@ -310,6 +311,7 @@ template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_gather_base(PBase B, int o0, int o1, int o2, int w, double *__restrict__ win,
                                                         double *__restrict__ dold, float *__restrict__ d32)
 {
+    pdl_begin();
     const int W = w * w * w;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
         const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(kBlock) k_gather_patch(PPatch par, int o0, int
                                                          double *__restrict__ win, double *__restrict__ dold,
                                                          float *__restrict__ d32)
 {
+    pdl_begin();
     const int W = w * w * w;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W; t += gridDim.x * blockDim.x) {
         const int x = t / (w * w), r = t - x * w * w, y = r / w, z = r - y * w;
@@ -368,6 +371,7 @@ template <bool DF>
 __global__ void __launch_bounds__(kBlock)
     k_interp_in(int lgn, PPatch P, const double *__restrict__ d, const float *__restrict__ d32, int w)
 {
+    pdl_begin();
     const int N = 1 << (3 * lgn), m = (1 << lgn) + 2 * PG;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
         int i, j, k;
@@ -389,6 +393,7 @@ __global__ void __launch_bounds__(kBlock)
 template <bool DF>
 __global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__restrict__ win, int w, PPatch P)
 {
+    pdl_begin();
     const int m = n + 2 * PG;
     const int a = 2 * PG * m * m;        // i slabs
     const int b = n * 2 * PG * m;        // j slabs
@@ -424,6 +429,7 @@ __global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__
 template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
 {
+    pdl_begin();
     const int half = 1 << (3 * P.lgn - 1);
     const int lh = P.lgn - 1, mk = (1 << P.lgn) - 1;
     df lam2 = {0.0f, 0.0f};
@@ -464,6 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_pgs(PPatch P, int color)
 template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_presid(PPatch P, double *__restrict__ eps, double *__restrict__ partials)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * P.lgn);
     df lam2 = {0.0f, 0.0f};
     if (DF && P.lam) lam2 = split_double(*P.lam * P.h2);
@@ -489,6 +496,7 @@ template <bool DF>
 __global__ void __launch_bounds__(kBlock) k_prestrict(int n, PPatch P, const double *__restrict__ eps,
                                                       double *__restrict__ Ru, double *__restrict__ Re)
 {
+    pdl_begin();
     const int nc = n / 2, m = n + 2 * PG;
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
@@ -513,6 +521,7 @@ __global__ void __launch_bounds__(kBlock) k_prestrict(int n, PPatch P, const dou
 template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_inject_u_base(PBase B, int o0, int o1, int o2, int nc, const double *__restrict__ Ru)
 {
+    pdl_begin();
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
@@ -528,6 +537,7 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_base(PBase B, int o0, int o
                                                           const double *__restrict__ Re, const double *__restrict__ lam,
                                                           double *__restrict__ partials)
 {
+    pdl_begin();
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     const double l = (FMT == PB_DF && lam) ? *lam : 0.0;
     double sf = 0.0;
@@ -545,6 +555,7 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_base(PBase B, int o0, int o
 template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_sum_f_base(PBase B, int o0, int o1, int o2, int nc, double *__restrict__ partials)
 {
+    pdl_begin();
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     double sf = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
@@ -558,6 +569,7 @@ template <bool DF>
 __global__ void __launch_bounds__(kBlock) k_inject_u_patch(PPatch par, int o0, int o1, int o2, int nc,
                                                            const double *__restrict__ Ru)
 {
+    pdl_begin();
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
@@ -570,6 +582,7 @@ template <int KIND, bool DF>
 __global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, int o1, int o2, int nc,
                                                            const double *__restrict__ Re)
 {
+    pdl_begin();
     const int Nc = nc * nc * nc, lc = 31 - __clz(nc), mc = nc - 1;  // nc a power of two
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Nc; t += gridDim.x * blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
@@ -615,6 +628,7 @@ template <int PARENT, bool DF>
 __global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, PPatch ch, int o0, int o1, int o2, int n,
                                                    double hc, double *__restrict__ flux)
 {
+    pdl_begin();
     const int nc = n / 2, m = n + 2 * PG;
     const int nq = 6 * nc * nc;
     const double hf = 0.5 * hc;
@@ -664,6 +678,7 @@ __global__ void __launch_bounds__(kBlock) k_reflux(PBase B, PPatch par, PPatch c
 __global__ void __launch_bounds__(kBlock) k_lambda(double *__restrict__ sc, const double *__restrict__ flux, int nq,
                                                    double N, double Ncov, double *__restrict__ lam)
 {
+    pdl_begin();
     double s = 0.0;
     for (int q = threadIdx.x; q < nq; q += kBlock) s += flux[q];
     block_sum2(s, 0.0, sc + 6);  // sc[6] = sum of the shell corrections
@@ -677,6 +692,7 @@ __global__ void __launch_bounds__(kBlock) k_lambda(double *__restrict__ sc, cons
 
 __global__ void __launch_bounds__(kBlock) k_sub_scalar(int64_t cnt, double *__restrict__ a, const double *__restrict__ m)
 {
+    pdl_begin();
     const double v = *m;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         a[t] -= v;
@@ -686,6 +702,7 @@ __global__ void __launch_bounds__(kBlock) k_sub_scalar(int64_t cnt, double *__re
 // ghosted interior <- natural n^3 (+ add)
 __global__ void __launch_bounds__(kBlock) k_to_ghosted(int lgn, const double *__restrict__ in, double *__restrict__ out, double add)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const int m = (1 << lgn) + 2 * PG;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -699,6 +716,7 @@ __global__ void __launch_bounds__(kBlock) k_to_ghosted(int lgn, const double *__
 template <bool DF>
 __global__ void __launch_bounds__(kBlock) k_u_load(int lgn, const double *__restrict__ in, PPatch P, double add)
 {
+    pdl_begin();
     const int N = 1 << (3 * lgn);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
         int i, j, k;
@@ -714,6 +732,7 @@ __global__ void __launch_bounds__(kBlock) k_u_store(int lgn, PPatch P, double *_
                                                     double *__restrict__ keep, double add,
                                                     const double *__restrict__ usum, double scale)
 {
+    pdl_begin();
     const int N = 1 << (3 * lgn);
     const double sh = add - (usum ? usum[0] * scale : 0.0);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
@@ -732,6 +751,7 @@ __global__ void __launch_bounds__(kBlock) k_u_store(int lgn, PPatch P, double *_
 template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_pcoef_df(PPatch P)
 {
+    pdl_begin();
     const int N = 1 << (3 * P.lgn);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
         int i, j, k;
@@ -789,6 +809,7 @@ __device__ void aij_at(int m, const double *const V[3], const double *U, double 
 // six ghosted arrays A6[q * M + cell]
 __global__ void __launch_bounds__(kBlock) k_paij(int n, double nh, PSetFld G, double *__restrict__ A6)
 {
+    pdl_begin();
     const int m = n + 2 * PG, e = n + 2;
     const int64_t M = (int64_t)m * m * m;
     const double *V[3] = {G.g[0], G.g[1], G.g[2]};
@@ -818,6 +839,7 @@ __global__ void __launch_bounds__(kBlock)
            double Kdot, double *__restrict__ f, double *__restrict__ c0, double *__restrict__ c1,
            double *__restrict__ partials)
 {
+    pdl_begin();
     const int64_t N = (int64_t)1 << (3 * lgn);
     const int m = (1 << lgn) + 2 * PG;
     const int64_t M = (int64_t)m * m * m;

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(128)
              const float *__restrict__ bias, int cout, int lg, int mode, const __nv_bfloat16 *__restrict__ mask,
              __nv_bfloat16 *__restrict__ y)
 {
+    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int vb = (blockIdx.x * 4 + warp) * (MT * 16);
     const int cb = blockIdx.y * (NT * 8);
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(128)
     k_conv3d_wgrad(const __nv_bfloat16 *__restrict__ x, int cin, const __nv_bfloat16 *__restrict__ dy, int cout,
                    int lg, int chunk, float *__restrict__ dw)
 {
+    pdl_begin();
     __shared__ float red[4][16 * NT * 8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int tap = blockIdx.y;
@@ -175,6 +177,7 @@ constexpr int kBiasBlocks = 456;
 __global__ void __launch_bounds__(256)
     k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int c, int64_t nv, float *__restrict__ db)
 {
+    pdl_begin();
     extern __shared__ float sbuf[];
     for (int k = threadIdx.x; k < c; k += blockDim.x) sbuf[k] = 0.0f;
     __syncthreads();
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(256)
 // 2^3 average pooling, channels-last; fine extent 2^lgf
 __global__ void k_pool(const __nv_bfloat16 *__restrict__ x, int c, int cstride, int lgf, __nv_bfloat16 *__restrict__ y)
 {
+    pdl_begin();
     const int lgc = lgf - 1, mc = (1 << lgc) - 1;
     const int64_t total = ((int64_t)1 << (3 * lgc)) * c;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -211,6 +215,7 @@ __global__ void k_pool(const __nv_bfloat16 *__restrict__ x, int c, int cstride, 
 __global__ void k_pool_back(const __nv_bfloat16 *__restrict__ dy, int c, int lgf, __nv_bfloat16 *__restrict__ dx,
                             int cstride, int accumulate)
 {
+    pdl_begin();
     const int mf = (1 << lgf) - 1, lgc = lgf - 1;
     const int64_t total = ((int64_t)1 << (3 * lgf)) * c;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -230,6 +235,7 @@ __global__ void k_pool_back(const __nv_bfloat16 *__restrict__ dy, int c, int lgf
 __global__ void k_upsample(const __nv_bfloat16 *__restrict__ x, int c, int lgc, __nv_bfloat16 *__restrict__ y,
                            int cstride)
 {
+    pdl_begin();
     const int lgf = lgc + 1, mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
     const int64_t total = ((int64_t)1 << (3 * lgf)) * c;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -259,6 +265,7 @@ __global__ void k_upsample(const __nv_bfloat16 *__restrict__ x, int c, int lgc, 
 __global__ void k_upsample_back(const __nv_bfloat16 *__restrict__ dy, int c, int cstride, int lgc,
                                 __nv_bfloat16 *__restrict__ dx)
 {
+    pdl_begin();
     const int lgf = lgc + 1, mf = (1 << lgf) - 1, mc = (1 << lgc) - 1;
     const int64_t total = ((int64_t)1 << (3 * lgc)) * c;
     const float wt[4] = {0.25f, 0.75f, 0.75f, 0.25f};
@@ -281,6 +288,7 @@ __global__ void k_upsample_back(const __nv_bfloat16 *__restrict__ dy, int c, int
 __global__ void k_copy_slice(const __nv_bfloat16 *__restrict__ x, int c, int xs, int xoff, __nv_bfloat16 *__restrict__ y,
                              int ys, int yoff, int64_t nv, int accumulate)
 {
+    pdl_begin();
     const int64_t total = nv * c;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int ch = (int)(e % c);
@@ -295,6 +303,7 @@ __global__ void k_copy_slice(const __nv_bfloat16 *__restrict__ x, int c, int xs,
 // g *= (a > 0) elementwise (ReLU backward where the gradient was summed first)
 __global__ void k_relu_mask(__nv_bfloat16 *__restrict__ gbuf, const __nv_bfloat16 *__restrict__ a, int64_t total)
 {
+    pdl_begin();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
         if (!(__bfloat162float(a[e]) > 0.0f)) gbuf[e] = __float2bfloat16(0.0f);
 }
@@ -306,6 +315,7 @@ __global__ void k_net_input(const double *__restrict__ s0, const double *__restr
                             const float *__restrict__ in_mean, const float *__restrict__ in_std,
                             __nv_bfloat16 *__restrict__ x)
 {
+    pdl_begin();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
         float f[4];
         f[0] = logf(kNetLogEps + (float)s0[v] * inv_rho);
@@ -322,6 +332,7 @@ __global__ void k_net_input(const double *__restrict__ s0, const double *__restr
 __global__ void k_head(const __nv_bfloat16 *__restrict__ a, const float *__restrict__ W, const float *__restrict__ b,
                        int64_t nv, float *__restrict__ out)
 {
+    pdl_begin();
     __shared__ float sw[kNetOut * 16 + kNetOut];
     for (int k = threadIdx.x; k < kNetOut * 16; k += blockDim.x) sw[k] = W[k];
     for (int k = threadIdx.x; k < kNetOut; k += blockDim.x) sw[kNetOut * 16 + k] = b[k];
@@ -344,6 +355,7 @@ __global__ void k_head_back(const __nv_bfloat16 *__restrict__ a, const float *__
                             __nv_bfloat16 *__restrict__ da, float *__restrict__ dW, float *__restrict__ db,
                             float *__restrict__ loss)
 {
+    pdl_begin();
     __shared__ float sw[kNetOut * 16], sdw[kNetOut * 16], sdb[kNetOut], sl[1];
     for (int k = threadIdx.x; k < kNetOut * 16; k += blockDim.x) {
         sw[k] = W[k];
@@ -389,6 +401,7 @@ __global__ void k_head_back(const __nv_bfloat16 *__restrict__ a, const float *__
 __global__ void k_net_target(FieldPtrs fields, int64_t nv, const float *__restrict__ mean,
                              const float *__restrict__ stdv, float *__restrict__ tgt)
 {
+    pdl_begin();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
         for (int o = 0; o < kNetOut; o++) {
             double val = fields.p[o][v];
@@ -401,6 +414,7 @@ __global__ void k_net_target(FieldPtrs fields, int64_t nv, const float *__restri
 __global__ void k_net_output(const float *__restrict__ out, int64_t nv, const float *__restrict__ mean,
                              const float *__restrict__ stdv, FieldPtrs fields)
 {
+    pdl_begin();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
         for (int o = 0; o < kNetOut; o++) {
             double val = (double)out[v * kNetOut + o] * stdv[o] + mean[o];
@@ -414,6 +428,7 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
                        const float *__restrict__ gr, int64_t cnt, float lr, float b1, float b2, float eps, float bc1,
                        float bc2)
 {
+    pdl_begin();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
         const float g = gr[e];
         const float mm = b1 * m[e] + (1.0f - b1) * g;
@@ -429,6 +444,7 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
 __global__ void k_conv_weights_bf16(const float *__restrict__ w, int cout, int cin, __nv_bfloat16 *__restrict__ wb,
                                     __nv_bfloat16 *__restrict__ wt)
 {
+    pdl_begin();
     const int64_t total = (int64_t)27 * cout * cin;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int ci = (int)(e % cin);
