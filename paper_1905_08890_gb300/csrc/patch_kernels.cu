@@ -30,9 +30,10 @@ namespace {
 
 constexpr int PG = 2;  // ghost layers
 
-__device__ __forceinline__ int64_t gxi(int m, int i, int j, int k)
+// 32-bit: a patch array has at most (512 + 4)^3 < 2^31 cells
+__device__ __forceinline__ int gxi(int m, int i, int j, int k)
 {
-    return ((int64_t)(i + PG) * m + (j + PG)) * m + (k + PG);
+    return ((i + PG) * m + (j + PG)) * m + (k + PG);
 }
 
 // natural and split-layout indices on the periodic base (n = 2^lgn; the
@@ -148,10 +149,9 @@ __device__ __forceinline__ void pu_set(const PPatch &P, int64_t c, double v)
 template <bool DF>
 __device__ __forceinline__ double p_nb(const PPatch &P, int i, int j, int k)
 {
-    const int m = P.m;
-    return pu_get<DF>(P, gxi(m, i + 1, j, k)) + pu_get<DF>(P, gxi(m, i - 1, j, k)) +
-           pu_get<DF>(P, gxi(m, i, j + 1, k)) + pu_get<DF>(P, gxi(m, i, j - 1, k)) +
-           pu_get<DF>(P, gxi(m, i, j, k + 1)) + pu_get<DF>(P, gxi(m, i, j, k - 1));
+    const int m = P.m, mm = m * m, c = gxi(m, i, j, k);
+    return pu_get<DF>(P, c + mm) + pu_get<DF>(P, c - mm) + pu_get<DF>(P, c + m) + pu_get<DF>(P, c - m) +
+           pu_get<DF>(P, c + 1) + pu_get<DF>(P, c - 1);
 }
 
 // L(u) at a patch cell in FP64 (the oracle's operator; FP64 coefficients c0, c1)
@@ -180,10 +180,9 @@ __device__ __forceinline__ bool p_covered(const PPatch &P, int i, int j, int k)
 template <int KIND>
 __device__ __forceinline__ df p_cell_df(const PPatch &P, df lam2, int i, int j, int k, float *inv)
 {
-    const int m = P.m;
-    const int64_t c = gxi(m, i, j, k);
-    const int64_t nb[6] = {gxi(m, i + 1, j, k), gxi(m, i - 1, j, k), gxi(m, i, j + 1, k),
-                           gxi(m, i, j - 1, k), gxi(m, i, j, k + 1), gxi(m, i, j, k - 1)};
+    const int m = P.m, mm = m * m;
+    const int c = gxi(m, i, j, k);
+    const int nb[6] = {c + mm, c - mm, c + m, c - m, c + 1, c - 1};
     float nh[6], nl[6];
 #pragma unroll
     for (int q = 0; q < 6; q++) {
