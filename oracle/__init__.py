@@ -104,6 +104,8 @@ def lib():
             L.orc_patch_ghosted.restype = None
             L.orc_patch_residual_at.argtypes = [I, I, D, P, P, D, D, D, I64, P, P, P]
             L.orc_patch_residual_at.restype = None
+            L.orc_patch_eq_setup.argtypes = [I, I, D, P, P, D, D, D, P, P, P, P]
+            L.orc_patch_eq_setup.restype = I
             _lib = L
     return _lib
 
@@ -437,3 +439,20 @@ def patch_residual_at(eq: int, n: int, nh: float, src: dict, G: dict, smean: flo
     lib().orc_patch_residual_at(eq, n, nh, sp, gp, smean, rho_hat, S_hat, idx.size, idx.ctypes.data,
                                 eps.ctypes.data, f.ctypes.data)
     return eps, f
+
+
+def patch_eq_setup(eq: int, n: int, nh: float, src: dict, G: dict, smean: float, rho_hat: float, S_hat: float = 0.0):
+    """(kind, f, c0, c1, ref) of equation eq on a patch of n cells at 1/h = nh
+    from its interior sources and ghosted fields G (by name); f, c0, c1 are
+    ghosted (n + 4)^3 arrays with the interior written."""
+    order = ("Vx", "Vy", "Vz", "U", "psi", "apsi", "Bx", "By", "Bz", "b")
+    srcs = [_f64(src[k]) for k in SOURCES]
+    gs = [_f64(G[k]) for k in order]
+    sp = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in srcs])
+    gp = (ctypes.c_void_p * 10)(*[a.ctypes.data for a in gs])
+    m = n + 4
+    f, c0, c1 = np.zeros((m, m, m)), np.zeros((m, m, m)), np.zeros((m, m, m))
+    ref = ctypes.c_double(0)
+    kind = lib().orc_patch_eq_setup(eq, n, nh, sp, gp, smean, rho_hat, S_hat, _p(f), _p(c0), _p(c1),
+                                    ctypes.byref(ref))
+    return kind, f, c0, c1, ref.value

@@ -1773,3 +1773,14 @@ void orc_patch_residual_at(int e, int n, double nh, const double *const *src, co
     free(c0);
     free(c1);
 }
+
+/* The set-up of one equation on a patch (patch_eq_setup), exported for the
+   test that holds it against orc_eq_setup on a full periodic grid: src are
+   the patch's 5 interior arrays, G its ten ghosted fields in setup order;
+   f, c0, c1 receive ghosted (n + 2 PG)^3 arrays (interior written).
+   Returns the kind. */
+int orc_patch_eq_setup(int e, int n, double nh, const double *const *src, const double *const *G, double smean,
+                       double rho_hat, double S_hat, double *f, double *c0, double *c1, double *ref)
+{
+    return patch_eq_setup(e, n, nh, src, G, smean, rho_hat, S_hat, f, c0, c1, ref);
+}

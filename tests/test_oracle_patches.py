@@ -284,3 +284,40 @@ def test_pointwise_patch_residual_of_a_converged_composite_solve(orc):
             eps = eps - eps.mean()
         r = np.sqrt(np.mean(eps ** 2)) / max(np.sqrt(np.mean(f ** 2)), 1e-300)
         assert r <= 30 * tol, (k, r)
+
+
+def test_patch_setups_equal_the_periodic_setups_on_a_window(orc):
+    """With ghosts taken from the same fine periodic grid, the set-up of every
+    equation on a patch (right-hand side, coefficients) equals the periodic
+    set-up of that grid on the window's cells: the patch formulas are the base
+    formulas (Poisson-type divergence sources differ only by their grid mean,
+    which vanishes up to rounding).  Random fields of order one, so that AA
+    and every term of the lapse coefficient matter."""
+    N, n, O = 32, 8, (27, 5, 14)  # the window wraps along x
+    rng = np.random.default_rng(21)
+    X, Y, Z = cell_grid([0, 0, 0], N, N)
+    fld = {}
+    for q, k in enumerate(orc.FIELDS):
+        fld[k] = sum(0.3 * rng.standard_normal() * np.sin(2 * np.pi * (a * X + b * Y + c * Z) + rng.random() * 6)
+                     for a, b, c in [(1, 0, 0), (0, 1, 1), (1, 1, 0), (2, 0, 1)])
+    fld["psi"] = 1.0 + 0.1 * fld["psi"]
+    fld["apsi"] = 1.0 + 0.1 * fld["apsi"]
+    src = {k: RHO * (1.0 + 0.5 * rng.random((N, N, N))) for k in orc.SOURCES}
+    for k in ("sx", "sy", "sz"):
+        src[k] = RHO * 0.01 * rng.standard_normal((N, N, N))
+    idx = [(np.arange(-2, n + 2) + O[d]) % N for d in range(3)]
+    inner = [(np.arange(n) + O[d]) % N for d in range(3)]
+    G = {k: np.ascontiguousarray(fld[k][np.ix_(*idx)]) for k in orc.FIELDS}
+    srcw = {k: np.ascontiguousarray(src[k][np.ix_(*inner)]) for k in orc.SOURCES}
+    sl = (slice(2, n + 2),) * 3
+    for e in range(10):
+        kind, f, c0, c1, ref = orc.eq_setup(e, src, fld, RHO)
+        smean = float(src[("sx", "sy", "sz")[e]].mean()) if e <= 2 else 0.0
+        pk, pf, pc0, pc1, pref = orc.patch_eq_setup(e, n, float(N), srcw, G, smean, RHO)
+        assert pk == kind, e
+        scale = max(np.abs(f).max(), 1e-300)
+        assert np.abs(pf[sl] - f[np.ix_(*inner)]).max() <= 1e-12 * scale, (e, "f")
+        if c0 is not None:
+            assert np.abs(pc0[sl] - c0[np.ix_(*inner)]).max() <= 1e-12 * np.abs(c0).max(), (e, "c0")
+        if c1 is not None:
+            assert np.abs(pc1[sl] - c1[np.ix_(*inner)]).max() <= 1e-12 * np.abs(c1).max(), (e, "c1")
