@@ -193,3 +193,20 @@ def test_three_patches_of_different_sizes(prec, tol, bar):
         assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k)
         for lvl in range(3):
             assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= bar, ("patch", lvl + 1, k, rel_linf(gp[lvl][k], ofldp[lvl][k]))
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8)])
+def test_composite_with_relativistic_velocities(prec, tol, bar):
+    """rms |u| = 0.3: the momentum sources, A_ij (AA reaches 1e-4 of 2 pi s0 in
+    the lapse coefficient) and the shift are large enough that every term of
+    the patch set-ups moves the solution far above the parity bar."""
+    n0 = 32
+    chain = centred_chain(n0, 16)
+    p = synth.zeldovich(n0, 17, 1.0, 0.3, True)
+    src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
+    rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, prec, tol)
+    assert rep["status_code"] == gr.GR_OK, rep
+    for k in oracle.FIELDS:
+        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k)
+        for lvl in range(2):
+            assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= bar, ("patch", lvl + 1, k, rel_linf(gp[lvl][k], ofldp[lvl][k]))
