@@ -5,7 +5,7 @@
 // the periodic Poisson-type equations, and the per-equation set-up).
 //
 // A patch of n^3 cells is stored natural-layout with two ghost layers,
-// (n + 4)^3 doubles, index ((i + 2) m + (j + 2)) m + (k + 2), m = n + 4,
+// (n + 4)^3 values per array, index ((i + 2) m + (j + 2)) m + (k + 2), m = n + 4,
 // -2 <= i, j, k < n + 2.  It refines the parent block o .. o + n/2 - 1 (per
 // axis) by 2; the parent window is the (n/2 + 4)^3 block of parent cells
 // o - 2 .. o + n/2 + 1, which every interpolation and correction of the
@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(kBlock) k_inject_f_patch(PPatch par, int o0, i
 // mean of the four fine fluxes (u_inner - u_ghost)/h_f, as the change
 // corr = -(T_f - T_c)/h_c of the parent's right-hand side there; flux[q]
 // keeps the correction in force.  PARENT: 0 a patch (ghosted arrays in par),
-// else the base in format PARENT.
+// else the base in format PARENT; DF: the patches' unknowns (and a patch
+// parent's right-hand side) are double-float pairs.
 __device__ __forceinline__ void shell_cell(int q, int nc, int n, int in[3], int out[3], int fi[4][3], int fg[4][3])
 {
     const int per = nc * nc;
