@@ -463,6 +463,74 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__
     }
 }
 
+// black-children prolongation over four coarse cells K = 4P .. 4P + 3 of a
+// coarse row per thread: fine k = 8P .. 8P + 7, whose black cells in each of
+// the four fine rows are one float4 of the black half-array; the coarse row's
+// values K = 4P - 1 .. 4P + 4 are two float2 and two scalar loads per
+// neighbouring coarse row
+__global__ void __launch_bounds__(kBlock) k_prolong_black4(int lgf, float *__restrict__ u, const float *__restrict__ uc,
+                                                           int rev)
+{
+    pdl_begin();
+    const int lgc = lgf - 1, mc = (1 << lgc) - 1, hc = lgc - 1, mq = (1 << hc) - 1;
+    const int halfc = 1 << (3 * lgc - 1), halff = 1 << (3 * lgf - 1);
+    const int lp = lgc - 2, mp = (1 << lp) - 1;  // P: coarse row / 4
+    const int cnt = 1 << (3 * lgc - 2);
+    const float w0 = 0.25f, w1 = 0.75f;
+    for (int tt = blockIdx.x * blockDim.x + threadIdx.x; tt < cnt; tt += gridDim.x * blockDim.x) {
+        const int t = rev ? cnt - 1 - tt : tt;
+        const int P = t & mp, J = (t >> lp) & mc, I = t >> (lp + lgc);
+        float z[3][3][8];
+#pragma unroll
+        for (int x = 0; x < 3; x++)
+#pragma unroll
+            for (int y = 0; y < 3; y++) {
+                const int Ii = (I + x - 1) & mc, Jj = (J + y - 1) & mc;
+                const int base = ((Ii << lgc) + Jj) << hc;
+                const int ce = ((Ii + Jj) & 1) ? halfc : 0;  // colour array of the even coarse K
+                const int co = halfc - ce;
+                const float2 ev = *reinterpret_cast<const float2 *>(uc + ce + base + 2 * P);  // K = 4P, 4P + 2
+                const float2 od = *reinterpret_cast<const float2 *>(uc + co + base + 2 * P);  // K = 4P + 1, 4P + 3
+                const float om = uc[co + base + ((2 * P - 1) & mq)];                         // K = 4P - 1
+                const float ep = uc[ce + base + ((2 * P + 2) & mq)];                         // K = 4P + 4
+                const float c[6] = {om, ev.x, od.x, ev.y, od.y, ep};
+#pragma unroll
+                for (int m = 0; m < 8; m++) {
+                    const int t0 = (m >> 1) + 1, t1 = (m & 1) ? t0 + 1 : t0 - 1;
+                    z[x][y][m] = w1 * c[t0] + w0 * c[t1];
+                }
+            }
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            float yv[3][8];
+#pragma unroll
+            for (int x = 0; x < 3; x++)
+#pragma unroll
+                for (int m = 0; m < 8; m++)
+                    yv[x][m] = b ? (w1 * z[x][1][m] + w0 * z[x][2][m]) : (w0 * z[x][0][m] + w1 * z[x][1][m]);
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const int kp = (a + b + 1) & 1;  // parity of the black fine k in this row
+                float val[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int m = kp + 2 * q;
+                    val[q] = a ? (w1 * yv[1][m] + w0 * yv[2][m]) : (w0 * yv[0][m] + w1 * yv[1][m]);
+                }
+                const int row = (((2 * I + a) << lgf) + 2 * J + b) << (lgf - 1);
+                float4 *blk = reinterpret_cast<float4 *>(u + halff + row + 4 * P);
+                float4 k4 = *blk;
+                k4.x += val[0];
+                k4.y += val[1];
+                k4.z += val[2];
+                k4.w += val[3];
+                *blk = k4;
+            }
+        }
+    }
+}
+
+
 // ---------------------------------------------------------------- 2^3 level
 template <typename T, int KIND>
 __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
@@ -759,8 +827,12 @@ void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st)
 
 void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st, int rev)
 {
-    GR_LAUNCH((k_prolong_add<float, 1>), wave_grid(k_prolong_add<float, 1>, (int64_t)nf * nf * nf / 16), kBlock, st,
-              log2i(nf), u, uc, rev);
+    if (nf >= 16)
+        GR_LAUNCH(k_prolong_black4, wave_grid(k_prolong_black4, (int64_t)nf * nf * nf / 32), kBlock, st, log2i(nf), u,
+                  uc, rev);
+    else
+        GR_LAUNCH((k_prolong_add<float, 1>), wave_grid(k_prolong_add<float, 1>, (int64_t)nf * nf * nf / 16), kBlock,
+                  st, log2i(nf), u, uc, rev);
 }
 
 template <typename T>
