@@ -217,9 +217,8 @@ __device__ __forceinline__ void p_cell(int lgn, int64_t t, int &i, int &j, int &
 
 // trilinear interpolation of a w^3 window at patch cell (i, j, k): fine
 // cell i sits in parent cell floor(i/2) (window index floor(i/2) + 2) and
-// leans 1/4 towards the neighbour on the side of its half; with `old`, of
-// the difference win - old
-__device__ __forceinline__ double interp(const double *win, const double *old, int w, int i, int j, int k)
+// leans 1/4 towards the neighbour on the side of its half
+__device__ __forceinline__ double interp(const double *win, int w, int i, int j, int k)
 {
     int I[2], J[2], K[2];
     I[0] = (i >> 1) + 2;
@@ -236,9 +235,7 @@ __device__ __forceinline__ double interp(const double *win, const double *old, i
         for (int b = 0; b < 2; b++)
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const int64_t q = ((int64_t)I[a] * w + J[b]) * w + K[c];
-                const double v = old ? win[q] - old[q] : win[q];
-                s += wt[a] * wt[b] * wt[c] * v;
+                s += wt[a] * wt[b] * wt[c] * win[(I[a] * w + J[b]) * w + K[c]];
             }
     return s;
 }
@@ -381,7 +378,7 @@ __global__ void __launch_bounds__(kBlock)
             P.uh[c] = s.hi;
             P.ul[c] = s.lo;
         } else {
-            P.u[c] += interp(d, nullptr, w, i, j, k);
+            P.u[c] += interp(d, w, i, j, k);
         }
     }
 }
@@ -415,7 +412,7 @@ __global__ void __launch_bounds__(kBlock) k_interp_ghost(int n, const double *__
             j = r - i * n;
             k = s < PG ? s - PG : n + s - PG;
         }
-        pu_set<DF>(P, gxi(m, i, j, k), interp(win, nullptr, w, i, j, k));
+        pu_set<DF>(P, gxi(m, i, j, k), interp(win, w, i, j, k));
     }
 }
 
