@@ -32,6 +32,13 @@
  *    multigrid scratch.
  *  - All work is queued on the context's stream.  Calls that return host
  *    scalars (norms, reports) synchronise that stream before returning.
+ *    Kernels are launched with programmatic dependent launch (a kernel may
+ *    be scheduled while its predecessor on the stream drains, and waits for
+ *    it before touching memory), so the stream's order of effects is that of
+ *    plain launches; a stream that refuses the attribute gets plain launches.
+ *  - Static nested refinement patches (gr_patch, gr_deposit_patches,
+ *    gr_opts.patch) extend the periodic base with a chain of finer cubic
+ *    regions solved as one composite problem.
  *  - No call aborts or throws.  Errors are returned as gr_status; the
  *    thread-local gr_last_error() describes the last one.  Arguments are
  *    validated before any GPU work is queued.
