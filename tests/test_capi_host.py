@@ -86,3 +86,37 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[t]) == ctypes.sizeof(cls), t
         for f in fields:
             assert int(out[f"{t}.{f}"]) == getattr(cls, f).offset, (t, f)
+
+
+def test_centred_chain_geometry():
+    """gr.centred_chain: patch 1's block is centred on the cell (wrapping on
+    the periodic base), each further patch sits in the middle of its parent,
+    and every patch lies where the C chain check accepts it."""
+    n0 = 512
+    chain = gr.centred_chain(n0, (508, 3, 256), (128, 128))
+    assert chain[0] == {"n": 128, "origin": [476, (3 - 32) % 512, 224]}
+    assert chain[1] == {"n": 128, "origin": [32, 32, 32]}
+    # the cell sits in the middle of both patches: base cell c covers patch-1 cells 2(c - o1) .. +1
+    for d, c in enumerate((508, 3, 256)):
+        i1 = 2 * ((c - chain[0]["origin"][d]) % n0)
+        assert i1 == 64
+        i2 = 2 * (i1 - chain[1]["origin"][d])
+        assert i2 == 64
+    for q, npar in zip(chain, (n0, 128)):
+        for o in q["origin"]:
+            if npar == n0:
+                assert 0 <= o < n0 and q["n"] // 2 + 4 <= n0
+            else:
+                assert o >= 2 and o + q["n"] // 2 + 2 <= npar
+
+
+def test_patch_options_marshalling():
+    """make_opts(patches=...) fills npatch and a gr_patch array whose entries
+    carry n, origin and NULL arrays where none are given."""
+    chain = [{"n": 16, "origin": [1, 2, 3]}, {"n": 8, "origin": [4, 5, 6]}]
+    o = gr.make_opts(patches=chain)
+    assert o.npatch == 2
+    assert o.patch[0].n == 16 and list(o.patch[0].origin) == [1, 2, 3]
+    assert o.patch[1].n == 8 and list(o.patch[1].origin) == [4, 5, 6]
+    assert not o.patch[0].src.s0 and not o.patch[1].fld.psi
+    assert gr.make_opts().npatch == 0 and not gr.make_opts().patch
