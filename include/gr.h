@@ -144,7 +144,8 @@ typedef struct {
                          pinned for overlap, or any memory cudaMemcpyAsync accepts), caller-owned.  Each field
                          is copied there as soon as its equation is solved, on a copy stream of the context,
                          so the copies overlap the remaining equations; the call's stream waits for the last
-                         copy before the call returns, so a synchronisation of that stream covers them. */
+                         copy before the call returns, so a synchronisation of that stream covers them.  The
+                         base fields only: patch fields stay in the patches' device arrays. */
     int npatch;       /* gr_solve_constraints only: 0 (default) solves the periodic base alone; 1..GR_MAX_PATCHES
                          solves the composite problem on the base and the chain patch[0..npatch-1] (composite-grid
                          FAS: a patch's ghost layers take the trilinear interpolation of its parent, the parent
