@@ -326,7 +326,9 @@ gr_status gr_net_activation(gr_net *net, int tensor, float *host, size_t count);
    they cannot create a gr_ctx.
    n: power of two, 4 <= n <= 256 (larger n returns GR_ERR_ARG: the fixed
    scratch covers at most 256^3 cells).  L > 0: box side.  V, s: device
-   arrays of n^3 doubles, natural layout (V_i and s_i).  res_field (device,
+   arrays of n^3 doubles, natural layout (V_i and s_i), on the current
+   device.  The C entry point cannot see buffer sizes: the caller owns that
+   every array holds n^3 doubles (the Python binding checks it).  res_field (device,
    n^3 doubles, may be NULL) receives eps = lap_h V - 8 pi (s - <s>);
    *rel_norm (host, may be NULL) receives RMS(eps) / RMS(8 pi (s - <s>))
    (reference 1 below 1e-300).  cuda_stream: cudaStream_t (NULL = legacy
@@ -335,7 +337,9 @@ gr_status gr_net_activation(gr_net *net, int tensor, float *host, size_t count);
    compiled into the library, present on every device that loads it until
    the process exits.  The first call on a device looks up that array's
    device address (cudaGetSymbolAddress), so make a first call on each device
-   before capturing any stream.  All calls share the array: every slot a
+   before capturing any stream.  The address is kept for the life of the
+   process: after cudaDeviceReset on a device this entry point must not be
+   called on that device again.  All calls share the array: every slot a
    call reads is written earlier in the same call, so stale contents are
    harmless, but calls that overlap on the GPU (different streams or host
    threads at the same time) race on it and must be serialised by the caller. */

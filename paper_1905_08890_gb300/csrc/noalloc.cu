@@ -72,22 +72,36 @@ __global__ void __launch_bounds__(kNaThreads)
     na_block_sum2(a, 0.0, scratch);
 }
 
-// totals of the block partials, fixed order, into scratch[dst], scratch[dst + 1]
-__global__ void k_na_total(double *__restrict__ scratch, int nblk, int dst)
+// totals of the block partials into scratch[dst], scratch[dst + 1]: each of
+// kNaThreads threads sums a strided subset in index order, then the block
+// reduces those in a fixed shuffle/shared-memory order (deterministic)
+__global__ void __launch_bounds__(kNaThreads) k_na_total(double *__restrict__ scratch, int nblk, int dst)
 {
     gr::pdl_begin();
     double a = 0.0, b = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += 32) {
+    for (int q = threadIdx.x; q < nblk; q += kNaThreads) {
         a += scratch[2 * q];
         b += scratch[2 * q + 1];
     }
+    __shared__ double sa[kNaThreads / 32], sb[kNaThreads / 32];
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         b += __shfl_down_sync(0xffffffffu, b, o);
     }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        scratch[dst] = a;
-        scratch[dst + 1] = b;
+        double ta = 0.0, tb = 0.0;
+        for (int q = 0; q < kNaThreads / 32; q++) {
+            ta += sa[q];
+            tb += sb[q];
+        }
+        scratch[dst] = ta;
+        scratch[dst + 1] = tb;
     }
 }
 
@@ -130,7 +144,8 @@ gr_status na_fail(gr_status s, const char *fmt, ...)
     return s;
 }
 
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array on the current device (looked up once
+// per device; a cudaDeviceReset invalidates it, see the header)
 gr_status na_scratch(double **out)
 {
     int dev = -1;
@@ -171,9 +186,9 @@ extern "C" gr_status gr_momentum_residual_noalloc(int n, double L, const double 
     const int64_t tot_s = 2 * (int64_t)kNaMaxBlocks, tot_r = tot_s + 2;
     const double h = L / n, ih2 = 1.0 / (h * h);
     GR_LAUNCH(k_na_sum, blocks, kNaThreads, stream, s, cells, scr);
-    GR_LAUNCH(k_na_total, 1, 32, stream, scr, blocks, (int)tot_s);
+    GR_LAUNCH(k_na_total, 1, kNaThreads, stream, scr, blocks, (int)tot_s);
     GR_LAUNCH(k_na_resid, blocks, kNaThreads, stream, lgn, ih2, V, s, res_field, scr, tot_s);
-    GR_LAUNCH(k_na_total, 1, 32, stream, scr, blocks, (int)tot_r);
+    GR_LAUNCH(k_na_total, 1, kNaThreads, stream, scr, blocks, (int)tot_r);
     double tot[2] = {0.0, 0.0};
     cudaError_t e = cudaMemcpyAsync(tot, scr + tot_r, sizeof(tot), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

@@ -303,9 +303,25 @@ def gr_kernel_launches() -> int:
 
 def gr_momentum_residual_noalloc(n: int, L: float, V, s, res_field=None, stream=None) -> float:
     """Allocation-free residual of lap V_i = 8 pi (s_i - <s_i>); returns the
-    relative norm (see include/gr.h).  V, s, res_field: float64 CUDA tensors."""
+    relative norm (see include/gr.h).  V, s, res_field: contiguous float64
+    CUDA tensors of n^3 elements on the current device; stream: a
+    torch.cuda.Stream or raw cudaStream_t (default: torch's current stream)."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    for name, t in (("V", V), ("s", s), ("res_field", res_field)):
+        if t is None and name == "res_field":
+            continue
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError(f"gr_momentum_residual_noalloc: {name} must be a contiguous float64 tensor")
+        if t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError(f"gr_momentum_residual_noalloc: {name} must be on cuda:{dev}, not {t.device}")
+        if t.numel() != n ** 3:
+            raise ValueError(f"gr_momentum_residual_noalloc: {name} has {t.numel()} elements, n^3 = {n ** 3}")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     r = ctypes.c_double(0)
-    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
     _check(lib().gr_momentum_residual_noalloc(n, L, _ptr(V), _ptr(s), _ptr(res_field), ctypes.byref(r), st),
            "gr_momentum_residual_noalloc")
     return r.value

@@ -30,9 +30,10 @@ def _case(n, seed):
 
 
 def test_noalloc_residual_matches_gr_residual_on_two_calls_in_a_row():
-    # the first call uses the larger grid, so the second runs on a scratch
-    # array still holding the first call's partial sums
-    for n, seed, comp in ((64, 11, 0), (32, 12, 2)):
+    # largest grid first, so each later call runs on a scratch array still
+    # holding the previous call's partial sums; 256 fills every partial slot
+    # (the totals sit right after the last one), 4 is a single part-filled block
+    for n, seed, comp in ((256, 10, 1), (64, 11, 0), (32, 12, 2), (4, 13, 0)):
         p, ctx, src, fld = _case(n, seed)
         vname, sname = ("Vx", "Vy", "Vz")[comp], ("sx", "sy", "sz")[comp]
         want = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
@@ -44,10 +45,27 @@ def test_noalloc_residual_matches_gr_residual_on_two_calls_in_a_row():
         assert rel_got == pytest.approx(rel_want, rel=1e-10), n
         assert 1e-6 < rel_got < 10
         ctx.close()
+        del ctx, src, fld, want, got
+        torch.cuda.empty_cache()
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
+    # straight through the C entry point: it refuses n = 512 before touching the buffers
+    import ctypes
+
     x = torch.zeros((4, 4, 4), dtype=torch.float64, device="cuda")
-    with pytest.raises(gr.GRError) as ei:
-        gr.gr_momentum_residual_noalloc(512, 1.0, x, x)
-    assert ei.value.status == gr.GR_ERR_ARG and "256" in str(ei.value)
+    r = ctypes.c_double(-1.0)
+    st = gr.lib().gr_momentum_residual_noalloc(512, 1.0, x.data_ptr(), x.data_ptr(), None, ctypes.byref(r),
+                                                torch.cuda.current_stream().cuda_stream)
+    assert st == gr.GR_ERR_ARG and "256" in gr.gr_last_error()
+    assert r.value == -1.0
+
+
+def test_noalloc_binding_checks_sizes_and_device():
+    x = torch.zeros((4, 4, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        gr.gr_momentum_residual_noalloc(8, 1.0, x, x)  # 64 elements, 8^3 wanted
+    with pytest.raises(ValueError):
+        gr.gr_momentum_residual_noalloc(4, 1.0, x, x.cpu())
+    with pytest.raises(TypeError):
+        gr.gr_momentum_residual_noalloc(4, 1.0, x.float(), x)
