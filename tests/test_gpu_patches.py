@@ -29,6 +29,23 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+def dev_linf(k, a, b):
+    """rel_linf of the deviations psi - 1 and alpha psi - 1 (other fields as they are)."""
+    d = 1.0 if k in ("psi", "apsi") else 0.0
+    return rel_linf(a - d, b - d)
+
+
+def check_levels(g0, gp, ofld0, ofldp, bar, dev_bar=None):
+    """Every field on the base and every patch within bar (relative L-inf);
+    with dev_bar, the deviations too."""
+    for k in oracle.FIELDS:
+        pairs = [("base", g0[k], ofld0[k])] + [(f"patch{i + 1}", gp[i][k], ofldp[i][k]) for i in range(len(gp))]
+        for lvl, a, b in pairs:
+            assert rel_linf(a, b) <= bar, (lvl, k, rel_linf(a, b))
+            if dev_bar is not None:
+                assert dev_linf(k, a, b) <= dev_bar, (lvl, k, "deviation", dev_linf(k, a, b))
+
+
 def centred_chain(n0, n, npatch=2):
     out, npar = [], n0
     for _ in range(npatch):
@@ -84,8 +101,15 @@ def test_patch_deposit_matches_the_oracle():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8), ("mixed", 1e-10, 1e-8)])
-def test_composite_solve_matches_the_oracle(prec, tol, bar):
+# FP64 at the oracle's own tolerance (1e-12): every field and deviation
+# within 1e-11 on every level (measured: 1.1e-14 whole, 1.9e-13 deviations).
+# Mixed modes to 1e-10: fields within 1e-8; to 1e-11 also the deviations
+# (measured 4.8e-9: the relative residual of psi and alpha psi is measured
+# against references some 25 times their deviations' forcing).
+@pytest.mark.parametrize("prec,tol,bar,dev_bar", [("fp64", 1e-12, 1e-11, 1e-11), ("mixed_df", 1e-10, 1e-8, None),
+                                                  ("mixed", 1e-10, 1e-8, None), ("mixed_df", 1e-11, 1e-8, 1e-8),
+                                                  ("mixed", 1e-11, 1e-8, 1e-8)])
+def test_composite_solve_matches_the_oracle(prec, tol, bar, dev_bar):
     n0 = 32
     chain = centred_chain(n0, 16)
     p = _problem(n0)
@@ -95,11 +119,7 @@ def test_composite_solve_matches_the_oracle(prec, tol, bar):
     for e in range(10):
         assert max(rep["res_level"][e][:3]) <= tol, (e, rep["res_level"][e])
         assert rep["res"][e] == max(rep["res_level"][e][:3])
-    for k in oracle.FIELDS:
-        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k, rel_linf(g0[k], ofld0[k]))
-        for lvl in range(2):
-            err = rel_linf(gp[lvl][k], ofldp[lvl][k])
-            assert err <= bar, ("patch", lvl + 1, k, err)
+    check_levels(g0, gp, ofld0, ofldp, bar, dev_bar)
 
 
 def test_composite_with_a_wrapping_first_patch_and_64_cubed_base():
@@ -124,9 +144,7 @@ def test_single_patch_fp64():
     src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
     rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, "fp64", 1e-12)
     assert rep["status_code"] == gr.GR_OK, rep
-    for k in oracle.FIELDS:
-        assert rel_linf(g0[k], ofld0[k]) <= 1e-9, ("base", k)
-        assert rel_linf(gp[0][k], ofldp[0][k]) <= 1e-9, ("patch", k)
+    check_levels(g0, gp, ofld0, ofldp, 1e-11, 1e-11)
 
 
 def test_invalid_chain_is_refused():
@@ -177,7 +195,7 @@ def test_context_reuse_across_chains_and_without_patches():
     ctx2.close()
 
 
-@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8)])
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-11), ("mixed_df", 1e-10, 1e-8)])
 def test_three_patches_of_different_sizes(prec, tol, bar):
     """A chain of three patches, 32^3, 16^3 and 8^3, off-centre in their
     parents (eight times the base resolution at the finest)."""
@@ -189,13 +207,10 @@ def test_three_patches_of_different_sizes(prec, tol, bar):
     assert rep["status_code"] == gr.GR_OK, rep
     for e in range(10):
         assert max(rep["res_level"][e][:4]) <= tol
-    for k in oracle.FIELDS:
-        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k)
-        for lvl in range(3):
-            assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= bar, ("patch", lvl + 1, k, rel_linf(gp[lvl][k], ofldp[lvl][k]))
+    check_levels(g0, gp, ofld0, ofldp, bar, bar if prec == "fp64" else None)
 
 
-@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-9), ("mixed_df", 1e-10, 1e-8)])
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-11), ("mixed_df", 1e-10, 1e-8)])
 def test_composite_with_relativistic_velocities(prec, tol, bar):
     """rms |u| = 0.3: the momentum sources, A_ij (AA reaches 1e-4 of 2 pi s0 in
     the lapse coefficient) and the shift are large enough that every term of
@@ -206,7 +221,4 @@ def test_composite_with_relativistic_velocities(prec, tol, bar):
     src0, srcp, ofld0, ofldp = _oracle_solve(n0, chain, p)
     rep, g0, gp, gsrc = _gpu_solve(n0, chain, p, prec, tol)
     assert rep["status_code"] == gr.GR_OK, rep
-    for k in oracle.FIELDS:
-        assert rel_linf(g0[k], ofld0[k]) <= bar, ("base", k)
-        for lvl in range(2):
-            assert rel_linf(gp[lvl][k], ofldp[lvl][k]) <= bar, ("patch", lvl + 1, k, rel_linf(gp[lvl][k], ofldp[lvl][k]))
+    check_levels(g0, gp, ofld0, ofldp, bar, bar if prec == "fp64" else None)
