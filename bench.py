@@ -7,14 +7,17 @@ residual in double-float, FP32 correction V-cycles); the plain FP64 GPU
 solve of the same step is timed next to it, and so is the same solve started by
 one full multigrid cycle per equation (a classical non-learned warm start),
 the composite solve with two static nested refinement patches (128^3 at
-2x and 4x the base resolution, centred on the densest cell), and the solve
-started from the previous solution after the particles drift by 0.05 cells
-(the warm start of a time loop).
+2x and 4x the base resolution, centred on the densest cell), and the full
+timestep of the time loop (deposit with the previous conformal factor, solve
+from the previous solution, kicks and drift of the particles).  The CPU
+oracle's bounded sample and its own time to residual run in a separate
+process that never initialises CUDA.
 Multi-GPU runs are independent replicas (one problem per rank, different
 seeds: weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec mixed_df|mixed|fp64]
                     [--no-fp64] [--no-fmg] [--no-e2e] [--no-learned] [--no-patches] [--no-cpu]
+                    [--no-cpu-solve] [--no-timestep]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 """
 from __future__ import annotations
@@ -135,27 +138,104 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(n, src_np, rho_hat, cycles=1):
+def oracle_sample(n, src_np, rho_hat, cycles=1, repeats=3, warm=True):
     """Time the FP64 CPU oracle (as it stands) on a bounded sample of the
     workload: `cycles` V(2,2) cycles of the V_x and psi equations at the full
-    grid, from the plain guess.  Returns (Gcell-updates/s, seconds, threads)."""
+    grid, from the plain guess.  One untimed sample warms the host (page
+    faults, thread start-up) unless warm is False, then `repeats` timed samples; returns
+    (median Gcell-updates/s, seconds of the median sample, threads, all rates)."""
     import numpy as np
 
     import oracle
 
     cells_per_cycle = sum(4 * (n >> l) ** 3 for l in range(0, int(math.log2(n)) - 1)) + 32 * 8
     fld = oracle.initial_fields(n)
-    t_total, updates = 0.0, 0
-    for eq in (0, 4):
-        kind, f, c0, c1, ref = oracle.eq_setup(eq, src_np, fld, rho_hat)
-        u = np.zeros((n, n, n))
-        t0 = time.perf_counter()
-        for _ in range(cycles):
-            oracle.vcycle(kind, u, f, c0, c1, rho_hat)
-        t_total += time.perf_counter() - t0
-        updates += cycles * cells_per_cycle
+    setups = [oracle.eq_setup(eq, src_np, fld, rho_hat) for eq in (0, 4)]
+    rates, secs = [], []
+    first = 0 if warm else 1
+    for rep in range(first, repeats + 1):
+        t_total, updates = 0.0, 0
+        for kind, f, c0, c1, ref in setups:
+            u = np.zeros((n, n, n))
+            t0 = time.perf_counter()
+            for _ in range(cycles):
+                oracle.vcycle(kind, u, f, c0, c1, rho_hat)
+            t_total += time.perf_counter() - t0
+            updates += cycles * cells_per_cycle
+        if rep:  # the first sample is the untimed warm-up
+            rates.append(updates / t_total / 1e9)
+            secs.append(t_total)
+    order = sorted(range(repeats), key=lambda i: rates[i])
+    mid = order[repeats // 2]
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return updates / t_total / 1e9, t_total, threads
+    return rates[mid], secs[mid], threads, rates
+
+
+def oracle_time_to_residual(src_np, rho_hat, tol):
+    """The FP64 CPU oracle's ten-equation solve of the bench's own sources from
+    the plain guess to relative residual tol (every field): wall seconds,
+    cycles and the cell updates it made (same counting as the GPU report)."""
+    import oracle
+
+    n = src_np["s0"].shape[0]
+    fld = oracle.initial_fields(n)
+    t0 = time.perf_counter()
+    st, rep = oracle.solve_constraints(src_np, fld, rho_hat, tol=tol, max_cycles=60)
+    secs = time.perf_counter() - t0
+    per_cycle = sum(4 * (n >> l) ** 3 for l in range(0, int(math.log2(n)) - 1)) + 32 * 8
+    updates = sum(rep["cycles"]) * per_cycle
+    return st, secs, rep["cycles"], updates
+
+
+def cpu_worker(folder):
+    """The CPU legs in a process of their own that never touches CUDA (so the
+    oracle runs on the host as it does in the reference arm): the bounded
+    sample and, if asked, the full time-to-residual solve, on the sources
+    saved in folder; prints one JSON line."""
+    import numpy as np
+
+    meta = json.load(open(os.path.join(folder, "meta.json")))
+    src = {k: np.load(os.path.join(folder, k + ".npy")) for k in ("s0", "sx", "sy", "sz", "sigma")}
+    n = src["s0"].shape[0]
+    val, secs, thr, rates = oracle_sample(n, src, meta["rho_hat"])
+    res = {"value": val, "secs": secs, "threads": thr, "rates": rates}
+    if meta["solve"]:
+        st, osecs, ocyc, oupd = oracle_time_to_residual(src, meta["rho_hat"], meta["tol"])
+        res.update(solve_status=st, solve_secs=osecs, solve_cycles=ocyc, solve_updates=oupd)
+    print(json.dumps(res), flush=True)
+
+
+def cpu_legs(src, rho_hat, tol, n, gpu_solve_ms, solve):
+    """Save the bench's sources, run cpu_worker in a fresh interpreter, and
+    shape its results into the cpu_baseline / cpu_time_to_residual keys."""
+    import shutil
+    import tempfile
+
+    import numpy as np
+
+    folder = tempfile.mkdtemp(prefix="gr_cpu_")
+    try:
+        for k, v in src.items():
+            np.save(os.path.join(folder, k + ".npy"), v.cpu().numpy())
+        json.dump({"rho_hat": rho_hat, "tol": tol, "solve": bool(solve)}, open(os.path.join(folder, "meta.json"), "w"))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", folder], capture_output=True,
+                           text=True, env=dict(os.environ))
+        if r.returncode != 0:
+            return {"cpu_baseline": {"error": r.stderr[-500:]}}
+        w = json.loads(r.stdout.strip().splitlines()[-1])
+    finally:
+        shutil.rmtree(folder, ignore_errors=True)
+    out = {"cpu_baseline": {"value": round(w["value"], 5), "unit": UNIT, "cores": w["threads"], "kind": "oracle",
+                            "sample": f"one V(2,2) cycle each of the V_x and psi equations at {n}^3 from the plain "
+                                      f"guess, median of {len(w['rates'])} after one untimed sample ({w['secs']:.1f} s "
+                                      f"each; rates {[round(x, 4) for x in w['rates']]}), in a process without CUDA"}}
+    if solve:
+        out["cpu_time_to_residual"] = {
+            "ms": round(1e3 * w["solve_secs"], 1), "status": w["solve_status"], "cycles": w["solve_cycles"],
+            "threads": w["threads"], "n": n, "gcell_updates_per_s": round(w["solve_updates"] / w["solve_secs"] / 1e9, 4),
+            "vs_gpu_time_to_residual": round(1e3 * w["solve_secs"] / gpu_solve_ms, 1),
+            "what": f"FP64 CPU oracle, ten-equation solve of this workload's sources to {tol:g} from the plain guess"}
+    return out
 
 
 # ------------------------------------------------------------------ main
@@ -170,11 +250,17 @@ def main():
     ap.add_argument("--no-fmg", action="store_true", help="skip the full multigrid start comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu-solve", action="store_true",
+                    help="skip the CPU oracle's full time-to-residual solve (about a minute at 512^3)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-timestep", action="store_true", help="skip the full timestep (deposit, solve, particle update)")
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison at 128^3")
     ap.add_argument("--no-patches", action="store_true",
                     help="skip the composite solve with two nested 128^3 refinement patches")
     args = ap.parse_args()
+    if args.cpu_worker:
+        return cpu_worker(args.cpu_worker)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,7 +388,7 @@ def main():
 
     # the end-to-end measurement runs first, on the state the timed steps left
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_measure(ctx, p, n, opts, world, min(args.steps, 3))
+        out["e2e"] = e2e_measure(ctx, p, n, opts, world, max(args.steps, 5))
 
     if rank == 0 and not args.no_fp64 and mixed:
         mixed_fields = {k: v.clone() for k, v in fld.items()}
@@ -328,24 +414,20 @@ def main():
     if rank == 0 and not args.no_fmg and mixed:
         out["fmg_start"] = fmg_measure(ctx, x, u, p, src, fld, opts)
 
-    if rank == 0 and mixed:
-        out["previous_solution_start"] = previous_solution_measure(ctx, x, u, p, src, fld, opts, n)
+    if rank == 0 and mixed and not args.no_timestep:
+        out["timestep"] = timestep_measure(ctx, x, u, p, fld, opts, n)
 
     if rank == 0 and not args.no_patches and n >= 256:
         out["patches"] = patches_measure(ctx, x, u, p, src, fld, opts, n)
 
     if rank == 0 and not args.no_learned:
         out["learned"] = learned_measure(args.prec)
+        if mixed and n > 128:
+            ctx.deposit(x, u, p.mass, src)
+            out["learned_full"] = learned_full_measure(ctx, p, src, fld, opts, n)
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        import numpy as np
-
-        src_np = {k: v.cpu().numpy() for k, v in src.items()}
-        del src, fld
-        val, secs, thr = oracle_sample(n, src_np, p.rho_hat)
-        out["cpu_baseline"] = {"value": round(val, 5), "unit": UNIT, "cores": thr, "kind": "oracle",
-                               "sample": f"one V(2,2) cycle each of the V_x and psi equations at {n}^3 from the "
-                                         f"plain guess ({secs:.1f} s)"}
+        out.update(cpu_legs(src, p.rho_hat, tol, n, solve_ms, not args.no_cpu_solve))
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -406,22 +488,32 @@ def e2e_measure(ctx, p, n, opts, world, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     updates = 0
-    per_step = []
+    per_step, phases = [], []
     for _ in range(steps):
         ts = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
         ctx.deposit(xh, uh, p.mass, src)
+        ev[1].record()
         fld["psi"].fill_(1.0)
         fld["apsi"].fill_(1.0)
         for k in ("Vx", "Vy", "Vz", "U", "Bx", "By", "Bz", "b"):
             fld[k].zero_()
         r = ctx.solve(src, fld, **o)
+        ev[2].record()  # after the solve's stream has waited for the last host_out copy
         updates += r["cell_updates"]
         torch.cuda.current_stream().synchronize()
         per_step.append(round(1e3 * (time.perf_counter() - ts), 1))
+        dep, rest = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        solve = 1e3 * sum(r["eq_seconds"])
+        phases.append({"deposit_from_host_ms": round(dep, 1), "solve_ms": round(solve, 1),
+                       "copy_tail_ms": round(max(rest - solve, 0.0), 1)})
     dt = time.perf_counter() - t0
+    med = sorted(per_step)[len(per_step) // 2]
     return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
             "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3),
-            "ms_each_step": per_step, "link_rates_before_steps": rates}
+            "ms_each_step": per_step, "median_ms_per_step": med, "phases_each_step": phases,
+            "link_rates_before_steps": rates}
 
 
 def fmg_measure(ctx, x, u, p, src, fld, opts):
@@ -495,37 +587,152 @@ def patches_measure(ctx, x, u, p, src, fld, opts, n, sizes=(128, 128)):
            "base_fields_max_rel_change_vs_no_patches": diff,
            "finest_patch_psi_range": [float(psi2.min()), float(psi2.max())],
            "base_psi_range": [float(f2["psi"].min()), float(f2["psi"].max())]}
+    # the plain FP64 composite solve (the comparator of the full-scale configuration), one timed run
+    for q in chain:
+        for k, v in q["fld"].items():
+            v.fill_(1.0 if k in ("psi", "apsi") else 0.0)
+    f4 = ctx.initial_fields()
+    torch.cuda.synchronize()
+    ev[0].record()
+    rep64 = ctx.solve(src, f4, patches=chain, **dict(opts, prec="fp64"))
+    ev[1].record()
+    torch.cuda.synchronize()
+    out["fp64_time_to_residual_ms"] = round(ev[0].elapsed_time(ev[1]), 3)
+    out["fp64_cycles"] = rep64["cycles"]
+    out["speedup_mixed_vs_fp64"] = round(out["fp64_time_to_residual_ms"] / ms, 3)
+    del f4
+    # the learned base guess (the network on the sources averaged down to its grid, interpolated
+    # back up); the patches start from the plain guess; one untimed and one timed run
+    net = _load_net()
+    if net is not None:
+        from paper_1905_08890_gb300 import learn
+
+        for it in range(2):
+            for q in chain:
+                for k, v in q["fld"].items():
+                    v.fill_(1.0 if k in ("psi", "apsi") else 0.0)
+            f5 = ctx.initial_fields()
+            torch.cuda.synchronize()
+            ev[0].record()
+            net.guess(n, src, f5, p.rho_hat, learn.V_RMS)
+            ev[1].record()
+            rep5 = ctx.solve(src, f5, patches=chain, **opts)
+            ev[2].record()
+            torch.cuda.synchronize()
+        out["learned_time_to_residual_ms"] = round(ev[0].elapsed_time(ev[2]), 3)
+        out["learned_inference_ms"] = round(ev[0].elapsed_time(ev[1]), 3)
+        out["learned_cycles"] = rep5["cycles"]
+        del f5
+        net.close()
     del f2, chain
     return out
 
 
-def previous_solution_measure(ctx, x, u, p, src, fld, opts, n, shift_cells=0.05):
-    """The natural warm start of a time loop (the previous step's solution as
-    the guess): the particles drift by dt u / W with dt chosen so that their
-    rms displacement is shift_cells cells (a stand-in for one step of the
-    particle update, which is not part of this library), the sources are
-    deposited again and the ten equations are solved from the headline
-    solve's fields.  One untimed and one timed run (CUDA events)."""
+def _load_net():
+    from paper_1905_08890_gb300 import learn
+
+    return learn.load(learn.WEIGHTS) if os.path.exists(learn.WEIGHTS) else None
+
+
+def learned_full_measure(ctx, p, src, fld, opts, n):
+    """The learned initial guess at the headline grid: the 128^3 network runs
+    on the sources averaged down to its grid and its ten fields are
+    interpolated back to n^3 (gr_net_guess); the solve then starts from them
+    with the per-equation guess check.  Against the plain guess and the full
+    multigrid start, same sources, one untimed and one timed pass (CUDA
+    events); the guess's error per field against the converged solution."""
     import torch
 
-    W = torch.sqrt(1.0 + (u * u).sum(0, keepdim=True))
-    v = u / W
-    dt = shift_cells / n / float(torch.sqrt((v * v).sum(0).mean()))
-    x2 = torch.remainder(x + dt * v, 1.0)
-    prev = {k: t.clone() for k, t in fld.items()}
+    from paper_1905_08890_gb300 import learn
+
+    net = _load_net()
+    if net is None:
+        return {"unavailable": "no trained weights"}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
     for it in range(2):
-        f2 = {k: t.clone() for k, t in prev.items()}
+        fp = ctx.initial_fields()
+        fl = ctx.initial_fields()
+        ff = ctx.initial_fields()
         torch.cuda.synchronize()
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record()
-        ctx.deposit(x2, u, p.mass, src)
-        rep = ctx.solve(src, f2, **opts)
-        t1.record()
+        ev[0].record()
+        rp = ctx.solve(src, fp, **opts)
+        ev[1].record()
+        net.guess(n, src, fl, p.rho_hat, learn.V_RMS)
+        ev[2].record()
+        guess = {k: v.clone() for k, v in fl.items()}
+        ev[3].record()
+        rl = ctx.solve(src, fl, check_guess=1, **opts)
+        ev[4].record()
+        rf = ctx.solve(src, ff, fmg=1, **opts)
+        ev[5].record()
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    del f2, prev, x2
-    return {"rms_shift_cells": shift_cells, "dt": dt, "time_to_residual_ms_incl_deposit": round(ms, 3),
-            "cycles": rep["cycles"], "res0": [float(f"{r:.3e}") for r in rep["res0"]]}
+
+    def dev(k, t):
+        return t - 1.0 if k in ("psi", "apsi") else t
+
+    err = {k: float((dev(k, guess[k]) - dev(k, fp[k])).abs().max() / dev(k, fp[k]).abs().max().clamp_min(1e-300))
+           for k in fp}
+    inf_ms = ev[1].elapsed_time(ev[2])
+    out = {"workload": "the headline workload; 128^3 network on sources averaged 4^3, fields interpolated back",
+           "time_to_residual_ms_plain": round(ev[0].elapsed_time(ev[1]), 3),
+           "time_to_residual_ms_learned": round(inf_ms + ev[3].elapsed_time(ev[4]), 3),
+           "inference_ms": round(inf_ms, 3), "time_to_residual_ms_fmg_start": round(ev[4].elapsed_time(ev[5]), 3),
+           "vcycles_plain": sum(rp["cycles"]), "vcycles_learned": sum(rl["cycles"]), "vcycles_fmg": sum(rf["cycles"]),
+           "cycles_learned": rl["cycles"], "guesses_rejected": sum(rl["guess_rejected"]),
+           "guess_rel_linf_error_of_deviation": {k: float(f"{v:.3g}") for k, v in err.items()}}
+    del fp, fl, ff, guess
+    net.close()
+    return out
+
+
+def timestep_measure(ctx, x, u, p, fld, opts, n, steps=5, shift_cells=0.05):
+    """The full timestep of the method's time loop (Sec. 4.2 steps 3 and 5-8)
+    on copies of the bench's particles: the deposit with the previous psi in
+    the Lorentz factor (gr_deposit_metric), the ten-equation solve started
+    from the previous solution, and the particle update (synchronising kick,
+    opening kick, drift: gr_particle_update), with dt set so that particles
+    at the rms speed move shift_cells cells.  One untimed opening step, then
+    `steps` timed steps (CUDA events per phase on the context's stream)."""
+    import torch
+
+    from paper_1905_08890_gb300 import gr
+
+    xs, us = x.clone(), u.clone()
+    W = torch.sqrt(1.0 + (us * us).sum(0))
+    dt = shift_cells / n / float(torch.sqrt(((us / W) ** 2).sum(0).mean()))
+    src = ctx.new_sources()
+    ctx.deposit(xs, us, p.mass, src)
+    f = {k: t.clone() for k, t in fld.items()}
+    ctx.solve(src, f, **opts)
+    ctx.particle_update(xs, us, f, dt, gr.GR_KICK_OPEN | gr.GR_DRIFT)
+    rows = []
+    for it in range(steps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        ctx.deposit_metric(xs, us, p.mass, f["psi"], src)
+        ev[1].record()
+        rep = ctx.solve(src, f, **opts)
+        ev[2].record()
+        ctx.particle_update(xs, us, f, dt)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if it:  # the first pass warms the update's scratch allocation
+            rows.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                         ev[0].elapsed_time(ev[3]), rep["cycles"]))
+    k = len(rows)
+    upd_ms = sum(r[2] for r in rows) / k
+    # algorithmic bytes of the update: per particle x, u read and written (96 B); per cell the
+    # fields read for alpha, beta (48 B) and the FP64 scratch written (32 B), that scratch read
+    # (40 B) and the 20 FP32 quantities written (80 B), and those read once by the gather (80 B)
+    upd_bytes = 96 * x.shape[1] + 280 * n ** 3
+    del xs, us, f, src
+    return {"dt": dt, "rms_shift_cells": shift_cells, "steps": k,
+            "ms_per_timestep": round(sum(r[3] for r in rows) / k, 3),
+            "deposit_metric_ms": round(sum(r[0] for r in rows) / k, 3),
+            "solve_ms": round(sum(r[1] for r in rows) / k, 3), "particle_update_ms": round(upd_ms, 3),
+            "particle_update_algorithmic_GBps": round(upd_bytes / (upd_ms * 1e-3) / 1e9, 1),
+            "cycles_each_step": [r[4] for r in rows]}
 
 
 def learned_measure(prec, seeds=(5000, 5001, 5002, 5003)):
@@ -617,10 +824,10 @@ def run_reference(args, rank, world, n, w, config):
     p = synth.zeldovich(n, w["seed"], w["sigma"], w["v_rms"], w["lognormal"])
     src_np = oracle.deposit(n, p.x, p.u, p.mass)
     for _ in range(args.warmup):
-        oracle_sample(n, src_np, p.rho_hat)
+        oracle_sample(n, src_np, p.rho_hat, repeats=1, warm=False)
     t_sum, v_sum = 0.0, []
     for _ in range(args.steps):
-        v, secs, thr = oracle_sample(n, src_np, p.rho_hat)
+        v, secs, thr, _ = oracle_sample(n, src_np, p.rho_hat, repeats=1, warm=False)
         t_sum += secs
         v_sum.append(v)
     value = sum(v_sum) / len(v_sum)
