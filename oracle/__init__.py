@@ -34,6 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gr_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "gr_particles.c")]
 _OUT_DIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -51,10 +52,10 @@ def build(force: bool = False) -> str:
     """Compile gr_oracle.c into oracle/_lib/liboracle.so (gcc, OpenMP, no
     fast-math, no FMA contraction so x86 and Arm round alike)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in _SRCS):
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -106,6 +107,12 @@ def lib():
             L.orc_patch_residual_at.restype = None
             L.orc_patch_eq_setup.argtypes = [I, I, D, P, P, D, D, D, P, P, P, P]
             L.orc_patch_eq_setup.restype = I
+            L.orc_particle_fields.argtypes = [I, P, P, P, P, P, P, P]
+            L.orc_particle_fields.restype = None
+            L.orc_particle_update.argtypes = [I, I64, P, P, P, D, I, I, I]
+            L.orc_particle_update.restype = None
+            L.orc_deposit_metric.argtypes = [I, I64, P, P, D, P, P, P, P, P, P]
+            L.orc_deposit_metric.restype = None
             _lib = L
     return _lib
 
@@ -134,6 +141,45 @@ def deposit(n: int, x: np.ndarray, u: np.ndarray, mass: float) -> dict:
     out = {k: _grid(n) for k in SOURCES}
     lib().orc_deposit(n, npart, _p(x), _p(u), mass, *[_p(out[k]) for k in SOURCES])
     return out
+
+
+def deposit_metric(n: int, x: np.ndarray, u: np.ndarray, mass: float, psi=None) -> dict:
+    """CIC sources with the Lorentz factor at the conformal factor psi (n^3,
+    interpolated to each particle; None: psi = 1) (Sec. 4.5)."""
+    x = _f64(x)
+    u = _f64(u)
+    npart = x.shape[1] if x.ndim == 2 else 0
+    out = {k: _grid(n) for k in SOURCES}
+    ps = None if psi is None else _f64(psi)
+    lib().orc_deposit_metric(n, npart, _p(x), _p(u), mass, _p(ps), *[_p(out[k]) for k in SOURCES])
+    return out
+
+
+# ---------------------------------------------------------------- particles
+PARTICLE_FIELDS = ("alpha", "psi", "beta_x", "beta_y", "beta_z", "dalpha_x", "dalpha_y", "dalpha_z", "dpsi_x",
+                   "dpsi_y", "dpsi_z") + tuple(f"dbeta{j}_{i}" for j in "xyz" for i in "xyz")
+
+
+def particle_fields(fld: dict) -> np.ndarray:
+    """The 20 grid quantities of the particle update (Sec. 4.4): alpha, psi,
+    beta^j and their central differences, as a (20, n, n, n) array in the
+    order PARTICLE_FIELDS (dbeta{j}_{i} = D_i beta^j)."""
+    n = fld["psi"].shape[0]
+    out = np.zeros((20, n, n, n))
+    a = [_f64(fld[k]) for k in ("psi", "apsi", "Bx", "By", "Bz", "b")]
+    lib().orc_particle_fields(n, *[_p(v) for v in a], _p(out))
+    return out
+
+
+def particle_update(fld: dict, x: np.ndarray, u: np.ndarray, dt: float, sync=True, open_=True, drift=True,
+                    fields=None):
+    """Kick(s) and drift of the particles (x, u: (3, np), updated in place)
+    in the solved fields (Sec. 4.4, App. A)."""
+    n = fld["psi"].shape[0]
+    assert x.dtype == np.float64 and x.flags.c_contiguous and u.dtype == np.float64 and u.flags.c_contiguous
+    g = particle_fields(fld) if fields is None else fields
+    npart = x.shape[1]
+    lib().orc_particle_update(n, npart, _p(x), _p(u), _p(g), dt, int(sync), int(open_), int(drift))
 
 
 # ---------------------------------------------------------------- operators
