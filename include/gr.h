@@ -303,6 +303,16 @@ gr_status gr_net_set_norm(gr_net *net, const float *in_mean, const float *in_std
                           const float *out_std);
 /* Write the network's guess of all ten fields into guess (device arrays). */
 gr_status gr_net_infer(gr_net *net, const gr_sources *src, double rho_hat, double v_rms, gr_fields *guess);
+/* The network's guess for a finer periodic grid of the same box: n_fine =
+   the network's n times 2^k (k >= 0, n_fine <= 1024).  The sources (device,
+   n_fine^3 each; sigma unused) are averaged over the 2^k cubed cells each
+   network cell covers, the network runs on the averages, and its ten
+   outputs are interpolated trilinearly between the network's (periodic)
+   cell centres to every fine cell of guess (device, n_fine^3 each).  k = 0
+   is gr_net_infer.  Scratch: four network-grid arrays of doubles, allocated
+   by the network on first use.  Queued on the network's stream. */
+gr_status gr_net_guess(gr_net *net, int n_fine, const gr_sources *src, double rho_hat, double v_rms,
+                       gr_fields *guess);
 /* Mean squared error of the standardised output against target (device
    fields, e.g. a converged solve) and its gradient; host_grads (may be NULL)
    receives gr_net_num_params floats.  Parameters are not changed. */
@@ -315,6 +325,53 @@ gr_status gr_net_train_step(gr_net *net, const gr_sources *src, const gr_fields 
    outputs, pools and concatenations) of the last forward pass to host FP32;
    count must equal its size. */
 gr_status gr_net_activation(gr_net *net, int tensor, float *host, size_t count);
+
+/* ---- the particle update around the solve (Sec. 4.2 steps 3 and 6-8;
+   Sec. 4.4; Sec. 4.5; App. A) ------------------------------------------
+   Geometric units with a = 1, c = 1: the spatial metric is psi^4 delta_ij,
+   alpha = (alpha psi) / psi, beta^i = B^i + d_i b, and the paper's code-unit
+   potentials are Phi = alpha - 1, Psi = 2 (1 - psi).  Particles: x, u are
+   device arrays [3][np] (SoA, x then y then z), positions in the periodic box
+   [0, L), u the lower-index spatial 4-velocity u_i per unit rest mass. */
+enum {
+    GR_KICK_SYNC = 1, /* the synchronising kick u^(n-1/2) -> u^n: substeps j = 1..5 (Eq. GR-K2) */
+    GR_KICK_OPEN = 2, /* the opening kick u^n -> u^(n+1/2): substeps j = 5..1 (Eq. GR-K1) */
+    GR_DRIFT = 4      /* the drift x^n -> x^(n+1) (Eq. GR-D) */
+};
+/* Kicks and drift of np particles in the solved fields fld (psi, alpha psi,
+   B^i, b are read; the other fields are not).  Each kick adds dt/2 F to u in
+   the five substeps of Sec. 4.4 (Eqs. coeff_j, coeff_4, coeff_5):
+   c_j = -u_j with (f_j)_i = -d_i beta^j (j = 1, 2, 3), c_4 = (W^2 - 1)/W
+   alpha/psi with (f_4)_i = -d_i Psi, c_5 = W with (f_5)_i = -d_i Phi, each
+   substep at the velocity the previous one left, W = sqrt(1 + psi^-4 |u|^2)
+   (Eq. Lorentz-factor).  The drift adds dt (alpha psi^-4 u_i / W - beta^i)
+   (Eq. V_exp) and wraps x into [0, L).  Everything is evaluated at the
+   particle's position on entry: the fields and their 3-point central
+   differences are formed on the grid and interpolated to the particle with
+   the cloud-in-cell weights of gr_deposit.  flags: any of GR_KICK_SYNC,
+   GR_KICK_OPEN (applied in that order), GR_DRIFT (after the kicks, with
+   the kicked velocity); a time loop calls it once per step with all three
+   after the solve (the first step without GR_KICK_SYNC).  Arithmetic: the
+   interpolated quantities and the substeps in FP32, positions and
+   velocities accumulated in FP64.  Scratch: the context's first-use
+   allocation of 20 n^3 floats.  Queued on the context's stream; x and u are
+   updated in place.  GR_ERR_ARG: NULL arrays, np < 0, host memory, dt not
+   finite or flags outside the three bits. */
+gr_status gr_particle_update(gr_ctx *ctx, int64_t np, double *x, double *u, const gr_fields *fld, double dt,
+                             int flags);
+/* gr_particle_update with flags GR_KICK_SYNC and/or GR_KICK_OPEN (x unchanged). */
+gr_status gr_kick(gr_ctx *ctx, int64_t np, const double *x, double *u, const gr_fields *fld, double dt, int flags);
+/* gr_particle_update with GR_DRIFT alone (u unchanged). */
+gr_status gr_drift(gr_ctx *ctx, int64_t np, double *x, const double *u, const gr_fields *fld, double dt);
+/* gr_deposit with the Lorentz factor of the current metric (Sec. 4.5 Eqs.
+   src_s0, src_si, src_sij): W = sqrt(1 + psi^-4 |u|^2) with psi (device,
+   n^3, natural layout: the previous solution's conformal factor) interpolated
+   to the particle by cloud-in-cell; s0 += m W w / h^3, s_l += m u_l w / h^3,
+   sigma += m |u|^2 / W w / h^3.  psi = NULL is gr_deposit (psi = 1).  Device
+   particle arrays only (GR_ERR_ARG otherwise).  Sets the default rho_hat
+   like gr_deposit. */
+gr_status gr_deposit_metric(gr_ctx *ctx, int64_t np, const double *x, const double *u, double mass, const double *psi,
+                            gr_sources *out);
 
 /* Allocation-free residual of one momentum-constraint equation,
    lap V_i = 8 pi (s_i - <s_i>): the same residual and relative norm as

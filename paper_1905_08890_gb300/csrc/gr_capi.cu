@@ -120,6 +120,8 @@ struct gr_ctx {
     std::vector<void *> palloc;
     double *pdev = nullptr, *phost = nullptr;
     bool pdf = false;  // the patches relax in double-float (mixed modes) rather than FP64
+    // particle update: the 20 FP32 interpolated quantities (allocated on first use)
+    float *pf = nullptr;
 };
 
 namespace {
@@ -1521,6 +1523,64 @@ gr_status gr_deposit_patches(gr_ctx *c, int npatch, const gr_patch *patch, int64
         gr::patch_deposit(np, x, u, mass, c->L, N, O, n, gr::PSetSrc{{f[0], f[1], f[2], f[3], f[4]}}, c->st);
     }
     return cuda_check("gr_deposit_patches");
+}
+
+gr_status gr_particle_update(gr_ctx *c, int64_t np, double *x, double *u, const gr_fields *fl, double dt, int flags)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if (np < 0 || (np > 0 && (!x || !u))) return fail(GR_ERR_ARG, "bad particle arrays");
+    if (!fl || !fl->psi || !fl->apsi || !fl->B[0] || !fl->B[1] || !fl->B[2] || !fl->b)
+        return fail(GR_ERR_ARG, "a field array is NULL");
+    if (!std::isfinite(dt)) return fail(GR_ERR_ARG, "dt must be finite");
+    if (flags & ~(GR_KICK_SYNC | GR_KICK_OPEN | GR_DRIFT)) return fail(GR_ERR_ARG, "flags = %d", flags);
+    if (np > 0 && (host_memory(x) || host_memory(u)))
+        return fail(GR_ERR_ARG, "gr_particle_update takes device particle arrays");
+    if (np == 0 || flags == 0) return GR_OK;
+    const size_t N = (size_t)c->n * c->n * c->n;
+    if (!c->pf) {
+        gr_status st = dalloc(c, &c->pf, 20 * N);
+        if (st != GR_OK) return st;
+    }
+    c->a_fmt = 0;  // A6 serves as the FP64 scratch of alpha and beta
+    gr::particle_fields(c->n, c->L, fl->psi, fl->apsi, fl->B[0], fl->B[1], fl->B[2], fl->b, c->A6, c->A6 + N, c->pf,
+                        c->st);
+    gr::particle_update(c->n, c->L, np, x, u, c->pf, dt, flags, c->st);
+    return cuda_check("gr_particle_update");
+}
+
+gr_status gr_kick(gr_ctx *c, int64_t np, const double *x, double *u, const gr_fields *fl, double dt, int flags)
+{
+    if (flags & ~(GR_KICK_SYNC | GR_KICK_OPEN)) {
+        g_err.clear();
+        return fail(GR_ERR_ARG, "gr_kick: flags = %d (GR_KICK_SYNC, GR_KICK_OPEN)", flags);
+    }
+    // the kernel writes x only under GR_DRIFT
+    return gr_particle_update(c, np, const_cast<double *>(x), u, fl, dt, flags);
+}
+
+gr_status gr_drift(gr_ctx *c, int64_t np, double *x, const double *u, const gr_fields *fl, double dt)
+{
+    // the kernel writes u only under a kick flag
+    return gr_particle_update(c, np, x, const_cast<double *>(u), fl, dt, GR_DRIFT);
+}
+
+gr_status gr_deposit_metric(gr_ctx *c, int64_t np, const double *x, const double *u, double mass, const double *psi,
+                            gr_sources *out)
+{
+    g_err.clear();
+    if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
+    if (np < 0) return fail(GR_ERR_ARG, "np < 0");
+    if (np > 0 && (!x || !u)) return fail(GR_ERR_ARG, "x or u is NULL");
+    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL");
+    if (!(mass >= 0) || !std::isfinite(mass)) return fail(GR_ERR_ARG, "mass must be finite and >= 0");
+    if (np > 0 && (host_memory(x) || host_memory(u)))
+        return fail(GR_ERR_ARG, "gr_deposit_metric takes device particle arrays");
+    if (!psi) return gr_deposit(c, np, x, u, mass, out);
+    if (host_memory(psi)) return fail(GR_ERR_ARG, "psi must be device memory");
+    gr::deposit_metric(c->n, c->L, np, x, u, mass, psi, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
+    c->rho_dep = mass * (double)np / (c->L * c->L * c->L);
+    return cuda_check("gr_deposit_metric");
 }
 
 }  // extern "C"

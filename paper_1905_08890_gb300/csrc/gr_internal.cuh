@@ -354,6 +354,19 @@ void apsi_setup(int n, double h2, const double *psi, const double *apsi, const d
 void shift_weight(int n, const double *psi, const double *apsi, double *w, cudaStream_t st);
 void shift_source(int n, double inv2h, const double *A, const double *w, int comp, double *f, cudaStream_t st);
 
+// ---- particles (particle_kernels.cu) ----------------------------------------
+// The 20 FP32 arrays of the particle update (alpha - 1, psi - 1, beta^j,
+// D_i alpha, D_i psi, D_i beta^j at index 11 + 3 j + i; each n^3) from the
+// natural FP64 fields; alpha (n^3) and beta (3 n^3) are FP64 scratch.
+void particle_fields(int n, double L, const double *psi, const double *apsi, const double *Bx, const double *By,
+                     const double *Bz, const double *b, double *alpha, double *beta, float *pf, cudaStream_t st);
+// Kicks and drift of np particles (x, u: [3][np] device SoA) with the flags
+// GR_KICK_SYNC, GR_KICK_OPEN, GR_DRIFT.
+void particle_update(int n, double L, int64_t np, double *x, double *u, const float *pf, double dt, int flags,
+                     cudaStream_t st);
+// The deposit with W = sqrt(1 + psi^-4 |u|^2), psi interpolated at the particle.
+void deposit_metric(int n, double L, int64_t np, const double *x, const double *u, double mass, const double *psi,
+                    double *s0, double *sx, double *sy, double *sz, double *sig, cudaStream_t st);
 
 // ---------------------------------------------------------------- nested patches
 // Base level as the patch kernels see it: natural FP64 fields (PB_NAT, nat),

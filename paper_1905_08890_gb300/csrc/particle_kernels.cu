@@ -1,0 +1,304 @@
+// particle_kernels.cu - the particle update around the constraint solve (kick
+// and drift in the solved metric) and the deposit with the metric's Lorentz
+// factor.
+//
+// Geometric units, a = 1, c = 1: the metric is psi^4 delta_ij, the lapse
+// alpha = (alpha psi) / psi and the shift beta^i = B^i + d_i b (Sec. 4.3.1).
+// With the paper's code-unit potentials Phi = alpha - 1 and Psi = 2 (1 - psi)
+// the kick splits the force of Sec. 4.4 (Eqs. force, coeff_j, coeff_4,
+// coeff_5) into five substeps, each using the velocity the previous one left:
+//     j = 1, 2, 3:  du_i += dt/2 (-u_j)(-D_i beta^j)
+//     j = 4:        du_i += dt/2 (W^2 - 1)/W alpha/psi (2 D_i psi)
+//     j = 5:        du_i += dt/2 W (-D_i alpha)
+// with W = sqrt(1 + psi^-4 |u|^2) (Eq. Lorentz-factor) at the current
+// velocity; the synchronising kick of the previous step runs j = 1..5 and the
+// opening kick j = 5..1 (Sec. 4.4; App. A Eqs. GR-K1, GR-K2).  The drift
+// moves x by dt (alpha psi^-4 u / W - beta) with the fields at the old
+// position (App. A Eqs. GR-D, V_exp).
+//
+// Design.  The fields and their 3-point central differences (the paper's
+// gradient stencil) are formed once per update on the grid in FP64 and
+// stored as 20 FP32 arrays (alpha - 1, psi - 1, beta^j, D_i alpha, D_i psi,
+// D_i beta^j); each particle gathers them with cloud-in-cell weights and runs
+// the substeps in FP32, accumulating its velocity change in FP32 and adding
+// it to the FP64 velocity once.  Positions, the cell index and the
+// cloud-in-cell fractions stay FP64 (a fraction loses nothing when rounded
+// to FP32 afterwards).  GB300 issues FP64 at 1/58 of the FP32 rate, so this
+// keeps the per-particle work off the FP64 pipe; the FP32 quantities carry a
+// relative error of a few 2^-24, far below the O(h^2) of the interpolation.
+#include <cuda_runtime.h>
+
+#include "../../include/gr.h"
+#include "gr_internal.cuh"
+
+namespace gr {
+
+namespace {
+
+// index of the 20 gathered quantities
+enum : int { Q_ALPHA = 0, Q_PSI = 1, Q_BETA = 2, Q_DALPHA = 5, Q_DPSI = 8, Q_DBETA = 11, Q_N = 20 };
+
+int log2i(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// pass 1 (FP64, natural layout): alpha = apsi / psi and beta^j = B^j + D_j b
+__global__ void __launch_bounds__(kBlock)
+    k_pf_alpha_beta(int lgn, double inv2h, const double *__restrict__ psi, const double *__restrict__ apsi,
+                    const double *__restrict__ Bx, const double *__restrict__ By, const double *__restrict__ Bz,
+                    const double *__restrict__ b, double *__restrict__ alpha, double *__restrict__ beta)
+{
+    pdl_begin();
+    const int m = (1 << lgn) - 1;
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t & m), j = (int)((t >> lgn) & m), i = (int)(t >> (2 * lgn));
+        const int64_t row = t - k, plane = t - ((int64_t)j << lgn) - k;
+        const int64_t xp = ((int64_t)((i + 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
+        const int64_t xm = ((int64_t)((i - 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
+        const int64_t yp = plane + ((int64_t)((j + 1) & m) << lgn) + k;
+        const int64_t ym = plane + ((int64_t)((j - 1) & m) << lgn) + k;
+        const int64_t zp = row + ((k + 1) & m), zm = row + ((k - 1) & m);
+        alpha[t] = apsi[t] / psi[t];
+        beta[t] = Bx[t] + (b[xp] - b[xm]) * inv2h;
+        beta[N + t] = By[t] + (b[yp] - b[ym]) * inv2h;
+        beta[2 * N + t] = Bz[t] + (b[zp] - b[zm]) * inv2h;
+    }
+}
+
+// pass 2: the 20 FP32 arrays of the gather: alpha - 1 and psi - 1 (so the
+// gathered FP32 value keeps its precision relative to the deviation), beta^j
+// and the central differences, each difference formed in FP64 and scaled by
+// 1/2h (a power of two) after the rounding to FP32
+__global__ void __launch_bounds__(kBlock)
+    k_pf_grad(int lgn, float inv2h, const double *__restrict__ alpha, const double *__restrict__ psi,
+              const double *__restrict__ beta, float *__restrict__ pf)
+{
+    pdl_begin();
+    const int m = (1 << lgn) - 1;
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t & m), j = (int)((t >> lgn) & m), i = (int)(t >> (2 * lgn));
+        const int64_t row = t - k, plane = t - ((int64_t)j << lgn) - k;
+        int64_t nb[3][2];
+        nb[0][0] = ((int64_t)((i + 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
+        nb[0][1] = ((int64_t)((i - 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
+        nb[1][0] = plane + ((int64_t)((j + 1) & m) << lgn) + k;
+        nb[1][1] = plane + ((int64_t)((j - 1) & m) << lgn) + k;
+        nb[2][0] = row + ((k + 1) & m);
+        nb[2][1] = row + ((k - 1) & m);
+        pf[Q_ALPHA * N + t] = (float)(alpha[t] - 1.0);
+        pf[Q_PSI * N + t] = (float)(psi[t] - 1.0);
+#pragma unroll
+        for (int q = 0; q < 3; q++) pf[(Q_BETA + q) * N + t] = (float)beta[q * N + t];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            pf[(Q_DALPHA + a) * N + t] = (float)(alpha[nb[a][0]] - alpha[nb[a][1]]) * inv2h;
+            pf[(Q_DPSI + a) * N + t] = (float)(psi[nb[a][0]] - psi[nb[a][1]]) * inv2h;
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+                pf[(Q_DBETA + 3 * q + a) * N + t] = (float)(beta[q * N + nb[a][0]] - beta[q * N + nb[a][1]]) * inv2h;
+        }
+    }
+}
+
+// one substep j (1..5) of a kick by hdt = dt/2 in FP32; the velocity is
+// u0 + du with the change du accumulated here; q holds alpha - 1 and psi - 1
+__device__ __forceinline__ void substep(int j, float hdt, const float *q, const float u0[3], float du[3])
+{
+    const float ux = u0[0] + du[0], uy = u0[1] + du[1], uz = u0[2] + du[2];
+    if (j <= 3) {
+        const float c = -(j == 1 ? ux : (j == 2 ? uy : uz));  // c_j = -u_j
+        const float *g = q + Q_DBETA + 3 * (j - 1);             // D_i beta^j, (f_j)_i = -D_i beta^j
+        du[0] = fmaf(hdt * c, -g[0], du[0]);
+        du[1] = fmaf(hdt * c, -g[1], du[1]);
+        du[2] = fmaf(hdt * c, -g[2], du[2]);
+        return;
+    }
+    const float ip = 1.0f / (1.0f + q[Q_PSI]);
+    const float ip2 = ip * ip;
+    const float g = ip2 * ip2 * fmaf(ux, ux, fmaf(uy, uy, uz * uz));  // psi^-4 |u|^2 = W^2 - 1
+    const float W = sqrtf(1.0f + g);
+    if (j == 4) {  // c_4 = (W^2 - 1)/W alpha/psi, (f_4)_i = 2 D_i psi
+        const float c = g / W * (1.0f + q[Q_ALPHA]) * ip;
+        du[0] = fmaf(hdt * c, 2.0f * q[Q_DPSI + 0], du[0]);
+        du[1] = fmaf(hdt * c, 2.0f * q[Q_DPSI + 1], du[1]);
+        du[2] = fmaf(hdt * c, 2.0f * q[Q_DPSI + 2], du[2]);
+    } else {  // c_5 = W, (f_5)_i = -D_i alpha
+        du[0] = fmaf(hdt * W, -q[Q_DALPHA + 0], du[0]);
+        du[1] = fmaf(hdt * W, -q[Q_DALPHA + 1], du[1]);
+        du[2] = fmaf(hdt * W, -q[Q_DALPHA + 2], du[2]);
+    }
+}
+
+// One thread per particle (blocks start in index order, so for lattice-ordered
+// particles the cells in flight are a few planes that L2 holds).
+__global__ void __launch_bounds__(kBlock)
+    k_particle_update(int lgn, double invh, int64_t np, double *__restrict__ x, double *__restrict__ u,
+                      const float *__restrict__ pf, float hdt, double dt, int flags)
+{
+    pdl_begin();
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int m = (1 << lgn) - 1;
+    const int64_t N = (int64_t)1 << (3 * lgn);
+    double xd[3];
+    int lo[3];
+    float fw[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        xd[d] = x[d * np + p];
+        const double t = fma(xd[d], invh, -0.5);
+        const double fl = floor(t);
+        const double fr = t - fl;
+        fw[d][0] = (float)(1.0 - fr);
+        fw[d][1] = (float)fr;
+        lo[d] = (int)((long long)fl & m);
+    }
+    float q[Q_N];
+#pragma unroll
+    for (int k = 0; k < Q_N; k++) q[k] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const float wab = fw[0][a] * fw[1][b];
+            const int64_t row = ((int64_t)((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m))) << lgn;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const float w = wab * fw[2][c];
+                const int64_t id = row + ((lo[2] + c) & m);
+#pragma unroll
+                for (int k = 0; k < Q_N; k++) q[k] = fmaf(w, __ldg(pf + k * N + id), q[k]);
+            }
+        }
+    const double ud[3] = {u[p], u[np + p], u[2 * np + p]};
+    const float u0[3] = {(float)ud[0], (float)ud[1], (float)ud[2]};
+    float du[3] = {0.0f, 0.0f, 0.0f};
+    if (flags & GR_KICK_SYNC)
+#pragma unroll
+        for (int j = 1; j <= 5; j++) substep(j, hdt, q, u0, du);
+    if (flags & GR_KICK_OPEN)
+#pragma unroll
+        for (int j = 5; j >= 1; j--) substep(j, hdt, q, u0, du);
+    if (flags & (GR_KICK_SYNC | GR_KICK_OPEN))
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d * np + p] = ud[d] + (double)du[d];
+    if (flags & GR_DRIFT) {
+        const float ux = u0[0] + du[0], uy = u0[1] + du[1], uz = u0[2] + du[2];
+        const float ip = 1.0f / (1.0f + q[Q_PSI]);
+        const float ip4 = (ip * ip) * (ip * ip);
+        const float W = sqrtf(1.0f + ip4 * fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+        const float fac = (1.0f + q[Q_ALPHA]) * ip4 / W;
+        const float v[3] = {fmaf(fac, ux, -q[Q_BETA + 0]), fmaf(fac, uy, -q[Q_BETA + 1]),
+                            fmaf(fac, uz, -q[Q_BETA + 2])};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double xn = fma(dt, (double)v[d], xd[d]);
+            x[d * np + p] = xn - floor(xn);
+        }
+    }
+}
+
+// Deposit with the Lorentz factor at psi: W = sqrt(1 + psi^-4 |u|^2), psi
+// at the particle by cloud-in-cell in FP64.  Charges as k_deposit:
+// s0 += q W w, s_l += q u_l w, sigma += q |u|^2 / W w; the products charge x
+// weight in FP64.
+__global__ void __launch_bounds__(kBlock)
+    k_deposit_metric(int lgn, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u,
+                     double q, const double *__restrict__ psi, double *__restrict__ s0, double *__restrict__ sx,
+                     double *__restrict__ sy, double *__restrict__ sz, double *__restrict__ sig)
+{
+    pdl_begin();
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int m = (1 << lgn) - 1;
+    int lo[3];
+    double fw[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double t = fma(x[d * np + p], invh, -0.5);
+        const double fl = floor(t);
+        const double fr = t - fl;
+        fw[d][0] = 1.0 - fr;
+        fw[d][1] = fr;
+        lo[d] = (int)((long long)fl & m);
+    }
+    double ps = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const double wab = fw[0][a] * fw[1][b];
+            const int64_t row = ((int64_t)((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m))) << lgn;
+#pragma unroll
+            for (int c = 0; c < 2; c++) ps = fma(wab * fw[2][c], __ldg(psi + row + ((lo[2] + c) & m)), ps);
+        }
+    const double ip2 = 1.0 / (ps * ps);
+    const double ux = u[p], uy = u[np + p], uz = u[2 * np + p];
+    const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+    const double w2 = fma(ip2 * ip2, u2, 1.0);
+    const double rw = rsqrt(w2);
+    const double Q[5] = {q * (w2 * rw), q * ux, q * uy, q * uz, (q * u2) * rw};
+    double *const out[5] = {s0, sx, sy, sz, sig};
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const double wab = fw[0][a] * fw[1][b];
+            const int64_t row = ((int64_t)((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m))) << lgn;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const double w = wab * fw[2][c];
+                const int64_t id = row + ((lo[2] + c) & m);
+#pragma unroll
+                for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, Q[k] * w);
+            }
+        }
+}
+
+}  // namespace
+
+void particle_fields(int n, double L, const double *psi, const double *apsi, const double *Bx, const double *By,
+                     const double *Bz, const double *b, double *alpha, double *beta, float *pf, cudaStream_t st)
+{
+    const int lgn = log2i(n);
+    const int64_t N = (int64_t)n * n * n;
+    const double inv2h = 0.5 * n / L;
+    GR_LAUNCH(k_pf_alpha_beta, wave_grid(k_pf_alpha_beta, N), kBlock, st, lgn, inv2h, psi, apsi, Bx, By, Bz, b,
+              alpha, beta);
+    GR_LAUNCH(k_pf_grad, wave_grid(k_pf_grad, N), kBlock, st, lgn, (float)inv2h, (const double *)alpha, psi,
+              (const double *)beta, pf);
+}
+
+void particle_update(int n, double L, int64_t np, double *x, double *u, const float *pf, double dt, int flags,
+                     cudaStream_t st)
+{
+    if (np <= 0) return;
+    const int64_t blocks = (np + kBlock - 1) / kBlock;
+    const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
+    GR_LAUNCH(k_particle_update, g, kBlock, st, log2i(n), (double)n / L, np, x, u, pf, (float)(0.5 * dt), dt,
+              flags);
+}
+
+void deposit_metric(int n, double L, int64_t np, const double *x, const double *u, double mass, const double *psi,
+                    double *s0, double *sx, double *sy, double *sz, double *sig, cudaStream_t st)
+{
+    const size_t bytes = (size_t)n * n * n * sizeof(double);
+    cudaMemsetAsync(s0, 0, bytes, st);
+    cudaMemsetAsync(sx, 0, bytes, st);
+    cudaMemsetAsync(sy, 0, bytes, st);
+    cudaMemsetAsync(sz, 0, bytes, st);
+    cudaMemsetAsync(sig, 0, bytes, st);
+    if (np <= 0) return;
+    const double h = L / n;
+    const int64_t blocks = (np + kBlock - 1) / kBlock;
+    const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
+    GR_LAUNCH(k_deposit_metric, g, kBlock, st, log2i(n), 1.0 / h, np, x, u, mass / (h * h * h), psi, s0, sx, sy, sz,
+              sig);
+}
+
+}  // namespace gr

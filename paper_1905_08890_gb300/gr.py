@@ -66,7 +66,9 @@ PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid"
 _lib = None
 _lock = threading.Lock()
 EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_deposit_patches", "gr_solve_constraints",
-            "gr_vcycle", "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc")
+            "gr_vcycle", "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc",
+            "gr_particle_update", "gr_kick", "gr_drift", "gr_deposit_metric")
+GR_KICK_SYNC, GR_KICK_OPEN, GR_DRIFT = 1, 2, 4
 
 
 def lib():
@@ -103,6 +105,16 @@ def lib():
             L.gr_momentum_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                        ctypes.POINTER(ctypes.c_double), _P]
             L.gr_momentum_residual_noalloc.restype = ctypes.c_int
+            L.gr_particle_update.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(gr_fields), ctypes.c_double,
+                                             ctypes.c_int]
+            L.gr_particle_update.restype = ctypes.c_int
+            L.gr_kick.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(gr_fields), ctypes.c_double, ctypes.c_int]
+            L.gr_kick.restype = ctypes.c_int
+            L.gr_drift.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(gr_fields), ctypes.c_double]
+            L.gr_drift.restype = ctypes.c_int
+            L.gr_deposit_metric.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.c_double, _P,
+                                            ctypes.POINTER(gr_sources)]
+            L.gr_deposit_metric.restype = ctypes.c_int
             FP = ctypes.POINTER(ctypes.c_float)
             L.gr_net_create.argtypes = [ctypes.c_int, _P, ctypes.c_uint64, ctypes.POINTER(_P)]
             L.gr_net_create.restype = ctypes.c_int
@@ -125,6 +137,9 @@ def lib():
             L.gr_net_train_step.argtypes = [_P, ctypes.POINTER(gr_sources), ctypes.POINTER(gr_fields),
                                             ctypes.c_double, ctypes.c_double, ctypes.c_float, FP]
             L.gr_net_train_step.restype = ctypes.c_int
+            L.gr_net_guess.argtypes = [_P, ctypes.c_int, ctypes.POINTER(gr_sources), ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(gr_fields)]
+            L.gr_net_guess.restype = ctypes.c_int
             L.gr_net_activation.argtypes = [_P, ctypes.c_int, _P, ctypes.c_size_t]
             L.gr_net_activation.restype = ctypes.c_int
             _lib = L
@@ -327,6 +342,35 @@ def gr_momentum_residual_noalloc(n: int, L: float, V, s, res_field=None, stream=
     return r.value
 
 
+def _particles(x, u):
+    np_ = int(x.shape[-1]) if x is not None and x.dim() == 2 else 0
+    if np_ and (tuple(x.shape) != (3, np_) or tuple(u.shape) != (3, np_)):
+        raise ValueError("x and u must both be (3, np)")
+    return np_
+
+
+def gr_particle_update(ctx, x, u, fld: dict, dt: float, flags: int = GR_KICK_SYNC | GR_KICK_OPEN | GR_DRIFT):
+    f = make_fields(fld)
+    _check(lib().gr_particle_update(ctx, _particles(x, u), _ptr(x), _ptr(u), ctypes.byref(f), dt, flags),
+           "gr_particle_update")
+
+
+def gr_kick(ctx, x, u, fld: dict, dt: float, flags: int):
+    f = make_fields(fld)
+    _check(lib().gr_kick(ctx, _particles(x, u), _ptr(x), _ptr(u), ctypes.byref(f), dt, flags), "gr_kick")
+
+
+def gr_drift(ctx, x, u, fld: dict, dt: float):
+    f = make_fields(fld)
+    _check(lib().gr_drift(ctx, _particles(x, u), _ptr(x), _ptr(u), ctypes.byref(f), dt), "gr_drift")
+
+
+def gr_deposit_metric(ctx, x, u, mass: float, psi, src: dict):
+    s = make_sources(src)
+    _check(lib().gr_deposit_metric(ctx, _particles(x, u), _ptr(x), _ptr(u), mass, _ptr(psi), ctypes.byref(s)),
+           "gr_deposit_metric")
+
+
 # ------------------------------------------------------------------ convenience
 class Context:
     """One n^3 periodic grid of side L on the current CUDA device."""
@@ -369,6 +413,18 @@ class Context:
         src = src if src is not None else self.new_sources()
         gr_deposit(self.h, x, u, mass, src)
         return src
+
+    def deposit_metric(self, x, u, mass: float, psi, src: dict | None = None) -> dict:
+        """CIC sources with the Lorentz factor at the conformal factor psi
+        (the previous solution's; None: psi = 1)."""
+        src = src if src is not None else self.new_sources()
+        gr_deposit_metric(self.h, x, u, mass, psi, src)
+        return src
+
+    def particle_update(self, x, u, fld: dict, dt: float, flags: int = GR_KICK_SYNC | GR_KICK_OPEN | GR_DRIFT):
+        """Kicks and drift of the particles (x, u: (3, np) float64 CUDA
+        tensors, updated in place) in the solved fields."""
+        gr_particle_update(self.h, x, u, fld, dt, flags)
 
     def patch_grid(self, n: int) -> dict:
         import torch
@@ -463,6 +519,12 @@ class Net:
     def infer(self, src: dict, fld: dict, rho_hat: float, v_rms: float):
         s, f = make_sources(src), make_fields(fld)
         _check(lib().gr_net_infer(self.h, ctypes.byref(s), rho_hat, v_rms, ctypes.byref(f)), "gr_net_infer")
+
+    def guess(self, n_fine: int, src: dict, fld: dict, rho_hat: float, v_rms: float):
+        """The network's guess on a finer grid (n_fine = n 2^k): sources
+        averaged down, inference, trilinear interpolation back up."""
+        s, f = make_sources(src), make_fields(fld)
+        _check(lib().gr_net_guess(self.h, n_fine, ctypes.byref(s), rho_hat, v_rms, ctypes.byref(f)), "gr_net_guess")
 
     def loss_grad(self, src: dict, target: dict, rho_hat: float, v_rms: float, want_grads=True):
         import numpy as np

@@ -120,3 +120,13 @@ def test_patch_options_marshalling():
     assert o.patch[1].n == 8 and list(o.patch[1].origin) == [4, 5, 6]
     assert not o.patch[0].src.s0 and not o.patch[1].fld.psi
     assert gr.make_opts().npatch == 0 and not gr.make_opts().patch
+
+
+def test_particle_entry_points_reject_bad_arguments_without_gpu():
+    L = gr.lib()
+    f = gr.gr_fields()
+    assert L.gr_particle_update(None, 0, None, None, ctypes.byref(f), 0.1, 7) == gr.GR_ERR_ARG
+    assert L.gr_kick(None, 0, None, None, ctypes.byref(f), 0.1, gr.GR_DRIFT) == gr.GR_ERR_ARG
+    assert "flags" in gr.gr_last_error()
+    assert L.gr_drift(None, 0, None, None, ctypes.byref(f), 0.1) == gr.GR_ERR_ARG
+    assert L.gr_deposit_metric(None, 0, None, None, 1.0, None, None) == gr.GR_ERR_ARG
