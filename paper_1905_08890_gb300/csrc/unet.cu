@@ -55,6 +55,7 @@ struct gr_net {
     // activations [v][c] (index = tensor id) and their gradients
     std::vector<bf16 *> act, grad;
     float *out = nullptr, *tgt = nullptr, *loss = nullptr, *hloss = nullptr;
+    double *coarse_src = nullptr;  // gr_net_guess: four averaged source arrays (allocated on first use)
     std::vector<void *> allocs;
 };
 
@@ -350,6 +351,37 @@ gr_status gr_net_infer(gr_net *net, const gr_sources *s, double rho_hat, double 
     forward(net, s, rho_hat, v_rms);
     gr::net_output(net->out, nvox(net, 0), net->norm + 8, net->norm + 18, field_ptrs(guess), net->st);
     return net_check("gr_net_infer");
+}
+
+gr_status gr_net_guess(gr_net *net, int n_fine, const gr_sources *s, double rho_hat, double v_rms, gr_fields *guess)
+{
+    if (!net || !s || !guess || !s->s0 || !s->s[0] || !s->s[1] || !s->s[2])
+        return nfail(GR_ERR_ARG, "gr_net_guess: NULL argument");
+    if (!(rho_hat > 0) || !(v_rms > 0)) return nfail(GR_ERR_ARG, "gr_net_guess: rho_hat and v_rms must be > 0");
+    int lr = 0;
+    while ((net->n << lr) < n_fine && lr < 8) ++lr;
+    if (n_fine < net->n || (net->n << lr) != n_fine || n_fine > 1024)
+        return nfail(GR_ERR_ARG, "gr_net_guess: n_fine must be the network's n times a power of two, at most 1024");
+    if (lr == 0) return gr_net_infer(net, s, rho_hat, v_rms, guess);
+    const int64_t nv = nvox(net, 0);
+    if (!net->coarse_src && !nalloc(net, &net->coarse_src, 4 * (size_t)nv))
+        return nfail(GR_ERR_NOMEM, "gr_net_guess: cudaMalloc");
+    FieldPtrs in = {}, cs = {};
+    const double *fin[4] = {s->s0, s->s[0], s->s[1], s->s[2]};
+    for (int a = 0; a < 4; a++) {
+        in.p[a] = const_cast<double *>(fin[a]);
+        cs.p[a] = net->coarse_src + a * nv;
+    }
+    gr::avg_down(in, cs, 4, net->lg0, lr, net->st);
+    gr_sources sc = {};
+    sc.s0 = cs.p[0];
+    sc.s[0] = cs.p[1];
+    sc.s[1] = cs.p[2];
+    sc.s[2] = cs.p[3];
+    sc.sigma = nullptr;
+    forward(net, &sc, rho_hat, v_rms);
+    gr::net_output_fine(net->out, net->lg0, lr, net->norm + 8, net->norm + 18, field_ptrs(guess), net->st);
+    return net_check("gr_net_guess");
 }
 
 gr_status gr_net_loss_grad(gr_net *net, const gr_sources *s, const gr_fields *target, double rho_hat, double v_rms,

@@ -39,6 +39,11 @@ void head_back(const __nv_bfloat16 *a, const float *W, const float *out, const f
 void net_target(FieldPtrs fields, int64_t nv, const float *mean, const float *stdv, float *tgt, cudaStream_t st);
 void net_output(const float *out, int64_t nv, const float *mean, const float *stdv, FieldPtrs fields,
                 cudaStream_t st);
+// the first narr arrays of in (fine, extent 2^(lgc + lr)) averaged over r^3 blocks into out (extent 2^lgc)
+void avg_down(FieldPtrs in, FieldPtrs out, int narr, int lgc, int lr, cudaStream_t st);
+// the network output on the 2^lgc grid interpolated to the 2^(lgc + lr) grid as the ten fields
+void net_output_fine(const float *out, int lgc, int lr, const float *mean, const float *stdv, FieldPtrs fields,
+                     cudaStream_t st);
 void adam(float *w, float *m, float *v, const float *g, int64_t cnt, float lr, float b1, float b2, float eps,
           float bc1, float bc2, cudaStream_t st);
 void conv_weights_bf16(const float *w, int cout, int cin, __nv_bfloat16 *wb, __nv_bfloat16 *wt, cudaStream_t st);

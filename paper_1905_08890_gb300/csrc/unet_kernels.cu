@@ -422,6 +422,75 @@ __global__ void k_net_output(const float *__restrict__ out, int64_t nv, const fl
         }
 }
 
+// ---------------------------------------------------------------- guesses on finer grids
+// Sources of a fine grid (extent nc << lr) averaged over the r^3 cells each
+// coarse cell covers (r = 2^lr), FP64; one thread per coarse cell and array.
+__global__ void __launch_bounds__(256)
+    k_avg_down(FieldPtrs in, FieldPtrs out, int narr, int lgc, int lr)
+{
+    pdl_begin();
+    const int64_t nvc = (int64_t)1 << (3 * lgc);
+    const int lgf = lgc + lr, r = 1 << lr;
+    const double inv = 1.0 / (double)((int64_t)1 << (3 * lr));
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nvc * narr;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t >> (3 * lgc));
+        const int64_t v = t & (nvc - 1);
+        const int64_t mc = ((int64_t)1 << lgc) - 1;
+        const int64_t K = v & mc, J = (v >> lgc) & mc, I = v >> (2 * lgc);
+        const double *f = in.p[a];
+        double acc = 0.0;
+        for (int di = 0; di < r; di++)
+            for (int dj = 0; dj < r; dj++) {
+                const int64_t row = ((((I << lr) + di) << lgf) + ((J << lr) + dj)) << lgf;
+                for (int dk = 0; dk < r; dk++) acc += f[row + (K << lr) + dk];
+            }
+        out.p[a][v] = acc * inv;
+    }
+}
+
+// The network's standardised output [vc][10] on the coarse grid, interpolated
+// trilinearly between periodic coarse cell centres to every cell of the fine
+// grid (extent nc << lr) and de-standardised (psi and alpha psi get their 1
+// back): FP32 arithmetic, FP64 stores.  One thread per fine cell.
+__global__ void __launch_bounds__(256)
+    k_net_output_fine(const float *__restrict__ out, int lgc, int lr, const float *__restrict__ mean,
+                      const float *__restrict__ stdv, FieldPtrs fields)
+{
+    pdl_begin();
+    const int lgf = lgc + lr;
+    const int64_t nvf = (int64_t)1 << (3 * lgf);
+    const int mc = (1 << lgc) - 1, mf = (1 << lgf) - 1;
+    const float r = (float)(1 << lr);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nvf; t += (int64_t)gridDim.x * blockDim.x) {
+        const int idx[3] = {(int)(t >> (2 * lgf)), (int)((t >> lgf) & mf), (int)(t & mf)};
+        int lo[3];
+        float w1[3];
+        for (int d = 0; d < 3; d++) {  // coarse position of the fine cell centre, in coarse cells
+            const float c = ((float)idx[d] + 0.5f) / r - 0.5f;
+            const float fl = floorf(c);
+            w1[d] = c - fl;
+            lo[d] = ((int)fl) & mc;
+        }
+        float acc[kNetOut];
+        for (int o = 0; o < kNetOut; o++) acc[o] = 0.0f;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                for (int c = 0; c < 2; c++) {
+                    const float w = (a ? w1[0] : 1.0f - w1[0]) * (b ? w1[1] : 1.0f - w1[1]) *
+                                    (c ? w1[2] : 1.0f - w1[2]);
+                    const int64_t v = ((((int64_t)((lo[0] + a) & mc) << lgc) + ((lo[1] + b) & mc)) << lgc) +
+                                      ((lo[2] + c) & mc);
+                    const float *rec = out + v * kNetOut;
+                    for (int o = 0; o < kNetOut; o++) acc[o] = fmaf(w, rec[o], acc[o]);
+                }
+        for (int o = 0; o < kNetOut; o++) {
+            const double val = (double)(acc[o] * stdv[o] + mean[o]);
+            fields.p[o][t] = o < 2 ? val + 1.0 : val;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- optimiser
 // Adam (Kingma & Ba 2015) on FP32 master weights; bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
 __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
@@ -529,6 +598,19 @@ void net_input(const double *s0, const double *sx, const double *sy, const doubl
                float inv_rv, const float *in_mean, const float *in_std, __nv_bfloat16 *x, cudaStream_t st)
 {
     GR_LAUNCH(k_net_input, cdiv(nv, 256), 256, st, s0, sx, sy, sz, nv, inv_rho, inv_rv, in_mean, in_std, x);
+}
+
+void avg_down(FieldPtrs in, FieldPtrs out, int narr, int lgc, int lr, cudaStream_t st)
+{
+    const int64_t tot = ((int64_t)narr) << (3 * lgc);
+    GR_LAUNCH(k_avg_down, cdiv(tot, 256), 256, st, in, out, narr, lgc, lr);
+}
+
+void net_output_fine(const float *out, int lgc, int lr, const float *mean, const float *stdv, FieldPtrs fields,
+                     cudaStream_t st)
+{
+    const int64_t nvf = (int64_t)1 << (3 * (lgc + lr));
+    GR_LAUNCH(k_net_output_fine, wave_grid(k_net_output_fine, nvf), 256, st, out, lgc, lr, mean, stdv, fields);
 }
 
 void head(const __nv_bfloat16 *a, const float *W, const float *b, int64_t nv, float *out, cudaStream_t st)
