@@ -402,10 +402,48 @@ static void subtract_mean(int n, double *f)
     for (int64_t c = 0; c < cells(n); c++) f[c] -= m;
 }
 
+/* The uniform part of the 2^3 level's error.  The Laplacian annihilates a
+   constant, so a red-black sweep damps the constant error mode of the
+   Helmholtz and psi equations only by 1/(1 + h^2 m / 6) per sweep, m the
+   equation's non-Laplacian coefficient (m = c0; psi: 2 pi s0 / psi^2 +
+   7 AA / (8 psi^8) + 10 pi rho psi^4): slow where m is small (a weak
+   background, e.g. a small Hubble rate in code units).  After each sweep
+   the level therefore takes the constant shift that zeroes the sum of its
+   residuals to first order, u -= sum(f - L(u)) / sum(m). */
+static void zero_mode(const hier_t *H, level_t *L)
+{
+    const int n = L->n;
+    const double ih2 = (double)n * n;
+    double sr = 0.0, sm = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) {
+                int64_t c = ix(n, i, j, k);
+                double u = L->u[c];
+                sr += L->f[c] - op_point(H->kind, u, nbsum(L->u, n, i, j, k), ih2, L->c0[c], L->c1 ? L->c1[c] : 0.0,
+                                         H->rho);
+                if (H->kind == ORC_HELMHOLTZ) {
+                    sm += L->c0[c];
+                } else {
+                    double v = 1.0 + u, v2 = v * v, v4 = v2 * v2;
+                    sm += 2.0 * PI * L->c0[c] / v2 + 7.0 * L->c1[c] / (8.0 * v4 * v4) + 10.0 * PI * H->rho * v4;
+                }
+            }
+    if (!(sm > 0.0)) return;
+    const double shift = -sr / sm; /* L(u + c) = L(u) - m c to first order */
+    for (int64_t c = 0; c < cells(n); c++) L->u[c] += shift;
+}
+
+/* The 2^3 level (Sec. 4.3.1, last paragraph): COARSEST_SWEEPS red-black
+   sweeps, each followed (Helmholtz, psi) by the zero-mode shift above;
+   Poisson: source mean removed before and solution mean after. */
 static void coarsest(const hier_t *H, level_t *L)
 {
     if (H->kind == ORC_POISSON) subtract_mean(L->n, L->f);
-    for (int s = 0; s < COARSEST_SWEEPS; s++) sweep(H, L);
+    for (int s = 0; s < COARSEST_SWEEPS; s++) {
+        sweep(H, L);
+        if (H->kind != ORC_POISSON) zero_mode(H, L);
+    }
     if (H->kind == ORC_POISSON) subtract_mean(L->n, L->u);
 }
 
