@@ -34,7 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gr_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "gr_particles.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "gr_particles.c"), os.path.join(_HERE, "gr_codeunits.c")]
 _OUT_DIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -113,6 +113,10 @@ def lib():
             L.orc_particle_update.restype = None
             L.orc_deposit_metric.argtypes = [I, I64, P, P, D, P, P, P, P, P, P]
             L.orc_deposit_metric.restype = None
+            L.orc_solve_code_units.argtypes = [I, D, D, D, P, P, D, I, P, P, P, P]
+            L.orc_solve_code_units.restype = I
+            L.orc_code_units_residual.argtypes = [I, D, D, D, P, P, P]
+            L.orc_code_units_residual.restype = I
             _lib = L
     return _lib
 
@@ -180,6 +184,46 @@ def particle_update(fld: dict, x: np.ndarray, u: np.ndarray, dt: float, sync=Tru
     g = particle_fields(fld) if fields is None else fields
     npart = x.shape[1]
     lib().orc_particle_update(n, npart, _p(x), _p(u), _p(g), dt, int(sync), int(open_), int(drift))
+
+
+# ---------------------------------------------------------------- code units (Sec. 4.1)
+def solve_code_units(src_code: dict, fld_code: dict, a: float, Omega_m: float, H0: float, tol=1e-10,
+                     max_cycles=50):
+    """The ten-equation solve in code units at scale factor a: code-unit
+    sources (s0, sx, sy, sz, sigma keys: st0, st_i, the trace) and fields
+    (psi key: Psi, apsi key: Phi, the others the code-unit potentials; guesses
+    in, solutions out, in place).  Returns (status, report)."""
+    n = src_code["s0"].shape[0]
+    srcs = [_f64(src_code[k]) for k in SOURCES]
+    for k in FIELDS:
+        assert fld_code[k].dtype == np.float64 and fld_code[k].flags.c_contiguous
+    sp = (ctypes.c_void_p * 5)(*[v.ctypes.data for v in srcs])
+    fp = (ctypes.c_void_p * 10)(*[fld_code[k].ctypes.data for k in FIELDS])
+    cyc = (ctypes.c_int * 10)()
+    r0 = (ctypes.c_double * 10)()
+    r = (ctypes.c_double * 10)()
+    sts = (ctypes.c_int * 10)()
+    st = lib().orc_solve_code_units(n, a, Omega_m, H0, sp, fp, tol, max_cycles, cyc, r0, r, sts)
+    return st, {"cycles": list(cyc), "res0": list(r0), "res": list(r), "status": list(sts)}
+
+
+def code_units_residual(src_code: dict, fld_code: dict, a: float, Omega_m: float, H0: float):
+    """Relative residuals of the paper's printed code-unit equations (solve
+    order: V_x, V_y, V_z, U, Psi, Phi, B^x, B^y, B^z, b)."""
+    n = src_code["s0"].shape[0]
+    srcs = [_f64(src_code[k]) for k in SOURCES]
+    flds = [_f64(fld_code[k]) for k in FIELDS]
+    sp = (ctypes.c_void_p * 5)(*[v.ctypes.data for v in srcs])
+    fp = (ctypes.c_void_p * 10)(*[v.ctypes.data for v in flds])
+    rel = np.zeros(10)
+    if lib().orc_code_units_residual(n, a, Omega_m, H0, sp, fp, _p(rel)) != 0:
+        raise MemoryError("orc_code_units_residual")
+    return rel
+
+
+def code_initial_fields(n: int) -> dict:
+    """The plain guess in code units: every potential 0 (psi = a^(1/2), alpha = 1)."""
+    return {k: _grid(n) for k in FIELDS}
 
 
 # ---------------------------------------------------------------- operators
