@@ -326,6 +326,39 @@ gr_status gr_net_train_step(gr_net *net, const gr_sources *src, const gr_fields 
    count must equal its size. */
 gr_status gr_net_activation(gr_net *net, int tensor, float *host, size_t count);
 
+/* ---- code units (Sec. 4.1) ----------------------------------------------
+   The paper's code units at a fiducial scale factor a: box L = 1, c = G = 1,
+   H0 the Hubble constant today in units of c/L, so the code-unit speed of
+   light is ct = 1/H0 and the critical density rho_c = 3 H0^2 / (8 pi). */
+typedef struct {
+    double a;       /* fiducial scale factor, > 0 */
+    double Omega_m; /* matter density parameter today, > 0 */
+    double Omega_L; /* Lambda density parameter today, >= 0: it sets a(t) (Eqs. 1-Friedmann-code,
+                       2-Friedmann-code) but enters none of the code-unit elliptic equations */
+    double H0;      /* Hubble constant today in units of c / L, > 0 */
+} gr_cosmology;
+/* The ten-equation solve in code units (Eqs. Wi-code-units, H-constraint-MG-1,
+   CMC-MG-1 with Q-function, MDC-code-units; Sec. 4.3.1 Eqs. MG-linear-1a,
+   MG-linear-1, MG-linear-2a, MG-linear-2).  src: the code-unit sources
+   st0 = s0 / (Omega_m rho_c), st_i = s_i / (Omega_m rho_c) and the trace
+   sigt = sum_l st_ll (device, n^3 each, not modified; a deposit with mass
+   m / (Omega_m rho_c) gives them).  fld: the code-unit fields, guesses in and
+   solutions out: the psi slot holds Psi and the apsi slot Phi, defined by
+   alpha = 1 + Phi / (a^2 ct^2), psi = a^(1/2) (1 - Psi / (2 a^2 ct^2)); V,
+   U, B, b hold Vt = a ct^2 V, Ut = a ct^2 U, Bt = a^2 ct B, bt = a^2 ct b
+   (all zero with Psi = Phi = 0 is the plain guess).  The problem is solved
+   as the equivalent a = 1 geometric problem (sources s0 / a, s_i / a^2,
+   sigma / a^3 of the geometric sources, rho_hat = Omega_m rho_c / a; the
+   fields psi / a^(1/2), alpha psi / a^(1/2), V / a^2, U / a^2, a B, a b),
+   with gr_solve_constraints and opts (its rho_hat and S_hat are replaced;
+   npatch and host_out must be 0 / NULL); rep and the return status are
+   that solve's, its residuals those of the a = 1 problem.  The context's box
+   side must be 1.  Scratch: the context's first-use allocation of 5 n^3
+   doubles.  GR_ERR_ARG: NULL pointers, parameters out of range, L != 1,
+   patches or host_out requested. */
+gr_status gr_solve_code_units(gr_ctx *ctx, const gr_cosmology *cosmo, const gr_sources *src, gr_fields *fld,
+                              const gr_opts *opts, gr_report *rep);
+
 /* ---- the particle update around the solve (Sec. 4.2 steps 3 and 6-8;
    Sec. 4.4; Sec. 4.5; App. A) ------------------------------------------
    Geometric units with a = 1, c = 1: the spatial metric is psi^4 delta_ij,

@@ -120,8 +120,10 @@ struct gr_ctx {
     std::vector<void *> palloc;
     double *pdev = nullptr, *phost = nullptr;
     bool pdf = false;  // the patches relax in double-float (mixed modes) rather than FP64
-    // particle update: the 20 FP32 interpolated quantities (allocated on first use)
+    // particle update: the per-cell records of 20 FP32 quantities (allocated on first use)
     float *pf = nullptr;
+    // code units: the scaled sources of the a = 1 problem (allocated on first use)
+    double *cu_src = nullptr;
 };
 
 namespace {
@@ -1542,8 +1544,8 @@ gr_status gr_particle_update(gr_ctx *c, int64_t np, double *x, double *u, const 
         gr_status st = dalloc(c, &c->pf, 20 * N);
         if (st != GR_OK) return st;
     }
-    c->a_fmt = 0;  // A6 serves as the FP64 scratch of alpha and beta
-    gr::particle_fields(c->n, c->L, fl->psi, fl->apsi, fl->B[0], fl->B[1], fl->B[2], fl->b, c->A6, c->A6 + N, c->pf,
+    c->a_fmt = 0;  // A6 serves as the FP32 scratch of pass 1 (5 n^3 floats)
+    gr::particle_fields(c->n, c->L, fl->psi, fl->apsi, fl->B[0], fl->B[1], fl->B[2], fl->b, (float *)c->A6, c->pf,
                         c->st);
     gr::particle_update(c->n, c->L, np, x, u, c->pf, dt, flags, c->st);
     return cuda_check("gr_particle_update");
@@ -1581,6 +1583,62 @@ gr_status gr_deposit_metric(gr_ctx *c, int64_t np, const double *x, const double
     gr::deposit_metric(c->n, c->L, np, x, u, mass, psi, out->s0, out->s[0], out->s[1], out->s[2], out->sigma, c->st);
     c->rho_dep = mass * (double)np / (c->L * c->L * c->L);
     return cuda_check("gr_deposit_metric");
+}
+
+gr_status gr_solve_code_units(gr_ctx *c, const gr_cosmology *cm, const gr_sources *s, gr_fields *fl, const gr_opts *o,
+                              gr_report *rep)
+{
+    g_err.clear();
+    if (!c || !cm) return fail(GR_ERR_ARG, "ctx or cosmology is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
+    if (o->npatch != 0 || o->host_out) return fail(GR_ERR_ARG, "gr_solve_code_units: no patches, no host_out");
+    if (c->L != 1.0) return fail(GR_ERR_ARG, "gr_solve_code_units: the context's box side must be 1");
+    const double a = cm->a, Om = cm->Omega_m, H0 = cm->H0;
+    if (!(a > 0) || !(Om > 0) || !(H0 > 0) || !(cm->Omega_L >= 0) || !std::isfinite(a) || !std::isfinite(Om) ||
+        !std::isfinite(H0) || !std::isfinite(cm->Omega_L))
+        return fail(GR_ERR_ARG, "gr_solve_code_units: need a, Omega_m, H0 > 0 and Omega_L >= 0, finite");
+    const int64_t N = (int64_t)c->n * c->n * c->n;
+    if (!c->cu_src) {
+        gr_status st = dalloc(c, &c->cu_src, 5 * (size_t)N);
+        if (st != GR_OK) return st;
+    }
+    const double ct = 1.0 / H0, q = Om * 3.0 * H0 * H0 / (8.0 * gr::kPi), a2c2 = a * a * ct * ct;
+    gr::CuScale sc = {};
+    sc.s[0] = q / a;
+    sc.s[1] = sc.s[2] = sc.s[3] = q / (a * a);
+    sc.s[4] = q / (a * a * a);
+    for (int f = 2; f < 10; f++) sc.f[f] = f < 6 ? 1.0 / (a * a * a * ct * ct) : 1.0 / (a * ct);
+    gr::CuPtrs sin = {}, sout = {}, fp = {};
+    const double *sp[5] = {s->s0, s->s[0], s->s[1], s->s[2], s->sigma};
+    for (int k = 0; k < 5; k++) {
+        sin.p[k] = const_cast<double *>(sp[k]);
+        sout.p[k] = c->cu_src + k * N;
+    }
+    for (int f = 0; f < GR_NEQ; f++) fp.p[f] = nullptr;
+    fp.p[0] = fl->psi;
+    fp.p[1] = fl->apsi;
+    for (int d = 0; d < 3; d++) {
+        fp.p[2 + d] = fl->V[d];
+        fp.p[6 + d] = fl->B[d];
+    }
+    fp.p[5] = fl->U;
+    fp.p[9] = fl->b;
+    gr::code_units_in(N, sin, sout, sc, fp, a2c2, c->st);
+    gr_sources s1 = {};
+    s1.s0 = sout.p[0];
+    for (int d = 0; d < 3; d++) s1.s[d] = sout.p[1 + d];
+    s1.sigma = sout.p[4];
+    gr_opts o1 = *o;
+    o1.rho_hat = q / a;
+    o1.S_hat = 0.0;
+    gr_status st = gr_solve_constraints(c, &s1, fl, &o1, rep);
+    std::string err = g_err;
+    gr::code_units_out(N, sc, fp, a2c2, c->st);
+    gr_status st2 = cuda_check("gr_solve_code_units");
+    if (st == GR_OK) return st2;
+    g_err = err;
+    return st;
 }
 
 }  // extern "C"

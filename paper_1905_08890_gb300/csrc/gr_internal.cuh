@@ -227,8 +227,11 @@ void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st, int r
 // FP32 coarse = 8-child average of fine (a right-hand side going down)
 void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st);
 
-// The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage);
-// Poisson: source mean removed before and solution mean after.  KHELM reads
+// The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage),
+// each followed (KHELM, KPSI) by the constant shift that zeroes the sum of the
+// eight residuals to first order (the Laplacian leaves that mode to the weak
+// non-Laplacian coefficient alone); Poisson: source mean removed before and
+// solution mean after.  KHELM reads
 // c0 = m (the inverse diagonal is formed in FP64).
 template <typename T>
 void coarsest(int kind, T *u, T *f, const T *c0, const T *c1, double h2, double ih2, double rho, cudaStream_t st);
@@ -355,18 +358,33 @@ void shift_weight(int n, const double *psi, const double *apsi, double *w, cudaS
 void shift_source(int n, double inv2h, const double *A, const double *w, int comp, double *f, cudaStream_t st);
 
 // ---- particles (particle_kernels.cu) ----------------------------------------
-// The 20 FP32 arrays of the particle update (alpha - 1, psi - 1, beta^j,
-// D_i alpha, D_i psi, D_i beta^j at index 11 + 3 j + i; each n^3) from the
-// natural FP64 fields; alpha (n^3) and beta (3 n^3) are FP64 scratch.
+// The per-cell records of the particle update: 20 FP32 quantities (alpha - 1,
+// psi - 1, beta^j, D_i alpha, D_i psi, D_i beta^j at 11 + 3 j + i), 80 bytes
+// per cell (rec: 20 n^3 floats, 16-byte aligned), from the natural FP64
+// fields; dev is FP32 scratch of 5 n^3 floats.
 void particle_fields(int n, double L, const double *psi, const double *apsi, const double *Bx, const double *By,
-                     const double *Bz, const double *b, double *alpha, double *beta, float *pf, cudaStream_t st);
+                     const double *Bz, const double *b, float *dev, float *rec, cudaStream_t st);
 // Kicks and drift of np particles (x, u: [3][np] device SoA) with the flags
 // GR_KICK_SYNC, GR_KICK_OPEN, GR_DRIFT.
-void particle_update(int n, double L, int64_t np, double *x, double *u, const float *pf, double dt, int flags,
+void particle_update(int n, double L, int64_t np, double *x, double *u, const float *rec, double dt, int flags,
                      cudaStream_t st);
 // The deposit with W = sqrt(1 + psi^-4 |u|^2), psi interpolated at the particle.
 void deposit_metric(int n, double L, int64_t np, const double *x, const double *u, double mass, const double *psi,
                     double *s0, double *sx, double *sy, double *sz, double *sig, cudaStream_t st);
+
+// ---- code units (codeunits.cu) ----------------------------------------------
+struct CuPtrs {
+    double *p[10];  // sources: s0 s_x s_y s_z sigma; fields: psi apsi V_x V_y V_z U B^x B^y B^z b
+};
+struct CuScale {
+    double s[5];   // source scales (code units -> the a = 1 problem)
+    double f[10];  // field scales of the potentials (entries 2..9)
+};
+// code-unit sources -> scaled copies; code-unit fields -> the a = 1 form, in place
+void code_units_in(int64_t N, const CuPtrs &src_in, const CuPtrs &src_out, const CuScale &sc, const CuPtrs &fld,
+                   double a2c2, cudaStream_t st);
+// the a = 1 solution -> code-unit fields, in place
+void code_units_out(int64_t N, const CuScale &sc, const CuPtrs &fld, double a2c2, cudaStream_t st);
 
 // ---------------------------------------------------------------- nested patches
 // Base level as the patch kernels see it: natural FP64 fields (PB_NAT, nat),

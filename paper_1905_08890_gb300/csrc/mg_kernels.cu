@@ -577,6 +577,37 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
             }
             __syncthreads();
         }
+        if (KIND != KPOISSON) {
+            // zero mode: the constant shift that zeroes the sum of the eight
+            // residuals to first order, u -= sum(f - L(u)) / sum(m), with m the
+            // non-Laplacian coefficient (a sweep damps the constant error only
+            // by 1/(1 + h^2 m / 6), slowly where m is small)
+            __shared__ double zr[8], zm[8];
+            if (t < 8) {
+                const int c = t >> 2, i = (t >> 1) & 1, j = t & 1, o = 4 * (c ^ 1);
+                const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
+                const double uc = su[t];
+                if (KIND == KHELM) {
+                    zr[t] = sf[t] - ((nb - 6.0 * uc) * ih2 - s0[t] * uc);
+                    zm[t] = s0[t];
+                } else {
+                    const double v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
+                    zr[t] = sf[t] - ((nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[t] / v + s1[t] / (8.0 * v4 * v2 * v) -
+                                     2.0 * kPi * rho * v4 * v);
+                    zm[t] = 2.0 * kPi * s0[t] / v2 + 7.0 * s1[t] / (8.0 * v4 * v4) + 10.0 * kPi * rho * v4;
+                }
+            }
+            __syncthreads();
+            if (t < 8) {
+                double sr = 0.0, sm = 0.0;
+                for (int q = 0; q < 8; q++) {
+                    sr += zr[q];
+                    sm += zm[q];
+                }
+                if (sm > 0.0) su[t] -= sr / sm;
+            }
+            __syncthreads();
+        }
     }
     if (KIND == KPOISSON && t == 0) {
         double m = 0.0;
@@ -1057,6 +1088,22 @@ __device__ void tail_coarsest(const TailLevel &Z)
                     const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
                     su[id] = KIND == KPOISSON ? (nb - h2 * sf[id]) / 6.0 : (nb - h2 * sf[id]) / (6.0 + h2 * sm[id]);
                 }
+                __syncwarp();
+            }
+            if (KIND == KHELM) {  // the zero-mode shift of k_coarsest
+                double zr = 0.0, zm = 0.0;
+                if (t < 8) {
+                    const int c = t >> 2, i = (t >> 1) & 1, j = t & 1, o = 4 * (c ^ 1);
+                    const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
+                    zr = sf[t] - ((nb - 6.0 * su[t]) / h2 - sm[t] * su[t]);
+                    zm = sm[t];
+                }
+                __syncwarp();
+                for (int off = 4; off > 0; off >>= 1) {
+                    zr += __shfl_xor_sync(0xffffffffu, zr, off);
+                    zm += __shfl_xor_sync(0xffffffffu, zm, off);
+                }
+                if (t < 8 && zm > 0.0) su[t] -= zr / zm;
                 __syncwarp();
             }
         }

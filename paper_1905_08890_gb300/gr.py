@@ -67,7 +67,7 @@ _lib = None
 _lock = threading.Lock()
 EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_deposit_patches", "gr_solve_constraints",
             "gr_vcycle", "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc",
-            "gr_particle_update", "gr_kick", "gr_drift", "gr_deposit_metric")
+            "gr_particle_update", "gr_kick", "gr_drift", "gr_deposit_metric", "gr_solve_code_units")
 GR_KICK_SYNC, GR_KICK_OPEN, GR_DRIFT = 1, 2, 4
 
 
@@ -115,6 +115,10 @@ def lib():
             L.gr_deposit_metric.argtypes = [_P, ctypes.c_int64, _P, _P, ctypes.c_double, _P,
                                             ctypes.POINTER(gr_sources)]
             L.gr_deposit_metric.restype = ctypes.c_int
+            L.gr_solve_code_units.argtypes = [_P, ctypes.POINTER(gr_cosmology), ctypes.POINTER(gr_sources),
+                                              ctypes.POINTER(gr_fields), ctypes.POINTER(gr_opts),
+                                              ctypes.POINTER(gr_report)]
+            L.gr_solve_code_units.restype = ctypes.c_int
             FP = ctypes.POINTER(ctypes.c_float)
             L.gr_net_create.argtypes = [ctypes.c_int, _P, ctypes.c_uint64, ctypes.POINTER(_P)]
             L.gr_net_create.restype = ctypes.c_int
@@ -342,6 +346,11 @@ def gr_momentum_residual_noalloc(n: int, L: float, V, s, res_field=None, stream=
     return r.value
 
 
+class gr_cosmology(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("Omega_m", ctypes.c_double), ("Omega_L", ctypes.c_double),
+                ("H0", ctypes.c_double)]
+
+
 def _particles(x, u):
     np_ = int(x.shape[-1]) if x is not None and x.dim() == 2 else 0
     if np_ and (tuple(x.shape) != (3, np_) or tuple(u.shape) != (3, np_)):
@@ -451,6 +460,23 @@ class Context:
     def solve(self, src, fld, **kw) -> dict:
         allow = kw.pop("allow_noconv", False)
         return gr_solve_constraints(self.h, src, fld, make_opts(**kw), allow_noconv=allow)
+
+    def solve_code_units(self, src, fld, a: float, Omega_m: float, H0: float, Omega_L: float = 0.0, **kw) -> dict:
+        """The ten-equation solve in the paper's code units at scale factor a
+        (include/gr.h gr_solve_code_units): src holds the code-unit sources
+        (keys as for solve), fld the code-unit fields (psi key: Psi, apsi key:
+        Phi, the others the code-unit potentials), guesses in, solutions out."""
+        allow = kw.pop("allow_noconv", False)
+        cm = gr_cosmology(a, Omega_m, Omega_L, H0)
+        o = make_opts(**kw)
+        s, f = make_sources(src), make_fields(fld)
+        r = gr_report()
+        st = lib().gr_solve_code_units(self.h, ctypes.byref(cm), ctypes.byref(s), ctypes.byref(f), ctypes.byref(o),
+                                       ctypes.byref(r))
+        _check(st, "gr_solve_code_units", allow=(GR_ERR_NOCONV,) if allow else ())
+        d = report_dict(r)
+        d["status_code"] = st
+        return d
 
     def vcycle(self, eq: int, src, fld, **kw) -> float:
         return gr_vcycle(self.h, eq, src, fld, make_opts(**kw))

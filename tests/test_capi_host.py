@@ -130,3 +130,9 @@ def test_particle_entry_points_reject_bad_arguments_without_gpu():
     assert "flags" in gr.gr_last_error()
     assert L.gr_drift(None, 0, None, None, ctypes.byref(f), 0.1) == gr.GR_ERR_ARG
     assert L.gr_deposit_metric(None, 0, None, None, 1.0, None, None) == gr.GR_ERR_ARG
+
+
+def test_code_unit_entry_point_rejects_bad_arguments_without_gpu():
+    o = gr.make_opts()
+    cm = gr.gr_cosmology(1.0, 1.0, 0.0, 1.0 / 3.0)
+    assert gr.lib().gr_solve_code_units(None, ctypes.byref(cm), None, None, ctypes.byref(o), None) == gr.GR_ERR_ARG
