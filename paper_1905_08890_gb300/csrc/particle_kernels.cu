@@ -16,16 +16,23 @@
 // moves x by dt (alpha psi^-4 u / W - beta) with the fields at the old
 // position (App. A Eqs. GR-D, V_exp).
 //
-// Design.  The fields and their 3-point central differences (the paper's
-// gradient stencil) are formed once per update on the grid in FP64 and
-// stored as 20 FP32 arrays (alpha - 1, psi - 1, beta^j, D_i alpha, D_i psi,
-// D_i beta^j); each particle gathers them with cloud-in-cell weights and runs
-// the substeps in FP32, accumulating its velocity change in FP32 and adding
-// it to the FP64 velocity once.  Positions, the cell index and the
-// cloud-in-cell fractions stay FP64 (a fraction loses nothing when rounded
-// to FP32 afterwards).  GB300 issues FP64 at 1/58 of the FP32 rate, so this
-// keeps the per-particle work off the FP64 pipe; the FP32 quantities carry a
-// relative error of a few 2^-24, far below the O(h^2) of the interpolation.
+// Design.  Pass 1 forms alpha - 1 = (alpha psi - psi)/psi, psi - 1 and
+// beta^j = B^j + D_j b per cell (the differences in FP64, the quotient and the
+// stores in FP32: deviations keep their relative precision); pass 2 forms the
+// 3-point central differences (the paper's gradient stencil) of those FP32
+// arrays and stores, per cell, one 80-byte record of the 20 quantities
+// (alpha - 1, psi - 1, beta^j, D_i alpha, D_i psi, D_i beta^j), so that a
+// particle's cloud-in-cell gather reads eight records with five 16-byte
+// loads each.  Each particle runs the substeps in FP32, accumulating its
+// velocity change in FP32 and adding it to the FP64 velocity once;
+// positions, the cell index and the cloud-in-cell fractions stay FP64 (a
+// fraction loses nothing when rounded to FP32 afterwards).  GB300 issues
+// FP64 at 1/58 of the FP32 rate, so this keeps the per-cell and per-particle
+// work off the FP64 pipe.  Error: the gathered values carry a few 2^-24 of
+// their own size; a central difference of FP32 deviations carries 2^-24 of
+// the deviation over kh (the field's wavenumber times h), about 1e-6 of the
+// gradient for grid-scale structure, far below the O(h^2) of the
+// interpolation.
 #include <cuda_runtime.h>
 
 #include "../../include/gr.h"
@@ -45,11 +52,12 @@ int log2i(int n)
     return l;
 }
 
-// pass 1 (FP64, natural layout): alpha = apsi / psi and beta^j = B^j + D_j b
+// pass 1 (natural layout): d[0] = alpha - 1, d[1] = psi - 1,
+// d[2 + j] = beta^j = B^j + D_j b, FP32 (n^3 each)
 __global__ void __launch_bounds__(kBlock)
-    k_pf_alpha_beta(int lgn, double inv2h, const double *__restrict__ psi, const double *__restrict__ apsi,
-                    const double *__restrict__ Bx, const double *__restrict__ By, const double *__restrict__ Bz,
-                    const double *__restrict__ b, double *__restrict__ alpha, double *__restrict__ beta)
+    k_pf_dev(int lgn, double inv2h, const double *__restrict__ psi, const double *__restrict__ apsi,
+             const double *__restrict__ Bx, const double *__restrict__ By, const double *__restrict__ Bz,
+             const double *__restrict__ b, float *__restrict__ d)
 {
     pdl_begin();
     const int m = (1 << lgn) - 1;
@@ -62,20 +70,18 @@ __global__ void __launch_bounds__(kBlock)
         const int64_t yp = plane + ((int64_t)((j + 1) & m) << lgn) + k;
         const int64_t ym = plane + ((int64_t)((j - 1) & m) << lgn) + k;
         const int64_t zp = row + ((k + 1) & m), zm = row + ((k - 1) & m);
-        alpha[t] = apsi[t] / psi[t];
-        beta[t] = Bx[t] + (b[xp] - b[xm]) * inv2h;
-        beta[N + t] = By[t] + (b[yp] - b[ym]) * inv2h;
-        beta[2 * N + t] = Bz[t] + (b[zp] - b[zm]) * inv2h;
+        const double ps = psi[t];
+        d[t] = (float)(apsi[t] - ps) / (float)ps;
+        d[N + t] = (float)(ps - 1.0);
+        d[2 * N + t] = (float)fma(b[xp] - b[xm], inv2h, Bx[t]);
+        d[3 * N + t] = (float)fma(b[yp] - b[ym], inv2h, By[t]);
+        d[4 * N + t] = (float)fma(b[zp] - b[zm], inv2h, Bz[t]);
     }
 }
 
-// pass 2: the 20 FP32 arrays of the gather: alpha - 1 and psi - 1 (so the
-// gathered FP32 value keeps its precision relative to the deviation), beta^j
-// and the central differences, each difference formed in FP64 and scaled by
-// 1/2h (a power of two) after the rounding to FP32
+// pass 2: the 80-byte record of every cell from the five FP32 arrays of pass 1
 __global__ void __launch_bounds__(kBlock)
-    k_pf_grad(int lgn, float inv2h, const double *__restrict__ alpha, const double *__restrict__ psi,
-              const double *__restrict__ beta, float *__restrict__ pf)
+    k_pf_grad(int lgn, float inv2h, const float *__restrict__ d, float4 *__restrict__ rec)
 {
     pdl_begin();
     const int m = (1 << lgn) - 1;
@@ -90,18 +96,20 @@ __global__ void __launch_bounds__(kBlock)
         nb[1][1] = plane + ((int64_t)((j - 1) & m) << lgn) + k;
         nb[2][0] = row + ((k + 1) & m);
         nb[2][1] = row + ((k - 1) & m);
-        pf[Q_ALPHA * N + t] = (float)(alpha[t] - 1.0);
-        pf[Q_PSI * N + t] = (float)(psi[t] - 1.0);
+        float q[Q_N];
 #pragma unroll
-        for (int q = 0; q < 3; q++) pf[(Q_BETA + q) * N + t] = (float)beta[q * N + t];
+        for (int v = 0; v < 5; v++) q[v] = d[v * N + t];  // alpha - 1, psi - 1, beta^x, beta^y, beta^z
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            pf[(Q_DALPHA + a) * N + t] = (float)(alpha[nb[a][0]] - alpha[nb[a][1]]) * inv2h;
-            pf[(Q_DPSI + a) * N + t] = (float)(psi[nb[a][0]] - psi[nb[a][1]]) * inv2h;
+            q[Q_DALPHA + a] = (d[nb[a][0]] - d[nb[a][1]]) * inv2h;
+            q[Q_DPSI + a] = (d[N + nb[a][0]] - d[N + nb[a][1]]) * inv2h;
 #pragma unroll
-            for (int q = 0; q < 3; q++)
-                pf[(Q_DBETA + 3 * q + a) * N + t] = (float)(beta[q * N + nb[a][0]] - beta[q * N + nb[a][1]]) * inv2h;
+            for (int c = 0; c < 3; c++)
+                q[Q_DBETA + 3 * c + a] = (d[(2 + c) * N + nb[a][0]] - d[(2 + c) * N + nb[a][1]]) * inv2h;
         }
+        float4 *r = rec + 5 * t;
+#pragma unroll
+        for (int v = 0; v < 5; v++) r[v] = make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
     }
 }
 
@@ -138,13 +146,12 @@ __device__ __forceinline__ void substep(int j, float hdt, const float *q, const 
 // particles the cells in flight are a few planes that L2 holds).
 __global__ void __launch_bounds__(kBlock)
     k_particle_update(int lgn, double invh, int64_t np, double *__restrict__ x, double *__restrict__ u,
-                      const float *__restrict__ pf, float hdt, double dt, int flags)
+                      const float4 *__restrict__ rec, float hdt, double dt, int flags)
 {
     pdl_begin();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
     const int m = (1 << lgn) - 1;
-    const int64_t N = (int64_t)1 << (3 * lgn);
     double xd[3];
     int lo[3];
     float fw[3][2];
@@ -170,9 +177,15 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float w = wab * fw[2][c];
-                const int64_t id = row + ((lo[2] + c) & m);
+                const float4 *r = rec + 5 * (row + ((lo[2] + c) & m));
 #pragma unroll
-                for (int k = 0; k < Q_N; k++) q[k] = fmaf(w, __ldg(pf + k * N + id), q[k]);
+                for (int v = 0; v < 5; v++) {
+                    const float4 g = __ldg(r + v);
+                    q[4 * v] = fmaf(w, g.x, q[4 * v]);
+                    q[4 * v + 1] = fmaf(w, g.y, q[4 * v + 1]);
+                    q[4 * v + 2] = fmaf(w, g.z, q[4 * v + 2]);
+                    q[4 * v + 3] = fmaf(w, g.w, q[4 * v + 3]);
+                }
             }
         }
     const double ud[3] = {u[p], u[np + p], u[2 * np + p]};
@@ -205,8 +218,9 @@ __global__ void __launch_bounds__(kBlock)
 
 // Deposit with the Lorentz factor at psi: W = sqrt(1 + psi^-4 |u|^2), psi
 // at the particle by cloud-in-cell in FP64.  Charges as k_deposit:
-// s0 += q W w, s_l += q u_l w, sigma += q |u|^2 / W w; the products charge x
-// weight in FP64.
+// s0 += q W w, s_l += q u_l w, sigma += q |u|^2 / W w, the forty products
+// charge x weight as double-float products (relative error about 2^-46)
+// joined for the FP64 atomic adds, as in the plain deposit.
 __global__ void __launch_bounds__(kBlock)
     k_deposit_metric(int lgn, double invh, int64_t np, const double *__restrict__ x, const double *__restrict__ u,
                      double q, const double *__restrict__ psi, double *__restrict__ s0, double *__restrict__ sx,
@@ -242,7 +256,8 @@ __global__ void __launch_bounds__(kBlock)
     const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
     const double w2 = fma(ip2 * ip2, u2, 1.0);
     const double rw = rsqrt(w2);
-    const double Q[5] = {q * (w2 * rw), q * ux, q * uy, q * uz, (q * u2) * rw};
+    const df Q[5] = {split_double(q * (w2 * rw)), split_double(q * ux), split_double(q * uy), split_double(q * uz),
+                     split_double((q * u2) * rw)};
     double *const out[5] = {s0, sx, sy, sz, sig};
 #pragma unroll
     for (int a = 0; a < 2; a++)
@@ -252,10 +267,10 @@ __global__ void __launch_bounds__(kBlock)
             const int64_t row = ((int64_t)((((lo[0] + a) & m) << lgn) + ((lo[1] + b) & m))) << lgn;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const double w = wab * fw[2][c];
+                const df w = split_double(wab * fw[2][c]);
                 const int64_t id = row + ((lo[2] + c) & m);
 #pragma unroll
-                for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, Q[k] * w);
+                for (int k = 0; k < 5; k++) atomicAdd(out[k] + id, join_double(df_mul(Q[k], w)));
             }
         }
 }
@@ -263,25 +278,23 @@ __global__ void __launch_bounds__(kBlock)
 }  // namespace
 
 void particle_fields(int n, double L, const double *psi, const double *apsi, const double *Bx, const double *By,
-                     const double *Bz, const double *b, double *alpha, double *beta, float *pf, cudaStream_t st)
+                     const double *Bz, const double *b, float *dev, float *rec, cudaStream_t st)
 {
     const int lgn = log2i(n);
     const int64_t N = (int64_t)n * n * n;
     const double inv2h = 0.5 * n / L;
-    GR_LAUNCH(k_pf_alpha_beta, wave_grid(k_pf_alpha_beta, N), kBlock, st, lgn, inv2h, psi, apsi, Bx, By, Bz, b,
-              alpha, beta);
-    GR_LAUNCH(k_pf_grad, wave_grid(k_pf_grad, N), kBlock, st, lgn, (float)inv2h, (const double *)alpha, psi,
-              (const double *)beta, pf);
+    GR_LAUNCH(k_pf_dev, wave_grid(k_pf_dev, N), kBlock, st, lgn, inv2h, psi, apsi, Bx, By, Bz, b, dev);
+    GR_LAUNCH(k_pf_grad, wave_grid(k_pf_grad, N), kBlock, st, lgn, (float)inv2h, (const float *)dev, (float4 *)rec);
 }
 
-void particle_update(int n, double L, int64_t np, double *x, double *u, const float *pf, double dt, int flags,
+void particle_update(int n, double L, int64_t np, double *x, double *u, const float *rec, double dt, int flags,
                      cudaStream_t st)
 {
     if (np <= 0) return;
     const int64_t blocks = (np + kBlock - 1) / kBlock;
     const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
-    GR_LAUNCH(k_particle_update, g, kBlock, st, log2i(n), (double)n / L, np, x, u, pf, (float)(0.5 * dt), dt,
-              flags);
+    GR_LAUNCH(k_particle_update, g, kBlock, st, log2i(n), (double)n / L, np, x, u, (const float4 *)rec,
+              (float)(0.5 * dt), dt, flags);
 }
 
 void deposit_metric(int n, double L, int64_t np, const double *x, const double *u, double mass, const double *psi,
