@@ -187,6 +187,56 @@ def oracle_time_to_residual(src_np, rho_hat, tol):
     return st, secs, rep["cycles"], updates
 
 
+def profile_case(case, n=None):
+    """One small workload for an ncu capture (two or three repetitions after the
+    set-up; prints one line of CUDA-event timings, not a bench value):
+      mixed      the headline double-float solve at n^3 (default 128), lognormal rms 5, tol 1e-8
+      fp64       the plain FP64 solve at n^3 (default 128: lognormal rms 1, rms |u| 0.003, tol 1e-10)
+      unet       three inferences of the trained network at 128^3 (held-out seed 5000)
+      particles  three particle updates and three deposits with the metric at n^3 (default 512)"""
+    import torch
+
+    from paper_1905_08890_gb300 import gr, learn, synth
+
+    torch.cuda.set_device(0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = []
+
+    def timed(fn, reps):
+        for _ in range(reps):
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            out.append(round(ev[0].elapsed_time(ev[1]), 3))
+
+    if case == "unet":
+        ctx = gr.Context(learn.N)
+        net = learn.load(learn.WEIGHTS)
+        src, rho = learn.sources(ctx, 5000)
+        fld = ctx.initial_fields()
+        timed(lambda: net.infer(src, fld, rho, learn.V_RMS), 3)
+        print(json.dumps({"case": case, "n": learn.N, "inference_ms": out}))
+        return
+    fp64 = case == "fp64"
+    n = n or (512 if case == "particles" else 128)
+    seed, sigma, tol = (2, 1.0, 1e-10) if fp64 else (4, 5.0, 1e-8)
+    x, u, mass = synth.zeldovich_torch(n, seed, sigma, 0.003, True)
+    ctx = gr.Context(n)
+    src = ctx.deposit(x, u, mass)
+    opts = dict(tol=tol, max_cycles=60, prec="fp64" if fp64 else "mixed_df", rho_hat=mass * n ** 3)
+    fld = ctx.initial_fields()
+    if case in ("mixed", "fp64"):
+        timed(lambda: ctx.solve(src, ctx.initial_fields(), **opts), 2)
+        print(json.dumps({"case": case, "n": n, "solve_ms": out}))
+        return
+    ctx.solve(src, fld, **opts)
+    dt = 0.05 / n / 0.003
+    timed(lambda: ctx.particle_update(x, u, fld, dt), 3)
+    timed(lambda: ctx.deposit_metric(x, u, mass, fld["psi"], src), 3)
+    print(json.dumps({"case": case, "n": n, "particle_update_ms": out[:3], "deposit_metric_ms": out[3:]}))
+
+
 def cpu_worker(folder):
     """The CPU legs in a process of their own that never touches CUDA (so the
     oracle runs on the host as it does in the reference arm): the bounded
@@ -255,12 +305,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-timestep", action="store_true", help="skip the full timestep (deposit, solve, particle update)")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--case", default=None, choices=["mixed", "fp64", "unet", "particles"],
+                    help="run one small profiling case instead of the bench (the commands of profiles/*.md)")
+    ap.add_argument("--n", type=int, default=None, help="grid of --case")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison at 128^3")
     ap.add_argument("--no-patches", action="store_true",
                     help="skip the composite solve with two nested 128^3 refinement patches")
     args = ap.parse_args()
     if args.cpu_worker:
         return cpu_worker(args.cpu_worker)
+    if args.case:
+        return profile_case(args.case, args.n)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
