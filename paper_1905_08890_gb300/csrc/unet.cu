@@ -199,12 +199,17 @@ void backward(gr_net *net)
     back(0, -1);
 }
 
-gr_status net_check(const char *where)
+gr_status net_check(const char *where, cudaStream_t st = nullptr)
 {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         char buf[256];
         snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+        return nfail(GR_ERR_CUDA, buf);
+    }
+    if (st && gr::conv3d_tc_error(st) != 0) {  // synchronises the network's stream
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s: a bounded wait of the tcgen05 convolution ran out", where);
         return nfail(GR_ERR_CUDA, buf);
     }
     return GR_OK;
@@ -350,7 +355,7 @@ gr_status gr_net_infer(gr_net *net, const gr_sources *s, double rho_hat, double 
     if (!(rho_hat > 0) || !(v_rms > 0)) return nfail(GR_ERR_ARG, "gr_net_infer: rho_hat and v_rms must be > 0");
     forward(net, s, rho_hat, v_rms);
     gr::net_output(net->out, nvox(net, 0), net->norm + 8, net->norm + 18, field_ptrs(guess), net->st);
-    return net_check("gr_net_infer");
+    return net_check("gr_net_infer", net->st);
 }
 
 gr_status gr_net_guess(gr_net *net, int n_fine, const gr_sources *s, double rho_hat, double v_rms, gr_fields *guess)
@@ -397,7 +402,7 @@ gr_status gr_net_loss_grad(gr_net *net, const gr_sources *s, const gr_fields *ta
         cudaMemcpyAsync(host_grads, net->grads, net->nparams * sizeof(float), cudaMemcpyDeviceToHost, net->st);
     cudaStreamSynchronize(net->st);
     if (loss_out) *loss_out = *net->hloss;
-    return net_check("gr_net_loss_grad");
+    return net_check("gr_net_loss_grad", net->st);
 }
 
 gr_status gr_net_train_step(gr_net *net, const gr_sources *s, const gr_fields *target, double rho_hat, double v_rms,
@@ -420,7 +425,7 @@ gr_status gr_net_train_step(gr_net *net, const gr_sources *s, const gr_fields *t
         cudaStreamSynchronize(net->st);
         *loss_out = *net->hloss;
     }
-    st = net_check("gr_net_train_step");
+    st = net_check("gr_net_train_step", net->st);
     return st;
 }
 

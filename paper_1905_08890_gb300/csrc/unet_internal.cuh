@@ -20,6 +20,13 @@ struct FieldPtrs {
 
 void conv3d(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const float *bias, int cout, int lg, int mode,
             const __nv_bfloat16 *mask, __nv_bfloat16 *y, cudaStream_t st);
+// the same convolution on tcgen05 (conv_tc.cu) for the cases conv3d_tc_fits
+// accepts (128^3 voxels, 16 input channels, cout 16, 32, 48 or 64);
+// conv3d_tc_error: synchronises st; nonzero once a bounded wait of that kernel ran out
+bool conv3d_tc_fits(int cin, int cout, int lg);
+void conv3d_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const float *bias, int cout, int mode,
+               const __nv_bfloat16 *mask, __nv_bfloat16 *y, cudaStream_t st);
+int conv3d_tc_error(cudaStream_t st);
 void conv3d_wgrad(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *dy, int cout, int lg, float *dw,
                   cudaStream_t st);
 void bias_grad(const __nv_bfloat16 *dy, int c, int64_t nv, float *db, cudaStream_t st);

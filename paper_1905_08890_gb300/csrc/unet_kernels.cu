@@ -1,14 +1,17 @@
 // unet_kernels.cu - kernels of the learned initial guess: a 3D U-Net with
 // circular 3^3 convolutions on channels-last BF16 activations [v][c],
 // v = (d n + h) n + w, FP32 accumulation on the tensor cores (mma.sync
-// m16n8k16 BF16).  Convolutions are implicit GEMMs: output voxels x output
-// channels, reduced over 27 taps x input channels, with the shifted input rows
-// gathered straight from global memory (the 27-fold reuse is served by L1).
+// m16n8k16 BF16; 128^3 grids on tcgen05, conv_tc.cu).  Convolutions are
+// implicit GEMMs: output voxels x output channels, reduced over 27 taps x
+// input channels, with the shifted input rows gathered straight from global
+// memory (the 27-fold reuse is served by L1).
 //
 // Weights: FP32 master and BF16 copies [27][cout][cin] (tap = (dd+1)*9 +
 // (dh+1)*3 + (dw+1)); the data gradient is the same convolution with the
 // flipped, transposed copy [27][cin][cout] (tap' = 26 - tap).
 #include <cuda_bf16.h>
+
+#include <cstdlib>
 
 #include "gr_internal.cuh"
 #include "unet_internal.cuh"
@@ -531,6 +534,12 @@ __global__ void k_conv_weights_bf16(const float *__restrict__ w, int cout, int c
 void conv3d(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const float *bias, int cout, int lg, int mode,
             const __nv_bfloat16 *mask, __nv_bfloat16 *y, cudaStream_t st)
 {
+    // 128^3 grids on the 5th-generation tensor cores (conv_tc.cu) unless GR_CONV_TC=0
+    const char *env = getenv("GR_CONV_TC");
+    if ((!env || env[0] != '0') && conv3d_tc_fits(cin, cout, lg)) {
+        conv3d_tc(x, cin, w, bias, cout, mode, mask, y, st);
+        return;
+    }
     const int64_t nv = (int64_t)1 << (3 * lg);
     if (cout % 32 == 0) {
         // 4 warps x 32 voxels, 32 channels per block

@@ -214,3 +214,77 @@ def test_guess_on_a_finer_grid(case):
         assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max() + 1e-6 * case["out_std"][k], name
     with pytest.raises(gr.GRError):
         net.guess(3 * N, {k: torch.from_numpy(v).cuda() for k, v in fine.items()}, out_f, rho, V_RMS)
+
+
+def _sampled_conv(params, k, x, vox):
+    """FP64 convolution k (with ReLU) and its rounding scale sum |W||x| + |b|
+    at the sampled output voxels vox (rows of (d, h, w)) of a channels-last
+    activation x [n, n, n, cin] (periodic)."""
+    layers, _ = unet_ref.unpack(params)
+    W, b = (t.numpy() for t in layers[k])  # W [cout][cin][3][3][3]
+    n = x.shape[0]
+    want = np.tile(b, (len(vox), 1)).astype(np.float64)
+    scale = np.tile(np.abs(b), (len(vox), 1)).astype(np.float64)
+    for dd in (-1, 0, 1):
+        for dh in (-1, 0, 1):
+            for dw in (-1, 0, 1):
+                xs = x[(vox[:, 0] + dd) % n, (vox[:, 1] + dh) % n, (vox[:, 2] + dw) % n].astype(np.float64)
+                Wt = W[:, :, dd + 1, dh + 1, dw + 1]
+                want += xs @ Wt.T
+                scale += np.abs(xs) @ np.abs(Wt).T
+    return np.maximum(want, 0.0), scale
+
+
+def test_tcgen05_convolutions_at_128_cubed(monkeypatch):
+    """At 128^3 the finest level's convolutions with 16 input channels run on
+    the 5th-generation tensor cores (conv_tc.cu: tcgen05.mma, TMEM
+    accumulator).  Each finest-level layer is held, at 6000 sampled voxels
+    including both row ends (the wrapped halo), to the FP64 convolution of its
+    own GPU input within 2^-8 (sum |W||x| + |b|) (the per-layer bound above);
+    the whole output agrees with the mma.sync path (GR_CONV_TC=0) to BF16
+    rounding; and the loss gradients of the two paths point the same way (the
+    data gradients of these layers into 16 and 48 channels run on tcgen05
+    too)."""
+    n = 128
+    p = synth.zeldovich(n, 33, 1.5, V_RMS, True)
+    ctx = gr.Context(n)
+    src = ctx.deposit(torch.from_numpy(p.x).cuda(), torch.from_numpy(p.u).cuda(), p.mass)
+    x_in = [torch.log(unet_ref.LOG_EPS + src["s0"] / p.rho_hat)] + [src[k] / (p.rho_hat * V_RMS) for k in
+                                                                     ("sx", "sy", "sz")]
+    in_mean = np.array([float(a.mean()) for a in x_in])
+    in_std = np.array([float(a.std()) for a in x_in])
+    net = gr.Net(n, seed=11)
+    net.set_norm(in_mean, in_std, np.zeros(10), np.ones(10) * 1e-4)
+    params = net.get_params()
+    outs, grads = [], []
+    target = {k: torch.zeros((n, n, n), dtype=torch.float64, device="cuda") for k in gr.FIELDS}
+    target["psi"] += 1.0
+    target["apsi"] += 1.0
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GR_CONV_TC", flag)
+        out = {k: torch.empty((n, n, n), dtype=torch.float64, device="cuda") for k in gr.FIELDS}
+        net.infer(src, out, p.rho_hat, V_RMS)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in out.items()})
+        if flag == "1":
+            rng = np.random.default_rng(5)
+            vox = rng.integers(0, n, size=(6000, 3))
+            vox[:200, 2] = 0
+            vox[200:400, 2] = n - 1
+            for k, (a, b) in ((0, ("x0", "e0a")), (1, ("e0a", "e0b")), (12, ("cat0", "d0a")), (13, ("d0a", "d0b"))):
+                x = net.activation(a)
+                got = net.activation(b)[vox[:, 0], vox[:, 1], vox[:, 2]]
+                want, scale = _sampled_conv(params, k, x, vox)
+                excess = np.abs(got - want) - 2.0 ** -8 * scale
+                assert excess.max() <= 0, (k, float(excess.max()))
+        loss, g = net.loss_grad(src, target, p.rho_hat, V_RMS)
+        grads.append(g)
+    for k in gr.FIELDS:
+        d = 1.0 if k in ("psi", "apsi") else 0.0
+        a, b = outs[0][k] - d, outs[1][k] - d
+        assert np.abs(a - b).max() <= 5e-2 * np.abs(b).max(), k
+    ga, gb = grads
+    cos = float(np.dot(ga, gb) / (np.linalg.norm(ga) * np.linalg.norm(gb)))
+    assert cos > 0.999, cos
+    net.close()
+    ctx.close()
