@@ -13,6 +13,7 @@
 // stages stay FP64.  Host-buffer I/O runs on a copy stream of the context.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -124,6 +125,10 @@ struct gr_ctx {
     float *pf = nullptr;
     // code units: the scaled sources of the a = 1 problem (allocated on first use)
     double *cu_src = nullptr;
+    // patch deposits: indices of the particles near the first patch, and their number
+    int *plist = nullptr;
+    int64_t plist_cap = 0;
+    unsigned *pcount = nullptr;
 };
 
 namespace {
@@ -1515,6 +1520,29 @@ gr_status gr_deposit_patches(gr_ctx *c, int npatch, const gr_patch *patch, int64
         return fail(GR_ERR_ARG, "gr_deposit_patches takes device particle arrays");
     for (int p = 0; p < npatch; p++)
         if (!src_ok(&patch[p].src)) return fail(GR_ERR_ARG, "patch %d: a source array is NULL", p);
+    // one pass over the particles lists those near the first patch (every
+    // later patch lies inside it); each patch then deposits from that list
+    if (np > 0 && np <= INT32_MAX && c->plist_cap < np) {
+        if (c->plist) {
+            cudaFree(c->plist);
+            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void *)c->plist), c->allocs.end());
+            c->plist = nullptr;
+            c->plist_cap = 0;
+        }
+        gr_status st = dalloc(c, &c->plist, (size_t)np);
+        if (st != GR_OK) return st;
+        c->plist_cap = np;
+    }
+    if (!c->pcount) {
+        gr_status st = dalloc(c, &c->pcount, 1);
+        if (st != GR_OK) return st;
+    }
+    const bool listed = np > 0 && np <= INT32_MAX;
+    if (listed) {
+        int lo[3];
+        for (int d = 0; d < 3; d++) lo[d] = patch[0].origin[d] - 1;
+        gr::patch_select(np, x, c->L, c->n, lo, patch[0].n / 2 + 2, c->plist, c->pcount, c->st);
+    }
     int O[3] = {0, 0, 0};
     for (int p = 0; p < npatch; p++) {
         const int N = c->n << (p + 1), n = patch[p].n;
@@ -1522,7 +1550,9 @@ gr_status gr_deposit_patches(gr_ctx *c, int npatch, const gr_patch *patch, int64
         const gr_sources &ps = patch[p].src;
         double *f[5] = {ps.s0, ps.s[0], ps.s[1], ps.s[2], ps.sigma};
         for (int k = 0; k < 5; k++) cudaMemsetAsync(f[k], 0, (size_t)n * n * n * sizeof(double), c->st);
-        gr::patch_deposit(np, x, u, mass, c->L, N, O, n, gr::PSetSrc{{f[0], f[1], f[2], f[3], f[4]}}, c->st);
+        const gr::PSetSrc out{{f[0], f[1], f[2], f[3], f[4]}};
+        if (listed) gr::patch_deposit_list(np, c->plist, c->pcount, x, u, mass, c->L, N, O, n, out, c->st);
+        else gr::patch_deposit(np, x, u, mass, c->L, N, O, n, out, c->st);
     }
     return cuda_check("gr_deposit_patches");
 }

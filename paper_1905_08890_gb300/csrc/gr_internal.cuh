@@ -428,6 +428,12 @@ struct PSetFld {
 };
 void patch_deposit(int64_t np, const double *x, const double *u, double mass, double L, int N, const int O[3], int nw,
                    const PSetSrc &out, cudaStream_t st);
+// indices of the particles in base cells [lo, lo + len) (mod n0) per axis -> list, their number -> count
+void patch_select(int64_t np, const double *x, double L, int n0, const int lo[3], int len, int *list,
+                  unsigned *count, cudaStream_t st);
+// patch_deposit over the particles of such a list (np: the particle arrays' length)
+void patch_deposit_list(int64_t np, const int *list, const unsigned *count, const double *x, const double *u,
+                        double mass, double L, int N, const int O[3], int nw, const PSetSrc &out, cudaStream_t st);
 // win = the parent's window; with dold, also dold := win - dold (and d32 its FP32 copy)
 void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st,
                        double *dold = nullptr, float *d32 = nullptr);

@@ -241,16 +241,41 @@ __device__ __forceinline__ double interp(const double *win, int w, int i, int j,
 }
 
 // ---------------------------------------------------------------- deposit
-// CIC at resolution N (spacing L/N; the base deposit's formulas in plain
-// FP64) onto the nw^3 window of cells O + a (mod N); one thread per particle.
+// The particles whose clouds may meet a box of base cells: base cell of the
+// position within [lo, lo + len) (mod n0) on every axis (the caller grows the
+// box by one cell on every side for the cloud's reach); their indices are
+// appended to list (order not kept), count holds how many.
 __global__ void __launch_bounds__(kBlock)
-    k_pdeposit(int64_t np, const double *__restrict__ x, const double *__restrict__ u, double mass, double L, int N,
-               int O0, int O1, int O2, int nw, double *__restrict__ s0, double *__restrict__ sx,
-               double *__restrict__ sy, double *__restrict__ sz, double *__restrict__ sig)
+    k_pselect(int64_t np, const double *__restrict__ x, double sn0, int n0, int lo0, int lo1, int lo2, int len,
+              int *__restrict__ list, unsigned *__restrict__ count)
 {
     pdl_begin();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= np) return;
+    bool in = p < np;
+    const int lo[3] = {lo0, lo1, lo2};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (!in) break;
+        const int c = (int)floor(x[d * np + p] * sn0);
+        in = ((c - lo[d]) & (n0 - 1)) < len;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, in);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (in) list[base + __popc(mask & ((1u << lane) - 1))] = (int)p;
+}
+
+// CIC at resolution N (spacing L/N; the base deposit's formulas in plain
+// FP64) onto the nw^3 window of cells O + a (mod N) of one particle
+__device__ __forceinline__ void pdeposit_one(int64_t p, int64_t np, const double *__restrict__ x,
+                                             const double *__restrict__ u, double mass, double L, int N, int O0,
+                                             int O1, int O2, int nw, double *__restrict__ s0,
+                                             double *__restrict__ sx, double *__restrict__ sy,
+                                             double *__restrict__ sz, double *__restrict__ sig)
+{
     // positions scaled by 1/L and N/L (multiplications: the FP64 divide is
     // the slowest FP64 instruction, and every particle passes here)
     const double iL = 1.0 / L, sN = (double)N / L, ivol = sN * sN * sN;
@@ -296,6 +321,25 @@ __global__ void __launch_bounds__(kBlock)
             }
         }
     }
+}
+
+// one thread per particle, or (list given) a grid-stride loop over the count
+// particles whose indices list holds
+__global__ void __launch_bounds__(kBlock)
+    k_pdeposit(int64_t np, const double *__restrict__ x, const double *__restrict__ u, double mass, double L, int N,
+               int O0, int O1, int O2, int nw, double *__restrict__ s0, double *__restrict__ sx,
+               double *__restrict__ sy, double *__restrict__ sz, double *__restrict__ sig,
+               const int *__restrict__ list, const unsigned *__restrict__ count)
+{
+    pdl_begin();
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (!list) {
+        if (t < np) pdeposit_one(t, np, x, u, mass, L, N, O0, O1, O2, nw, s0, sx, sy, sz, sig);
+        return;
+    }
+    const int64_t cnt = (int64_t)*count;
+    for (int64_t e = t; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+        pdeposit_one(list[e], np, x, u, mass, L, N, O0, O1, O2, nw, s0, sx, sy, sz, sig);
 }
 
 // ---------------------------------------------------------------- windows
@@ -912,7 +956,24 @@ void patch_deposit(int64_t np, const double *x, const double *u, double mass, do
     if (np <= 0) return;
     const int64_t g = (np + kBlock - 1) / kBlock;
     GR_LAUNCH(k_pdeposit, (unsigned)g, kBlock, st, np, x, u, mass, L, N, O[0], O[1], O[2], nw, out.s[0], out.s[1],
-              out.s[2], out.s[3], out.s[4]);
+              out.s[2], out.s[3], out.s[4], (const int *)nullptr, (const unsigned *)nullptr);
+}
+
+void patch_select(int64_t np, const double *x, double L, int n0, const int lo[3], int len, int *list,
+                  unsigned *count, cudaStream_t st)
+{
+    cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+    if (np <= 0) return;
+    const int64_t g = (np + kBlock - 1) / kBlock;
+    GR_LAUNCH(k_pselect, (unsigned)g, kBlock, st, np, x, n0 / L, n0, lo[0], lo[1], lo[2], len, list, count);
+}
+
+void patch_deposit_list(int64_t np, const int *list, const unsigned *count, const double *x, const double *u,
+                        double mass, double L, int N, const int O[3], int nw, const PSetSrc &out, cudaStream_t st)
+{
+    if (np <= 0) return;
+    GR_LAUNCH(k_pdeposit, wave_grid(k_pdeposit, np), kBlock, st, np, x, u, mass, L, N, O[0], O[1], O[2], nw,
+              out.s[0], out.s[1], out.s[2], out.s[3], out.s[4], list, count);
 }
 
 void patch_gather_base(int fmt, const PBase &B, const int o[3], int w, double *win, cudaStream_t st, double *dold,
