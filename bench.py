@@ -44,6 +44,7 @@ DEFAULT_WORKLOAD = "zeldovich512_lognormal5"
 BYTES = {
     # class: {kind: bytes per finest-level cell}
     "sweep32": {"poisson": 6.0, "helm": 8.0},  # one colour pass
+    "smooth3": {"poisson": 10.0, "helm": 14.0},  # three colour passes fused: other colour + f (+ inv) in, e out
     "sweep64": {"poisson": 12.0, "helm": 16.0, "psi": 24.0},
     "resid_restrict32": {"poisson": 9.0, "helm": 13.0},
     "resid_restrict32_red": {"poisson": 7.0, "helm": 9.0},  # red children only, after a black pass
@@ -60,18 +61,23 @@ EQ_KIND = ["poisson"] * 4 + ["psi", "helm"] + ["poisson"] * 4
 EQ_KIND32 = ["poisson"] * 4 + ["helm", "helm"] + ["poisson"] * 4
 
 
-def class_bytes(cls, cycles, n, nu1, nu2, prec):
+def class_bytes(cls, cycles, n, nu1, nu2, prec, fused=False):
     """Algorithmic bytes of every finest-level launch of one profiled class
     over a solve with the given per-equation cycle counts (n >= 8, nu1, nu2 >= 1).
     In the double-float mode the residual kernel also makes the first red
-    pass of each cycle and the last black pass is fused with the update."""
+    pass of each cycle and the last black pass is fused with the update.
+    fused: three of the colour passes of each smoothing (nu1 = nu2 = 2) run as
+    one fused launch (class smooth3)."""
     mixed, dfm = prec != "fp64", prec == "mixed_df"
     cells = float(n) ** 3
     total = 0.0
     for eq, cyc in enumerate(cycles):
         k64, k32 = EQ_KIND[eq], EQ_KIND32[eq]
         if cls == "sweep32" and mixed:
-            total += cyc * (2 * (nu1 + nu2) - (2 if dfm else 0)) * BYTES["sweep32"][k32] * cells
+            passes = 2 * (nu1 + nu2) - (2 if dfm else 0) - (6 if fused else 0)
+            total += cyc * passes * BYTES["sweep32"][k32] * cells
+        elif cls == "smooth3" and mixed and fused:
+            total += cyc * 2 * BYTES["smooth3"][k32] * cells
         elif cls == "sweep64" and not mixed:
             total += cyc * 2 * (nu1 + nu2) * BYTES["sweep64"][k64] * cells
         elif cls == "resid_restrict":
@@ -193,7 +199,8 @@ def profile_case(case, n=None):
       mixed      the headline double-float solve at n^3 (default 128), lognormal rms 5, tol 1e-8
       fp64       the plain FP64 solve at n^3 (default 128: lognormal rms 1, rms |u| 0.003, tol 1e-10)
       unet       three inferences of the trained network at 128^3 (held-out seed 5000)
-      particles  three particle updates and three deposits with the metric at n^3 (default 512)"""
+      particles  three particle updates and three deposits with the metric at n^3 (default 512)
+      fma        the FP64 and FP32 FMA issue rates of the GPU (gr_fma_rate)"""
     import torch
 
     from paper_1905_08890_gb300 import gr, learn, synth
@@ -210,6 +217,12 @@ def profile_case(case, n=None):
             torch.cuda.synchronize()
             out.append(round(ev[0].elapsed_time(ev[1]), 3))
 
+    if case == "fma":
+        # FMA issue rates (FP64, FP32) over the whole GPU: the denominators of
+        # the ALU-bound rooflines
+        rates = {k: round(gr.gr_fma_rate(k == "fp64", 1 << 17) / 1e12, 3) for k in ("fp64", "fp32")}
+        print(json.dumps({"case": case, "fma_tflops": rates}))
+        return
     if case == "unet":
         ctx = gr.Context(learn.N)
         net = learn.load(learn.WEIGHTS)
@@ -305,7 +318,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-timestep", action="store_true", help="skip the full timestep (deposit, solve, particle update)")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--case", default=None, choices=["mixed", "fp64", "unet", "particles"],
+    ap.add_argument("--case", default=None, choices=["mixed", "fp64", "unet", "particles", "fma"],
                     help="run one small profiling case instead of the bench (the commands of profiles/*.md)")
     ap.add_argument("--n", type=int, default=None, help="grid of --case")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison at 128^3")
@@ -397,6 +410,7 @@ def main():
     mixed = args.prec != "fp64"
     hbm, peak_kind = peaks()
     kernels = {}
+    fused = any(r["prof"]["smooth3"]["launches"] > 0 for r in reps)
     for cls, d in reps[0]["prof"].items():
         tot_ms = sum(r["prof"][cls]["ms"] for r in reps)
         launches_c = sum(r["prof"][cls]["launches"] for r in reps)
@@ -405,7 +419,7 @@ def main():
         if cls in ("setup", "coarse", "patch"):
             kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "share_of_step": round(tot_ms / ms, 3)}
             continue
-        byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, args.prec) for r in reps)
+        byt = sum(class_bytes(cls, r["cycles"], n, 2, 2, args.prec, fused) for r in reps)
         gbs = byt / (tot_ms * 1e-3) / 1e9
         kernels[cls] = {"launches": launches_c, "ms": round(tot_ms, 3), "avg_us": round(1e3 * tot_ms / launches_c, 2),
                         "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3),
@@ -427,7 +441,7 @@ def main():
             traffic = ent["bytes_per_launch"]
     roofline = None
     if dom:
-        avg_bytes = class_bytes(dom, reps[0]["cycles"], n, 2, 2, args.prec) / reps[0]["prof"][dom]["launches"]
+        avg_bytes = class_bytes(dom, reps[0]["cycles"], n, 2, 2, args.prec, fused) / reps[0]["prof"][dom]["launches"]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["algorithmic_GBps"], "peak": hbm,
                     "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
                     "algorithmic_bytes_per_launch": round(avg_bytes), "peak_source": f"{peak_kind} hbm_gbs"}

@@ -170,6 +170,7 @@ typedef enum {
     GR_PROF_SETUP,         /* sources, coefficients and layout changes of the finest level */
     GR_PROF_COARSE,        /* every multigrid kernel below the finest level (and full multigrid's coarser cycles) */
     GR_PROF_PATCH,         /* nested patches: set-up, relaxation, residual, transfers and injection */
+    GR_PROF_SMOOTH3,       /* three FP32 colour passes fused into one pass over memory (finest level, nu = 2) */
     GR_NPROF
 } gr_prof_class;
 
@@ -435,6 +436,16 @@ gr_status gr_deposit_metric(gr_ctx *ctx, int64_t np, const double *x, const doub
    threads at the same time) race on it and must be serialised by the caller. */
 gr_status gr_momentum_residual_noalloc(int n, double L, const double *V, const double *s, double *res_field,
                                        double *rel_norm, void *cuda_stream);
+
+/* Diagnostic, not part of the method: the FMA issue rate of the current
+   device, in FLOP/s (2 per fused multiply-add), FP64 (fp64 != 0) or FP32.
+   Eight blocks of 256 threads per SM each run 8 independent chains of `iters`
+   FMAs (1 <= iters <= 2^32) after a short warm-up launch; the time is taken
+   with CUDA events on cuda_stream (NULL = legacy default stream), which the
+   call synchronises.  Allocates and frees a small device array.
+   *flops_per_s (host) receives the rate (0 on error).  Errors: GR_ERR_ARG,
+   GR_ERR_NOMEM, GR_ERR_CUDA. */
+gr_status gr_fma_rate(int fp64, long long iters, void *cuda_stream, double *flops_per_s);
 
 #ifdef __cplusplus
 }

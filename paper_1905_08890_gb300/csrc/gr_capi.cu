@@ -52,6 +52,7 @@ struct Level {
     double h = 0, h2 = 0, ih2 = 0;
     double *u = nullptr, *f = nullptr, *c0 = nullptr, *c1 = nullptr, *ur = nullptr;  // FP64
     float *e = nullptr, *r = nullptr, *m = nullptr, *inv = nullptr;                 // FP32
+    float *e2 = nullptr;  // finest level: second correction buffer of the fused colour passes
 };
 
 // one patch of a chain (gr_patch): ghosted (n + 4)^3 FP64 work arrays
@@ -96,6 +97,9 @@ struct gr_ctx {
     int a_fmt = 0;
     int w_fmt = 0;
     bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
+    int s3_min = 1 << 30;  // finest grids from this size fuse three colour passes per smoothing: off unless
+                           // GR_SMOOTH3=1 (from 512^3, or from GR_SMOOTH3_MIN)
+    int s3_rt = 0;         // row tiles of the fused colour passes on the finest level
     int dir = 0;           // traversal direction of the next finest-level launch (alternates)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // host-buffer I/O: a copy stream, its events and two particle staging buffers
@@ -551,15 +555,38 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
         if (nu2 > 0) gr::prolong_add_black(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st, dir_of(c->lev[l]));
         else gr::prolong_add<float>(c->lev[l].n, c->lev[l].e, c->lev[l - 1].e, c->st);
     };
-    timed(c, cls(GR_PROF_SWEEP32), [&] {
-        if (start == START_RED_DONE && nu1 > 0) {
-            gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st, dir_of(F));
-            smooth(F, nu1 - 1);
+    // finest level with two sweeps: three of the colour passes fused into one
+    // pass over memory (smooth3.cu), colour `first` first; the result lands in
+    // the second buffer, which becomes the level's correction
+    auto fused3 = [&](int nu, int first) {
+        if (!fine || nu != 2 || !F.e2 || !gr::smooth3_fits(kind32, F.n)) return false;
+        timed(c, GR_PROF_SMOOTH3, [&] {
+            gr::smooth3(kind32, F.n, F.e, F.e2, F.r, F.inv, F.h2, first, c->s3_rt, c->st);
+        });
+        std::swap(F.e, F.e2);
+        return true;
+    };
+    // nu red + black sweeps of the finest level
+    auto smooth_fine = [&](int nu) {
+        if (fused3(nu, 0)) {
+            timed(c, cls(GR_PROF_SWEEP32), [&] {
+                gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st, dir_of(F));
+            });
         } else {
-            if (start != START_GIVEN) cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
-            smooth(F, nu1);
+            timed(c, cls(GR_PROF_SWEEP32), [&] { smooth(F, nu); });
         }
-    });
+    };
+    if (start == START_RED_DONE && nu1 > 0) {
+        if (!fused3(nu1, 1)) {
+            timed(c, cls(GR_PROF_SWEEP32), [&] {
+                gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 1, c->st, dir_of(F));
+                smooth(F, nu1 - 1);
+            });
+        }
+    } else {
+        if (start != START_GIVEN) cudaMemsetAsync(F.e, 0, sizeof(float) * (size_t)F.n * F.n * F.n, c->st);
+        smooth_fine(nu1);
+    }
     timed(c, cls(GR_PROF_RESTRICT), [&] { down(top); });
     timed(c, GR_PROF_COARSE, [&] {
         for (int l = top - 1; l >= (tail ? tail + 1 : 1); l--) {
@@ -589,13 +616,15 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
     });
     timed(c, cls(GR_PROF_PROLONG), [&] { up(top); });
     if (!uh) {
-        timed(c, cls(GR_PROF_SWEEP32), [&] { smooth(F, nu2); });
+        smooth_fine(nu2);
         return;
     }
-    timed(c, GR_PROF_SWEEP32, [&] {
-        smooth(F, nu2 - 1);
-        gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 0, c->st, dir_of(F));
-    });
+    if (!fused3(nu2, 0)) {
+        timed(c, GR_PROF_SWEEP32, [&] {
+            smooth(F, nu2 - 1);
+            gr::sweep_colour<float>(kind32, F.n, F.e, F.r, F.m, F.inv, F.h2, F.ih2, 0.0, 0, c->st, dir_of(F));
+        });
+    }
     timed(c, GR_PROF_MIXED_UPDATE,
           [&] { gr::df_black_update(kind32, F.n, F.e, F.r, F.inv, F.h2, uh, ul, c->st, dir_of(F)); });
 }
@@ -1308,6 +1337,12 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     c->n = n;
     c->L = L;
     if (const char *env = getenv("GR_COARSE_TAIL")) c->tail_on = env[0] != '0';
+    if (const char *env = getenv("GR_SMOOTH3")) {
+        if (env[0] == '1') {
+            c->s3_min = 512;
+            if (const char *m = getenv("GR_SMOOTH3_MIN")) c->s3_min = atoi(m);
+        }
+    }
     if (const char *env = getenv("GR_HOST_CHUNK")) {
         const long long v = atoll(env);
         if (v > 0) c->host_chunk = v;
@@ -1335,6 +1370,19 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
         if (st == GR_OK) st = dalloc(c, &A.inv, N);
     }
     const size_t N = (size_t)n * n * n;
+    if (st == GR_OK && n >= c->s3_min && gr::smooth3_fits(KPOISSON, n)) {
+        Level &F = c->lev[c->nlev - 1];
+        st = dalloc(c, &F.e2, N);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c->s3_rt = gr::smooth3_row_tiles(n, sms > 0 ? sms : 1);
+        // GR_SMOOTH3_RT: another row-tile count (tiles of at most 14 rows)
+        if (const char *env = getenv("GR_SMOOTH3_RT")) {
+            const int rt = atoi(env);
+            if (rt >= (n + 13) / 14 && rt <= n) c->s3_rt = rt;
+        }
+    }
     if (st == GR_OK) st = dalloc(c, &c->A6, 6 * N);
     if (st == GR_OK) st = dalloc(c, &c->dfu, 2 * N);
     if (st == GR_OK) st = dalloc(c, &c->dff, 2 * N);

@@ -465,4 +465,13 @@ void patch_aij(int n, double nh, const PSetFld &G, double *A6, cudaStream_t st);
 int patch_setup(int eq, int n, double nh, const PSetSrc &S, const PSetFld &G, const double *A6, double smean,
                 double K2, double Kdot, double *f, double *c0, double *c1, double *partials, cudaStream_t st);
 
+// Three FP32 colour passes of the correction equation (KPOISSON, KHELM) in
+// one pass over memory: colour c1 from the other colour of ein, then the other
+// colour, then c1 again; both colours of the result go to eout (smooth3.cu).
+// inv: KHELM's 1/(6 + h^2 m).  rt: row tiles (smooth3_row_tiles).
+bool smooth3_fits(int kind, int n);
+int smooth3_row_tiles(int n, int sms);
+void smooth3(int kind, int n, const float *ein, float *eout, const float *f, const float *inv, double h2, int c1,
+             int rt, cudaStream_t st);
+
 }  // namespace gr

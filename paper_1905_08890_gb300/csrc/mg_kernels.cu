@@ -166,15 +166,17 @@ __global__ void __launch_bounds__(kBlock) k_sweep4(int lgn, float *__restrict__ 
         nb.y = A.y + B.y + C.y + D.y + E.y + Sh.y;
         nb.z = A.z + B.z + C.z + D.z + E.z + Sh.z;
         nb.w = A.w + B.w + C.w + D.w + E.w + Sh.w;
+        // nb - h^2 f as one fused multiply-add (the fused three-pass kernel,
+        // smooth3.cu, forms it the same way, bit for bit)
         float4 out;
         if (KIND == KPOISSON) {
             const float s6 = 1.0f / 6.0f;
-            out = make_float4((nb.x - h2 * F.x) * s6, (nb.y - h2 * F.y) * s6, (nb.z - h2 * F.z) * s6,
-                              (nb.w - h2 * F.w) * s6);
+            out = make_float4(__fmaf_rn(-h2, F.x, nb.x) * s6, __fmaf_rn(-h2, F.y, nb.y) * s6,
+                              __fmaf_rn(-h2, F.z, nb.z) * s6, __fmaf_rn(-h2, F.w, nb.w) * s6);
         } else {
             const float4 G = *reinterpret_cast<const float4 *>(c1 + off + t);
-            out = make_float4((nb.x - h2 * F.x) * G.x, (nb.y - h2 * F.y) * G.y, (nb.z - h2 * F.z) * G.z,
-                              (nb.w - h2 * F.w) * G.w);
+            out = make_float4(__fmaf_rn(-h2, F.x, nb.x) * G.x, __fmaf_rn(-h2, F.y, nb.y) * G.y,
+                              __fmaf_rn(-h2, F.z, nb.z) * G.z, __fmaf_rn(-h2, F.w, nb.w) * G.w);
         }
         *reinterpret_cast<float4 *>(own + t) = out;
     }

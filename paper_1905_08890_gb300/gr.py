@@ -55,19 +55,19 @@ class gr_report(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int * 10), ("res0", ctypes.c_double * 10), ("res", ctypes.c_double * 10),
                 ("eq_status", ctypes.c_int * 10), ("seconds", ctypes.c_double), ("eq_seconds", ctypes.c_double * 10),
                 ("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
-                ("prof_launches", ctypes.c_int * 10), ("prof_ms", ctypes.c_double * 10),
+                ("prof_launches", ctypes.c_int * 11), ("prof_ms", ctypes.c_double * 11),
                 ("guess_rejected", ctypes.c_int * 10), ("res_level", (ctypes.c_double * (MAX_PATCHES + 1)) * 10)]
 
 
 PROF_CLASSES = ("sweep64", "sweep32", "resid_restrict", "prolong", "mixed_resid", "mixed_update", "norm64", "setup",
-                "coarse", "patch")
+                "coarse", "patch", "smooth3")
 
 
 _lib = None
 _lock = threading.Lock()
 EXPORTED = ("gr_default_opts", "gr_create", "gr_destroy", "gr_deposit", "gr_deposit_patches", "gr_solve_constraints",
             "gr_vcycle", "gr_residual", "gr_last_error", "gr_kernel_launches", "gr_momentum_residual_noalloc",
-            "gr_particle_update", "gr_kick", "gr_drift", "gr_deposit_metric", "gr_solve_code_units")
+            "gr_particle_update", "gr_kick", "gr_drift", "gr_deposit_metric", "gr_solve_code_units", "gr_fma_rate")
 GR_KICK_SYNC, GR_KICK_OPEN, GR_DRIFT = 1, 2, 4
 
 
@@ -102,6 +102,8 @@ def lib():
             L.gr_last_error.restype = ctypes.c_char_p
             L.gr_kernel_launches.argtypes = []
             L.gr_kernel_launches.restype = ctypes.c_longlong
+            L.gr_fma_rate.argtypes = [ctypes.c_int, ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_double)]
+            L.gr_fma_rate.restype = ctypes.c_int
             L.gr_momentum_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                        ctypes.POINTER(ctypes.c_double), _P]
             L.gr_momentum_residual_noalloc.restype = ctypes.c_int
@@ -318,6 +320,18 @@ def gr_last_error() -> str:
 
 def gr_kernel_launches() -> int:
     return int(lib().gr_kernel_launches())
+
+
+def gr_fma_rate(fp64: bool, iters: int = 1 << 16, stream=None) -> float:
+    """Measured FMA issue rate of the current device in FLOP/s (a diagnostic)."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    out = ctypes.c_double(0.0)
+    _check(lib().gr_fma_rate(int(bool(fp64)), int(iters), st, ctypes.byref(out)), "gr_fma_rate")
+    return out.value
 
 
 def gr_momentum_residual_noalloc(n: int, L: float, V, s, res_field=None, stream=None) -> float:
