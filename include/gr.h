@@ -83,7 +83,9 @@ typedef enum {
 
 typedef struct gr_ctx gr_ctx; /* opaque */
 
-/* CIC sources, device arrays of n^3 doubles each:
+/* CIC sources, device arrays of n^3 doubles each, natural layout, each
+   starting on a 16-byte boundary (the kernels move them in 16-byte vectors;
+   an entry point given a NULL or misaligned array returns GR_ERR_ARG):
    s0 = sqrt(gamma) rho, s[l] = sqrt(gamma) S_l, sigma = sum_l s_ll (Sec. 3). */
 typedef struct {
     double *s0;
@@ -91,7 +93,8 @@ typedef struct {
     double *sigma;
 } gr_sources;
 
-/* The ten potentials, device arrays of n^3 doubles each.  psi is the
+/* The ten potentials, device arrays of n^3 doubles each, natural layout,
+   16-byte aligned like the sources.  psi is the
    conformal factor, apsi = alpha psi; beta^i = B^i + d^i b and
    W_i = V_i + d_i U (Sec. 4.3.1). */
 typedef struct {

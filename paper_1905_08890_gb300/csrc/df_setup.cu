@@ -61,7 +61,6 @@ constexpr int kChunk = 2;
 struct PairPos {
     int i, j, k0, c0;
     int64_t t, half;
-    __device__ __forceinline__ int64_t split(int e) const { return ((c0 ^ (e & 1)) ? half : 0) + t + (e >> 1); }
 };
 
 __device__ __forceinline__ PairPos pair_pos(int lgn, int64_t t)
@@ -75,6 +74,48 @@ __device__ __forceinline__ PairPos pair_pos(int lgn, int64_t t)
     p.i = (int)(t >> (lgh + lgn));
     p.c0 = (p.i + p.j) & 1;
     return p;
+}
+
+// The four cells k0 .. k0 + 3 of a thread (kChunk = 2): natural-layout
+// values by two 16-byte loads, split-layout pairs by 8-byte loads and stores
+// (cells 0 and 2 have colour c0 and split indices t, t + 1; cells 1 and 3 the
+// other colour).
+static_assert(kChunk == 2, "the vector accesses below assume four cells per thread");
+
+__device__ __forceinline__ void ld4(const double *__restrict__ a, int id0, df v[4])
+{
+    const double2 x = *reinterpret_cast<const double2 *>(a + id0), y = *reinterpret_cast<const double2 *>(a + id0 + 2);
+    v[0] = split_double(x.x), v[1] = split_double(x.y), v[2] = split_double(y.x), v[3] = split_double(y.y);
+}
+
+__device__ __forceinline__ void st4(double *__restrict__ a, int id0, const double v[4])
+{
+    *reinterpret_cast<double2 *>(a + id0) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(a + id0 + 2) = make_double2(v[2], v[3]);
+}
+
+__device__ __forceinline__ void stp4(float *__restrict__ h, float *__restrict__ l, const PairPos &p, const df v[4])
+{
+    const int64_t a = (p.c0 ? p.half : 0) + p.t, b = (p.c0 ? 0 : p.half) + p.t;
+    *reinterpret_cast<float2 *>(h + a) = make_float2(v[0].hi, v[2].hi);
+    *reinterpret_cast<float2 *>(l + a) = make_float2(v[0].lo, v[2].lo);
+    *reinterpret_cast<float2 *>(h + b) = make_float2(v[1].hi, v[3].hi);
+    *reinterpret_cast<float2 *>(l + b) = make_float2(v[1].lo, v[3].lo);
+}
+
+__device__ __forceinline__ void stf4(float *__restrict__ h, const PairPos &p, const float v[4])
+{
+    const int64_t a = (p.c0 ? p.half : 0) + p.t, b = (p.c0 ? 0 : p.half) + p.t;
+    *reinterpret_cast<float2 *>(h + a) = make_float2(v[0], v[2]);
+    *reinterpret_cast<float2 *>(h + b) = make_float2(v[1], v[3]);
+}
+
+__device__ __forceinline__ void ldp4(const float *__restrict__ h, const float *__restrict__ l, const PairPos &p, df v[4])
+{
+    const int64_t a = (p.c0 ? p.half : 0) + p.t, b = (p.c0 ? 0 : p.half) + p.t;
+    const float2 ha = *reinterpret_cast<const float2 *>(h + a), la = *reinterpret_cast<const float2 *>(l + a);
+    const float2 hb = *reinterpret_cast<const float2 *>(h + b), lb = *reinterpret_cast<const float2 *>(l + b);
+    v[0] = {ha.x, la.x}, v[1] = {hb.x, lb.x}, v[2] = {ha.y, la.y}, v[3] = {hb.y, lb.y};
 }
 
 // running sum of df values (high parts through two-sum, errors and low parts
@@ -182,16 +223,18 @@ __global__ void __launch_bounds__(kBlock, SRC == SRC_SHIFT ? 2 : 3) k_dfs_poisso
     for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
          tc += (int64_t)gridDim.x * blockDim.x) {
         const PairPos p = pair_pos(lgn, tc * kChunk);
+        df fv[4], uv[4], sv[4];
+        ld4(a.fld, nat(lgn, p.i, p.j, p.k0), uv);
+        if (SRC == SRC_MEAN) ld4(a.s[0], nat(lgn, p.i, p.j, p.k0), sv);
 #pragma unroll
         for (int e = 0; e < 2 * kChunk; e++) {
             const int i = p.i, j = p.j, k = p.k0 + e;
-            const int id = nat(lgn, i, j, k);
             const int nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
                                       {nat(lgn, i, (j + 1) & mn, k), nat(lgn, i, (j - 1) & mn, k)},
                                       {nat(lgn, i, j, (k + 1) & mn), nat(lgn, i, j, (k - 1) & mn)}};
             df f;
             if (SRC == SRC_MEAN) {
-                f = df_mul(df_add_acc(ld(a.s[0], id), nmu), a.scale);
+                f = df_mul(df_add_acc(sv[e], nmu), a.scale);
             } else if (SRC == SRC_DIV) {
                 df d = df_add(ld(a.s[0], nb[0][0]), df_neg(ld(a.s[0], nb[0][1])));
 #pragma unroll
@@ -208,11 +251,11 @@ __global__ void __launch_bounds__(kBlock, SRC == SRC_SHIFT ? 2 : 3) k_dfs_poisso
                 }
                 f = df_mul(d, a.scale);
             }
-            const int64_t sid = p.split(e);
-            stp(a.fh, a.fl, sid, f);
-            stp(a.uh, a.ul, sid, ld(a.fld, id));
+            fv[e] = f;
             acc.add(f);
         }
+        stp4(a.fh, a.fl, p, fv);
+        stp4(a.uh, a.ul, p, uv);
     }
     acc.flush(partials);
 }
@@ -309,17 +352,24 @@ __global__ void __launch_bounds__(kBlock)
     for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
          tc += (int64_t)gridDim.x * blockDim.x) {
         const PairPos p = pair_pos(lgn, tc * kChunk);
+        const int id0 = nat(lgn, p.i, p.j, p.k0);
+        df sv[4], pv[4], uo[4], ao[4], bo[4];
+        const df zo[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        ld4(s0, id0, sv);
+        ld4(psi, id0, pv);
+        const float4 Ah = *reinterpret_cast<const float4 *>(AAh + id0), Al = *reinterpret_cast<const float4 *>(AAl + id0);
+        const df av[4] = {{Ah.x, Al.x}, {Ah.y, Al.y}, {Ah.z, Al.z}, {Ah.w, Al.w}};
 #pragma unroll
         for (int e = 0; e < 2 * kChunk; e++) {
-            const int id = nat(lgn, p.i, p.j, p.k0 + e);
-            const int64_t sid = p.split(e);
-            const df s = ld(s0, id);
-            stp(uh, ul, sid, df_add_acc(ld(psi, id), m1));
-            stp(ah, al, sid, df_mul(s, a_scale));
-            stp(bh, bl, sid, df_mul(ldp(AAh, AAl, id), b_scale));
-            stp(fh, fl, sid, df{0.0f, 0.0f});
-            acc.add(s);
+            uo[e] = df_add_acc(pv[e], m1);
+            ao[e] = df_mul(sv[e], a_scale);
+            bo[e] = df_mul(av[e], b_scale);
+            acc.add(sv[e]);
         }
+        stp4(uh, ul, p, uo);
+        stp4(ah, al, p, ao);
+        stp4(bh, bl, p, bo);
+        stp4(fh, fl, p, zo);
     }
     acc.flush(partials);
 }
@@ -343,25 +393,37 @@ __global__ void __launch_bounds__(kBlock)
     for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
          tc += (int64_t)gridDim.x * blockDim.x) {
         const PairPos p = pair_pos(lgn, tc * kChunk);
+        const int id0 = nat(lgn, p.i, p.j, p.k0);
+        df psv[4], apv[4], s0v[4], sgv[4], uo[4], ao[4], fo[4];
+        float mo[4], io[4];
+        ld4(psi, id0, psv);
+        ld4(apsi, id0, apv);
+        ld4(s0, id0, s0v);
+        ld4(sig, id0, sgv);
+        const float4 Ah = *reinterpret_cast<const float4 *>(AAh + id0), Al = *reinterpret_cast<const float4 *>(AAl + id0);
+        const df av[4] = {{Ah.x, Al.x}, {Ah.y, Al.y}, {Ah.z, Al.z}, {Ah.w, Al.w}};
 #pragma unroll
         for (int e = 0; e < 2 * kChunk; e++) {
-            const int id = nat(lgn, p.i, p.j, p.k0 + e);
-            const int64_t sid = p.split(e);
-            const df ps = ld(psi, id);
+            const df ps = psv[e];
             const df ip = df_recip(ps);
             const df ip2 = df_mul(ip, ip), ip4 = df_mul(ip2, ip2), ip8 = df_mul(ip4, ip4);
             const df p2 = df_mul(ps, ps), p4 = df_mul(p2, p2), p5 = df_mul(p4, ps);
-            const df inner = df_add(ld(s0, id), df_mul(df_scale2(ld(sig, id), 2.0f), ip4));
-            const df mm = df_add(df_add(df_mul(df_mul(two_pi, ip2), inner), df_mulf(df_mul(ldp(AAh, AAl, id), ip8), 0.875f)),
+            const df inner = df_add(s0v[e], df_mul(df_scale2(sgv[e], 2.0f), ip4));
+            const df mm = df_add(df_add(df_mul(df_mul(two_pi, ip2), inner), df_mulf(df_mul(av[e], ip8), 0.875f)),
                                  df_mul(p4, k2c));
             const df src = df_mul(p5, kdot);
-            stp(uh, ul, sid, df_add_acc(ld(apsi, id), m1));
-            stp(ah, al, sid, df_mul(mm, h2d));
-            stp(fh, fl, sid, df_mul(df_add(mm, df_neg(src)), h2d));
-            m32[sid] = mm.hi;
-            inv32[sid] = 1.0f / (6.0f + h2 * mm.hi);
+            uo[e] = df_add_acc(apv[e], m1);
+            ao[e] = df_mul(mm, h2d);
+            fo[e] = df_mul(df_add(mm, df_neg(src)), h2d);
+            mo[e] = mm.hi;
+            io[e] = 1.0f / (6.0f + h2 * mm.hi);
             acc.add(src);
         }
+        stp4(uh, ul, p, uo);
+        stp4(ah, al, p, ao);
+        stp4(fh, fl, p, fo);
+        stf4(m32, p, mo);
+        stf4(inv32, p, io);
     }
     acc.flush(partials);
 }
@@ -394,14 +456,16 @@ __global__ void __launch_bounds__(kBlock)
     for (int64_t tc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tc < (N >> 1) / kChunk;
          tc += (int64_t)gridDim.x * blockDim.x) {
         const PairPos p = pair_pos(lgn, tc * kChunk);
+        df v[4];
+        double d[4];
+        ldp4(uh, ul, p, v);
 #pragma unroll
         for (int e = 0; e < 2 * kChunk; e++) {
-            df v = ldp(uh, ul, p.split(e));
-            if (sum) v = df_add_acc(v, nmu);
-            double d = join_double(v);
-            if (DEV) d += 1.0;
-            out[nat(lgn, p.i, p.j, p.k0 + e)] = d;
+            if (sum) v[e] = df_add_acc(v[e], nmu);
+            d[e] = join_double(v[e]);
+            if (DEV) d[e] += 1.0;
         }
+        st4(out, nat(lgn, p.i, p.j, p.k0), d);
     }
 }
 

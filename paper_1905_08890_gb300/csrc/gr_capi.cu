@@ -178,14 +178,19 @@ bool valid_opts(const gr_opts *o)
            o->npatch >= 0 && o->npatch <= GR_MAX_PATCHES && (o->npatch == 0 || o->patch);
 }
 
+// non-NULL and on a 16-byte boundary (the set-up and write-back kernels move
+// the natural-layout arrays in 16-byte vectors)
+bool a16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
+
 bool src_ok(const gr_sources *s)
 {
-    return s && s->s0 && s->s[0] && s->s[1] && s->s[2] && s->sigma;
+    return s && a16(s->s0) && a16(s->s[0]) && a16(s->s[1]) && a16(s->s[2]) && a16(s->sigma);
 }
 
 bool fld_ok(const gr_fields *f)
 {
-    return f && f->psi && f->apsi && f->V[0] && f->V[1] && f->V[2] && f->U && f->B[0] && f->B[1] && f->B[2] && f->b;
+    return f && a16(f->psi) && a16(f->apsi) && a16(f->V[0]) && a16(f->V[1]) && a16(f->V[2]) && a16(f->U) &&
+           a16(f->B[0]) && a16(f->B[1]) && a16(f->B[2]) && a16(f->b);
 }
 
 double *field_ptr(const gr_fields *f, int eq)
@@ -1414,7 +1419,7 @@ gr_status gr_deposit(gr_ctx *c, int64_t np, const double *x, const double *u, do
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
     if (np < 0) return fail(GR_ERR_ARG, "np < 0");
     if (np > 0 && (!x || !u)) return fail(GR_ERR_ARG, "x or u is NULL");
-    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL");
+    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL or not 16-byte aligned");
     if (!(mass >= 0) || !std::isfinite(mass)) return fail(GR_ERR_ARG, "mass must be finite and >= 0");
     const bool hx = np > 0 && host_memory(x), hu = np > 0 && host_memory(u);
     if (hx != hu) return fail(GR_ERR_ARG, "x and u must both be device or both host memory");
@@ -1432,13 +1437,13 @@ gr_status gr_solve_constraints(gr_ctx *c, const gr_sources *s, gr_fields *fl, co
 {
     g_err.clear();
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
-    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL or not 16-byte aligned");
     if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
     if (o->npatch > 0) {
         if (!chain_valid(c, o->npatch, o->patch)) return fail(GR_ERR_ARG, "invalid patch chain");
         for (int p = 0; p < o->npatch; p++)
             if (!src_ok(&o->patch[p].src) || !fld_ok(&o->patch[p].fld))
-                return fail(GR_ERR_ARG, "patch %d: a source or field array is NULL", p);
+                return fail(GR_ERR_ARG, "patch %d: a source or field array is NULL or not 16-byte aligned", p);
     }
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
@@ -1520,7 +1525,7 @@ gr_status gr_vcycle(gr_ctx *c, gr_eq eq, const gr_sources *s, gr_fields *fl, con
     g_err.clear();
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
     if ((int)eq < 0 || (int)eq >= GR_NEQ) return fail(GR_ERR_ARG, "bad equation %d", (int)eq);
-    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL or not 16-byte aligned");
     if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
@@ -1541,7 +1546,7 @@ gr_status gr_residual(gr_ctx *c, gr_eq eq, const gr_sources *s, const gr_fields 
     g_err.clear();
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
     if ((int)eq < 0 || (int)eq >= GR_NEQ) return fail(GR_ERR_ARG, "bad equation %d", (int)eq);
-    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL or not 16-byte aligned");
     if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
     double rho, S_hat;
     gr_status st = resolve_bg(c, o, &rho, &S_hat);
@@ -1567,7 +1572,7 @@ gr_status gr_deposit_patches(gr_ctx *c, int npatch, const gr_patch *patch, int64
     if (np > 0 && (host_memory(x) || host_memory(u)))
         return fail(GR_ERR_ARG, "gr_deposit_patches takes device particle arrays");
     for (int p = 0; p < npatch; p++)
-        if (!src_ok(&patch[p].src)) return fail(GR_ERR_ARG, "patch %d: a source array is NULL", p);
+        if (!src_ok(&patch[p].src)) return fail(GR_ERR_ARG, "patch %d: a source array is NULL or not 16-byte aligned", p);
     // one pass over the particles lists those near the first patch (every
     // later patch lies inside it); each patch then deposits from that list
     if (np > 0 && np <= INT32_MAX && c->plist_cap < np) {
@@ -1652,7 +1657,7 @@ gr_status gr_deposit_metric(gr_ctx *c, int64_t np, const double *x, const double
     if (!c) return fail(GR_ERR_ARG, "ctx is NULL");
     if (np < 0) return fail(GR_ERR_ARG, "np < 0");
     if (np > 0 && (!x || !u)) return fail(GR_ERR_ARG, "x or u is NULL");
-    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL");
+    if (!src_ok(out)) return fail(GR_ERR_ARG, "a source array is NULL or not 16-byte aligned");
     if (!(mass >= 0) || !std::isfinite(mass)) return fail(GR_ERR_ARG, "mass must be finite and >= 0");
     if (np > 0 && (host_memory(x) || host_memory(u)))
         return fail(GR_ERR_ARG, "gr_deposit_metric takes device particle arrays");
@@ -1668,7 +1673,7 @@ gr_status gr_solve_code_units(gr_ctx *c, const gr_cosmology *cm, const gr_source
 {
     g_err.clear();
     if (!c || !cm) return fail(GR_ERR_ARG, "ctx or cosmology is NULL");
-    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL");
+    if (!src_ok(s) || !fld_ok(fl)) return fail(GR_ERR_ARG, "a source or field array is NULL or not 16-byte aligned");
     if (!valid_opts(o)) return fail(GR_ERR_ARG, "invalid gr_opts");
     if (o->npatch != 0 || o->host_out) return fail(GR_ERR_ARG, "gr_solve_code_units: no patches, no host_out");
     if (c->L != 1.0) return fail(GR_ERR_ARG, "gr_solve_code_units: the context's box side must be 1");
