@@ -453,6 +453,12 @@ def main():
            "data": "synthetic (seeded Zel'dovich particles)", "config": config,
            "time_to_residual_ms": round(solve_ms, 3), "path": args.prec, "learned": None,
            "cycles": reps[-1]["cycles"], "res": [float(f"{r:.3e}") for r in reps[-1]["res"]],
+           # the same cell updates over the solve alone (no deposit, no field reset), and the
+           # fine-equivalent rate: n^3 cells times the cycles of all ten equations per solve second
+           "solve_gcell_updates_per_s": round(sum(r["cell_updates"] for r in reps) / len(reps)
+                                              / (solve_ms * 1e-3) / 1e9 * world, 3),
+           "fine_equivalent_gcells_per_s": round(float(n) ** 3 * sum(reps[-1]["cycles"]) / (solve_ms * 1e-3) / 1e9
+                                                 * world, 3),
            "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels, "clocks": clk}
 
     # the end-to-end measurement runs first, on the state the timed steps left

@@ -281,8 +281,37 @@ __global__ void __launch_bounds__(kBlock)
 // natural-layout pairs, from the pairs of V_x, V_y, V_z, U (hi at P[f],
 // lo at P[f] + n^3); D_a V_l central, U's second derivatives by the
 // three-point and four-corner stencils (Eq. U-cross-deriv), differences by
-// the plain double-float sum as in the Poisson right-hand sides.
-__global__ void __launch_bounds__(kBlock)
+// the plain double-float sum as in the Poisson right-hand sides.  Each thread
+// makes four consecutive cells k0 .. k0 + 3 of a row: every neighbour row is
+// read once as a pair of float4 (with the two wrapped end values where the
+// k neighbours are needed), and the outputs are written as float4.  The
+// double-float operations of each cell are those of a cell-by-cell
+// evaluation, in the same order; the components are formed one after another
+// (AA's sums of squares accumulate in the order xx, yy, zz and xy, xz, yz).
+
+// values k0 .. k0 + 3 of the row starting at r of a pair array f (lo at f + N)
+__device__ __forceinline__ void prow4(const float *__restrict__ f, int64_t N, int r, int k0, df o[4])
+{
+    const float4 h = *reinterpret_cast<const float4 *>(f + r + k0), l = *reinterpret_cast<const float4 *>(f + N + r + k0);
+    o[0] = {h.x, l.x}, o[1] = {h.y, l.y}, o[2] = {h.z, l.z}, o[3] = {h.w, l.w};
+}
+
+// values k0 - 1 .. k0 + 4 (periodic) of the row starting at r
+__device__ __forceinline__ void prow6(const float *__restrict__ f, int64_t N, int r, int k0, int m, df o[6])
+{
+    const int km = r + ((k0 - 1) & m), kp = r + ((k0 + 4) & m);
+    o[0] = {f[km], f[N + km]};
+    prow4(f, N, r, k0, o + 1);
+    o[5] = {f[kp], f[N + kp]};
+}
+
+__device__ __forceinline__ void pst4(float *__restrict__ h, float *__restrict__ l, int t, const df v[4])
+{
+    *reinterpret_cast<float4 *>(h + t) = make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi);
+    *reinterpret_cast<float4 *>(l + t) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
+}
+
+__global__ void __launch_bounds__(kBlock, 2)
     k_dfs_aij(int lgn, df inv2h, df ih2, const float *__restrict__ Pvx, const float *__restrict__ Pvy,
               const float *__restrict__ Pvz, const float *__restrict__ Pu, float *__restrict__ A,
               float *__restrict__ AAh, float *__restrict__ AAl)
@@ -292,47 +321,94 @@ __global__ void __launch_bounds__(kBlock)
     const int m = (1 << lgn) - 1;
     const float *V[3] = {Pvx, Pvy, Pvz};
     const df qih2 = df_scale2(ih2, 0.25f);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)N; t += gridDim.x * blockDim.x) {
-        const int k = t & m, j = (t >> lgn) & m, i = t >> (2 * lgn);
-        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m, kp = (k + 1) & m,
-                  km = (k - 1) & m;
-        const int plus[3] = {nat(lgn, ip, j, k), nat(lgn, i, jp, k), nat(lgn, i, j, kp)};
-        const int minus[3] = {nat(lgn, im, j, k), nat(lgn, i, jm, k), nat(lgn, i, j, km)};
-        auto P = [&](const float *f, int id) { return ldp(f, f + N, id); };
-        auto diff = [&](df a, df b) { return df_add(a, df_neg(b)); };
-        df D[3][3];
+    auto diff = [&](df a, df b) { return df_add(a, df_neg(b)); };
+    for (int tc = blockIdx.x * blockDim.x + threadIdx.x; tc < (int)(N >> 2); tc += gridDim.x * blockDim.x) {
+        const int t = tc << 2;
+        const int k0 = t & m, j = (t >> lgn) & m, i = t >> (2 * lgn);
+        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+        const int r = t - k0;                                   // row (i, j)
+        const int rp[2] = {nat(lgn, ip, j, 0), nat(lgn, i, jp, 0)};  // rows (i + 1, j), (i, j + 1)
+        const int rm[2] = {nat(lgn, im, j, 0), nat(lgn, i, jm, 0)};  // rows (i - 1, j), (i, j - 1)
+        // D_ax V_l of the four cells: x and y from the neighbour rows, z along the own row
+        auto dv = [&](int ax, int l, df d[4]) {
+            if (ax < 2) {
+                df a[4], b[4];
+                prow4(V[l], N, rp[ax], k0, a);
+                prow4(V[l], N, rm[ax], k0, b);
 #pragma unroll
-        for (int ax = 0; ax < 3; ax++)
+                for (int e = 0; e < 4; e++) d[e] = df_mul(diff(a[e], b[e]), inv2h);
+            } else {
+                df z[6];
+                prow6(V[l], N, r, k0, m, z);
 #pragma unroll
-            for (int l = 0; l < 3; l++) D[ax][l] = df_mul(diff(P(V[l], plus[ax]), P(V[l], minus[ax])), inv2h);
-        const df divV = df_add(df_add(D[0][0], D[1][1]), D[2][2]);
-        const df u0m2 = df_scale2(P(Pu, t), -2.0f);
-        df Ad[3], Ao[3];
+                for (int e = 0; e < 4; e++) d[e] = df_mul(diff(z[e + 2], z[e]), inv2h);
+            }
+        };
+        df Dd[3][4], divV[4], dd[4], oo[4], u0m2[4], U6[6];
+        dv(0, 0, Dd[0]);
+        dv(1, 1, Dd[1]);
+        dv(2, 2, Dd[2]);
+        prow6(Pu, N, r, k0, m, U6);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            divV[e] = df_add(df_add(Dd[0][e], Dd[1][e]), Dd[2][e]);
+            u0m2[e] = df_scale2(U6[e + 1], -2.0f);
+        }
+        // diagonal components
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
-            const df Uaa = df_mul(df_add(df_add(P(Pu, plus[ax]), P(Pu, minus[ax])), u0m2), ih2);
-            Ad[ax] = df_add(df_add(df_scale2(D[ax][ax], 2.0f), df_scale2(divV, -0.5f)), df_scale2(Uaa, 2.0f));
+            df up[4], um[4], Ad[4];
+            if (ax < 2) {
+                prow4(Pu, N, rp[ax], k0, up);
+                prow4(Pu, N, rm[ax], k0, um);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) up[e] = U6[e + 2], um[e] = U6[e];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const df Uaa = df_mul(df_add(df_add(up[e], um[e]), u0m2[e]), ih2);
+                Ad[e] = df_add(df_add(df_scale2(Dd[ax][e], 2.0f), df_scale2(divV[e], -0.5f)), df_scale2(Uaa, 2.0f));
+                const df sq = df_mul(Ad[e], Ad[e]);
+                dd[e] = ax == 0 ? sq : df_add(dd[e], sq);
+            }
+            pst4(A + 2 * ax * N, A + (2 * ax + 1) * N, t, Ad);
         }
-        const df Uxy = df_mul(diff(df_add(P(Pu, nat(lgn, ip, jp, k)), P(Pu, nat(lgn, im, jm, k))),
-                                   df_add(P(Pu, nat(lgn, im, jp, k)), P(Pu, nat(lgn, ip, jm, k)))),
-                              qih2);
-        const df Uxz = df_mul(diff(df_add(P(Pu, nat(lgn, ip, j, kp)), P(Pu, nat(lgn, im, j, km))),
-                                   df_add(P(Pu, nat(lgn, im, j, kp)), P(Pu, nat(lgn, ip, j, km)))),
-                              qih2);
-        const df Uyz = df_mul(diff(df_add(P(Pu, nat(lgn, i, jp, kp)), P(Pu, nat(lgn, i, jm, km))),
-                                   df_add(P(Pu, nat(lgn, i, jm, kp)), P(Pu, nat(lgn, i, jp, km)))),
-                              qih2);
-        Ao[0] = df_add(df_add(D[0][1], D[1][0]), df_scale2(Uxy, 2.0f));
-        Ao[1] = df_add(df_add(D[0][2], D[2][0]), df_scale2(Uxz, 2.0f));
-        Ao[2] = df_add(df_add(D[1][2], D[2][1]), df_scale2(Uyz, 2.0f));
+        // off-diagonal components xy, xz, yz: D_a V_b + D_b V_a + 2 U_ab
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            stp(A + 2 * c * N, A + (2 * c + 1) * N, t, Ad[c]);
-            stp(A + 2 * (3 + c) * N, A + (2 * (3 + c) + 1) * N, t, Ao[c]);
+            const int a = c < 2 ? 0 : 1, b = c == 0 ? 1 : 2;
+            df Dab[4], Dba[4], Uab[4], Ao[4];
+            dv(a, b, Dab);
+            dv(b, a, Dba);
+            if (c == 0) {  // corners (i +- 1, j +- 1) at k
+                df pp[4], mm[4], mp[4], pm[4];
+                prow4(Pu, N, nat(lgn, ip, jp, 0), k0, pp);
+                prow4(Pu, N, nat(lgn, im, jm, 0), k0, mm);
+                prow4(Pu, N, nat(lgn, im, jp, 0), k0, mp);
+                prow4(Pu, N, nat(lgn, ip, jm, 0), k0, pm);
+#pragma unroll
+                for (int e = 0; e < 4; e++) Uab[e] = df_mul(diff(df_add(pp[e], mm[e]), df_add(mp[e], pm[e])), qih2);
+            } else {  // corners (x_a +- 1, k +- 1): rows (i +- 1, j) (c = 1) or (i, j +- 1) (c = 2)
+                df P6[6], M6[6];
+                prow6(Pu, N, rp[c - 1], k0, m, P6);
+                prow6(Pu, N, rm[c - 1], k0, m, M6);
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    Uab[e] = df_mul(diff(df_add(P6[e + 2], M6[e]), df_add(M6[e + 2], P6[e])), qih2);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                Ao[e] = df_add(df_add(Dab[e], Dba[e]), df_scale2(Uab[e], 2.0f));
+                const df sq = df_mul(Ao[e], Ao[e]);
+                oo[e] = c == 0 ? sq : df_add(oo[e], sq);
+            }
+            pst4(A + 2 * (3 + c) * N, A + (2 * (3 + c) + 1) * N, t, Ao);
         }
-        const df dd = df_add(df_add(df_mul(Ad[0], Ad[0]), df_mul(Ad[1], Ad[1])), df_mul(Ad[2], Ad[2]));
-        const df oo = df_add(df_add(df_mul(Ao[0], Ao[0]), df_mul(Ao[1], Ao[1])), df_mul(Ao[2], Ao[2]));
-        stp(AAh, AAl, t, df_add(dd, df_scale2(oo, 2.0f)));
+        df aa[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) aa[e] = df_add(dd[e], df_scale2(oo[e], 2.0f));
+        pst4(AAh, AAl, t, aa);
     }
 }
 
@@ -551,7 +627,7 @@ void dfs_aij(int n, double inv2h, double ih2, const double *Vx, const double *Vy
     const int64_t N = (int64_t)n * n * n;
     GR_LAUNCH(k_dfs_split4, grid_for(N), kBlock, st, N, Vx, Vy, Vz, U, scratch[0], scratch[1], scratch[2],
               scratch[3]);
-    GR_LAUNCH(k_dfs_aij, wave_grid(k_dfs_aij, N), kBlock, st, lgn, df_from_double_host(inv2h), df_from_double_host(ih2),
+    GR_LAUNCH(k_dfs_aij, wave_grid(k_dfs_aij, N / 4), kBlock, st, lgn, df_from_double_host(inv2h), df_from_double_host(ih2),
               scratch[0], scratch[1], scratch[2], scratch[3], A, AAh, AAl);
 }
 
