@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBlock)
 // half the loads and a third of the index arithmetic of one thread per coarse
 // cell.  FIRST as in k_resid_restrict.
 template <int KIND, int FIRST>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, KIND == KPOISSON ? 5 : 4)
     k_restrict_red2(int lgf, const float *__restrict__ e, const float *__restrict__ r, const float *__restrict__ m,
                     float ih2, float *__restrict__ ec, float *__restrict__ rc, const float *__restrict__ cinv,
                     float h2c, int rev)
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(int lgf, T *__restrict__
 // the four fine rows are one float4 of the black half-array; the coarse row's
 // values K = 4P - 1 .. 4P + 4 are two float2 and two scalar loads per
 // neighbouring coarse row
-__global__ void __launch_bounds__(kBlock) k_prolong_black4(int lgf, float *__restrict__ u, const float *__restrict__ uc,
+__global__ void __launch_bounds__(kBlock, 5) k_prolong_black4(int lgf, float *__restrict__ u, const float *__restrict__ uc,
                                                            int rev)
 {
     pdl_begin();
