@@ -561,6 +561,8 @@ def e2e_measure(ctx, p, n, opts, world, steps):
     del probe_d
     ctx.deposit(xh, uh, p.mass, src)  # untimed: the context allocates its staging buffers on first use
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     t0 = time.perf_counter()
     updates = 0
     per_step, phases = [], []
@@ -584,11 +586,12 @@ def e2e_measure(ctx, p, n, opts, world, steps):
         phases.append({"deposit_from_host_ms": round(dep, 1), "solve_ms": round(solve, 1),
                        "copy_tail_ms": round(max(rest - solve, 0.0), 1)})
     dt = time.perf_counter() - t0
+    clk = clocks.stop()
     med = sorted(per_step)[len(per_step) // 2]
     return {"value": round(updates * world / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 48 * n ** 3,
             "d2h_bytes_per_step": 80 * n ** 3, "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3),
             "ms_each_step": per_step, "median_ms_per_step": med, "phases_each_step": phases,
-            "link_rates_before_steps": rates}
+            "link_rates_before_steps": rates, "clocks": clk}
 
 
 def fmg_measure(ctx, x, u, p, src, fld, opts):
