@@ -311,6 +311,85 @@ __global__ void k_relu_mask(__nv_bfloat16 *__restrict__ gbuf, const __nv_bfloat1
         if (!(__bfloat162float(a[e]) > 0.0f)) gbuf[e] = __float2bfloat16(0.0f);
 }
 
+// Eight channels per thread (c and the channel strides and offsets multiples
+// of 8, 16-byte aligned rows): the same per-channel arithmetic as k_upsample
+// and k_copy_slice with 16-byte loads and stores and the weights and indices
+// formed once per eight channels.
+__device__ __forceinline__ void bf8_unpack(uint4 r, float f[8])
+{
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float2 t = __bfloat1622float2(h[m]);
+        f[2 * m] = t.x, f[2 * m + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 bf8_pack(const float f[8])
+{
+    uint4 r;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int m = 0; m < 4; m++) h[m] = __floats2bfloat162_rn(f[2 * m], f[2 * m + 1]);
+    return r;
+}
+
+__global__ void k_upsample8(const __nv_bfloat16 *__restrict__ x, int lgc8, int lgc, __nv_bfloat16 *__restrict__ y,
+                            int cstride)
+{
+    pdl_begin();
+    const int lgf = lgc + 1, mf = (1 << lgf) - 1, mc = (1 << lgc) - 1, c = 8 << lgc8;
+    const int total = 1 << (3 * lgf + lgc8);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int ch = (e & ((1 << lgc8) - 1)) << 3;
+        const int v = e >> lgc8;
+        const int k = v & mf, j = (v >> lgf) & mf, i = v >> (2 * lgf);
+        int I[2], J[2], K[2];
+        I[0] = i >> 1;
+        I[1] = (i & 1) ? ((I[0] + 1) & mc) : ((I[0] - 1) & mc);
+        J[0] = j >> 1;
+        J[1] = (j & 1) ? ((J[0] + 1) & mc) : ((J[0] - 1) & mc);
+        K[0] = k >> 1;
+        K[1] = (k & 1) ? ((K[0] + 1) & mc) : ((K[0] - 1) & mc);
+        const float wt[2] = {0.75f, 0.25f};
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const float w = wt[a] * wt[b] * wt[q];
+                    float xv[8];
+                    bf8_unpack(*reinterpret_cast<const uint4 *>(x + (size_t)((((I[a] << lgc) + J[b]) << lgc) + K[q]) * c + ch), xv);
+#pragma unroll
+                    for (int m = 0; m < 8; m++) s[m] += w * xv[m];
+                }
+        *reinterpret_cast<uint4 *>(y + (size_t)v * cstride + ch) = bf8_pack(s);
+    }
+}
+
+__global__ void k_copy_slice8(const __nv_bfloat16 *__restrict__ x, int lgc8, int xs, int xoff,
+                              __nv_bfloat16 *__restrict__ y, int ys, int yoff, int nv, int accumulate)
+{
+    pdl_begin();
+    const int total = nv << lgc8;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int ch = (e & ((1 << lgc8) - 1)) << 3;
+        const int v = e >> lgc8;
+        float val[8];
+        bf8_unpack(*reinterpret_cast<const uint4 *>(x + (size_t)v * xs + xoff + ch), val);
+        uint4 *o = reinterpret_cast<uint4 *>(y + (size_t)v * ys + yoff + ch);
+        if (accumulate) {
+            float prev[8];
+            bf8_unpack(*o, prev);
+#pragma unroll
+            for (int m = 0; m < 8; m++) val[m] += prev[m];
+        }
+        *o = bf8_pack(val);
+    }
+}
+
 // ---------------------------------------------------------------- input, head, loss
 // x[v][0..15]: standardised log(eps + s0/rho), s_i/(rho v_rms), zeros; from natural-layout sources
 __global__ void k_net_input(const double *__restrict__ s0, const double *__restrict__ sx, const double *__restrict__ sy,
@@ -325,9 +404,13 @@ __global__ void k_net_input(const double *__restrict__ s0, const double *__restr
         f[1] = (float)sx[v] * inv_rv;
         f[2] = (float)sy[v] * inv_rv;
         f[3] = (float)sz[v] * inv_rv;
-        __nv_bfloat16 *o = x + v * kNetCin;
-        for (int c = 0; c < 4; c++) o[c] = __float2bfloat16((f[c] - in_mean[c]) / in_std[c]);
-        for (int c = 4; c < kNetCin; c++) o[c] = __float2bfloat16(0.0f);
+        // the voxel's 16 channels (4 used, 12 zero) as two 16-byte stores
+        float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = 0; c < 4; c++) g[c] = (f[c] - in_mean[c]) / in_std[c];
+        static_assert(kNetCin == 16, "two 8-channel vectors per voxel");
+        uint4 *o = reinterpret_cast<uint4 *>(x + v * kNetCin);
+        o[0] = bf8_pack(g);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -419,9 +502,21 @@ __global__ void k_net_output(const float *__restrict__ out, int64_t nv, const fl
 {
     pdl_begin();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
-        for (int o = 0; o < kNetOut; o++) {
-            double val = (double)out[v * kNetOut + o] * stdv[o] + mean[o];
-            fields.p[o][v] = o < 2 ? val + 1.0 : val;
+        {
+            const float2 *o2 = reinterpret_cast<const float2 *>(out + v * kNetOut);
+            float ov[kNetOut];
+#pragma unroll
+            for (int o = 0; o < kNetOut / 2; o++) {
+                const float2 t2 = o2[o];
+                ov[2 * o] = t2.x, ov[2 * o + 1] = t2.y;
+            }
+#pragma unroll
+            for (int o = 0; o < kNetOut; o++) {
+                // FP32 de-standardisation as in k_net_output_fine (the guess carries BF16 accuracy),
+                // so only the conversion and psi's and alpha psi's + 1 use the narrow FP64 pipe
+                const double val = (double)(ov[o] * stdv[o] + mean[o]);
+                fields.p[o][v] = o < 2 ? val + 1.0 : val;
+            }
         }
 }
 
@@ -582,8 +677,22 @@ void pool_back(const __nv_bfloat16 *dy, int c, int lgf, __nv_bfloat16 *dx, int c
     GR_LAUNCH(k_pool_back, cdiv(((int64_t)1 << (3 * lgf)) * c, 256), 256, st, dy, c, lgf, dx, cstride, accumulate);
 }
 
+// exponent of a power of two, -1 otherwise
+static int pow2_log(int c)
+{
+    if (c <= 0 || (c & (c - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < c) ++l;
+    return l;
+}
+
 void upsample(const __nv_bfloat16 *x, int c, int lgc, __nv_bfloat16 *y, int cstride, cudaStream_t st)
 {
+    const int l8 = pow2_log(c) - 3;
+    if (l8 >= 0 && cstride % 8 == 0 && 3 * lgc + 3 + l8 < 31) {
+        GR_LAUNCH(k_upsample8, cdiv((int64_t)1 << (3 * lgc + 3 + l8), 256), 256, st, x, l8, lgc, y, cstride);
+        return;
+    }
     GR_LAUNCH(k_upsample, cdiv(((int64_t)1 << (3 * lgc + 3)) * c, 256), 256, st, x, c, lgc, y, cstride);
 }
 
@@ -595,6 +704,11 @@ void upsample_back(const __nv_bfloat16 *dy, int c, int cstride, int lgc, __nv_bf
 void copy_slice(const __nv_bfloat16 *x, int c, int xs, int xoff, __nv_bfloat16 *y, int ys, int yoff, int64_t nv,
                 int accumulate, cudaStream_t st)
 {
+    const int l8 = pow2_log(c) - 3;
+    if (l8 >= 0 && xs % 8 == 0 && ys % 8 == 0 && xoff % 8 == 0 && yoff % 8 == 0 && (nv << l8) < (1LL << 31)) {
+        GR_LAUNCH(k_copy_slice8, cdiv(nv << l8, 256), 256, st, x, l8, xs, xoff, y, ys, yoff, (int)nv, accumulate);
+        return;
+    }
     GR_LAUNCH(k_copy_slice, cdiv(nv * c, 256), 256, st, x, c, xs, xoff, y, ys, yoff, nv, accumulate);
 }
 
