@@ -136,3 +136,11 @@ def test_code_unit_entry_point_rejects_bad_arguments_without_gpu():
     o = gr.make_opts()
     cm = gr.gr_cosmology(1.0, 1.0, 0.0, 1.0 / 3.0)
     assert gr.lib().gr_solve_code_units(None, ctypes.byref(cm), None, None, ctypes.byref(o), None) == gr.GR_ERR_ARG
+
+
+def test_fma_rate_rejects_bad_arguments_without_gpu():
+    L = gr.lib()
+    out = ctypes.c_double(-1.0)
+    assert L.gr_fma_rate(1, 0, None, ctypes.byref(out)) == gr.GR_ERR_ARG
+    assert L.gr_fma_rate(0, (1 << 32) + 1, None, ctypes.byref(out)) == gr.GR_ERR_ARG
+    assert L.gr_fma_rate(1, 100, None, None) == gr.GR_ERR_ARG
