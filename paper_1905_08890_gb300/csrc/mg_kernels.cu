@@ -539,13 +539,15 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
                            double h2, double ih2, double rho)
 {
     pdl_begin();
-    __shared__ double su[8], sf[8], s0[8], s1[8];
+    __shared__ double su[8], sf[8], s0[8], s1[8], sd[8];
     const int t = threadIdx.x;
     if (t < 8) {
         su[t] = (double)u[t];
         sf[t] = (double)f[t];
         s0[t] = (KIND == KPOISSON) ? 0.0 : (double)c0[t];
         s1[t] = (KIND == KPSI) ? (double)c1[t] : 0.0;
+        // inverse diagonal of the linear kinds, formed once: the sweeps multiply
+        sd[t] = (KIND == KHELM) ? 1.0 / (6.0 + h2 * s0[t]) : 1.0 / 6.0;
     }
     __syncthreads();
     if (KIND == KPOISSON && t == 0) {
@@ -564,10 +566,8 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
                 const int id = 4 * color + t;
                 const int o = 4 * (color ^ 1);
                 const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                if (KIND == KPOISSON) {
-                    su[id] = (nb - h2 * sf[id]) / 6.0;
-                } else if (KIND == KHELM) {
-                    su[id] = (nb - h2 * sf[id]) / (6.0 + h2 * s0[id]);
+                if (KIND == KPOISSON || KIND == KHELM) {
+                    su[id] = (nb - h2 * sf[id]) * sd[id];
                 } else {
                     const double uc = su[id], v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
                     const double g = (nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[id] / v + s1[id] / (8.0 * v4 * v2 * v) -
@@ -991,46 +991,79 @@ __device__ __forceinline__ int tail_sidx(int lg, int i, int j, int k)
     return ((i + j + k) & 1) * (1 << (3 * lg - 1)) + ((((i << lg) + j) << (lg - 1)) + (k >> 1));
 }
 
-template <int KIND>
-__device__ void tail_sweep(const TailLevel &L, int color)
+// one colour pass on a level of the tail, W consecutive half-indices of a row
+// per thread (W = 4 from 8^3, 2 on 4^3), with the addressing and the order of
+// additions of the full-grid colour pass (k_sweep4)
+template <int KIND, int W>
+__device__ void tail_sweep_w(const TailLevel &L, int color)
 {
-    const int lg = L.lg, n1 = (1 << lg) - 1, half = 1 << (3 * lg - 1);
-    for (int t = threadIdx.x; t < half; t += blockDim.x) {
-        const int q = t & ((1 << (lg - 1)) - 1);
-        const int j = (t >> (lg - 1)) & n1, i = t >> (2 * lg - 1);
-        const int k = 2 * q + ((i + j + color) & 1);
-        const float nb = L.e[tail_sidx(lg, (i + 1) & n1, j, k)] + L.e[tail_sidx(lg, (i - 1) & n1, j, k)] +
-                         L.e[tail_sidx(lg, i, (j + 1) & n1, k)] + L.e[tail_sidx(lg, i, (j - 1) & n1, k)] +
-                         L.e[tail_sidx(lg, i, j, (k + 1) & n1)] + L.e[tail_sidx(lg, i, j, (k - 1) & n1)];
-        const int id = color * half + t;
-        L.e[id] = KIND == KPOISSON ? (nb - L.h2 * L.r[id]) * (1.0f / 6.0f) : (nb - L.h2 * L.r[id]) * L.inv[id];
+    const int lgn = L.lg, lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
+    const int half = 1 << (3 * lgn - 1), off = color ? half : 0;
+    float *own = L.e + off;
+    const float *oth = L.e + (half - off);
+    for (int v = threadIdx.x; v < half / W; v += blockDim.x) {
+        const int t = v * W;
+        const int q = t & mh, j = (t >> lgh) & mn, i = t >> (lgh + lgn);
+        const int p = (i + j + color) & 1;
+        const int r0 = t - q, ri = j << lgh;
+        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri, rim = (((i - 1) & mn) << (lgn + lgh)) + ri;
+        const int rj = i << (lgn + lgh);
+        const int rjp = rj + (((j + 1) & mn) << lgh), rjm = rj + (((j - 1) & mn) << lgh);
+        const float x = oth[r0 + ((q + (p ? W : -1)) & mh)];
+#pragma unroll
+        for (int e = 0; e < W; e++) {
+            const float E = oth[r0 + q + e];
+            const float sh = p ? (e + 1 < W ? oth[r0 + q + e + 1] : x) : (e > 0 ? oth[r0 + q + e - 1] : x);
+            const float nb = oth[rip + q + e] + oth[rim + q + e] + oth[rjp + q + e] + oth[rjm + q + e] + E + sh;
+            const int id = off + t + e;
+            const float g = KIND == KPOISSON ? 1.0f / 6.0f : L.inv[id];
+            own[t + e] = __fmaf_rn(-L.h2, L.r[id], nb) * g;
+        }
     }
     __syncthreads();
 }
 
 template <int KIND>
-__device__ void tail_down(const TailLevel &A, const TailLevel &C)
+__device__ void tail_sweep(const TailLevel &L, int color)
 {
-    const int lc = C.lg, mc = (1 << lc) - 1, nf1 = (1 << A.lg) - 1;
+    if (L.lg >= 3) tail_sweep_w<KIND, 4>(L, color);
+    else tail_sweep_w<KIND, 2>(L, color);
+}
+
+// residual L(e) - r of every cell of level A into A's scratch row array res
+// (split layout), then the 8-child averages, negated, as the next level's
+// right-hand side (its correction starts at zero)
+template <int KIND>
+__device__ void tail_down(const TailLevel &A, const TailLevel &C, float *res)
+{
+    const int lgn = A.lg, lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
+    const int half = 1 << (3 * lgn - 1);
+    for (int tt = threadIdx.x; tt < 2 * half; tt += blockDim.x) {
+        const int color = tt >= half, t = tt - (color ? half : 0);
+        const int off = color ? half : 0;
+        const float *oth = A.e + (half - off);
+        const int q = t & mh, j = (t >> lgh) & mn, i = t >> (lgh + lgn);
+        const int p = (i + j + color) & 1;
+        const int r0 = t - q, ri = j << lgh;
+        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri, rim = (((i - 1) & mn) << (lgn + lgh)) + ri;
+        const int rj = i << (lgn + lgh);
+        const int rjp = rj + (((j + 1) & mn) << lgh), rjm = rj + (((j - 1) & mn) << lgh);
+        const float nb = oth[rip + q] + oth[rim + q] + oth[rjp + q] + oth[rjm + q] + oth[r0 + q] +
+                         oth[r0 + ((q + (p ? 1 : -1)) & mh)];
+        const int id = off + t;
+        const float u = A.e[id];
+        float lap = (nb - 6.0f * u) * A.ih2;
+        if (KIND == KHELM) lap -= A.m[id] * u;
+        res[id] = lap - A.r[id];
+    }
+    __syncthreads();
+    const int lc = C.lg, mc = (1 << lc) - 1;
     for (int t = threadIdx.x; t < (1 << (3 * lc)); t += blockDim.x) {
         const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
         float s = 0.0f;
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++)
-                for (int c = 0; c < 2; c++) {
-                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
-                    const int id = tail_sidx(A.lg, i, j, k);
-                    const float u = A.e[id];
-                    const float nb = A.e[tail_sidx(A.lg, (i + 1) & nf1, j, k)] +
-                                     A.e[tail_sidx(A.lg, (i - 1) & nf1, j, k)] +
-                                     A.e[tail_sidx(A.lg, i, (j + 1) & nf1, k)] +
-                                     A.e[tail_sidx(A.lg, i, (j - 1) & nf1, k)] +
-                                     A.e[tail_sidx(A.lg, i, j, (k + 1) & nf1)] +
-                                     A.e[tail_sidx(A.lg, i, j, (k - 1) & nf1)];
-                    float lap = (nb - 6.0f * u) * A.ih2;
-                    if (KIND == KHELM) lap -= A.m[id] * u;
-                    s += lap - A.r[id];
-                }
+                for (int c = 0; c < 2; c++) s += res[tail_sidx(A.lg, 2 * I + a, 2 * J + b, 2 * K + c)];
         const int cid = tail_sidx(lc, I, J, K);
         C.r[cid] = -(0.125f * s);
         C.e[cid] = 0.0f;
@@ -1038,11 +1071,19 @@ __device__ void tail_down(const TailLevel &A, const TailLevel &C)
     __syncthreads();
 }
 
-__device__ void tail_up(const TailLevel &A, const TailLevel &C)
+// trilinear prolongation of the coarser level's correction added to level A;
+// black_only: a red pass follows, which does not read the red values, so only
+// the black cells take the correction (as prolong_add_black)
+__device__ void tail_up(const TailLevel &A, const TailLevel &C, bool black_only)
 {
-    const int lc = C.lg, mc = (1 << lc) - 1, lf = A.lg, nf1 = (1 << lf) - 1;
-    for (int t = threadIdx.x; t < (1 << (3 * lf)); t += blockDim.x) {
-        const int k = t & nf1, j = (t >> lf) & nf1, i = t >> (2 * lf);
+    const int lc = C.lg, mc = (1 << lc) - 1, lf = A.lg, nf1 = (1 << lf) - 1, lgh = lf - 1, mh = (1 << lgh) - 1;
+    const int half = 1 << (3 * lf - 1);
+    const int ncell = black_only ? half : 2 * half;
+    for (int tt = threadIdx.x; tt < ncell; tt += blockDim.x) {
+        // split index: colour 1 (black) first when black_only, else both colours
+        const int color = black_only ? 1 : (tt >= half), t = tt - ((!black_only && color) ? half : 0);
+        const int q = t & mh, j = (t >> lgh) & nf1, i = t >> (lgh + lf);
+        const int k = 2 * q + ((i + j + color) & 1);
         int Ia[2], Jb[2], Kc[2];
         Ia[0] = i >> 1;
         Ia[1] = (i & 1) ? ((Ia[0] + 1) & mc) : ((Ia[0] - 1) & mc);
@@ -1056,7 +1097,7 @@ __device__ void tail_up(const TailLevel &A, const TailLevel &C)
             for (int b = 0; b < 2; b++)
                 z[a][b] = w[0] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[0])] + w[1] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[1])];
         const float y0 = w[0] * z[0][0] + w[1] * z[0][1], y1 = w[0] * z[1][0] + w[1] * z[1][1];
-        A.e[tail_sidx(lf, i, j, k)] += w[0] * y0 + w[1] * y1;
+        A.e[(color ? half : 0) + t] += w[0] * y0 + w[1] * y1;
     }
     __syncthreads();
 }
@@ -1066,13 +1107,14 @@ __device__ void tail_up(const TailLevel &A, const TailLevel &C)
 template <int KIND>
 __device__ void tail_coarsest(const TailLevel &Z)
 {
-    __shared__ double su[8], sf[8], sm[8];
+    __shared__ double su[8], sf[8], sm[8], sd[8];
     const int t = threadIdx.x;
     if (t < 32) {
         if (t < 8) {
             su[t] = Z.e[t];
             sf[t] = Z.r[t];
             sm[t] = KIND == KPOISSON ? 0.0 : (double)Z.m[t];
+            sd[t] = KIND == KPOISSON ? 1.0 / 6.0 : 1.0 / (6.0 + (double)Z.h2 * sm[t]);  // as k_coarsest
         }
         __syncwarp();
         if (KIND == KPOISSON && t == 0) {
@@ -1088,7 +1130,7 @@ __device__ void tail_coarsest(const TailLevel &Z)
                 if (t < 4) {
                     const int i = t >> 1, j = t & 1, id = 4 * color + t, o = 4 * (color ^ 1);
                     const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                    su[id] = KIND == KPOISSON ? (nb - h2 * sf[id]) / 6.0 : (nb - h2 * sf[id]) / (6.0 + h2 * sm[id]);
+                    su[id] = (nb - h2 * sf[id]) * sd[id];
                 }
                 __syncwarp();
             }
@@ -1135,7 +1177,9 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs g, int nu
     pdl_begin();
     extern __shared__ float sh[];
     TailLevel L[4];
-    float *p = sh;
+    float *res = sh;  // residual scratch of the finest tail level (16^3 cells)
+    float *p = sh + (1 << 12);
+#pragma unroll
     for (int l = 0; l < 4; l++) {
         const int cells = 1 << (3 * (l + 1));
         L[l].lg = l + 1;
@@ -1158,16 +1202,18 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs g, int nu
         }
     }
     __syncthreads();
+#pragma unroll
     for (int l = 3; l >= 1; l--) {
         for (int s = 0; s < nu1; s++) {
             tail_sweep<KIND>(L[l], 0);
             tail_sweep<KIND>(L[l], 1);
         }
-        tail_down<KIND>(L[l], L[l - 1]);
+        tail_down<KIND>(L[l], L[l - 1], res);
     }
     tail_coarsest<KIND>(L[0]);
+#pragma unroll
     for (int l = 1; l <= 3; l++) {
-        tail_up(L[l], L[l - 1]);
+        tail_up(L[l], L[l - 1], nu2 > 0);
         for (int s = 0; s < nu2; s++) {
             tail_sweep<KIND>(L[l], 0);
             tail_sweep<KIND>(L[l], 1);
@@ -1191,7 +1237,7 @@ void coarse_tail(int kind, float *const *e, float *const *r, const float *const 
         a.inv[l] = inv[l];
         a.h2[l] = (float)h2[l];
     }
-    const size_t smem = 4 * sizeof(float) * (8 + 64 + 512 + 4096);
+    const size_t smem = sizeof(float) * (4096 + 4 * (8 + 64 + 512 + 4096));  // residual scratch + e, r, m, inv
     static bool attr_set[2] = {false, false};
     if (kind == KPOISSON) {
         if (!attr_set[0]) {
