@@ -27,6 +27,8 @@
 
 #include <cstdint>
 
+#include <mutex>
+
 #include "gr_internal.cuh"
 #include "unet_internal.cuh"
 
@@ -261,7 +263,9 @@ void launch_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const fl
 {
     const size_t smem = 128 + (size_t)27 * (cin / 16) * N * 32 + kAStage;
     static int grid_of[16] = {};  // per cin / 16
+    static std::mutex mu;         // host threads may launch concurrently
     const int ci = cin / 16;
+    std::lock_guard<std::mutex> lock(mu);
     if (!grid_of[ci]) {
         int dev = 0, optin = 0, per_sm = 0, sms = 0;
         cudaGetDevice(&dev);

@@ -1238,18 +1238,16 @@ void coarse_tail(int kind, float *const *e, float *const *r, const float *const 
         a.h2[l] = (float)h2[l];
     }
     const size_t smem = sizeof(float) * (4096 + 4 * (8 + 64 + 512 + 4096));  // residual scratch + e, r, m, inv
-    static bool attr_set[2] = {false, false};
+    // once per kernel (function-local statics are initialised once, even with several host threads)
     if (kind == KPOISSON) {
-        if (!attr_set[0]) {
-            cudaFuncSetAttribute(k_coarse_tail<KPOISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set[0] = true;
-        }
+        static const bool attr = cudaFuncSetAttribute(k_coarse_tail<KPOISSON>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+        (void)attr;
         GR_LAUNCH_SMEM(k_coarse_tail<KPOISSON>, 1, kTailThreads, smem, st, a, nu1, nu2);
     } else {
-        if (!attr_set[1]) {
-            cudaFuncSetAttribute(k_coarse_tail<KHELM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set[1] = true;
-        }
+        static const bool attr = cudaFuncSetAttribute(k_coarse_tail<KHELM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)smem) == cudaSuccess;
+        (void)attr;
         GR_LAUNCH_SMEM(k_coarse_tail<KHELM>, 1, kTailThreads, smem, st, a, nu1, nu2);
     }
 }

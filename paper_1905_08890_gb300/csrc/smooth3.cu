@@ -374,11 +374,10 @@ void launch_s3(void (*kern)(S3Args), int n, const float *ein, float *eout, const
 {
     const S3Layout<KIND, D> L{kTJMax};
     const size_t smem = (size_t)L.total() * sizeof(float4);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // once per kernel (a function-local static is initialised once, even with several host threads)
+    static const bool attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                             cudaSuccess;
+    (void)attr;
     int lgn = 0;
     while ((1 << lgn) < n) ++lgn;
     S3Args a{ein, eout, f, g, (float)h2, lgn, c1, rt};
