@@ -145,7 +145,7 @@ __device__ __forceinline__ void substep(int j, float hdt, const float *q, const 
 // One thread per particle (blocks start in index order, so for lattice-ordered
 // particles the cells in flight are a few planes that L2 holds).
 __global__ void __launch_bounds__(kBlock)
-    k_particle_update(int lgn, double invh, int64_t np, double *__restrict__ x, double *__restrict__ u,
+    k_particle_update(int lgn, double invh, double L, double invL, int64_t np, double *__restrict__ x, double *__restrict__ u,
                       const float4 *__restrict__ rec, float hdt, double dt, int flags)
 {
     pdl_begin();
@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(kBlock)
                             fmaf(fac, uz, -q[Q_BETA + 2])};
 #pragma unroll
         for (int d = 0; d < 3; d++) {
+            // back into [0, L) (x - L floor(x / L); for L = 1 exactly x - floor(x))
             const double xn = fma(dt, (double)v[d], xd[d]);
-            x[d * np + p] = xn - floor(xn);
+            x[d * np + p] = fma(-L, floor(xn * invL), xn);
         }
     }
 }
@@ -293,7 +294,7 @@ void particle_update(int n, double L, int64_t np, double *x, double *u, const fl
     if (np <= 0) return;
     const int64_t blocks = (np + kBlock - 1) / kBlock;
     const int g = (int)(blocks < 0x7fffffff ? blocks : 0x7fffffff);
-    GR_LAUNCH(k_particle_update, g, kBlock, st, log2i(n), (double)n / L, np, x, u, (const float4 *)rec,
+    GR_LAUNCH(k_particle_update, g, kBlock, st, log2i(n), (double)n / L, L, 1.0 / L, np, x, u, (const float4 *)rec,
               (float)(0.5 * dt), dt, flags);
 }
 

@@ -195,3 +195,36 @@ def test_three_step_time_loop_matches_oracle():
         for k in oracle.FIELDS:
             fg[k].copy_(_t(fo[k]))
     ctx.close()
+
+
+def test_box_side_scaling_is_exact():
+    """A box of side L = 2 with the same grid values of psi, alpha psi and B^i
+    and twice those of b: the shift beta = B + grad b is then the same, every
+    force term holds one gradient (halved, h doubles), and the CIC position in
+    cells is unchanged, so particles at 2x stepped by dt end at exactly twice
+    the positions, with exactly the velocities, of particles at x in the unit
+    box stepped by dt/2 (all scalings are powers of two).  Particles near the
+    faces drift out and must wrap into [0, L)."""
+    n, npart = 16, 3000
+    rng = np.random.default_rng(11)
+    x0 = rng.random((3, npart))
+    x0[:, :6] = [[1e-9, 1 - 1e-9, 0.5, 0.999, 0.001, 0.25]] * 3
+    u0 = 0.5 * (2 * rng.random((3, npart)) - 1)
+    u0[:, :6] = [[-0.4, 0.4, 0.1, 0.4, -0.4, 0.0]] * 3
+    f1 = _strong_fields(n)
+    fld = {k: _t(v) for k, v in f1.items()}
+    fld2 = dict(fld, b=_t(2 * f1["b"]))
+    dt = 0.05
+    flags = gr.GR_KICK_SYNC | gr.GR_KICK_OPEN | gr.GR_DRIFT
+    c1, c2 = gr.Context(n), gr.Context(n, L=2.0)
+    xa, ua = _t(x0), _t(u0)
+    xb, ub = _t(2 * x0), _t(u0)
+    c1.particle_update(xa, ua, fld, dt / 2, flags)
+    c2.particle_update(xb, ub, fld2, dt, flags)
+    torch.cuda.synchronize()
+    assert torch.equal(ub, ua)
+    assert torch.equal(xb, 2 * xa)
+    assert bool(((xb >= 0) & (xb < 2)).all())
+    assert bool((xb[:, :6] < 0.1).any() and (xb[:, :6] > 1.9).any())  # some wrapped each way
+    c1.close()
+    c2.close()
