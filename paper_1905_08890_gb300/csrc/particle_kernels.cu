@@ -79,21 +79,30 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
-// pass 2: the 80-byte record of every cell from the five FP32 arrays of pass 1
+// pass 2: the 80-byte record of every cell from the five FP32 arrays of pass 1.
+// A warp makes 32 consecutive cells; their records (2560 contiguous bytes) go
+// through shared memory so that the stores are coalesced 16-byte accesses
+// (written straight from each lane they would stride 80 bytes apart).
+// 32-bit offsets: n <= 1024.
 __global__ void __launch_bounds__(kBlock)
     k_pf_grad(int lgn, float inv2h, const float *__restrict__ d, float4 *__restrict__ rec)
 {
     pdl_begin();
+    __shared__ float4 stage[kBlock / 32][32 * 5];
     const int m = (1 << lgn) - 1;
-    const int64_t N = (int64_t)1 << (3 * lgn);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t & m), j = (int)((t >> lgn) & m), i = (int)(t >> (2 * lgn));
-        const int64_t row = t - k, plane = t - ((int64_t)j << lgn) - k;
-        int64_t nb[3][2];
-        nb[0][0] = ((int64_t)((i + 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
-        nb[0][1] = ((int64_t)((i - 1) & m) << (2 * lgn)) + ((int64_t)j << lgn) + k;
-        nb[1][0] = plane + ((int64_t)((j + 1) & m) << lgn) + k;
-        nb[1][1] = plane + ((int64_t)((j - 1) & m) << lgn) + k;
+    const int N = 1 << (3 * lgn);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *st = stage[warp];
+    // whole warps step through the cells (N is a multiple of 32 for n >= 4)
+    for (int base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)); base < N; base += gridDim.x * blockDim.x) {
+        const int t = base + lane;
+        const int k = t & m, j = (t >> lgn) & m, i = t >> (2 * lgn);
+        const int row = t - k, plane = t - (j << lgn) - k;
+        int nb[3][2];
+        nb[0][0] = (((i + 1) & m) << (2 * lgn)) + (j << lgn) + k;
+        nb[0][1] = (((i - 1) & m) << (2 * lgn)) + (j << lgn) + k;
+        nb[1][0] = plane + (((j + 1) & m) << lgn) + k;
+        nb[1][1] = plane + (((j - 1) & m) << lgn) + k;
         nb[2][0] = row + ((k + 1) & m);
         nb[2][1] = row + ((k - 1) & m);
         float q[Q_N];
@@ -107,9 +116,13 @@ __global__ void __launch_bounds__(kBlock)
             for (int c = 0; c < 3; c++)
                 q[Q_DBETA + 3 * c + a] = (d[(2 + c) * N + nb[a][0]] - d[(2 + c) * N + nb[a][1]]) * inv2h;
         }
-        float4 *r = rec + 5 * t;
 #pragma unroll
-        for (int v = 0; v < 5; v++) r[v] = make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
+        for (int v = 0; v < 5; v++) st[5 * lane + v] = make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
+        __syncwarp();
+        float4 *r = rec + 5 * (int64_t)base;
+#pragma unroll
+        for (int v = 0; v < 5; v++) r[32 * v + lane] = st[32 * v + lane];
+        __syncwarp();
     }
 }
 
