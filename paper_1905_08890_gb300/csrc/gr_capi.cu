@@ -90,7 +90,8 @@ struct gr_ctx {
     std::vector<Level> lev;  // lev[0] is 2^3, lev[nlev-1] the finest
     double *A6 = nullptr, *AA = nullptr, *tmp = nullptr;
     float *dfu = nullptr, *dff = nullptr, *dfa = nullptr, *dfb = nullptr;  // finest level hi|lo pairs
-    double *partials = nullptr, *dscal = nullptr, *hscal = nullptr;
+    double *partials = nullptr, *dscal = nullptr;
+    double *hscal = nullptr, *hscal_dev = nullptr;  // mapped pinned host scalars and their device alias
     double rho_dep = NAN;
     // what A6/AA hold for the V, U in the fields, and tmp (alpha psi psi^-7) for
     // the psi, alpha psi in the fields: 0 nothing current, 1 FP64, 2 double-float pairs
@@ -123,7 +124,7 @@ struct gr_ctx {
     // Poisson solvability constant, 1..8: its sums, 16..: set-up sums, 32..: norms)
     std::vector<PatchLevel> pl;
     std::vector<void *> palloc;
-    double *pdev = nullptr, *phost = nullptr;
+    double *pdev = nullptr, *phost = nullptr, *phost_dev = nullptr;  // phost: mapped pinned, phost_dev its alias
     bool pdf = false;  // the patches relax in double-float (mixed modes) rather than FP64
     // particle update: the per-cell records of 20 FP32 quantities (allocated on first use)
     float *pf = nullptr;
@@ -261,14 +262,17 @@ void prof_collect(gr_ctx *c)
 
 gr_status read_scalars(gr_ctx *c, double *a, double *b)
 {
-    cudaMemcpyAsync(c->hscal, c->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    // a kernel store, not a copy: a device-to-host copy would wait for the
+    // field copies that host_out keeps in flight on the copy stream
+    gr::scalars_out(c->dscal, c->hscal_dev, 2, c->st);
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return fail(GR_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     gr_status s = cuda_check("kernel");
     if (s != GR_OK) return s;
     if (c->prof_on) prof_collect(c);
-    *a = c->hscal[0];
-    if (b) *b = c->hscal[1];
+    const volatile double *h = c->hscal;
+    *a = h[0];
+    if (b) *b = h[1];
     return GR_OK;
 }
 
@@ -771,10 +775,12 @@ gr_status ensure_patches(gr_ctx *c, int np, const gr_patch *P)
     if (!c->pdev) {
         gr_status st = dalloc(c, &c->pdev, 64);
         if (st != GR_OK) return st;
-        if (cudaMallocHost(&c->phost, 64 * sizeof(double)) != cudaSuccess) {
+        if (cudaHostAlloc((void **)&c->phost, 64 * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&c->phost_dev, c->phost, 0) != cudaSuccess) {
             cudaGetLastError();
-            c->phost = nullptr;
-            return fail(GR_ERR_NOMEM, "cudaMallocHost");
+            if (c->phost) cudaFreeHost(c->phost);
+            c->phost = c->phost_dev = nullptr;
+            return fail(GR_ERR_NOMEM, "cudaHostAlloc (mapped patch scalars)");
         }
     }
     bool same = (int)c->pl.size() == np;
@@ -937,7 +943,7 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
         if (c->pdf) gr::patch_coef_df(in.kind, patch_view(c, p, in, rho), c->st);
         gr::finalize(c->partials, g, c->pdev + 16 + 2 * p, c->st);
     }
-    cudaMemcpyAsync(c->phost + 16, c->pdev + 16, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    gr::scalars_out(c->pdev + 16, c->phost_dev + 16, 2 * np, c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check("patch set-up");
     for (int p = 0; p < np; p++) {
         PatchLevel &L = c->pl[p];
@@ -963,8 +969,8 @@ gr_status patch_setup_eq(gr_ctx *c, int eq, const gr_opts *o, const EqInfo &in, 
 
 // patches fine to coarse: nu sweeps, residual (norm into pdev[32 + 2p]),
 // restriction, injection into the parent with flux matching; for Poisson the
-// solvability constant after the base injection.  Queues the norms' copy to
-// phost (the caller's next synchronisation covers it).
+// solvability constant after the base injection.  Queues the norms' store
+// to the mapped phost (the caller's next synchronisation covers it).
 void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
 {
     const int np = (int)c->pl.size();
@@ -1002,7 +1008,7 @@ void patch_down(gr_ctx *c, const EqInfo &in, int fmt, int nu, double rho)
             gr::patch_reflux(-1, gr::PBase{}, par, V, c->pdf, L.o, Q.h, L.flux, c->st);
         }
     }
-    cudaMemcpyAsync(c->phost + 32, c->pdev + 32, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    gr::scalars_out(c->pdev + 32, c->phost_dev + 32, 2 * np, c->st);
 }
 
 // patches coarse to fine: the parent's correction P(u_new - u_old), fresh ghosts, nu sweeps
@@ -1397,9 +1403,10 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     if (st == GR_OK) st = dalloc(c, &c->tmp, N);
     if (st == GR_OK) st = dalloc(c, &c->partials, 2 * kMaxRedBlocks);
     if (st == GR_OK) st = dalloc(c, &c->dscal, 16);
-    if (st == GR_OK && cudaMallocHost((void **)&c->hscal, 16 * sizeof(double)) != cudaSuccess) {
+    if (st == GR_OK && (cudaHostAlloc((void **)&c->hscal, 16 * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+                        cudaHostGetDevicePointer((void **)&c->hscal_dev, c->hscal, 0) != cudaSuccess)) {
         cudaGetLastError();
-        st = fail(GR_ERR_NOMEM, "cudaMallocHost");
+        st = fail(GR_ERR_NOMEM, "cudaHostAlloc (mapped scalars)");
     }
     if (st == GR_OK && (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)) {
         cudaGetLastError();

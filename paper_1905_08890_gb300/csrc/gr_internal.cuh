@@ -252,6 +252,9 @@ int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1
                double *partials, double *eps_nat, cudaStream_t st);
 // out[0] = sum of partials[2b], out[1] = sum of partials[2b + 1].
 void finalize(const double *partials, int nblk, double *out, cudaStream_t st);
+// dst_mapped[0 .. cnt) = src[0 .. cnt) (cnt <= 32): dst_mapped is the device
+// alias of pinned host memory allocated with cudaHostAllocMapped.
+void scalars_out(const double *src, double *dst_mapped, int cnt, cudaStream_t st);
 
 // The FP32 correction cycle's levels coarse_tail_n()^3 .. 2^3 in one thread
 // block (shared memory): e/r/m/inv of levels 2^3, 4^3, 8^3, 16^3 (index 0 =

@@ -718,6 +718,16 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const double *__restrict__ 
     block_sum2(a, b, out);
 }
 
+// cnt (<= 32) doubles from device memory to host-mapped pinned memory: the
+// host reads them after a stream synchronisation without a copy-engine
+// transfer, which would queue behind large copies in flight on other streams
+__global__ void k_scalars_out(const double *__restrict__ src, double *dst, int cnt)
+{
+    pdl_begin();
+    if ((int)threadIdx.x < cnt) dst[threadIdx.x] = src[threadIdx.x];
+    __threadfence_system();
+}
+
 // ---------------------------------------------------------------- mixed precision
 template <int KIND>
 __global__ void __launch_bounds__(kBlock)
@@ -927,6 +937,11 @@ int resid_norm(int kind, int n, const T *u, const T *f, const T *c0, const T *c1
 void finalize(const double *partials, int nblk, double *out, cudaStream_t st)
 {
     GR_LAUNCH(k_finalize, 1, kBlock, st, partials, nblk, out);
+}
+
+void scalars_out(const double *src, double *dst_mapped, int cnt, cudaStream_t st)
+{
+    GR_LAUNCH(k_scalars_out, 1, 32, st, src, dst_mapped, cnt);
 }
 
 int mixed_resid(int kind, int n, const double *u, const double *f, const double *c0, const double *c1, double ih2,
