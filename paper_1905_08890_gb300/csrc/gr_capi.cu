@@ -98,6 +98,8 @@ struct gr_ctx {
     int a_fmt = 0;
     int w_fmt = 0;
     bool tail_on = true;   // FP32 cycles: levels <= 16^3 in one block (GR_COARSE_TAIL=0 turns it off)
+    bool cluster_on = false;  // FP32 cycles under a 128^3 or finer top: levels <= 64^3 in one
+                              // 16-CTA cluster (GR_COARSE_CLUSTER=1; measured slower)
     int s3_min = 1 << 30;  // finest grids from this size fuse three colour passes per smoothing: off unless
                            // GR_SMOOTH3=1 (from 512^3, or from GR_SMOOTH3_MIN)
     int s3_rt = 0;         // row tiles of the fused colour passes on the finest level
@@ -441,16 +443,18 @@ void restrict_coefs32(gr_ctx *c)
     }
 }
 
-// cells relaxed by one V-cycle whose top is level top (default: the finest)
-long long vcycle_cells(const gr_ctx *c, int nu1, int nu2, int top = -1)
+// cells relaxed by one V-cycle whose top is level top (default: the finest);
+// coarsest: the cell updates of the 2^3 solve (8 for the exact solve of a
+// linear level, 8 per sweep for the nonlinear one)
+long long vcycle_cells(const gr_ctx *c, int nu1, int nu2, int top = -1, long long coarsest = 8)
 {
     if (top < 0) top = c->nlev - 1;
     long long s = 0;
     for (int l = 1; l <= top; l++) s += (long long)(nu1 + nu2) * c->lev[l].n * c->lev[l].n * c->lev[l].n;
-    return s + (long long)kCoarsestSweeps * 8;
+    return s + coarsest;
 }
 
-// cells relaxed by one full multigrid cycle (fmg32)
+// cells relaxed by one full multigrid cycle (fmg32, linear correction levels)
 long long fmg_cells(const gr_ctx *c, int nu1, int nu2)
 {
     long long s = 2 * vcycle_cells(c, nu1, nu2, 3);
@@ -597,12 +601,28 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
         smooth_fine(nu1);
     }
     timed(c, cls(GR_PROF_RESTRICT), [&] { down(top); });
+    // levels 64^3 .. 2^3 in one cluster launch below a 128^3 or finer top
+    const bool clus = tail && c->cluster_on && top >= 6 && nu1 > 0 && nu2 > 0 && gr::coarse_cluster_ok(kind32);
+    const int low = clus ? 5 : tail;  // the levels up to `low` run inside one launch
     timed(c, GR_PROF_COARSE, [&] {
-        for (int l = top - 1; l >= (tail ? tail + 1 : 1); l--) {
+        for (int l = top - 1; l >= (low ? low + 1 : 1); l--) {
             smooth_after_restrict(c->lev[l], l);
             down(l);
         }
-        if (tail) {
+        if (clus) {
+            float *e[6], *r[6];
+            const float *m[6], *iv[6];
+            double h2[6], ih2[6];
+            for (int l = 0; l < 6; l++) {
+                e[l] = c->lev[l].e;
+                r[l] = c->lev[l].r;
+                m[l] = c->lev[l].m;
+                iv[l] = c->lev[l].inv;
+                h2[l] = c->lev[l].h2;
+                ih2[l] = c->lev[l].ih2;
+            }
+            gr::coarse_cluster(kind32, e, r, m, iv, h2, ih2, nu1, nu2, c->st);
+        } else if (tail) {
             float *e[4], *r[4];
             const float *m[4], *iv[4];
             double h2[4];
@@ -618,7 +638,7 @@ void vcycle32(gr_ctx *c, int kind32, int nu1, int nu2, Start start, float *uh = 
             Level &Z = c->lev[0];
             gr::coarsest<float>(kind32, Z.e, Z.r, Z.m, Z.inv, Z.h2, Z.ih2, 0.0, c->st);
         }
-        for (int l = tail ? tail + 1 : 1; l < top; l++) {
+        for (int l = low ? low + 1 : 1; l < top; l++) {
             up(l);
             smooth(c->lev[l], nu2);
         }
@@ -1092,7 +1112,8 @@ gr_status solve_eq(gr_ctx *c, int eq, const gr_sources *s, gr_fields *fl, const 
         }
     }
     const bool mixed = o->prec == GR_PREC_MIXED || dfm;
-    const long long per_cycle = vcycle_cells(c, o->nu1, o->nu2);
+    const long long per_cycle =
+        vcycle_cells(c, o->nu1, o->nu2, -1, (!mixed && in.kind == KPSI) ? 8LL * kCoarsestSweeps : 8LL);
     if (mixed) {
         if (in.kind == KHELM) {
             if (!dfm) {  // the double-float set-up wrote m and its inverse diagonal
@@ -1348,6 +1369,7 @@ gr_status gr_create(int n, double L, void *stream, gr_ctx **out)
     c->n = n;
     c->L = L;
     if (const char *env = getenv("GR_COARSE_TAIL")) c->tail_on = env[0] != '0';
+    if (const char *env = getenv("GR_COARSE_CLUSTER")) c->cluster_on = env[0] == '1';
     if (const char *env = getenv("GR_SMOOTH3")) {
         if (env[0] == '1') {
             c->s3_min = 512;

@@ -227,12 +227,12 @@ void prolong_add_black(int nf, float *u, const float *uc, cudaStream_t st, int r
 // FP32 coarse = 8-child average of fine (a right-hand side going down)
 void restrict_avg(int nf, const float *fine, float *coarse, cudaStream_t st);
 
-// The 2^3 level: kCoarsestSweeps red-black sweeps in FP64 (any T storage),
-// each followed (KHELM, KPSI) by the constant shift that zeroes the sum of the
-// eight residuals to first order (the Laplacian leaves that mode to the weak
-// non-Laplacian coefficient alone); Poisson: source mean removed before and
-// solution mean after.  KHELM reads
-// c0 = m (the inverse diagonal is formed in FP64).
+// The 2^3 level in FP64 (any T storage).  KPOISSON, KHELM: solved exactly
+// (Walsh-Hadamard diagonalisation; Gauss-Jordan elimination), Poisson with
+// the source mean removed before and the solution mean after; KHELM reads
+// c0 = m.  KPSI: kCoarsestSweeps Newton red-black sweeps, each followed by
+// the constant shift that zeroes the sum of the eight residuals to first
+// order (the Laplacian leaves that mode to the weak non-Laplacian terms).
 template <typename T>
 void coarsest(int kind, T *u, T *f, const T *c0, const T *c1, double h2, double ih2, double rho, cudaStream_t st);
 
@@ -262,6 +262,15 @@ void scalars_out(const double *src, double *dst_mapped, int cnt, cudaStream_t st
 int coarse_tail_n();
 void coarse_tail(int kind, float *const *e, float *const *r, const float *const *m, const float *const *inv,
                  const double *h2, int nu1, int nu2, cudaStream_t st);
+
+// The FP32 correction cycle's levels 64^3 .. 2^3 in one 16-CTA thread-block
+// cluster (coarse_cluster.cu): arrays of levels 2^3 .. 64^3 (index 0 = 2^3);
+// e and r of 64^3 in (its first red pass made by the restriction), e out.
+// Needs nu1, nu2 >= 1.  coarse_cluster_ok: the device runs such a cluster
+// (KPOISSON, KHELM).
+bool coarse_cluster_ok(int kind);
+void coarse_cluster(int kind, float *const *e, float *const *r, const float *const *m, const float *const *inv,
+                    const double *h2, const double *ih2, int nu1, int nu2, cudaStream_t st);
 
 // ---- mixed precision -------------------------------------------------------
 // FP64 residual on the fine level; writes r32 = -eps (split), and for KPSI

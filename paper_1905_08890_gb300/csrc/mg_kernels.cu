@@ -8,6 +8,7 @@
 // Relaxation: red-black Gauss-Seidel, one Newton step per cell for KPSI (Sec. 4.3.2).
 // Transfers: R = average of the 8 children, P = cell-centred trilinear (3/4, 1/4).
 #include "gr_internal.cuh"
+#include "coarse_tail.cuh"
 
 namespace gr {
 namespace {
@@ -534,20 +535,20 @@ __global__ void __launch_bounds__(kBlock, 5) k_prolong_black4(int lgf, float *__
 
 
 // ---------------------------------------------------------------- 2^3 level
+// Linear kinds: the exact solve (coarsest_exact).  KPSI: Newton red-black
+// sweeps, each followed by the zero-mode shift.
 template <typename T, int KIND>
 __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__restrict__ c0, const T *__restrict__ c1,
                            double h2, double ih2, double rho)
 {
     pdl_begin();
-    __shared__ double su[8], sf[8], s0[8], s1[8], sd[8];
+    __shared__ double su[8], sf[8], s0[8], s1[8];
     const int t = threadIdx.x;
     if (t < 8) {
         su[t] = (double)u[t];
         sf[t] = (double)f[t];
         s0[t] = (KIND == KPOISSON) ? 0.0 : (double)c0[t];
         s1[t] = (KIND == KPSI) ? (double)c1[t] : 0.0;
-        // inverse diagonal of the linear kinds, formed once: the sweeps multiply
-        sd[t] = (KIND == KHELM) ? 1.0 / (6.0 + h2 * s0[t]) : 1.0 / 6.0;
     }
     __syncthreads();
     if (KIND == KPOISSON && t == 0) {
@@ -557,18 +558,23 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
         for (int q = 0; q < 8; q++) sf[q] -= m;
     }
     __syncthreads();
-    // on 2^3 the split index of (i, j, k) is 4 c + 2 i + j; every neighbour
-    // along an axis is the same cell, counted twice
-    for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
-        for (int color = 0; color < 2; color++) {
-            if (t < 4) {
-                const int i = t >> 1, j = t & 1;
-                const int id = 4 * color + t;
-                const int o = 4 * (color ^ 1);
-                const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                if (KIND == KPOISSON || KIND == KHELM) {
-                    su[id] = (nb - h2 * sf[id]) * sd[id];
-                } else {
+    if (KIND != KPSI) {
+        // lane x holds cell x = 4i + 2j + k, split index 4 ((i + j + k) & 1) + 2i + j
+        const int x = t & 7, i = x >> 2, j = (x >> 1) & 1, k = x & 1;
+        const int id = 4 * ((i + j + k) & 1) + 2 * i + j;
+        const double e = coarsest_exact<KIND>(sf[id], s0[id], h2);
+        if (t < 8) su[id] = e;
+        __syncthreads();
+    } else {
+        // on 2^3 the split index of (i, j, k) is 4 c + 2 i + j; every
+        // neighbour along an axis is the same cell, counted twice
+        for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
+            for (int color = 0; color < 2; color++) {
+                if (t < 4) {
+                    const int i = t >> 1, j = t & 1;
+                    const int id = 4 * color + t;
+                    const int o = 4 * (color ^ 1);
+                    const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
                     const double uc = su[id], v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
                     const double g = (nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[id] / v + s1[id] / (8.0 * v4 * v2 * v) -
                                      2.0 * kPi * rho * v4 * v - sf[id];
@@ -576,28 +582,21 @@ __global__ void k_coarsest(T *__restrict__ u, T *__restrict__ f, const T *__rest
                         -6.0 * ih2 - 2.0 * kPi * s0[id] / v2 - 7.0 * s1[id] / (8.0 * v4 * v4) - 10.0 * kPi * rho * v4;
                     su[id] = uc - g / dg;
                 }
+                __syncthreads();
             }
-            __syncthreads();
-        }
-        if (KIND != KPOISSON) {
             // zero mode: the constant shift that zeroes the sum of the eight
-            // residuals to first order, u -= sum(f - L(u)) / sum(m), with m the
-            // non-Laplacian coefficient (a sweep damps the constant error only
-            // by 1/(1 + h^2 m / 6), slowly where m is small)
+            // residuals to first order, u -= sum(f - N(u)) / sum(-dN/du) (a
+            // sweep damps the constant error only by 1/(1 + h^2 m / 6), slowly
+            // where the non-Laplacian coefficient m is small)
             __shared__ double zr[8], zm[8];
             if (t < 8) {
                 const int c = t >> 2, i = (t >> 1) & 1, j = t & 1, o = 4 * (c ^ 1);
                 const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
                 const double uc = su[t];
-                if (KIND == KHELM) {
-                    zr[t] = sf[t] - ((nb - 6.0 * uc) * ih2 - s0[t] * uc);
-                    zm[t] = s0[t];
-                } else {
-                    const double v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
-                    zr[t] = sf[t] - ((nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[t] / v + s1[t] / (8.0 * v4 * v2 * v) -
-                                     2.0 * kPi * rho * v4 * v);
-                    zm[t] = 2.0 * kPi * s0[t] / v2 + 7.0 * s1[t] / (8.0 * v4 * v4) + 10.0 * kPi * rho * v4;
-                }
+                const double v = 1.0 + uc, v2 = v * v, v4 = v2 * v2;
+                zr[t] = sf[t] - ((nb - 6.0 * uc) * ih2 + 2.0 * kPi * s0[t] / v + s1[t] / (8.0 * v4 * v2 * v) -
+                                 2.0 * kPi * rho * v4 * v);
+                zm[t] = 2.0 * kPi * s0[t] / v2 + 7.0 * s1[t] / (8.0 * v4 * v4) + 10.0 * kPi * rho * v4;
             }
             __syncthreads();
             if (t < 8) {
@@ -992,192 +991,6 @@ GR_INST(float)
 // the coarse levels cost one launch per cycle instead of about thirty.
 namespace {
 
-constexpr int kTailN = 16;
-constexpr int kTailThreads = 1024;
-
-struct TailLevel {
-    float *e, *r, *m, *inv;
-    int lg;
-    float h2, ih2;
-};
-
-__device__ __forceinline__ int tail_sidx(int lg, int i, int j, int k)
-{
-    return ((i + j + k) & 1) * (1 << (3 * lg - 1)) + ((((i << lg) + j) << (lg - 1)) + (k >> 1));
-}
-
-// one colour pass on a level of the tail, W consecutive half-indices of a row
-// per thread (W = 4 from 8^3, 2 on 4^3), with the addressing and the order of
-// additions of the full-grid colour pass (k_sweep4)
-template <int KIND, int W>
-__device__ void tail_sweep_w(const TailLevel &L, int color)
-{
-    const int lgn = L.lg, lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
-    const int half = 1 << (3 * lgn - 1), off = color ? half : 0;
-    float *own = L.e + off;
-    const float *oth = L.e + (half - off);
-    for (int v = threadIdx.x; v < half / W; v += blockDim.x) {
-        const int t = v * W;
-        const int q = t & mh, j = (t >> lgh) & mn, i = t >> (lgh + lgn);
-        const int p = (i + j + color) & 1;
-        const int r0 = t - q, ri = j << lgh;
-        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri, rim = (((i - 1) & mn) << (lgn + lgh)) + ri;
-        const int rj = i << (lgn + lgh);
-        const int rjp = rj + (((j + 1) & mn) << lgh), rjm = rj + (((j - 1) & mn) << lgh);
-        const float x = oth[r0 + ((q + (p ? W : -1)) & mh)];
-#pragma unroll
-        for (int e = 0; e < W; e++) {
-            const float E = oth[r0 + q + e];
-            const float sh = p ? (e + 1 < W ? oth[r0 + q + e + 1] : x) : (e > 0 ? oth[r0 + q + e - 1] : x);
-            const float nb = oth[rip + q + e] + oth[rim + q + e] + oth[rjp + q + e] + oth[rjm + q + e] + E + sh;
-            const int id = off + t + e;
-            const float g = KIND == KPOISSON ? 1.0f / 6.0f : L.inv[id];
-            own[t + e] = __fmaf_rn(-L.h2, L.r[id], nb) * g;
-        }
-    }
-    __syncthreads();
-}
-
-template <int KIND>
-__device__ void tail_sweep(const TailLevel &L, int color)
-{
-    if (L.lg >= 3) tail_sweep_w<KIND, 4>(L, color);
-    else tail_sweep_w<KIND, 2>(L, color);
-}
-
-// residual L(e) - r of every cell of level A into A's scratch row array res
-// (split layout), then the 8-child averages, negated, as the next level's
-// right-hand side (its correction starts at zero)
-template <int KIND>
-__device__ void tail_down(const TailLevel &A, const TailLevel &C, float *res)
-{
-    const int lgn = A.lg, lgh = lgn - 1, mn = (1 << lgn) - 1, mh = (1 << lgh) - 1;
-    const int half = 1 << (3 * lgn - 1);
-    for (int tt = threadIdx.x; tt < 2 * half; tt += blockDim.x) {
-        const int color = tt >= half, t = tt - (color ? half : 0);
-        const int off = color ? half : 0;
-        const float *oth = A.e + (half - off);
-        const int q = t & mh, j = (t >> lgh) & mn, i = t >> (lgh + lgn);
-        const int p = (i + j + color) & 1;
-        const int r0 = t - q, ri = j << lgh;
-        const int rip = (((i + 1) & mn) << (lgn + lgh)) + ri, rim = (((i - 1) & mn) << (lgn + lgh)) + ri;
-        const int rj = i << (lgn + lgh);
-        const int rjp = rj + (((j + 1) & mn) << lgh), rjm = rj + (((j - 1) & mn) << lgh);
-        const float nb = oth[rip + q] + oth[rim + q] + oth[rjp + q] + oth[rjm + q] + oth[r0 + q] +
-                         oth[r0 + ((q + (p ? 1 : -1)) & mh)];
-        const int id = off + t;
-        const float u = A.e[id];
-        float lap = (nb - 6.0f * u) * A.ih2;
-        if (KIND == KHELM) lap -= A.m[id] * u;
-        res[id] = lap - A.r[id];
-    }
-    __syncthreads();
-    const int lc = C.lg, mc = (1 << lc) - 1;
-    for (int t = threadIdx.x; t < (1 << (3 * lc)); t += blockDim.x) {
-        const int K = t & mc, J = (t >> lc) & mc, I = t >> (2 * lc);
-        float s = 0.0f;
-        for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++)
-                for (int c = 0; c < 2; c++) s += res[tail_sidx(A.lg, 2 * I + a, 2 * J + b, 2 * K + c)];
-        const int cid = tail_sidx(lc, I, J, K);
-        C.r[cid] = -(0.125f * s);
-        C.e[cid] = 0.0f;
-    }
-    __syncthreads();
-}
-
-// trilinear prolongation of the coarser level's correction added to level A;
-// black_only: a red pass follows, which does not read the red values, so only
-// the black cells take the correction (as prolong_add_black)
-__device__ void tail_up(const TailLevel &A, const TailLevel &C, bool black_only)
-{
-    const int lc = C.lg, mc = (1 << lc) - 1, lf = A.lg, nf1 = (1 << lf) - 1, lgh = lf - 1, mh = (1 << lgh) - 1;
-    const int half = 1 << (3 * lf - 1);
-    const int ncell = black_only ? half : 2 * half;
-    for (int tt = threadIdx.x; tt < ncell; tt += blockDim.x) {
-        // split index: colour 1 (black) first when black_only, else both colours
-        const int color = black_only ? 1 : (tt >= half), t = tt - ((!black_only && color) ? half : 0);
-        const int q = t & mh, j = (t >> lgh) & nf1, i = t >> (lgh + lf);
-        const int k = 2 * q + ((i + j + color) & 1);
-        int Ia[2], Jb[2], Kc[2];
-        Ia[0] = i >> 1;
-        Ia[1] = (i & 1) ? ((Ia[0] + 1) & mc) : ((Ia[0] - 1) & mc);
-        Jb[0] = j >> 1;
-        Jb[1] = (j & 1) ? ((Jb[0] + 1) & mc) : ((Jb[0] - 1) & mc);
-        Kc[0] = k >> 1;
-        Kc[1] = (k & 1) ? ((Kc[0] + 1) & mc) : ((Kc[0] - 1) & mc);
-        const float w[2] = {0.75f, 0.25f};
-        float z[2][2];
-        for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++)
-                z[a][b] = w[0] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[0])] + w[1] * C.e[tail_sidx(lc, Ia[a], Jb[b], Kc[1])];
-        const float y0 = w[0] * z[0][0] + w[1] * z[0][1], y1 = w[0] * z[1][0] + w[1] * z[1][1];
-        A.e[(color ? half : 0) + t] += w[0] * y0 + w[1] * y1;
-    }
-    __syncthreads();
-}
-
-// FP64 solve of the 2^3 level (same steps as k_coarsest), by the first warp
-// alone so that its 64 half-sweeps need warp, not block, barriers
-template <int KIND>
-__device__ void tail_coarsest(const TailLevel &Z)
-{
-    __shared__ double su[8], sf[8], sm[8], sd[8];
-    const int t = threadIdx.x;
-    if (t < 32) {
-        if (t < 8) {
-            su[t] = Z.e[t];
-            sf[t] = Z.r[t];
-            sm[t] = KIND == KPOISSON ? 0.0 : (double)Z.m[t];
-            sd[t] = KIND == KPOISSON ? 1.0 / 6.0 : 1.0 / (6.0 + (double)Z.h2 * sm[t]);  // as k_coarsest
-        }
-        __syncwarp();
-        if (KIND == KPOISSON && t == 0) {
-            double m = 0.0;
-            for (int q = 0; q < 8; q++) m += sf[q];
-            m *= 0.125;
-            for (int q = 0; q < 8; q++) sf[q] -= m;
-        }
-        __syncwarp();
-        const double h2 = (double)Z.h2;
-        for (int sweep = 0; sweep < kCoarsestSweeps; sweep++) {
-            for (int color = 0; color < 2; color++) {
-                if (t < 4) {
-                    const int i = t >> 1, j = t & 1, id = 4 * color + t, o = 4 * (color ^ 1);
-                    const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                    su[id] = (nb - h2 * sf[id]) * sd[id];
-                }
-                __syncwarp();
-            }
-            if (KIND == KHELM) {  // the zero-mode shift of k_coarsest
-                double zr = 0.0, zm = 0.0;
-                if (t < 8) {
-                    const int c = t >> 2, i = (t >> 1) & 1, j = t & 1, o = 4 * (c ^ 1);
-                    const double nb = 2.0 * (su[o + 2 * (i ^ 1) + j] + su[o + 2 * i + (j ^ 1)] + su[o + 2 * i + j]);
-                    zr = sf[t] - ((nb - 6.0 * su[t]) / h2 - sm[t] * su[t]);
-                    zm = sm[t];
-                }
-                __syncwarp();
-                for (int off = 4; off > 0; off >>= 1) {
-                    zr += __shfl_xor_sync(0xffffffffu, zr, off);
-                    zm += __shfl_xor_sync(0xffffffffu, zm, off);
-                }
-                if (t < 8 && zm > 0.0) su[t] -= zr / zm;
-                __syncwarp();
-            }
-        }
-        if (KIND == KPOISSON && t == 0) {
-            double m = 0.0;
-            for (int q = 0; q < 8; q++) m += su[q];
-            m *= 0.125;
-            for (int q = 0; q < 8; q++) su[q] -= m;
-        }
-        __syncwarp();
-        if (t < 8) Z.e[t] = (float)su[t];
-    }
-    __syncthreads();
-}
-
 // gl: the global arrays of levels 2^3 .. 16^3 (index 0 = 2^3); e/r of 16^3
 // in and out, m/inv read for KHELM.
 struct TailArgs {
@@ -1217,23 +1030,7 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs g, int nu
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int l = 3; l >= 1; l--) {
-        for (int s = 0; s < nu1; s++) {
-            tail_sweep<KIND>(L[l], 0);
-            tail_sweep<KIND>(L[l], 1);
-        }
-        tail_down<KIND>(L[l], L[l - 1], res);
-    }
-    tail_coarsest<KIND>(L[0]);
-#pragma unroll
-    for (int l = 1; l <= 3; l++) {
-        tail_up(L[l], L[l - 1], nu2 > 0);
-        for (int s = 0; s < nu2; s++) {
-            tail_sweep<KIND>(L[l], 0);
-            tail_sweep<KIND>(L[l], 1);
-        }
-    }
+    tail_cycle<KIND>(L, res, nu1, nu2);
     for (int t = threadIdx.x; t < (1 << 12); t += blockDim.x) g.e[3][t] = L[3].e[t];
 }
 
