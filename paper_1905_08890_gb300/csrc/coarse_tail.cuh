@@ -25,9 +25,24 @@ __device__ __forceinline__ int tail_sidx(int lg, int i, int j, int k)
     return ((i + j + k) & 1) * (1 << (3 * lg - 1)) + ((((i << lg) + j) << (lg - 1)) + (k >> 1));
 }
 
+// W consecutive floats (W = 4 or 2, aligned to W) as one vector access
+template <int W>
+__device__ __forceinline__ void tail_ldv(const float *p, float (&v)[W])
+{
+    if (W == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
+}
+
 // one colour pass on a level of the tail, W consecutive half-indices of a row
 // per thread (W = 4 from 8^3, 2 on 4^3), with the addressing and the order of
-// additions of the full-grid colour pass (k_sweep4)
+// additions of the full-grid colour pass (k_sweep4); each row's W values are
+// one vector access (scalar accesses W floats apart put W threads of a warp
+// on each shared-memory bank)
 template <int KIND, int W>
 __device__ void tail_sweep_w(const TailLevel &L, int color)
 {
@@ -44,15 +59,23 @@ __device__ void tail_sweep_w(const TailLevel &L, int color)
         const int rj = i << (lgn + lgh);
         const int rjp = rj + (((j + 1) & mn) << lgh), rjm = rj + (((j - 1) & mn) << lgh);
         const float x = oth[r0 + ((q + (p ? W : -1)) & mh)];
+        float A[W], B[W], C[W], D[W], E[W], F[W], G[W];
+        tail_ldv<W>(oth + rip + q, A);
+        tail_ldv<W>(oth + rim + q, B);
+        tail_ldv<W>(oth + rjp + q, C);
+        tail_ldv<W>(oth + rjm + q, D);
+        tail_ldv<W>(oth + r0 + q, E);
+        tail_ldv<W>(L.r + off + t, F);
+        if (KIND != KPOISSON) tail_ldv<W>(L.inv + off + t, G);
+        float out[W];
 #pragma unroll
         for (int e = 0; e < W; e++) {
-            const float E = oth[r0 + q + e];
-            const float sh = p ? (e + 1 < W ? oth[r0 + q + e + 1] : x) : (e > 0 ? oth[r0 + q + e - 1] : x);
-            const float nb = oth[rip + q + e] + oth[rim + q + e] + oth[rjp + q + e] + oth[rjm + q + e] + E + sh;
-            const int id = off + t + e;
-            const float g = KIND == KPOISSON ? 1.0f / 6.0f : L.inv[id];
-            own[t + e] = __fmaf_rn(-L.h2, L.r[id], nb) * g;
+            const float sh = p ? (e + 1 < W ? E[e + 1 < W ? e + 1 : 0] : x) : (e > 0 ? E[e > 0 ? e - 1 : 0] : x);
+            const float nb = A[e] + B[e] + C[e] + D[e] + E[e] + sh;
+            out[e] = __fmaf_rn(-L.h2, F[e], nb) * (KIND == KPOISSON ? 1.0f / 6.0f : G[e]);
         }
+        if (W == 4) *reinterpret_cast<float4 *>(own + t) = make_float4(out[0], out[1], out[2], out[3]);
+        else *reinterpret_cast<float2 *>(own + t) = make_float2(out[0], out[1 % W]);
     }
     __syncthreads();
 }
