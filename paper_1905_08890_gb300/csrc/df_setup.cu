@@ -182,6 +182,30 @@ __global__ void __launch_bounds__(kBlock)
     acc.flush(partials);
 }
 
+// Row reads of four consecutive cells k0 .. k0 + 3 (k0 a multiple of 4) of
+// the natural row starting at r, with the two periodic end values k0 - 1 and
+// k0 + 4 for the six-value forms: pair arrays (h, l) by 16-byte loads, FP64
+// arrays by two 16-byte loads and split.
+__device__ __forceinline__ void hl_row4(const float *__restrict__ h, const float *__restrict__ l, int r, int k0, df o[4])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(h + r + k0), b = *reinterpret_cast<const float4 *>(l + r + k0);
+    o[0] = {a.x, b.x}, o[1] = {a.y, b.y}, o[2] = {a.z, b.z}, o[3] = {a.w, b.w};
+}
+__device__ __forceinline__ void hl_row6(const float *__restrict__ h, const float *__restrict__ l, int r, int k0, int m,
+                                        df o[6])
+{
+    const int km = r + ((k0 - 1) & m), kp = r + ((k0 + 4) & m);
+    o[0] = {h[km], l[km]};
+    hl_row4(h, l, r, k0, o + 1);
+    o[5] = {h[kp], l[kp]};
+}
+__device__ __forceinline__ void d_row6(const double *__restrict__ a, int r, int k0, int m, df o[6])
+{
+    o[0] = ld(a, r + ((k0 - 1) & m));
+    ld4(a, r + k0, o + 1);
+    o[5] = ld(a, r + ((k0 + 4) & m));
+}
+
 // ---------------------------------------------------------------- Poisson right-hand sides
 // SRC_MEAN: f = scale (s - <s>), <s> = sum[0] inv_cnt           (V_i, Eq. MG-linear-1a)
 // SRC_DIV:  f = scale sum_l (F_l(+l) - F_l(-l)), scale = -1/(8h) (U and b, Eqs. MG-linear-1, -2)
@@ -226,34 +250,62 @@ __global__ void __launch_bounds__(kBlock, SRC == SRC_SHIFT ? 2 : 3) k_dfs_poisso
         df fv[4], uv[4], sv[4];
         ld4(a.fld, nat(lgn, p.i, p.j, p.k0), uv);
         if (SRC == SRC_MEAN) ld4(a.s[0], nat(lgn, p.i, p.j, p.k0), sv);
+        if (SRC == SRC_MEAN) {
 #pragma unroll
-        for (int e = 0; e < 2 * kChunk; e++) {
-            const int i = p.i, j = p.j, k = p.k0 + e;
-            const int nb[3][2] = {{nat(lgn, (i + 1) & mn, j, k), nat(lgn, (i - 1) & mn, j, k)},
-                                      {nat(lgn, i, (j + 1) & mn, k), nat(lgn, i, (j - 1) & mn, k)},
-                                      {nat(lgn, i, j, (k + 1) & mn), nat(lgn, i, j, (k - 1) & mn)}};
-            df f;
-            if (SRC == SRC_MEAN) {
-                f = df_mul(df_add_acc(sv[e], nmu), a.scale);
-            } else if (SRC == SRC_DIV) {
-                df d = df_add(ld(a.s[0], nb[0][0]), df_neg(ld(a.s[0], nb[0][1])));
+            for (int e = 0; e < 2 * kChunk; e++) fv[e] = df_mul(df_add_acc(sv[e], nmu), a.scale);
+        } else {
+            // the +l and -l neighbours of the four cells: rows (i +- 1, j), (i, j +- 1), and the own row's
+            // values k0 - 1 .. k0 + 4; per cell the sum over l = x, y, z of the differences, in that order
+            const int rows[2][2] = {{nat(lgn, (p.i + 1) & mn, p.j, 0), nat(lgn, (p.i - 1) & mn, p.j, 0)},
+                                    {nat(lgn, p.i, (p.j + 1) & mn, 0), nat(lgn, p.i, (p.j - 1) & mn, 0)}};
+            const int own = nat(lgn, p.i, p.j, 0);
+            df d[4];
 #pragma unroll
-                for (int l = 1; l < 3; l++) d = df_add(d, df_add(ld(a.s[l], nb[l][0]), df_neg(ld(a.s[l], nb[l][1]))));
-                f = df_mul(d, a.scale);
-            } else {
-                df d = {0.0f, 0.0f};
+            for (int l = 0; l < 3; l++) {
+                df P[4], M[4];
+                if (SRC == SRC_DIV) {
+                    if (l < 2) {
+                        ld4(a.s[l], rows[l][0] + p.k0, P);
+                        ld4(a.s[l], rows[l][1] + p.k0, M);
+                    } else {
+                        df z[6];
+                        d_row6(a.s[2], own, p.k0, mn, z);
 #pragma unroll
-                for (int l = 0; l < 3; l++) {
+                        for (int e = 0; e < 4; e++) P[e] = z[e + 2], M[e] = z[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const df q = df_add(P[e], df_neg(M[e]));
+                        d[e] = l == 0 ? q : df_add(d[e], q);
+                    }
+                } else {
                     const float *Ah = a.A + 2 * tab[l] * N, *Al = Ah + N;
-                    const df fp = df_mul(ldp(Ah, Al, nb[l][0]), ldp(a.wh, a.wl, nb[l][0]));
-                    const df fm = df_mul(ldp(Ah, Al, nb[l][1]), ldp(a.wh, a.wl, nb[l][1]));
-                    d = df_add(d, df_add(fp, df_neg(fm)));
+                    df WP[4], WM[4];
+                    if (l < 2) {
+                        hl_row4(Ah, Al, rows[l][0], p.k0, P);
+                        hl_row4(Ah, Al, rows[l][1], p.k0, M);
+                        hl_row4(a.wh, a.wl, rows[l][0], p.k0, WP);
+                        hl_row4(a.wh, a.wl, rows[l][1], p.k0, WM);
+                    } else {
+                        df za[6], zw[6];
+                        hl_row6(Ah, Al, own, p.k0, mn, za);
+                        hl_row6(a.wh, a.wl, own, p.k0, mn, zw);
+#pragma unroll
+                        for (int e = 0; e < 4; e++) P[e] = za[e + 2], M[e] = za[e], WP[e] = zw[e + 2], WM[e] = zw[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const df fp = df_mul(P[e], WP[e]);
+                        const df fm = df_mul(M[e], WM[e]);
+                        d[e] = df_add(l == 0 ? df{0.0f, 0.0f} : d[e], df_add(fp, df_neg(fm)));
+                    }
                 }
-                f = df_mul(d, a.scale);
             }
-            fv[e] = f;
-            acc.add(f);
+#pragma unroll
+            for (int e = 0; e < 4; e++) fv[e] = df_mul(d[e], a.scale);
         }
+#pragma unroll
+        for (int e = 0; e < 2 * kChunk; e++) acc.add(fv[e]);
         stp4(a.fh, a.fl, p, fv);
         stp4(a.uh, a.ul, p, uv);
     }
