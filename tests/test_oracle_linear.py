@@ -154,3 +154,52 @@ def test_bad_grid_sizes_are_rejected(orc):
         u = np.zeros((n, n, n))
         st, *_ = orc.solve_eq(orc.POISSON, u, np.zeros((n, n, n)))
         assert st == orc.ERR_ARG
+
+
+@pytest.mark.parametrize("kind,mscale", [("poisson", 0.0), ("helmholtz", 1.0), ("helmholtz", 1e-3)])
+def test_coarsest_level_is_solved_exactly(orc, kind, mscale):
+    """The 2^3 level is solved (Sec. 4.3.1, last paragraph).  With no
+    smoothing, one V-cycle at n = 4 is the two-grid correction u + P e, where
+    e solves the 2^3 equation L_c e = -R eps with R-restricted coefficients.
+    Here the 2^3 system is assembled from the 7-point stencil on the periodic
+    2^3 grid (h = 1/2) and solved densely (Poisson: the mean-free solution of
+    the mean-free right-hand side); the oracle's red-black sweeps (with the
+    zero-mode shift for Helmholtz) must reach it.  The same R and P enter both
+    sides, so the 2^3 solve alone is under test; it is also the fixed point
+    the GPU's exact 2^3 solve computes.  A weak background (m ~ 1e-3) leaves
+    the constant mode to the zero-mode shift: sweeps alone damp it by only
+    1/(1 + h^2 m / 6) each."""
+    n, nc = 4, 2
+    rng = np.random.default_rng(21)
+    k = orc.POISSON if kind == "poisson" else orc.HELMHOLTZ
+    u = rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    c0 = None
+    if k == orc.POISSON:
+        f -= f.mean()
+    else:
+        c0 = mscale * rng.uniform(0.2, 3.0, (n, n, n))
+    got = u.copy()
+    orc.vcycle(k, got, f, c0, nu1=0, nu2=0)
+
+    eps, _ = orc.residual(k, u, f, c0)
+    rc = -orc.restrict(eps)
+    A = np.zeros((8, 8))
+    idx = lambda i, j, kk: (i % nc) * 4 + (j % nc) * 2 + (kk % nc)
+    mc = orc.restrict(c0) if c0 is not None else np.zeros((nc, nc, nc))
+    for i in range(nc):
+        for j in range(nc):
+            for kk in range(nc):
+                x = idx(i, j, kk)
+                for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    A[x, idx(i + d[0], j + d[1], kk + d[2])] += nc * nc
+                A[x, x] -= 6 * nc * nc + mc[i, j, kk]
+    b = rc.reshape(8)
+    if k == orc.POISSON:
+        e = np.linalg.lstsq(A, b - b.mean(), rcond=None)[0]
+        e -= e.mean()
+    else:
+        e = np.linalg.solve(A, b)
+    want = u.copy()
+    orc.prolong_add(e.reshape(nc, nc, nc), want)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
