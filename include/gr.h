@@ -184,7 +184,8 @@ typedef struct {
     gr_status eq_status[GR_NEQ];
     double seconds;               /* wall time of the whole call (host clock around the stream) */
     double eq_seconds[GR_NEQ];    /* per equation, CUDA events */
-    long long cell_updates;       /* cells relaxed: every sweep on every level, all equations */
+    long long cell_updates;       /* cells relaxed: every sweep on every level, all equations (the exact
+                                     solve of a linear 2^3 level counts its 8 cells once) */
     long long kernel_launches;    /* kernels this call launched */
     int prof_launches[GR_NPROF];  /* with gr_opts.profile: launches per gr_prof_class */
     double prof_ms[GR_NPROF];     /* with gr_opts.profile: summed CUDA-event time per class */
@@ -201,8 +202,9 @@ void gr_default_opts(gr_opts *o);
 /* Create a context for an n^3 grid of box side L.  n must be a power of two,
    4 <= n <= 1024; L > 0.  cuda_stream is a cudaStream_t (NULL = the legacy
    default stream); the device is the current device of the calling thread.
-   Allocates the multigrid scratch (about 12 n^3 doubles).  On success *out
-   owns it; release with gr_destroy. */
+   Allocates the multigrid scratch (about 12 n^3 doubles) and 16 doubles of
+   mapped pinned host memory, which kernels write the residual norms into for
+   the host to read.  On success *out owns both; release with gr_destroy. */
 gr_status gr_create(int n, double L, void *cuda_stream, gr_ctx **out);
 
 /* Release a context and its device memory (synchronises its stream).  NULL is ignored. */
