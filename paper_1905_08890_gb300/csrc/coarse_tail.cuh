@@ -166,57 +166,71 @@ __device__ void tail_up(const TailLevel &A, const TailLevel &C, bool black_only)
 // KPOISSON (m = 0): the 8-point Walsh-Hadamard basis (-1)^(s.x)
 // diagonalises the operator, eigenvalue 4|s| (|s| the number of bits set in
 // s), so e = W diag(1 / (4|s|)) W (-h^2 r) / 8 with the s = 0 component, the
-// mean, set to zero: the mean-free solution.  KHELM (m > 0): Gauss-Jordan
-// elimination, one row per lane (symmetric and diagonally dominant, no
-// pivoting).  The red-black sweeps this replaces converge to the same
+// mean, set to zero: the mean-free solution.  KHELM (m >= 0, not all zero):
+// Gauss-Jordan elimination, one row per lane (symmetric and diagonally
+// dominant, no pivoting); m = 0 on all eight cells takes the Poisson solve.  The red-black sweeps this replaces converge to the same
 // solution (the 2^3 level is solved, Sec. 4.3.1).  Called by a whole warp;
 // lane x < 8 passes r_x and m_x of cell x and receives e_x (lanes 8..31
 // repeat lanes 0..7).
+// the KPOISSON solve (whole warp, lanes in groups of eight)
+__device__ __forceinline__ double coarsest_wht(double rx, double h2)
+{
+    const unsigned full = 0xffffffffu;
+    const int x = threadIdx.x & 7;
+    double v = -h2 * rx;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const double w = __shfl_xor_sync(full, v, 1 << b);
+        v = ((x >> b) & 1) ? w - v : v + w;
+    }
+    const int s = __popc(x);
+    v = s ? v / (4.0 * s) : 0.0;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const double w = __shfl_xor_sync(full, v, 1 << b);
+        v = ((x >> b) & 1) ? w - v : v + w;
+    }
+    return 0.125 * v;
+}
+
 template <int KIND>
 __device__ __forceinline__ double coarsest_exact(double rx, double mx, double h2)
 {
     const unsigned full = 0xffffffffu;
     const int x = threadIdx.x & 7;
-    if (KIND == KPOISSON) {
-        double v = -h2 * rx;
+    if (KIND == KPOISSON) return coarsest_wht(rx, h2);
+    // m = 0 on every cell would leave the Laplacian, singular on the constant
+    // mode: then its mean-free solution.  No caller reaches it: the contexts
+    // require rho_hat > 0, which puts K^2 = 24 pi rho_hat into the lapse's m
+    // and 10 pi rho_hat psi^4 into the psi equation's Newton coefficient.
+    // (The sum is the same in every group of eight lanes.)
+    double ms = mx;
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
-            const double w = __shfl_xor_sync(full, v, 1 << b);
-            v = ((x >> b) & 1) ? w - v : v + w;
+    for (int b = 0; b < 3; b++) ms += __shfl_xor_sync(full, ms, 1 << b);
+    if (!(ms > 0.0)) return coarsest_wht(rx, h2);
+    double a[8];
+#pragma unroll
+    for (int y = 0; y < 8; y++) a[y] = y == x ? 6.0 + h2 * mx : (__popc(x ^ y) == 1 ? -2.0 : 0.0);
+    double b = -h2 * rx;
+#pragma unroll
+    for (int p = 0; p < 8; p++) {
+        const int src = (threadIdx.x & ~7) + p;  // row p of this lane's group of eight
+        const double piv = __shfl_sync(full, a[p], src);
+        const double bp = __shfl_sync(full, b, src);
+        double row[8];
+#pragma unroll
+        for (int k = p + 1; k < 8; k++) row[k] = __shfl_sync(full, a[k], src);
+        if (x != p) {
+            const double f = a[p] / piv;
+#pragma unroll
+            for (int k = p + 1; k < 8; k++) a[k] = fma(-f, row[k], a[k]);
+            b = fma(-f, bp, b);
         }
-        const int s = __popc(x);
-        v = s ? v / (4.0 * s) : 0.0;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            const double w = __shfl_xor_sync(full, v, 1 << b);
-            v = ((x >> b) & 1) ? w - v : v + w;
-        }
-        return 0.125 * v;
-    } else {
-        double a[8];
-#pragma unroll
-        for (int y = 0; y < 8; y++) a[y] = y == x ? 6.0 + h2 * mx : (__popc(x ^ y) == 1 ? -2.0 : 0.0);
-        double b = -h2 * rx;
-#pragma unroll
-        for (int p = 0; p < 8; p++) {
-            const int src = (threadIdx.x & ~7) + p;  // row p of this lane's group of eight
-            const double piv = __shfl_sync(full, a[p], src);
-            const double bp = __shfl_sync(full, b, src);
-            double row[8];
-#pragma unroll
-            for (int k = p + 1; k < 8; k++) row[k] = __shfl_sync(full, a[k], src);
-            if (x != p) {
-                const double f = a[p] / piv;
-#pragma unroll
-                for (int k = p + 1; k < 8; k++) a[k] = fma(-f, row[k], a[k]);
-                b = fma(-f, bp, b);
-            }
-        }
-        double d = a[0];
-#pragma unroll
-        for (int y = 1; y < 8; y++) d = y == x ? a[y] : d;
-        return b / d;
     }
+    double d = a[0];
+#pragma unroll
+    for (int y = 1; y < 8; y++) d = y == x ? a[y] : d;
+    return b / d;
 }
 
 // FP64 solve of the 2^3 level (as k_coarsest), by the first warp: the
