@@ -1,17 +1,18 @@
 // conv_tc.cu - the U-Net's circular 3^3 convolution on the 5th-generation
 // tensor cores (tcgen05.mma, FP32 accumulator in tensor memory), for grids of
 // 128^3 voxels (rows of exactly 128 voxels: the network's finest level, where
-// two thirds of its arithmetic sits) with 16 input channels.
+// two thirds of its arithmetic sits) with 16 or 48 input channels.
 //
 // Implicit GEMM per output row (d, h): D[128 voxels w][N = cout] = sum over
 // taps (dd, dh, dw) of A[w][k] = x[(d + dd, h + dh, w + dw)][k] times
-// B[k][n] = W[tap][n][k] (16 input channels k).  The input rows (d + dd, h + dh)
-// are staged in shared memory in the canonical no-swizzle K-major layout of
-// the tensor core (core matrices of 8 voxels x 16 bytes; plane 0 holds
-// channels 0-7 of every voxel, plane 1 channels 8-15), with one wrapped halo
+// B[k][n] = W[tap][n][k] (input channels k, 16 per MMA).  The input rows
+// (d + dd, h + dh) are staged in shared memory in the canonical no-swizzle
+// K-major layout of the tensor core (core matrices of 8 voxels x 16 bytes;
+// plane p holds channels 8p .. 8p + 7 of every voxel), with one wrapped halo
 // voxel on each side, so the A operand of tap dw is the same row read from a
-// start address 16 (dw + 1) bytes further on: the 27 MMAs of a row read their
-// operands straight from shared memory, with no per-tap copy.  A block takes
+// start address 16 (dw + 1) bytes further on, and that of channel chunk c two
+// planes further on: the 27 cin/16 MMAs of a row read their operands straight
+// from shared memory, with no per-tap copy.  A block takes
 // a contiguous range of output rows and rolls the staged rows along h (three
 // new input rows per output row, copied asynchronously one row ahead).  The
 // weights of all taps sit in shared memory for the whole (persistent) block.  One thread issues
@@ -40,9 +41,15 @@ namespace {
 
 constexpr int kRowVox = 128;                 // voxels per output row (= MMA M)
 constexpr int kHaloVox = kRowVox + 2;        // staged voxels per input row
-constexpr int kPlaneB = kHaloVox * 16;       // bytes of one channel plane of one staged row (2080)
-constexpr int kRowB = 2 * kPlaneB;           // bytes of one staged row, both planes (4160)
-constexpr int kAStage = 12 * kRowB;          // four rolling slots of the three rows d + dd (49920)
+constexpr int kPlaneB = kHaloVox * 16;       // bytes of one 8-channel plane of one staged row (2080)
+
+// dynamic shared memory: mbarrier and tensor-memory slot, the weights of every
+// tap and 16-channel chunk, and four rolling slots of the three rows d + dd
+// (cin / 8 planes each)
+constexpr size_t tc_smem(int cin, int cout)
+{
+    return 128 + (size_t)27 * (cin / 16) * cout * 32 + (size_t)12 * (cin / 8) * kPlaneB;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -126,10 +133,11 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
-// x: [128^3][16] BF16, w: [27][N][16] BF16, bias [N] (CONV_RELU), mask
+// x: [128^3][cin] BF16, w: [27][N][cin] BF16, bias [N] (CONV_RELU), mask
 // [128^3][N] (CONV_MASK), y: [128^3][N] BF16; N = cout (16..64, multiple of
-// 16).  Dynamic shared memory: 128 + 27 N 32 + kAStage bytes; several blocks
-// per SM overlap one another's copies, MMAs and epilogues.
+// 16), cin a multiple of 16.  Dynamic shared memory: tc_smem(cin, N) bytes;
+// several blocks per SM (where it fits) overlap one another's copies, MMAs
+// and epilogues.
 template <int N>
 __global__ void __launch_bounds__(128, 1)
     k_conv3d_tc(const __nv_bfloat16 *__restrict__ x, int cin, const __nv_bfloat16 *__restrict__ w,
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(128, 1)
     pdl_begin();
     extern __shared__ __align__(128) uint8_t sm[];
     constexpr uint32_t NCOL = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
-    const int nch = cin >> 4;
+    const int nch = cin >> 4, planes = cin >> 3, rowB = planes * kPlaneB;
     uint8_t *Bs = sm + 128;
     uint8_t *As = Bs + 27 * nch * N * 32;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -169,10 +177,10 @@ __global__ void __launch_bounds__(128, 1)
     // the three input rows (d + dd, hh) of all dd, with the wrapped halo voxel on each side
     auto issue_rows = [&](int d, int hh) {
         const int sl = (hh + 4) & 3;
-        for (int e = tid; e < 3 * kHaloVox * 2; e += 128) {
-            const int p = e & 1, hv = (e >> 1) % kHaloVox, r = (e >> 1) / kHaloVox;  // r = dd + 1
+        for (int e = tid; e < 3 * kHaloVox * planes; e += 128) {
+            const int p = e % planes, hv = (e / planes) % kHaloVox, r = (e / planes) / kHaloVox;  // r = dd + 1
             const int v = (((((d + r - 1) & 127) << 7) + (hh & 127)) << 7) + ((hv - 1) & 127);
-            cp16(as + (r * 4 + sl) * kRowB + p * kPlaneB + 16 * hv, x + (size_t)v * cin + 8 * p);
+            cp16(as + (r * 4 + sl) * rowB + p * kPlaneB + 16 * hv, x + (size_t)v * cin + 8 * p);
         }
     };
     uint32_t phase = 0u;
@@ -203,9 +211,11 @@ __global__ void __launch_bounds__(128, 1)
         if (tid == 0) {
             for (int tap = 0; tap < 27; tap++) {
                 const int dd = tap / 9, dh = (tap / 3) % 3 - 1, sl = (h + dh + 4) & 3;
-                const uint64_t ad = sdesc(as + (dd * 4 + sl) * kRowB + 16 * (tap % 3), kPlaneB, 128);
-                const uint64_t bd = sdesc(bs + tap * N * 32, N * 16, 128);
-                mma_tc(tmem, ad, bd, id, tap > 0 ? 1u : 0u);
+                for (int c = 0; c < nch; c++) {
+                    const uint64_t ad = sdesc(as + (dd * 4 + sl) * rowB + 16 * (tap % 3) + c * 2 * kPlaneB, kPlaneB, 128);
+                    const uint64_t bd = sdesc(bs + (c * 27 + tap) * N * 32, N * 16, 128);
+                    mma_tc(tmem, ad, bd, id, (tap > 0 || c > 0) ? 1u : 0u);
+                }
             }
             mma_commit(mbar);
         }
@@ -261,7 +271,7 @@ template <int N>
 void launch_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const float *bias, int mode,
                const __nv_bfloat16 *mask, __nv_bfloat16 *y, cudaStream_t st)
 {
-    const size_t smem = 128 + (size_t)27 * (cin / 16) * N * 32 + kAStage;
+    const size_t smem = tc_smem(cin, N);
     static int grid_of[16] = {};  // per cin / 16
     static std::mutex mu;         // host threads may launch concurrently
     const int ci = cin / 16;
@@ -292,10 +302,14 @@ void launch_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const fl
 
 bool conv3d_tc_fits(int cin, int cout, int lg)
 {
-    // shared memory: the weights of every tap and chunk plus one chunk's nine input rows
-    // one 16-channel chunk: with more, each row's nine input rows are staged once per chunk and the
-    // mma.sync kernel measured faster (48 -> 16 at 128^3: 573 against 390 us; 16 -> 16: 170 against 238 us)
-    return lg == 7 && cin == 16 && (cout == 16 || cout == 32 || cout == 48 || cout == 64);
+    // 16 input channels, or the decoder's 48 -> 16: one block per SM (191 KB of shared memory), the
+    // rolled input rows holding all 48 channels, so a row's three new input rows are staged once; it
+    // measured at parity with the mma.sync kernel (701 against 699 us, cold launch list), its 81
+    // dependent MMAs per row (N = 16) not overlapped by other blocks.  (An earlier version that staged
+    // each 16-channel chunk's nine rows separately took 573 us against 390 us timed alone.)
+    if (lg != 7) return false;
+    if (cin == 16) return cout == 16 || cout == 32 || cout == 48 || cout == 64;
+    return cin == 48 && cout == 16 && tc_smem(cin, cout) <= 227 * 1024;
 }
 
 void conv3d_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *w, const float *bias, int cout, int mode,

@@ -236,9 +236,9 @@ def _sampled_conv(params, k, x, vox):
 
 
 def test_tcgen05_convolutions_at_128_cubed(monkeypatch):
-    """At 128^3 the finest level's convolutions with 16 input channels run on
-    the 5th-generation tensor cores (conv_tc.cu: tcgen05.mma, TMEM
-    accumulator).  Each finest-level layer is held, at 6000 sampled voxels
+    """At 128^3 the finest level's convolutions with 16 input channels, and
+    the decoder's 48 -> 16 one, run on the 5th-generation tensor cores
+    (conv_tc.cu: tcgen05.mma, TMEM accumulator).  Each finest-level layer is held, at 6000 sampled voxels
     including both row ends (the wrapped halo), to the FP64 convolution of its
     own GPU input within 2^-8 (sum |W||x| + |b|) (the per-layer bound above);
     the whole output agrees with the mma.sync path (GR_CONV_TC=0) to BF16
